@@ -1,0 +1,170 @@
+/*
+ * spamm.h: C ABI of the GB300 (sm_103a) Sparse Approximate Matrix Multiply library.
+ *
+ * SpAMM (Challacombe and Bock, "Fast Multiplication of Matrices with Decay") computes
+ * C ~ A B for matrices whose elements decay away from the diagonal. Each operand is
+ * held as a quadtree (Eq. 1) with the Frobenius norm of every block (Sec. III); the
+ * product recursion of Eq. 4 drops every block sub-product A^k B^k with
+ * ||A^k||_F ||B^k||_F < tau at any tier k, and the dense leaf-block products that
+ * survive are summed into C.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a spamm_status. No C++ exception crosses this boundary.
+ *     A failing call stores a message that spamm_last_error(ctx) returns.
+ *   - Matrices cross the boundary as dense n x n FP64 row-major arrays, on the host or
+ *     on the device as each call's flags say. The caller owns those arrays; the
+ *     library copies what it needs and owns all device memory behind its handles.
+ *   - All device work is ordered on the context's CUDA stream. Calls that return data
+ *     to the host (spamm_stats, spamm_triples, spamm_tree_norms, spamm_tree_to_dense
+ *     with a host destination, spamm_sync) synchronise that stream first.
+ *   - Sizes: n >= 1; leaf in {16, 32, 64, 128}; tau >= 0 and finite. The padded
+ *     quadtree has NB = 2^kmax leaf blocks per side, NB the smallest power of two with
+ *     NB * leaf >= n; padding is zero.
+ *   - A device-side failure (a bounded wait that ran out, an internal capacity
+ *     overflow) is recorded in a status word on the device and returned by the next
+ *     synchronising call on that context; the context stays usable.
+ */
+#ifndef SPAMM_H
+#define SPAMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SPAMM_API __attribute__((visibility("default")))
+#else
+#define SPAMM_API
+#endif
+
+typedef struct spamm_ctx_s *spamm_ctx;
+typedef struct spamm_tree_s *spamm_tree;
+
+typedef enum {
+  SPAMM_OK = 0,
+  SPAMM_EINVAL = 1,        /* bad argument: null handle, n < 1, leaf not supported,
+                              tau < 0 or not finite, operands of unequal n or leaf,
+                              an operand without the copy the precision needs */
+  SPAMM_ENOMEM = 2,        /* device or pinned host allocation failed */
+  SPAMM_ECUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+  SPAMM_ERANGE = 4,        /* a caller buffer or an internal capacity is too small;
+                              the size needed is returned where the call says */
+  SPAMM_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+  SPAMM_EUNSUPPORTED = 6   /* valid request this build does not implement */
+} spamm_status;
+
+/* Arithmetic of the dense leaf products. Culling always uses the FP64 norms of the
+   FP64 operands, so every precision multiplies the same surviving leaf triples. */
+typedef enum {
+  SPAMM_FP64 = 0,    /* FP64 operands, FP64 accumulation (CUDA cores) */
+  SPAMM_TF32 = 1,    /* operands rounded to TF32, FP32 accumulation (tensor cores) */
+  SPAMM_BF16 = 2,    /* operands rounded to BF16, FP32 accumulation (tensor cores) */
+  SPAMM_FP16 = 3,    /* operands rounded to FP16, FP32 accumulation (tensor cores) */
+  SPAMM_BF16X3 = 4   /* split BF16: a = hi + lo, hi = bf16(a), lo = bf16(a - hi);
+                        A B ~ Ahi Bhi + Ahi Blo + Alo Bhi, FP32 accumulation */
+} spamm_prec;
+
+/* ---- flags of spamm_tree_build and spamm_multiply ---- */
+#define SPAMM_HOST_INPUT   0x0001  /* spamm_tree_build: A is a host pointer (else device) */
+#define SPAMM_SYMMETRIC    0x0002  /* caller asserts A == A^T: one low-precision copy then
+                                      serves both operand roles (leaf (k,j) of A^T is
+                                      leaf (j,k) of A, transposed) */
+#define SPAMM_KEEP_FP64    0x0004  /* keep FP64 leaf tiles (needed by SPAMM_FP64 products) */
+#define SPAMM_COPY_TF32    0x0010  /* write TF32 leaf copies */
+#define SPAMM_COPY_BF16    0x0020  /* write BF16 leaf copies */
+#define SPAMM_COPY_FP16    0x0040  /* write FP16 leaf copies */
+#define SPAMM_COPY_BF16X3  0x0080  /* write BF16 hi and lo leaf copies */
+#define SPAMM_NO_RIGHT     0x0100  /* the tree is never a right operand: skip the
+                                      transposed copies a non-symmetric tree needs */
+
+#define SPAMM_MAX_LEVELS 24
+
+/* Per-product counters, as the recursion of Eq. 4 would count them. */
+typedef struct {
+  int32_t levels;                          /* kmax + 1 tiers, 0 = root */
+  int32_t leaf;                            /* leaf block size b */
+  int64_t n;                               /* matrix order */
+  int64_t tested[SPAMM_MAX_LEVELS];        /* norm-product tests made at each tier */
+  int64_t culled[SPAMM_MAX_LEVELS];        /* tests that dropped the sub-product */
+  double culled_bound[SPAMM_MAX_LEVELS];   /* sum of ||A^k|| ||B^k|| over the dropped ones;
+                                              their total bounds ||C~ - AB||_F (Eq. 3) */
+  int64_t leaf_products;                   /* surviving leaf triples (i, j, k) */
+  int64_t output_blocks;                   /* output leaf blocks with a surviving k */
+  double leaf_flops;                       /* 2 b^3 leaf_products */
+  double dense_equiv_flops;                /* 2 n^3 */
+  double mma_flops;                        /* flops issued by the leaf kernel, counting
+                                              zero-filled operand halves and the three
+                                              products of SPAMM_BF16X3 */
+  double ms_cull;                          /* phase times (ms), when the context was made
+                                              with timing on; else 0 */
+  double ms_leaf;
+  int32_t prec;                            /* spamm_prec of the product */
+  double tau;
+} spamm_stats_t;
+
+/* ---- context ---- */
+
+/* Create a context on CUDA device `device`, ordering its work on `cuda_stream`
+   (a cudaStream_t; NULL = the legacy default stream). `timing` != 0 records CUDA
+   events around the cull and leaf phases of every multiply (spamm_stats ms_*).
+   Errors: SPAMM_EINVAL (out == NULL), SPAMM_ECUDA (no such device). */
+SPAMM_API spamm_status spamm_ctx_create(int device, void *cuda_stream, int32_t timing, spamm_ctx *out);
+SPAMM_API spamm_status spamm_ctx_destroy(spamm_ctx ctx);
+/* Wait for the context's stream and return the first device-side error, if any. */
+SPAMM_API spamm_status spamm_sync(spamm_ctx ctx);
+/* Message of the last failed call on this context ("" if none). Owned by the context. */
+SPAMM_API const char *spamm_last_error(spamm_ctx ctx);
+/* Number of kernels this context has launched since it was created. */
+SPAMM_API int64_t spamm_kernel_launches(spamm_ctx ctx);
+
+/* ---- quadtree build (Eq. 1, Frobenius norms of Sec. III) ----
+   Builds the padded quadtree of the n x n FP64 row-major matrix A: the squared
+   Frobenius norm of every leaf block (one FP64 pass over A), the norm of every upper
+   tier as the sum of its four children's squared norms, and the leaf copies `flags`
+   asks for (converted in the same pass, round-to-nearest-even from FP64).
+   A is a device pointer unless SPAMM_HOST_INPUT is set. On success *out is a new
+   tree. Errors: SPAMM_EINVAL, SPAMM_ENOMEM, SPAMM_ECUDA. */
+SPAMM_API spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t leaf,
+                              int32_t flags, spamm_tree *out);
+SPAMM_API spamm_status spamm_tree_free(spamm_tree t);
+/* Shape of a tree: order n, leaf size, padded blocks per side NB, and kmax. */
+SPAMM_API spamm_status spamm_tree_info(spamm_tree t, int64_t *n, int32_t *leaf, int32_t *nb_padded,
+                             int32_t *kmax);
+/* Copy the squared Frobenius norms of tier `level` (0 = root .. kmax), a
+   2^level x 2^level row-major FP64 grid, to the host buffer `out`. */
+SPAMM_API spamm_status spamm_tree_norms(spamm_tree t, int32_t level, double *out);
+/* Write the tree as a dense n x n FP64 row-major matrix to `out` (a host pointer if
+   out_is_host, else a device pointer). Product trees in TF32/BF16/FP16/BF16X3 hold
+   an FP32 C, widened to FP64 here. */
+SPAMM_API spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host);
+
+/* ---- the product (Eq. 4) ----
+   C ~ A B with tolerance tau: the tier-by-tier cull of Eq. 4 from the root
+   (a sub-product survives iff ||A^k||_F ||B^k||_F >= tau), then the surviving leaf
+   products in precision `prec`, each output block summed over its k in ascending
+   order with no atomics. `flags` may request leaf copies of C (SPAMM_COPY_*,
+   SPAMM_SYMMETRIC, SPAMM_NO_RIGHT) so that C can be the operand of a next product.
+   *C == NULL creates the product tree; otherwise *C is reused and must have the
+   same n and leaf. A and B must have equal n and leaf and hold the copies `prec`
+   needs (SPAMM_KEEP_FP64 for SPAMM_FP64, SPAMM_COPY_<prec> otherwise, and for B
+   either SPAMM_SYMMETRIC or no SPAMM_NO_RIGHT).
+   Supported: SPAMM_FP64 for every leaf; tensor-core precisions for leaf 64 and 128.
+   Errors: SPAMM_EINVAL, SPAMM_EUNSUPPORTED, SPAMM_ENOMEM, SPAMM_ECUDA. */
+SPAMM_API spamm_status spamm_multiply(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau,
+                            spamm_prec prec, int32_t flags, spamm_tree *C);
+
+/* Counters of the product that made tree C. Errors: SPAMM_EINVAL if C is not a product. */
+SPAMM_API spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out);
+
+/* The surviving leaf triples (i, j, k) of the product that made C, sorted by
+   (i, j, k), three uint32 per triple, into the host buffer ijk of `cap` triples.
+   *count receives the number of triples; SPAMM_ERANGE if it exceeds cap. */
+SPAMM_API spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPAMM_H */

@@ -1,0 +1,520 @@
+// C ABI of the SpAMM library: contexts, trees, the product, counters, exports.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+
+spamm_status fail(spamm_ctx ctx, spamm_status st, const char *fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+spamm_status cuda_fail(spamm_ctx ctx, cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(ctx, SPAMM_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(ctx, SPAMM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                              \
+  do {                                              \
+    cudaError_t _e = (call);                        \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, what); \
+  } while (0)
+
+bool valid_leaf(int32_t b) { return b == 16 || b == 32 || b == 64 || b == 128; }
+
+template <typename T>
+cudaError_t dmalloc(T **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  return cudaMalloc((void **)p, bytes);
+}
+
+void dfree(void *p) {
+  if (p) cudaFree(p);
+}
+
+// Which leaf copies a flag word asks for; transposed copies only when the tree may be a
+// right operand and is not declared symmetric.
+void wanted_copies(int32_t flags, bool want[CK_COUNT]) {
+  for (int k = 0; k < CK_COUNT; k++) want[k] = false;
+  const bool right_t = !(flags & SPAMM_SYMMETRIC) && !(flags & SPAMM_NO_RIGHT);
+  if (flags & SPAMM_KEEP_FP64) want[CK_F64] = true;
+  if (flags & SPAMM_COPY_TF32) { want[CK_TF32] = true; want[CK_TF32_T] = right_t; }
+  if (flags & SPAMM_COPY_BF16) { want[CK_BF16] = true; want[CK_BF16_T] = right_t; }
+  if (flags & SPAMM_COPY_FP16) { want[CK_FP16] = true; want[CK_FP16_T] = right_t; }
+  if (flags & SPAMM_COPY_BF16X3) {
+    want[CK_BF16] = true;
+    want[CK_BF16LO] = true;
+    want[CK_BF16_T] = right_t;
+    want[CK_BF16LO_T] = right_t;
+  }
+}
+
+void shape(int64_t n, int32_t b, int32_t *nb, int32_t *NB, int32_t *kmax) {
+  *nb = (int32_t)((n + b - 1) / b);
+  *NB = 1;
+  *kmax = 0;
+  while (*NB < *nb) {
+    *NB *= 2;
+    (*kmax)++;
+  }
+}
+
+void free_tree_memory(spamm_tree t) {
+  dfree(t->norm2);
+  dfree(t->norm);
+  dfree(t->nz);
+  for (int k = 0; k < CK_COUNT; k++) dfree(t->copy[k]);
+  for (int l = 0; l <= SPAMM_MAX_LEVELS; l++) {
+    dfree(t->tiers[l].gij);
+    dfree(t->tiers[l].gstart);
+    dfree(t->tiers[l].glen);
+    dfree(t->tiers[l].K);
+  }
+  dfree(t->mask);
+  dfree(t->bound_part);
+  dfree(t->look);
+  dfree(t->counts);
+  for (int k = 0; k < 3; k++)
+    if (t->ev[k]) cudaEventDestroy(t->ev[k]);
+}
+
+spamm_status alloc_tree(spamm_ctx ctx, int64_t n, int32_t b, int32_t flags, spamm_tree *out) {
+  spamm_tree t = new (std::nothrow) spamm_tree_s();
+  if (!t) return fail(ctx, SPAMM_ENOMEM, "host allocation failed");
+  t->ctx = ctx;
+  t->n = n;
+  t->b = b;
+  t->flags = flags;
+  shape(n, b, &t->nb, &t->NB, &t->kmax);
+  if (t->kmax >= SPAMM_MAX_LEVELS - 1 || t->NB > 65536) {
+    delete t;
+    return fail(ctx, SPAMM_EUNSUPPORTED, "n / leaf too large (NB = %d)", t->NB);
+  }
+  const size_t levels = (size_t)level_offset(t->kmax + 1);
+  cudaError_t e = dmalloc(&t->norm2, levels * sizeof(double));
+  if (e == cudaSuccess) e = dmalloc(&t->norm, levels * sizeof(double));
+  if (e == cudaSuccess) e = dmalloc(&t->nz, (size_t)t->NB * t->NB);
+  bool want[CK_COUNT];
+  wanted_copies(flags, want);
+  const size_t elems = (size_t)t->nb * t->nb * (size_t)b * b;
+  for (int k = 0; k < CK_COUNT && e == cudaSuccess; k++)
+    if (want[k]) e = dmalloc(&t->copy[k], elems * copy_elem_bytes(k));
+  if (e != cudaSuccess) {
+    free_tree_memory(t);
+    delete t;
+    return cuda_fail(ctx, e, "tree allocation");
+  }
+  *out = t;
+  return SPAMM_OK;
+}
+
+// Worst-case workspace of a product tree: tier l holds at most 4^l groups and
+// min(8^l, kEntryCap) entries, so no product can overflow it below that cap.
+spamm_status alloc_product_workspace(spamm_ctx ctx, spamm_tree C) {
+  if (C->counts) return SPAMM_OK;
+  cudaError_t e = cudaSuccess;
+  // tiers[0]: the virtual tier -1 (one group, one entry)
+  for (int li = 0; li <= C->kmax && e == cudaSuccess; li++) {
+    TierList &T = C->tiers[li];
+    const int l = li - 1;
+    T.cap_groups = l < 0 ? 1 : (int64_t(1) << (2 * l));
+    T.cap_entries = l < 0 ? 1 : std::min<int64_t>(int64_t(1) << (3 * l), kEntryCap);
+    e = dmalloc(&T.gij, T.cap_groups * 4);
+    if (e == cudaSuccess) e = dmalloc(&T.gstart, T.cap_groups * 4);
+    if (e == cudaSuccess) e = dmalloc(&T.glen, T.cap_groups * 4);
+    if (e == cudaSuccess) e = dmalloc(&T.K, T.cap_entries * 2);
+  }
+  if (e == cudaSuccess) {
+    C->cap_mask = C->tiers[C->kmax].cap_entries;
+    e = dmalloc(&C->mask, (size_t)C->cap_mask);
+  }
+  std::vector<int64_t> offs(C->kmax + 1);
+  if (e == cudaSuccess) {
+    C->cap_bound = cull_bound_words(C->kmax, offs.data());
+    e = dmalloc(&C->bound_part, (size_t)C->cap_bound * 8 + (C->kmax + 1) * sizeof(int64_t));
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(C->bound_part + C->cap_bound, offs.data(), (C->kmax + 1) * sizeof(int64_t),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    C->cap_look = cull_look_words(C->kmax);
+    e = dmalloc(&C->look, (size_t)C->cap_look * 8);
+  }
+  if (e == cudaSuccess) e = dmalloc(&C->counts, sizeof(DevCounts));
+  if (e == cudaSuccess && ctx->timing)
+    for (int k = 0; k < 3 && e == cudaSuccess; k++) e = cudaEventCreate(&C->ev[k]);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "product workspace allocation");
+  return SPAMM_OK;
+}
+
+spamm_status check_device_status(spamm_ctx ctx) {
+  uint32_t st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->dev_status, 4, cudaMemcpyDeviceToHost, ctx->stream), "status read");
+  CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  if (st) {
+    CK(cudaMemsetAsync(ctx->dev_status, 0, 4, ctx->stream), "status reset");
+    if (st & DEV_TIMEOUT) return fail(ctx, SPAMM_ETIMEOUT, "a device-side wait timed out");
+    if (st & DEV_OVERFLOW) return fail(ctx, SPAMM_ERANGE, "a tier list exceeded its capacity");
+    return fail(ctx, SPAMM_ECUDA, "device-side argument check failed (0x%x)", st);
+  }
+  return SPAMM_OK;
+}
+
+spamm_status ensure_stage(spamm_ctx ctx, size_t bytes) {
+  if (ctx->stage_bytes >= bytes) return SPAMM_OK;
+  if (ctx->stage) {
+    CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+  }
+  CK(cudaMalloc(&ctx->stage, bytes), "staging buffer");
+  ctx->stage_bytes = bytes;
+  return SPAMM_OK;
+}
+
+}  // namespace
+
+// Internal flag: the product tree keeps an FP32 master (tensor-core precisions).
+#define SPAMM_INTERNAL_F32 0x10000
+
+extern "C" {
+
+spamm_status spamm_ctx_create(int device, void *cuda_stream, int32_t timing, spamm_ctx *out) {
+  if (!out) return SPAMM_EINVAL;
+  *out = nullptr;
+  spamm_ctx ctx = new (std::nothrow) spamm_ctx_s();
+  if (!ctx) return SPAMM_ENOMEM;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->dev_status, 4);
+  if (e == cudaSuccess) e = cudaMemset(ctx->dev_status, 0, 4);
+  if (e != cudaSuccess) {
+    if (ctx->dev_status) cudaFree(ctx->dev_status);
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? SPAMM_ENOMEM : SPAMM_ECUDA;
+  }
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->timing = timing != 0;
+  *out = ctx;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_ctx_destroy(spamm_ctx ctx) {
+  if (!ctx) return SPAMM_EINVAL;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->dev_status) cudaFree(ctx->dev_status);
+  delete ctx;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_sync(spamm_ctx ctx) {
+  if (!ctx) return SPAMM_EINVAL;
+  return check_device_status(ctx);
+}
+
+const char *spamm_last_error(spamm_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t spamm_kernel_launches(spamm_ctx ctx) { return ctx ? ctx->launches : -1; }
+
+spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t leaf,
+                              int32_t flags, spamm_tree *out) {
+  if (!ctx) return SPAMM_EINVAL;
+  if (!A || !out) return fail(ctx, SPAMM_EINVAL, "tree_build: null pointer");
+  if (n < 1) return fail(ctx, SPAMM_EINVAL, "tree_build: n = %lld < 1", (long long)n);
+  if (!valid_leaf(leaf)) return fail(ctx, SPAMM_EINVAL, "tree_build: leaf %d not in {16,32,64,128}", leaf);
+  if (flags & ~0x01FF) return fail(ctx, SPAMM_EINVAL, "tree_build: unknown flag bits 0x%x", flags);
+  *out = nullptr;
+  spamm_tree t = nullptr;
+  spamm_status st = alloc_tree(ctx, n, leaf, flags, &t);
+  if (st != SPAMM_OK) return st;
+  const double *src = A;
+  if (flags & SPAMM_HOST_INPUT) {
+    st = ensure_stage(ctx, (size_t)n * n * sizeof(double));
+    if (st != SPAMM_OK) {
+      free_tree_memory(t);
+      delete t;
+      return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(ctx->stage, A, (size_t)n * n * sizeof(double),
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+      free_tree_memory(t);
+      delete t;
+      return cuda_fail(ctx, e, "tree_build: host to device copy");
+    }
+    src = (const double *)ctx->stage;
+  }
+  cudaError_t e = launch_tree_build(t, src, ctx->stream);
+  if (e == cudaSuccess) e = launch_pyramid(t, ctx->stream);
+  ctx->launches += 1 + 1 + (t->kmax >= 2 ? 1 : 0);
+  if (e != cudaSuccess) {
+    free_tree_memory(t);
+    delete t;
+    return cuda_fail(ctx, e, "tree_build: launch");
+  }
+  *out = t;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_tree_free(spamm_tree t) {
+  if (!t) return SPAMM_EINVAL;
+  cudaStreamSynchronize(t->ctx->stream);
+  free_tree_memory(t);
+  delete t;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_tree_info(spamm_tree t, int64_t *n, int32_t *leaf, int32_t *nb_padded,
+                             int32_t *kmax) {
+  if (!t) return SPAMM_EINVAL;
+  if (n) *n = t->n;
+  if (leaf) *leaf = t->b;
+  if (nb_padded) *nb_padded = t->NB;
+  if (kmax) *kmax = t->kmax;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_tree_norms(spamm_tree t, int32_t level, double *out) {
+  if (!t) return SPAMM_EINVAL;
+  spamm_ctx ctx = t->ctx;
+  if (!out || level < 0 || level > t->kmax)
+    return fail(ctx, SPAMM_EINVAL, "tree_norms: level %d outside 0..%d", level, t->kmax);
+  const size_t cnt = (size_t)1 << (2 * level);
+  CK(cudaMemcpyAsync(out, t->norm2 + level_offset(level), cnt * sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->stream), "tree_norms: copy");
+  return check_device_status(ctx);
+}
+
+spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host) {
+  if (!t) return SPAMM_EINVAL;
+  spamm_ctx ctx = t->ctx;
+  if (!out) return fail(ctx, SPAMM_EINVAL, "tree_to_dense: null output");
+  if (!t->copy[CK_F64] && !t->copy[CK_F32])
+    return fail(ctx, SPAMM_EINVAL, "tree_to_dense: the tree keeps no FP64/FP32 tiles (SPAMM_KEEP_FP64)");
+  const size_t bytes = (size_t)t->n * t->n * sizeof(double);
+  double *dst = out;
+  if (out_is_host) {
+    spamm_status st = ensure_stage(ctx, bytes);
+    if (st != SPAMM_OK) return st;
+    dst = (double *)ctx->stage;
+  }
+  CK(launch_to_dense(t, dst, ctx->stream), "tree_to_dense: launch");
+  ctx->launches++;
+  if (out_is_host) {
+    CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream), "tree_to_dense: copy");
+    return check_device_status(ctx);
+  }
+  return SPAMM_OK;
+}
+
+spamm_status spamm_multiply(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau,
+                            spamm_prec prec, int32_t flags, spamm_tree *C) {
+  if (!ctx) return SPAMM_EINVAL;
+  if (!A || !B || !C) return fail(ctx, SPAMM_EINVAL, "multiply: null handle");
+  if (A->n != B->n || A->b != B->b)
+    return fail(ctx, SPAMM_EINVAL, "multiply: operands differ (n %lld/%lld, leaf %d/%d)",
+                (long long)A->n, (long long)B->n, A->b, B->b);
+  if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(ctx, SPAMM_EINVAL, "multiply: tau must be finite and >= 0");
+  if (flags & ~0x01F6) return fail(ctx, SPAMM_EINVAL, "multiply: unknown flag bits 0x%x", flags);
+  const bool tc = prec != SPAMM_FP64;
+  if (prec < SPAMM_FP64 || prec > SPAMM_BF16X3) return fail(ctx, SPAMM_EINVAL, "multiply: unknown precision %d", (int)prec);
+  if (!tc) {
+    if (!A->copy[CK_F64] || !B->copy[CK_F64])
+      return fail(ctx, SPAMM_EINVAL, "multiply: SPAMM_FP64 needs SPAMM_KEEP_FP64 operands");
+  } else {
+    if (A->b != 64 && A->b != 128)
+      return fail(ctx, SPAMM_EUNSUPPORTED, "multiply: tensor-core precisions need leaf 64 or 128");
+    int row = prec == SPAMM_TF32 ? CK_TF32 : prec == SPAMM_FP16 ? CK_FP16 : CK_BF16;
+    int rowT = row + 1;
+    if (!A->copy[row] || (prec == SPAMM_BF16X3 && !A->copy[CK_BF16LO]))
+      return fail(ctx, SPAMM_EINVAL, "multiply: left operand lacks the leaf copy for this precision");
+    const bool bsym = (B->flags & SPAMM_SYMMETRIC) != 0;
+    if (bsym ? !B->copy[row] : !B->copy[rowT])
+      return fail(ctx, SPAMM_EINVAL, "multiply: right operand lacks the leaf copy for this precision");
+    if (prec == SPAMM_BF16X3 && (bsym ? !B->copy[CK_BF16LO] : !B->copy[CK_BF16LO_T]))
+      return fail(ctx, SPAMM_EINVAL, "multiply: right operand lacks the BF16 lo copy");
+  }
+  spamm_tree Ct = *C;
+  const int32_t cflags = (flags & 0x01F2) | (tc ? SPAMM_INTERNAL_F32 : SPAMM_KEEP_FP64);
+  if (!Ct) {
+    spamm_status st = alloc_tree(ctx, A->n, A->b, cflags & 0x01FF, &Ct);
+    if (st != SPAMM_OK) return st;
+    if (tc) {
+      cudaError_t e = dmalloc(&Ct->copy[CK_F32], (size_t)Ct->nb * Ct->nb * Ct->b * Ct->b * 4);
+      if (e != cudaSuccess) {
+        free_tree_memory(Ct);
+        delete Ct;
+        return cuda_fail(ctx, e, "multiply: product allocation");
+      }
+    }
+    Ct->flags = cflags;
+  } else {
+    if (Ct == A || Ct == B) return fail(ctx, SPAMM_EINVAL, "multiply: output aliases an operand");
+    if (Ct->n != A->n || Ct->b != A->b) return fail(ctx, SPAMM_EINVAL, "multiply: reused output has another shape");
+    bool want[CK_COUNT];
+    wanted_copies(cflags & 0x01FF, want);
+    for (int k = 0; k < CK_COUNT; k++)
+      if (want[k] && !Ct->copy[k]) return fail(ctx, SPAMM_EINVAL, "multiply: reused output lacks a requested copy");
+    if (tc ? !Ct->copy[CK_F32] : !Ct->copy[CK_F64])
+      return fail(ctx, SPAMM_EINVAL, "multiply: reused output was made for another precision class");
+  }
+  spamm_status st = alloc_product_workspace(ctx, Ct);
+  if (st != SPAMM_OK) {
+    if (!*C) { free_tree_memory(Ct); delete Ct; }
+    return st;
+  }
+  *C = Ct;
+  Ct->is_product = true;
+  Ct->prec = prec;
+  Ct->tau = tau;
+  Ct->stats_valid = false;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(Ct->counts, 0, sizeof(DevCounts), s), "multiply: memset");
+  CK(cudaMemsetAsync(Ct->look, 0, (size_t)Ct->cap_look * 8, s), "multiply: memset");
+  CK(cudaMemsetAsync(Ct->norm2 + level_offset(Ct->kmax), 0, (size_t)Ct->NB * Ct->NB * 8, s), "multiply: memset");
+  CK(cudaMemsetAsync(Ct->nz, 0, (size_t)Ct->NB * Ct->NB, s), "multiply: memset");
+  if (ctx->timing) CK(cudaEventRecord(Ct->ev[0], s), "event");
+  int launches = 0;
+  CK(launch_cull(A, B, Ct, tau, ctx->dev_status, ctx->sm_count, s, &launches), "multiply: cull launch");
+  if (ctx->timing) CK(cudaEventRecord(Ct->ev[1], s), "event");
+  if (tc) {
+    CK(launch_leaf_tc(A, B, Ct, prec, ctx->dev_status, ctx->sm_count, s), "multiply: leaf launch");
+  } else {
+    CK(launch_leaf_f64(A, B, Ct, ctx->dev_status, ctx->sm_count, s), "multiply: leaf launch");
+  }
+  launches++;
+  if (ctx->timing) CK(cudaEventRecord(Ct->ev[2], s), "event");
+  CK(launch_pyramid(Ct, s), "multiply: pyramid launch");
+  launches += 1 + (Ct->kmax >= 2 ? 1 : 0);
+  CK(launch_finish_stats(Ct, s), "multiply: stats launch");
+  launches++;
+  bool want[CK_COUNT];
+  wanted_copies(cflags & 0x01FF, want);
+  bool any_copy = false;
+  for (int k = CK_TF32; k < CK_COUNT; k++) any_copy |= want[k];
+  if (any_copy) {
+    CK(launch_tile_convert(Ct, s), "multiply: copy launch");
+    launches++;
+  }
+  ctx->launches += launches;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out) {
+  if (!C) return SPAMM_EINVAL;
+  spamm_ctx ctx = C->ctx;
+  if (!out) return fail(ctx, SPAMM_EINVAL, "stats: null output");
+  if (!C->is_product) return fail(ctx, SPAMM_EINVAL, "stats: not a product tree");
+  if (!C->stats_valid) {
+    DevCounts h;
+    CK(cudaMemcpyAsync(&h, C->counts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "stats: copy");
+    spamm_status st = check_device_status(ctx);
+    if (st != SPAMM_OK) return st;
+    spamm_stats_t &S = C->host_stats;
+    memset(&S, 0, sizeof S);
+    S.levels = C->kmax + 1;
+    S.leaf = C->b;
+    S.n = C->n;
+    for (int l = 0; l <= C->kmax; l++) {
+      S.tested[l] = (int64_t)h.tested[l];
+      S.culled[l] = (int64_t)h.culled[l];
+      S.culled_bound[l] = h.culled_bound[l];
+    }
+    S.leaf_products = (int64_t)h.leaf_products;
+    S.output_blocks = (int64_t)h.output_blocks;
+    const double b = C->b;
+    S.leaf_flops = 2.0 * b * b * b * (double)h.leaf_products;
+    S.dense_equiv_flops = 2.0 * (double)C->n * (double)C->n * (double)C->n;
+    S.mma_flops = C->prec == SPAMM_FP64 ? S.leaf_flops : (double)h.mma_tiles;
+    S.prec = C->prec;
+    S.tau = C->tau;
+    if (ctx->timing && C->ev[0]) {
+      float a = 0, c = 0;
+      cudaEventElapsedTime(&a, C->ev[0], C->ev[1]);
+      cudaEventElapsedTime(&c, C->ev[1], C->ev[2]);
+      S.ms_cull = a;
+      S.ms_leaf = c;
+    }
+    C->stats_valid = true;
+  }
+  *out = C->host_stats;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, int64_t *count) {
+  if (!C) return SPAMM_EINVAL;
+  spamm_ctx ctx = C->ctx;
+  if (!count) return fail(ctx, SPAMM_EINVAL, "triples: null count");
+  if (!C->is_product) return fail(ctx, SPAMM_EINVAL, "triples: not a product tree");
+  DevCounts h;
+  CK(cudaMemcpyAsync(&h, C->counts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "triples: copy");
+  spamm_status st = check_device_status(ctx);
+  if (st != SPAMM_OK) return st;
+  const TierList &T = C->tiers[C->kmax];
+  const int64_t ng = (int64_t)h.ngroups[C->kmax];
+  const int64_t ne = (int64_t)h.nentries[C->kmax];
+  *count = (int64_t)h.leaf_products;
+  if (!ijk) return SPAMM_OK;
+  if (*count > cap) return fail(ctx, SPAMM_ERANGE, "triples: %lld needed, cap %lld", (long long)*count, (long long)cap);
+  std::vector<uint32_t> gij(ng), gs(ng), gl(ng);
+  std::vector<uint16_t> K(ne);
+  std::vector<uint8_t> m(ne);
+  if (ng) {
+    CK(cudaMemcpyAsync(gij.data(), T.gij, ng * 4, cudaMemcpyDeviceToHost, ctx->stream), "triples: copy");
+    CK(cudaMemcpyAsync(gs.data(), T.gstart, ng * 4, cudaMemcpyDeviceToHost, ctx->stream), "triples: copy");
+    CK(cudaMemcpyAsync(gl.data(), T.glen, ng * 4, cudaMemcpyDeviceToHost, ctx->stream), "triples: copy");
+  }
+  if (ne) {
+    CK(cudaMemcpyAsync(K.data(), T.K, ne * 2, cudaMemcpyDeviceToHost, ctx->stream), "triples: copy");
+    CK(cudaMemcpyAsync(m.data(), C->mask, ne, cudaMemcpyDeviceToHost, ctx->stream), "triples: copy");
+  }
+  CK(cudaStreamSynchronize(ctx->stream), "triples: synchronize");
+  std::vector<uint64_t> keys;
+  keys.reserve((size_t)*count);
+  const int sh = 21;
+  for (int64_t g = 0; g < ng; g++) {
+    const uint64_t I = gij[g] >> 16, J = gij[g] & 0xFFFF;
+    for (uint32_t p = 0; p < gl[g]; p++) {
+      const uint64_t e = gs[g] + p;
+      if ((int64_t)e >= ne) break;
+      const uint32_t bits = m[e];
+      for (int q = 0; q < 8; q++)
+        if ((bits >> q) & 1u) {
+          const uint64_t a = (q >> 2) & 1, c = (q >> 1) & 1, ee = q & 1;
+          const uint64_t i = 2 * I + a, j = 2 * J + c, k = 2 * (uint64_t)K[e] + ee;
+          keys.push_back((i << (2 * sh)) | (j << sh) | k);
+        }
+    }
+  }
+  if ((int64_t)keys.size() != *count)
+    return fail(ctx, SPAMM_ECUDA, "triples: mask count %zu != counter %lld", keys.size(), (long long)*count);
+  std::sort(keys.begin(), keys.end());
+  const uint64_t mk = (1ull << sh) - 1;
+  for (size_t t = 0; t < keys.size(); t++) {
+    ijk[3 * t] = (uint32_t)(keys[t] >> (2 * sh));
+    ijk[3 * t + 1] = (uint32_t)((keys[t] >> sh) & mk);
+    ijk[3 * t + 2] = (uint32_t)(keys[t] & mk);
+  }
+  return SPAMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// Internal declarations of the SpAMM CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/spamm.h"
+
+// Device-side status bits (ctx->dev_status), set with atomicOr by kernels.
+enum : uint32_t {
+  DEV_TIMEOUT = 1u << 0,    // a bounded spin-wait ran out
+  DEV_OVERFLOW = 1u << 1,   // a tier's entry list exceeded its capacity
+  DEV_BADARG = 1u << 2,     // a kernel found an index outside its buffers
+};
+
+// Bounded waits give up after this many nanoseconds of %globaltimer.
+constexpr unsigned long long kSpinLimitNs = 2000000000ull;
+
+// Maximum entries of one tier's triple list (uint32 offsets, 31 bits).
+constexpr int64_t kEntryCap = int64_t(1) << 30;
+
+struct spamm_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  bool timing = false;
+  std::string err;
+  uint32_t *dev_status = nullptr;   // device word of DEV_* bits
+  int64_t launches = 0;
+  // staging buffer for host input / output (device)
+  void *stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+// Leaf copies a tree can hold. Index into spamm_tree_s::copy.
+enum CopyKind : int {
+  CK_F64 = 0,     // FP64 tiles (row orientation)
+  CK_F32,         // FP32 tiles (product trees of tensor-core precisions)
+  CK_TF32,        // TF32-rounded values in FP32 storage
+  CK_TF32_T,      // ... transposed leaves
+  CK_BF16,
+  CK_BF16_T,
+  CK_FP16,
+  CK_FP16_T,
+  CK_BF16LO,      // low half of the BF16 split
+  CK_BF16LO_T,
+  CK_COUNT
+};
+
+inline int copy_elem_bytes(int ck) {
+  switch (ck) {
+    case CK_F64: return 8;
+    case CK_F32: case CK_TF32: case CK_TF32_T: return 4;
+    default: return 2;
+  }
+}
+
+// Surviving triples of one tier: a group per output block (I, J) of the tier, each
+// with its ascending list of K (uint16).
+struct TierList {
+  uint32_t *gij = nullptr;     // (I << 16) | J
+  uint32_t *gstart = nullptr;  // first entry of the group
+  uint32_t *glen = nullptr;    // number of entries
+  uint16_t *K = nullptr;       // entries
+  int64_t cap_groups = 0, cap_entries = 0;
+};
+
+struct DevCounts {                     // device-resident counters of one product
+  unsigned long long ngroups[SPAMM_MAX_LEVELS + 1];   // groups per tier list (index l+1)
+  unsigned long long nentries[SPAMM_MAX_LEVELS + 1];  // entries per tier list (index l+1)
+  unsigned long long tested[SPAMM_MAX_LEVELS];
+  unsigned long long culled[SPAMM_MAX_LEVELS];
+  unsigned long long leaf_products;
+  unsigned long long output_blocks;
+  unsigned long long mma_tiles;        // leaf-kernel MMA tile-steps issued
+  unsigned int tile_ctr[SPAMM_MAX_LEVELS + 2];        // dynamic tile counters
+  unsigned int work_ctr;
+  double culled_bound[SPAMM_MAX_LEVELS];
+};
+
+struct spamm_tree_s {
+  spamm_ctx ctx = nullptr;
+  int64_t n = 0;
+  int32_t b = 0, nb = 0, NB = 0, kmax = 0;
+  int32_t flags = 0;
+  double *norm2 = nullptr;   // every tier: tier l at offset (4^l - 1) / 3, 2^l x 2^l
+  double *norm = nullptr;    // sqrt of norm2, same layout
+  uint8_t *nz = nullptr;     // NB x NB: 1 if tile storage holds leaf (i, j)
+  void *copy[CK_COUNT] = {};
+  // product trees
+  bool is_product = false;
+  int32_t prec = 0;
+  double tau = 0;
+  TierList tiers[SPAMM_MAX_LEVELS + 1];   // tiers[l + 1] lists tier l; tiers[0] the virtual root
+  uint8_t *mask = nullptr;                // 8 child bits per entry of tier kmax - 1
+  int64_t cap_mask = 0;
+  double *bound_part = nullptr;           // per parent group partial culled bounds
+  int64_t cap_bound = 0;
+  uint64_t *look = nullptr;               // look-back tile status words
+  int64_t cap_look = 0;
+  DevCounts *counts = nullptr;            // device
+  spamm_stats_t host_stats{};
+  bool stats_valid = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+__host__ __device__ inline int64_t level_offset(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
+
+// ---- launchers (each returns a cudaError_t from the launch) ----
+cudaError_t launch_tree_build(spamm_tree t, const double *A, cudaStream_t s);
+cudaError_t launch_pyramid(spamm_tree t, cudaStream_t s);
+cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s);
+cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau,
+                        uint32_t *dev_status, int sm_count, cudaStream_t s, int *launches);
+cudaError_t launch_leaf_f64(spamm_tree A, spamm_tree B, spamm_tree C, uint32_t *dev_status,
+                            int sm_count, cudaStream_t s);
+cudaError_t launch_leaf_tc(spamm_tree A, spamm_tree B, spamm_tree C, int prec,
+                           uint32_t *dev_status, int sm_count, cudaStream_t s);
+cudaError_t launch_finish_stats(spamm_tree C, cudaStream_t s);
+cudaError_t launch_tile_convert(spamm_tree t, cudaStream_t s);
+int64_t cull_look_words(int kmax);
+int64_t cull_bound_words(int kmax, int64_t *offsets);

@@ -1,0 +1,363 @@
+// Tier-by-tier cull of the product space (Eq. 4), with the surviving triples kept
+// grouped by output block.
+//
+// Tier l holds the triples (I, J, K), I, J, K < 2^l, whose test
+// ||A^l_IK||_F ||B^l_KJ||_F >= tau passed and whose ancestors all passed: exactly the
+// calls of the Eq. 4 recursion that neither return 0 nor reach the leaves. A tier
+// list is a sequence of groups, one per output block (I, J), each with its K in
+// ascending order; groups follow the Morton order of (I, J).
+//
+// One launch expands tier l-1 into tier l: every parent entry (I, J, K) proposes the
+// eight children (2I+a, 2J+c, 2K+e) and tests them with the tier-l norms. The children
+// of parent group (I, J) form the four child groups (2I+a, 2J+c), each listing 2K+e
+// for K ascending, then e ascending, so the new lists are again sorted by K. A warp
+// handles one parent group; a CTA handles a tile of 8 parent groups, fetched
+// dynamically, and places its 32 child groups after those of all earlier tiles with
+// a decoupled look-back scan (Merrill and Garland, "Single-pass Parallel Prefix Scan
+// with Decoupled Look-back", NVIDIA tech report NVR-2016-002). The last tier
+// (l = kmax) is not materialised: each entry of tier kmax-1 gets an 8-bit mask of its
+// surviving leaf children instead, bit ((a*2 + c)*2 + e).
+//
+// Counters: tests, culls and the sum of culled norm products per tier. Integer
+// counters use atomics (exact); the FP64 sums are written per parent group and summed
+// in a fixed order afterwards, so they are reproducible run to run.
+#include "internal.cuh"
+#include "sync.cuh"
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr uint64_t kFlagAgg = 1ull << 62, kFlagPrefix = 2ull << 62, kFlagMask = 3ull << 62;
+constexpr uint64_t kEntMask = (1ull << 31) - 1;
+
+__device__ __forceinline__ uint64_t pack(uint64_t flag, uint64_t groups, uint64_t entries) {
+  return flag | ((groups & ((1ull << 31) - 1)) << 31) | (entries & kEntMask);
+}
+
+struct CullArgs {
+  const double *nA, *nB;    // norms (not squared) of tier l, 2^l x 2^l
+  int32_t l, D, nb, final_tier;
+  double tau;
+  const uint32_t *pgij, *pgstart, *pglen;
+  const uint16_t *pK;
+  const unsigned long long *p_ngroups;
+  int64_t p_cap_entries;
+  uint32_t *cgij, *cgstart, *cglen;
+  uint16_t *cK;
+  int64_t cap_entries, cap_groups;
+  unsigned long long *c_ngroups, *c_nentries;
+  uint8_t *mask;
+  uint64_t *look;
+  unsigned int *tile_ctr;
+  unsigned long long *tested, *culled, *leaf_products, *output_blocks;
+  double *bound_part;
+  uint32_t *status;
+};
+
+// Children of entry (I, J, K) tested at tier l: survival bits, test count, and the
+// culled norm products summed in a fixed order.
+__device__ __forceinline__ uint32_t child_bits(const CullArgs &a, uint32_t I, uint32_t J,
+                                               uint32_t K, int &tests, double &bound) {
+  uint32_t bits = 0;
+#pragma unroll
+  for (int e = 0; e < 2; e++) {
+    const uint32_t k = 2 * K + e;
+    if (k >= (uint32_t)a.D) continue;
+#pragma unroll
+    for (int ai = 0; ai < 2; ai++) {
+      const uint32_t i = 2 * I + ai;
+      if (i >= (uint32_t)a.D) continue;
+      const double na = a.nA[(int64_t)i * a.D + k];
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        const uint32_t j = 2 * J + c;
+        if (j >= (uint32_t)a.D) continue;
+        const double p = na * a.nB[(int64_t)k * a.D + j];
+        tests++;
+        if (p < a.tau) bound += p;
+        else bits |= 1u << (((ai * 2 + c) * 2) + e);
+      }
+    }
+  }
+  return bits;
+}
+
+__global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
+  __shared__ unsigned int s_tile;
+  __shared__ unsigned int s_cnt[kWarps * 4];
+  __shared__ unsigned int s_off[kWarps * 4];
+  __shared__ unsigned int s_gix[kWarps * 4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long ngroups = *a.p_ngroups;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
+    __syncthreads();
+    const unsigned int tile = s_tile;
+    __syncthreads();
+    if ((unsigned long long)tile * kWarps >= ngroups) break;
+    const unsigned long long g = (unsigned long long)tile * kWarps + warp;
+    const bool has = g < ngroups;
+    uint32_t I = 0, J = 0, start = 0, len = 0;
+    if (has) {
+      const uint32_t ij = a.pgij[g];
+      I = ij >> 16;
+      J = ij & 0xFFFFu;
+      start = a.pgstart[g];
+      len = a.pglen[g];
+      // an overflowed parent tier (already flagged) is read only inside its buffer
+      if ((int64_t)start >= a.p_cap_entries) len = 0;
+      else if ((int64_t)start + len > a.p_cap_entries) len = (uint32_t)(a.p_cap_entries - start);
+    }
+    // pass 1: per child-quadrant counts (and, on the last tier, the masks)
+    unsigned int cnt[4] = {0, 0, 0, 0};
+    int tests = 0;
+    double bound = 0.0;
+    for (uint32_t p0 = 0; p0 < len; p0 += 32) {
+      const uint32_t p = p0 + lane;
+      uint32_t bits = 0;
+      if (p < len) {
+        const uint32_t K = a.pK[start + p];
+        bits = child_bits(a, I, J, K, tests, bound);
+        if (a.final_tier) a.mask[start + p] = (uint8_t)bits;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) cnt[q] += __popc((bits >> (2 * q)) & 3u);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) cnt[q] = warp_sum(cnt[q]);
+    tests = warp_sum(tests);
+    bound = warp_sum(bound);
+    if (has && lane == 0) {
+      const unsigned int surv = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+      atomicAdd(a.tested, (unsigned long long)tests);
+      atomicAdd(a.culled, (unsigned long long)(tests - (int)surv));
+      a.bound_part[g] = bound;
+      if (a.final_tier) {
+        atomicAdd(a.leaf_products, (unsigned long long)surv);
+        unsigned int blocks = 0;
+        for (int q = 0; q < 4; q++)
+          if (cnt[q] && 2 * I + (q >> 1) < (uint32_t)a.nb && 2 * J + (q & 1) < (uint32_t)a.nb) blocks++;
+        if (blocks) atomicAdd(a.output_blocks, (unsigned long long)blocks);
+      }
+    }
+    if (a.final_tier) continue;
+
+    // tile scan of the 32 child groups (warp w, quadrant q) in order
+    if (lane < 4) s_cnt[warp * 4 + lane] = has ? cnt[lane] : 0u;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned int v = s_cnt[lane];
+      const unsigned int f = v ? 1u : 0u;
+      const unsigned int inc_v = warp_inclusive_scan(v);
+      const unsigned int inc_f = warp_inclusive_scan(f);
+      const uint64_t agg_e = __shfl_sync(0xffffffffu, inc_v, 31);
+      const uint64_t agg_g = __shfl_sync(0xffffffffu, inc_f, 31);
+      uint64_t ex_e = 0, ex_g = 0;
+      if (tile == 0) {
+        if (lane == 0) st_release_u64(a.look + tile, pack(kFlagPrefix, agg_g, agg_e));
+      } else {
+        if (lane == 0) st_release_u64(a.look + tile, pack(kFlagAgg, agg_g, agg_e));
+        // look back over predecessors, 32 at a time
+        int64_t base = (int64_t)tile - 1;
+        const unsigned long long t0 = globaltimer_ns();
+        bool timed_out = false;
+        for (;;) {
+          const int64_t idx = base - lane;
+          uint64_t w = idx >= 0 ? ld_acquire_u64(a.look + idx) : kFlagPrefix;
+          unsigned spins = 0;
+          for (;;) {   // warp-uniform: every lane leaves together
+            const bool pending = (w & kFlagMask) == 0;
+            if (!__any_sync(0xffffffffu, pending)) break;
+            if (pending) w = ld_acquire_u64(a.look + idx);
+            if ((++spins & 255u) == 0 &&
+                __any_sync(0xffffffffu, globaltimer_ns() - t0 > kSpinLimitNs)) {
+              timed_out = true;
+              break;
+            }
+          }
+          if (timed_out) {
+            if (lane == 0) flag_error(a.status, DEV_TIMEOUT);
+            break;
+          }
+          const unsigned pre = __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagPrefix);
+          const int stop = pre ? __ffs(pre) - 1 : 31;   // nearest tile with a full prefix
+          uint64_t e = lane <= stop ? (w & kEntMask) : 0;
+          uint64_t gg = lane <= stop ? ((w >> 31) & ((1ull << 31) - 1)) : 0;
+          ex_e += warp_sum(e);
+          ex_g += warp_sum(gg);
+          if (pre) break;
+          base -= 32;
+        }
+        if (lane == 0) st_release_u64(a.look + tile, pack(kFlagPrefix, ex_g + agg_g, ex_e + agg_e));
+      }
+      s_off[lane] = (unsigned int)(ex_e + inc_v - v);
+      s_gix[lane] = (unsigned int)(ex_g + inc_f - f);
+      if (lane == 0 && (unsigned long long)(tile + 1) * kWarps >= ngroups) {
+        *a.c_nentries = ex_e + agg_e;
+        *a.c_ngroups = ex_g + agg_g;
+        if ((int64_t)(ex_e + agg_e) > a.cap_entries) flag_error(a.status, DEV_OVERFLOW);
+      }
+    }
+    __syncthreads();
+    if (!has) continue;
+
+    // pass 2: child group records and child entries
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (lane == 0 && cnt[q]) {
+        const unsigned int gi = s_gix[warp * 4 + q];
+        if ((int64_t)gi < a.cap_groups) {
+          a.cgij[gi] = ((2 * I + (q >> 1)) << 16) | (2 * J + (q & 1));
+          a.cgstart[gi] = s_off[warp * 4 + q];
+          a.cglen[gi] = cnt[q];
+        }
+      }
+    }
+    unsigned int run[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) run[q] = s_off[warp * 4 + q];
+    for (uint32_t p0 = 0; p0 < len; p0 += 32) {
+      const uint32_t p = p0 + lane;
+      uint32_t bits = 0, K = 0;
+      int dummy_t = 0;
+      double dummy_b = 0.0;
+      if (p < len) {
+        K = a.pK[start + p];
+        bits = child_bits(a, I, J, K, dummy_t, dummy_b);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const uint32_t two = (bits >> (2 * q)) & 3u;
+        const unsigned int m = __popc(two);
+        const unsigned int inc = warp_inclusive_scan(m);
+        unsigned int pos = run[q] + inc - m;
+        if (two & 1u) {
+          if ((int64_t)pos < a.cap_entries) a.cK[pos] = (uint16_t)(2 * K);
+          pos++;
+        }
+        if (two & 2u) {
+          if ((int64_t)pos < a.cap_entries) a.cK[pos] = (uint16_t)(2 * K + 1);
+        }
+        run[q] += __shfl_sync(0xffffffffu, inc, 31);
+      }
+    }
+  }
+}
+
+// Seeds the virtual tier -1: one group (0, 0) holding K = 0, whose only in-range
+// child is the root triple (0, 0, 0).
+__global__ void k_cull_seed(uint32_t *gij, uint32_t *gstart, uint32_t *glen, uint16_t *K,
+                            DevCounts *cnt) {
+  if (threadIdx.x == 0) {
+    gij[0] = 0;
+    gstart[0] = 0;
+    glen[0] = 1;
+    K[0] = 0;
+    cnt->ngroups[0] = 1;
+    cnt->nentries[0] = 1;
+  }
+}
+
+// Fixed-order sum of the per-group culled bounds of every tier, one CTA per tier.
+__global__ void __launch_bounds__(256) k_bound_reduce(const double *part, const int64_t *off,
+                                                      DevCounts *cnt) {
+  const int l = blockIdx.x;
+  const unsigned long long ng = cnt->ngroups[l];   // parent groups of tier l
+  const double *p = part + off[l];
+  double s = 0.0;
+  for (unsigned long long g = threadIdx.x; g < ng; g += blockDim.x) s += p[g];
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cnt->culled_bound[l] = sh[0];
+}
+
+}  // namespace
+
+// Offsets of each tier's per-group bound partials (tier l uses the parent groups of
+// list l, at most 4^(l-1) of them, 1 for l = 0).
+static int64_t bound_groups_cap(int l) { return l == 0 ? 1 : (int64_t(1) << (2 * (l - 1))); }
+
+cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau,
+                        uint32_t *dev_status, int sm_count, cudaStream_t s, int *launches) {
+  const int kmax = A->kmax;
+  DevCounts *cnt = C->counts;
+  const TierList &root = C->tiers[0];
+  k_cull_seed<<<1, 32, 0, s>>>(root.gij, root.gstart, root.glen, root.K, cnt);
+  (*launches)++;
+  int64_t look_off = 0, bound_off = 0;
+  for (int l = 0; l <= kmax; l++) {
+    CullArgs a{};
+    a.nA = A->norm + level_offset(l);
+    a.nB = B->norm + level_offset(l);
+    a.l = l;
+    a.D = 1 << l;
+    a.nb = A->nb;
+    a.final_tier = (l == kmax);
+    a.tau = tau;
+    const TierList &par = C->tiers[l];
+    a.pgij = par.gij;
+    a.pgstart = par.gstart;
+    a.pglen = par.glen;
+    a.pK = par.K;
+    a.p_ngroups = &cnt->ngroups[l];
+    a.p_cap_entries = par.cap_entries;
+    if (!a.final_tier) {
+      const TierList &ch = C->tiers[l + 1];
+      a.cgij = ch.gij;
+      a.cgstart = ch.gstart;
+      a.cglen = ch.glen;
+      a.cK = ch.K;
+      a.cap_entries = ch.cap_entries;
+      a.cap_groups = ch.cap_groups;
+      a.c_ngroups = &cnt->ngroups[l + 1];
+      a.c_nentries = &cnt->nentries[l + 1];
+    } else {
+      a.mask = C->mask;
+    }
+    const int64_t pg = bound_groups_cap(l);
+    const int64_t tiles = (pg + kWarps - 1) / kWarps;
+    a.look = C->look + look_off;
+    a.tile_ctr = &cnt->tile_ctr[l];
+    a.tested = &cnt->tested[l];
+    a.culled = &cnt->culled[l];
+    a.leaf_products = &cnt->leaf_products;
+    a.output_blocks = &cnt->output_blocks;
+    a.bound_part = C->bound_part + bound_off;
+    a.status = dev_status;
+    look_off += tiles;
+    bound_off += pg;
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)sm_count * 8);
+    k_cull_tier<<<(unsigned)grid, kWarps * 32, 0, s>>>(a);
+    (*launches)++;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_stats(spamm_tree C, cudaStream_t s) {
+  // bound offsets table lives in the tail of bound_part's allocation
+  const int kmax = C->kmax;
+  int64_t *off = reinterpret_cast<int64_t *>(C->bound_part + C->cap_bound);
+  k_bound_reduce<<<kmax + 1, 256, 0, s>>>(C->bound_part, off, C->counts);
+  return cudaGetLastError();
+}
+
+int64_t cull_look_words(int kmax) {
+  int64_t t = 0;
+  for (int l = 0; l <= kmax; l++) t += (bound_groups_cap(l) + kWarps - 1) / kWarps;
+  return t;
+}
+
+int64_t cull_bound_words(int kmax, int64_t *offsets) {
+  int64_t t = 0;
+  for (int l = 0; l <= kmax; l++) {
+    if (offsets) offsets[l] = t;
+    t += bound_groups_cap(l);
+  }
+  return t;
+}

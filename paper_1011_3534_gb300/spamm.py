@@ -1,0 +1,212 @@
+"""Thin Python binding of the C ABI in include/spamm.h (argument marshalling only).
+
+Every function here forwards to the entry point of the same name in libspamm.so; all
+computation runs in the library's CUDA kernels. Device buffers may be given as torch
+CUDA tensors (their data_ptr is passed), host buffers as numpy arrays. The module fails
+loudly at import if the library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SPAMM_OK, SPAMM_EINVAL, SPAMM_ENOMEM, SPAMM_ECUDA, SPAMM_ERANGE, SPAMM_ETIMEOUT, SPAMM_EUNSUPPORTED = range(7)
+SPAMM_FP64, SPAMM_TF32, SPAMM_BF16, SPAMM_FP16, SPAMM_BF16X3 = range(5)
+PRECISIONS = {"fp64": SPAMM_FP64, "tf32": SPAMM_TF32, "bf16": SPAMM_BF16, "fp16": SPAMM_FP16,
+              "bf16x3": SPAMM_BF16X3}
+
+SPAMM_HOST_INPUT = 0x0001
+SPAMM_SYMMETRIC = 0x0002
+SPAMM_KEEP_FP64 = 0x0004
+SPAMM_COPY_TF32 = 0x0010
+SPAMM_COPY_BF16 = 0x0020
+SPAMM_COPY_FP16 = 0x0040
+SPAMM_COPY_BF16X3 = 0x0080
+SPAMM_NO_RIGHT = 0x0100
+COPY_FLAG = {SPAMM_FP64: SPAMM_KEEP_FP64, SPAMM_TF32: SPAMM_COPY_TF32, SPAMM_BF16: SPAMM_COPY_BF16,
+             SPAMM_FP16: SPAMM_COPY_FP16, SPAMM_BF16X3: SPAMM_COPY_BF16X3}
+MAX_LEVELS = 24
+
+# Every entry point declared in include/spamm.h.
+EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_error",
+           "spamm_kernel_launches", "spamm_tree_build", "spamm_tree_free", "spamm_tree_info",
+           "spamm_tree_norms", "spamm_tree_to_dense", "spamm_multiply", "spamm_stats",
+           "spamm_triples")
+
+
+class SpammError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+class StatsT(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("leaf", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("tested", ctypes.c_int64 * MAX_LEVELS), ("culled", ctypes.c_int64 * MAX_LEVELS),
+                ("culled_bound", ctypes.c_double * MAX_LEVELS),
+                ("leaf_products", ctypes.c_int64), ("output_blocks", ctypes.c_int64),
+                ("leaf_flops", ctypes.c_double), ("dense_equiv_flops", ctypes.c_double),
+                ("mma_flops", ctypes.c_double), ("ms_cull", ctypes.c_double),
+                ("ms_leaf", ctypes.c_double), ("prec", ctypes.c_int32), ("tau", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
+    st = ctypes.c_int
+    L.spamm_ctx_create.argtypes = [ctypes.c_int, _P, _I32, ctypes.POINTER(_P)]
+    L.spamm_ctx_destroy.argtypes = [_P]
+    L.spamm_sync.argtypes = [_P]
+    L.spamm_last_error.argtypes = [_P]
+    L.spamm_last_error.restype = ctypes.c_char_p
+    L.spamm_kernel_launches.argtypes = [_P]
+    L.spamm_kernel_launches.restype = _I64
+    L.spamm_tree_build.argtypes = [_P, _P, _I64, _I32, _I32, ctypes.POINTER(_P)]
+    L.spamm_tree_free.argtypes = [_P]
+    L.spamm_tree_info.argtypes = [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32),
+                                  ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
+    L.spamm_tree_norms.argtypes = [_P, _I32, _P]
+    L.spamm_tree_to_dense.argtypes = [_P, _P, _I32]
+    L.spamm_multiply.argtypes = [_P, _P, _P, _D, ctypes.c_int, _I32, ctypes.POINTER(_P)]
+    L.spamm_stats.argtypes = [_P, ctypes.POINTER(StatsT)]
+    L.spamm_triples.argtypes = [_P, _P, _I64, ctypes.POINTER(_I64)]
+    for name in EXPORTS:
+        if name not in ("spamm_last_error", "spamm_kernel_launches"):
+            getattr(L, name).restype = st
+    return L
+
+
+def _load() -> ctypes.CDLL:
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libspamm.so is not built ({path}); run __graft_entry__.build()")
+    return _declare(ctypes.CDLL(path))
+
+
+LIB = _load()
+
+
+def _ptr(x) -> int:
+    """Raw address of a torch tensor (device or host) or a numpy array."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(type(x))
+
+
+class Ctx:
+    def __init__(self, handle: int):
+        self.h = handle
+
+    def check(self, status: int, what: str = ""):
+        if status != SPAMM_OK:
+            raise SpammError(status, f"{what}: {LIB.spamm_last_error(self.h).decode()}")
+
+
+class Tree:
+    def __init__(self, ctx: Ctx, handle: int):
+        self.ctx = ctx
+        self.h = handle
+        n, leaf, nbp, kmax = _I64(), _I32(), _I32(), _I32()
+        LIB.spamm_tree_info(handle, ctypes.byref(n), ctypes.byref(leaf), ctypes.byref(nbp), ctypes.byref(kmax))
+        self.n, self.leaf, self.NB, self.kmax = n.value, leaf.value, nbp.value, kmax.value
+
+
+def spamm_ctx_create(device: int = 0, stream=None, timing: bool = False) -> Ctx:
+    h = _P()
+    s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = LIB.spamm_ctx_create(device, s, 1 if timing else 0, ctypes.byref(h))
+    if rc != SPAMM_OK:
+        raise SpammError(rc, "spamm_ctx_create failed (is a CUDA device present?)")
+    return Ctx(h.value)
+
+
+def spamm_ctx_destroy(ctx: Ctx):
+    if ctx.h:
+        LIB.spamm_ctx_destroy(ctx.h)
+        ctx.h = None
+
+
+def spamm_sync(ctx: Ctx):
+    ctx.check(LIB.spamm_sync(ctx.h), "spamm_sync")
+
+
+def spamm_last_error(ctx: Ctx) -> str:
+    return LIB.spamm_last_error(ctx.h).decode()
+
+
+def spamm_kernel_launches(ctx: Ctx) -> int:
+    return LIB.spamm_kernel_launches(ctx.h)
+
+
+def spamm_tree_build(ctx: Ctx, A, n: int, leaf: int, flags: int) -> Tree:
+    """A: torch CUDA tensor (device) or numpy array (host; SPAMM_HOST_INPUT is added)."""
+    if isinstance(A, np.ndarray):
+        assert A.dtype == np.float64 and A.flags.c_contiguous
+        flags |= SPAMM_HOST_INPUT
+    h = _P()
+    ctx.check(LIB.spamm_tree_build(ctx.h, _ptr(A), n, leaf, flags, ctypes.byref(h)), "spamm_tree_build")
+    return Tree(ctx, h.value)
+
+
+def spamm_tree_free(t: Tree):
+    if t.h:
+        LIB.spamm_tree_free(t.h)
+        t.h = None
+
+
+def spamm_tree_norms(t: Tree, level: int) -> np.ndarray:
+    d = 1 << level
+    out = np.empty((d, d), dtype=np.float64)
+    t.ctx.check(LIB.spamm_tree_norms(t.h, level, out.ctypes.data), "spamm_tree_norms")
+    return out
+
+
+def spamm_tree_to_dense(t: Tree, out=None):
+    """Dense n x n FP64 copy: into `out` (numpy host or torch device), or a new numpy array."""
+    if out is None:
+        out = np.empty((t.n, t.n), dtype=np.float64)
+    host = isinstance(out, np.ndarray) or (hasattr(out, "is_cuda") and not out.is_cuda)
+    t.ctx.check(LIB.spamm_tree_to_dense(t.h, _ptr(out), 1 if host else 0), "spamm_tree_to_dense")
+    return out
+
+
+def spamm_multiply(ctx: Ctx, A: Tree, B: Tree, tau: float, prec: int = SPAMM_FP64, flags: int = 0,
+                   C: Tree | None = None) -> Tree:
+    h = _P(C.h if C is not None else None)
+    ctx.check(LIB.spamm_multiply(ctx.h, A.h, B.h, float(tau), int(prec), flags, ctypes.byref(h)),
+              "spamm_multiply")
+    return C if C is not None else Tree(ctx, h.value)
+
+
+def spamm_stats(C: Tree) -> dict:
+    s = StatsT()
+    C.ctx.check(LIB.spamm_stats(C.h, ctypes.byref(s)), "spamm_stats")
+    L = s.levels
+    return dict(levels=L, leaf=s.leaf, n=s.n, tested=list(s.tested[:L]), culled=list(s.culled[:L]),
+                culled_bound=list(s.culled_bound[:L]), leaf_products=s.leaf_products,
+                output_blocks=s.output_blocks, leaf_flops=s.leaf_flops,
+                dense_equiv_flops=s.dense_equiv_flops, mma_flops=s.mma_flops, ms_cull=s.ms_cull,
+                ms_leaf=s.ms_leaf, prec=s.prec, tau=s.tau)
+
+
+def spamm_triples(C: Tree) -> np.ndarray:
+    """Surviving leaf triples (i, j, k), sorted, as a (count, 3) uint32 array."""
+    cnt = _I64()
+    C.ctx.check(LIB.spamm_triples(C.h, None, 0, ctypes.byref(cnt)), "spamm_triples")
+    out = np.empty((max(cnt.value, 1), 3), dtype=np.uint32)
+    C.ctx.check(LIB.spamm_triples(C.h, out.ctypes.data, out.shape[0], ctypes.byref(cnt)), "spamm_triples")
+    return out[:cnt.value]
