@@ -74,7 +74,9 @@ def _load(path: str) -> ctypes.CDLL:
                                  ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(_Stats)]
     lib.oracle_spamm.restype = ctypes.c_int
-    lib.oracle_spamm_block.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _D]
+    lib.oracle_spamm_values.argtypes = [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, _D]
+    lib.oracle_spamm_values.restype = ctypes.c_int
+    lib.oracle_spamm_block.argtypes = [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _D]
     lib.oracle_spamm_block.restype = ctypes.c_int
     lib.oracle_triples_flat.argtypes = [_P, _P, ctypes.c_double, _U32, ctypes.c_int64]
     lib.oracle_triples_flat.restype = ctypes.c_int64
@@ -161,9 +163,19 @@ def spamm(A: Tree, B: Tree, tau: float, *, product: bool = True, triples: bool =
     return out
 
 
-def spamm_block(A: Tree, B: Tree, tau: float, i: int, j: int) -> np.ndarray:
+def spamm_values(A: Tree, B: Tree, Av: Tree, Bv: Tree, tau: float, threads: int = 1) -> np.ndarray:
+    """SpAMM with the tier tests of A, B and the leaf products of Av, Bv."""
+    C = np.empty((A.n, A.n), dtype=np.float64)
+    if A.L.oracle_spamm_values(A.h, B.h, Av.h, Bv.h, tau, threads, _dptr(C)):
+        raise RuntimeError("oracle_spamm_values failed")
+    return C
+
+
+def spamm_block(A: Tree, B: Tree, tau: float, i: int, j: int, Av: Tree | None = None,
+                Bv: Tree | None = None) -> np.ndarray:
     out = np.empty((A.leaf, A.leaf), dtype=np.float64)
-    if A.L.oracle_spamm_block(A.h, B.h, tau, i, j, _dptr(out)):
+    if A.L.oracle_spamm_block(A.h, B.h, Av.h if Av else None, Bv.h if Bv else None, tau, i, j,
+                              _dptr(out)):
         raise ValueError((i, j))
     return out
 

@@ -138,6 +138,7 @@ int oracle_tree_level_norm2(const oracle_tree *t, int32_t l, double *out) {
 /* ---- the Eq. 4 recursion ---- */
 typedef struct {
   const oracle_tree *A, *B;
+  const oracle_tree *Av, *Bv;  /* operands whose values the leaf products use (A, B) */
   double tau;
   double *C;            /* N x N padded accumulator, or NULL (norm tests only) */
   uint32_t *trip;       /* recorded leaf triples (i, j, k), or NULL */
@@ -159,7 +160,7 @@ static int cull(double nA2, double nB2, double tau) {
 }
 
 static void leaf_product(const rec_ctx *c, int32_t I, int32_t J, int32_t K) {
-  const oracle_tree *A = c->A, *B = c->B;
+  const oracle_tree *A = c->Av, *B = c->Bv;
   const int64_t N = A->N, b = A->b;
   for (int64_t r = 0; r < b; r++) {
     double *crow = c->C + (I * b + r - c->row0) * N + J * b;
@@ -264,7 +265,7 @@ int oracle_spamm(const oracle_tree *A, const oracle_tree *B, double tau, int32_t
   if (threads > 1 && (triples || stats)) return 1;
   rec_ctx c;
   memset(&c, 0, sizeof c);
-  c.A = A; c.B = B; c.tau = tau; c.trip = triples; c.cap = cap; c.st = stats;
+  c.A = A; c.B = B; c.Av = A; c.Bv = B; c.tau = tau; c.trip = triples; c.cap = cap; c.st = stats;
   if (stats) memset(stats, 0, sizeof *stats);
   double *Cp = NULL;
   if (C) {
@@ -293,14 +294,51 @@ int oracle_spamm(const oracle_tree *A, const oracle_tree *B, double tau, int32_t
 }
 
 /*
- * One output leaf block C_IJ (b x b, row-major) of SpAMM(A, B): the same recursion,
+ * SpAMM(A, B) with the tier tests of A and B (their FP64 norms) but the leaf products
+ * A^k B^k taken from the values of Av and Bv (same n and leaf): the result of a leaf
+ * arithmetic that rounds the operands first, e.g. to a narrower format, with every
+ * surviving product then summed exactly as above in FP64.
+ */
+int oracle_spamm_values(const oracle_tree *A, const oracle_tree *B, const oracle_tree *Av,
+                        const oracle_tree *Bv, double tau, int32_t threads, double *C) {
+  if (!compatible(A, B) || !compatible(A, Av) || !compatible(B, Bv) || !(tau >= 0.0) || !C)
+    return 1;
+  rec_ctx c;
+  memset(&c, 0, sizeof c);
+  c.A = A; c.B = B; c.Av = Av; c.Bv = Bv; c.tau = tau;
+  double *Cp = (double *)calloc((size_t)(A->N * A->N), sizeof(double));
+  if (!Cp) return 2;
+  c.C = Cp;
+  if (threads > 1) {
+    c.task_depth = A->kmax < 4 ? A->kmax : 4;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(threads)
+#pragma omp single
+#endif
+    rec(&c, 0, 0, 0, 0);
+  } else {
+    c.task_depth = -1;
+    rec(&c, 0, 0, 0, 0);
+  }
+  for (int64_t i = 0; i < A->n; i++)
+    memcpy(C + i * A->n, Cp + i * A->N, (size_t)A->n * sizeof(double));
+  free(Cp);
+  return 0;
+}
+
+/*
+ * One output leaf block C_IJ (b x b, row-major) of SpAMM(A, B), with leaf products taken
+ * from Av, Bv when given (NULL: from A, B): the same recursion,
  * followed only into the quadrants that contain block (I, J); every other output
  * block is independent of it, and its own sum runs in the same order as in the full
  * recursion.
  */
-int oracle_spamm_block(const oracle_tree *A, const oracle_tree *B, double tau, int32_t I,
-                       int32_t J, double *out) {
-  if (!compatible(A, B) || !(tau >= 0.0) || I < 0 || J < 0 || I >= A->NB || J >= A->NB)
+int oracle_spamm_block(const oracle_tree *A, const oracle_tree *B, const oracle_tree *Av,
+                       const oracle_tree *Bv, double tau, int32_t I, int32_t J, double *out) {
+  if (!Av) Av = A;
+  if (!Bv) Bv = B;
+  if (!compatible(A, B) || !compatible(A, Av) || !compatible(B, Bv) || !(tau >= 0.0) || I < 0 ||
+      J < 0 || I >= A->NB || J >= A->NB)
     return 1;
   const int64_t b = A->b, N = A->N;
   /* accumulate into a strip holding the b padded rows of block row I */
@@ -308,7 +346,7 @@ int oracle_spamm_block(const oracle_tree *A, const oracle_tree *B, double tau, i
   if (!strip) return 2;
   rec_ctx c;
   memset(&c, 0, sizeof c);
-  c.A = A; c.B = B; c.tau = tau; c.task_depth = -1; c.target = 1; c.ti = I; c.tj = J;
+  c.A = A; c.B = B; c.Av = Av; c.Bv = Bv; c.tau = tau; c.task_depth = -1; c.target = 1; c.ti = I; c.tj = J;
   c.C = strip;
   c.row0 = (int64_t)I * b; /* strip row 0 is padded row I*b */
   rec(&c, 0, 0, 0, 0);

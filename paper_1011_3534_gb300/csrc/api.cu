@@ -444,7 +444,9 @@ spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out) {
     const double b = C->b;
     S.leaf_flops = 2.0 * b * b * b * (double)h.leaf_products;
     S.dense_equiv_flops = 2.0 * (double)C->n * (double)C->n * (double)C->n;
-    S.mma_flops = C->prec == SPAMM_FP64 ? S.leaf_flops : (double)h.mma_tiles;
+    // tensor-core kernel: one stage = a 128 x 128 x (128-byte K chunk) MMA chain
+    const double chunk_k = C->prec == SPAMM_TF32 ? 32.0 : 64.0;
+    S.mma_flops = C->prec == SPAMM_FP64 ? S.leaf_flops : (double)h.mma_tiles * 2.0 * 128.0 * 128.0 * chunk_k;
     S.prec = C->prec;
     S.tau = C->tau;
     if (ctx->timing && C->ev[0]) {

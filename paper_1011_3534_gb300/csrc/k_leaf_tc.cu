@@ -1,6 +1,437 @@
-// Tensor-core leaf products (tcgen05) — placeholder until the kernel lands.
-#include "internal.cuh"
+// Tensor-core leaf products (the k = k_max case of Eq. 4) with tcgen05, TMA and TMEM.
+//
+// Work item. Leaf 64: one tier kmax-1 group (I, J), i.e. the 2 x 2 output blocks
+// (2I + a, 2J + c), a 128 x 128 FP32 accumulator in TMEM. Leaf 128: one output block
+// (2I + a, 2J + c), also 128 x 128. Items are dealt to a persistent grid of one CTA per
+// SM round-robin in Morton order of the output blocks.
+//
+// Candidates. For each entry K of the group (ascending) and e = 0, 1, the surviving
+// children form a 2 x 2 pattern over (a, c). A pattern that is an outer product of a
+// row mask and a column mask is one pass: the A leaves (2I + a, k) of unmasked rows and
+// the B leaves (k, 2J + c) of unmasked columns are loaded, the others are zero-filled
+// by the TMA (a leaf coordinate past the end of the tensor), and one 128 x 128 x b MMA
+// chain adds exactly the surviving products. Other patterns take one pass per row.
+// Each output block therefore sums its surviving k in ascending order, in FP32.
+//
+// Pipeline (one CTA, 192 threads): warp 0 issues TMA loads into a ring of 6 stages of
+// 32 KB (A 128 x 128 B, B 128 x 128 B, 128-byte swizzle, one 128-byte K chunk per stage);
+// warp 1 issues tcgen05.mma (4 K-steps of 32 bytes per stage) into one of two TMEM
+// accumulators and commits to the stage's empty barrier; warps 2-5 drain a finished
+// accumulator with tcgen05.ld, store C (FP32 tiles) and its squared Frobenius norms
+// (FP64, fixed-order sums) while the next item accumulates in the other buffer.
+// Every wait is bounded; a wait that runs out sets an error bit and the CTA unwinds.
+#include <cudaTypedefs.h>
 
-cudaError_t launch_leaf_tc(spamm_tree, spamm_tree, spamm_tree, int, uint32_t *, int, cudaStream_t) {
-  return cudaErrorNotSupported;
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int kStages = 6;
+constexpr int kStageA = 16384;
+constexpr int kStageBytes = 32768;
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 256;
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024;
+
+struct TcArgs {
+  const uint32_t *gij, *gstart, *glen;
+  const uint16_t *K;
+  const uint8_t *mask;
+  const unsigned long long *ngroups;
+  int64_t cap_entries;
+  const uint8_t *nzA, *nzB;
+  int32_t nb, NB;
+  int32_t bsym;          // B leaf (k, j) is read as leaf (j, k) of a symmetric tree
+  uint32_t idesc;
+  int32_t chunks;        // 128-byte K chunks per leaf
+  int32_t chunk_elems;   // elements per chunk
+  int32_t nsrc;          // 1, or 3 for the split BF16 products (hi hi, hi lo, lo hi)
+  float *C;
+  uint8_t *nzC;
+  double *leaf_norm2C;
+  unsigned long long *mma_stages;
+  uint32_t *status;
+};
+
+struct Item {
+  uint32_t I, J, start, len;
+  int q;   // leaf 128: output quadrant a * 2 + c of the group
+};
+
+template <int LEAF>
+__device__ __forceinline__ Item decode(const TcArgs &p, unsigned long long item) {
+  Item it;
+  const unsigned long long g = LEAF == 64 ? item : (item >> 2);
+  it.q = LEAF == 64 ? 0 : (int)(item & 3);
+  const uint32_t ij = p.gij[g];
+  it.I = ij >> 16;
+  it.J = ij & 0xFFFFu;
+  it.start = p.gstart[g];
+  it.len = p.glen[g];
+  if ((int64_t)it.start + it.len > p.cap_entries) it.len = 0;
+  return it;
+}
+
+// Passes of candidate (mask m, e): row masks rm (bit a) and column masks cm (bit c).
+template <int LEAF>
+__device__ __forceinline__ int passes(uint32_t m, int e, int q, uint32_t (&rm)[2], uint32_t (&cm)[2]) {
+  if (LEAF == 128) {
+    if ((m >> (2 * q + e)) & 1u) {
+      rm[0] = 1;
+      cm[0] = 1;
+      return 1;
+    }
+    return 0;
+  }
+  const uint32_t r0 = ((m >> e) & 1u) | (((m >> (2 + e)) & 1u) << 1);   // a = 0: c = 0, 1
+  const uint32_t r1 = ((m >> (4 + e)) & 1u) | (((m >> (6 + e)) & 1u) << 1);   // a = 1
+  if (!r0 && !r1) return 0;
+  if (!r0 || !r1 || r0 == r1) {
+    rm[0] = (r0 ? 1u : 0u) | (r1 ? 2u : 0u);
+    cm[0] = r0 | r1;
+    return 1;
+  }
+  rm[0] = 1;
+  cm[0] = r0;
+  rm[1] = 2;
+  cm[1] = r1;
+  return 2;
+}
+
+template <int LEAF, bool TF32>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_leaf_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+              const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo,
+              TcArgs p) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[2], acce[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+  __shared__ double s_norm[4][2];
+  constexpr int RA = LEAF == 64 ? 2 : 1;        // A leaves stacked along M
+  constexpr int RC = LEAF == 64 ? 2 : 1;        // B leaves stacked along N
+  constexpr uint32_t kBox = LEAF * 128;         // bytes of one leaf box (LEAF rows x 128 B)
+
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; a++) {
+      mbar_init(&accf[a], 1);
+      mbar_init(&acce[a], 128);
+    }
+    s_abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&s_tmem, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const unsigned long long ng = *p.ngroups;
+  const unsigned long long nitems = LEAF == 64 ? ng : 4ull * ng;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    tma_prefetch_desc(&mA);
+    tma_prefetch_desc(&mB);
+    if (p.nsrc == 3) {
+      tma_prefetch_desc(&mAlo);
+      tma_prefetch_desc(&mBlo);
+    }
+    const int oob = p.nb * p.nb;
+    int stage = 0;
+    uint32_t phase = 0;
+    for (unsigned long long item = blockIdx.x; item < nitems && !s_abort; item += gridDim.x) {
+      const Item it = decode<LEAF>(p, item);
+      for (uint32_t pe = 0; pe < it.len && !s_abort; pe++) {
+        const uint32_t m = p.mask[it.start + pe];
+        if (!m) continue;
+        const int K2 = 2 * (int)p.K[it.start + pe];
+        for (int e = 0; e < 2; e++) {
+          uint32_t rm[2], cm[2];
+          const int np = passes<LEAF>(m, e, it.q, rm, cm);
+          const int k = K2 + e;
+          for (int ps = 0; ps < np; ps++) {
+            for (int src = 0; src < p.nsrc; src++) {
+              const CUtensorMap *ma = src == 2 ? &mAlo : &mA;
+              const CUtensorMap *mb = src == 1 ? &mBlo : &mB;
+              for (int ch = 0; ch < p.chunks; ch++) {
+                if (!mbar_wait(&empty[stage], phase ^ 1u, &s_abort)) {
+                  s_abort = 1;
+                  flag_error(p.status, DEV_TIMEOUT);
+                  break;
+                }
+                mbar_expect_tx(&full[stage], kStageBytes);
+                const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
+#pragma unroll
+                for (int a = 0; a < RA; a++) {
+                  const int i = LEAF == 64 ? (int)(2 * it.I) + a : (int)(2 * it.I) + (it.q >> 1);
+                  const bool ok = ((rm[ps] >> a) & 1u) && i < p.nb && k < p.nb &&
+                                  p.nzA[(int64_t)i * p.NB + k];
+                  tma_load_3d(sa + a * kBox, ma, &full[stage], ch * p.chunk_elems, 0, ok ? i * p.nb + k : oob);
+                }
+#pragma unroll
+                for (int c = 0; c < RC; c++) {
+                  const int j = LEAF == 64 ? (int)(2 * it.J) + c : (int)(2 * it.J) + (it.q & 1);
+                  const bool ok = ((cm[ps] >> c) & 1u) && j < p.nb && k < p.nb &&
+                                  p.nzB[(int64_t)k * p.NB + j];
+                  const int leaf = p.bsym ? j * p.nb + k : k * p.nb + j;
+                  tma_load_3d(sb + c * kBox, mb, &full[stage], ch * p.chunk_elems, 0, ok ? leaf : oob);
+                }
+                if (++stage == kStages) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    unsigned long long nst = 0;
+    for (unsigned long long item = blockIdx.x; item < nitems && !s_abort; item += gridDim.x) {
+      const Item it = decode<LEAF>(p, item);
+      if (!mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort)) {
+        s_abort = 1;
+        flag_error(p.status, DEV_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)acc * 128u;
+      uint32_t accum = 0;
+      for (uint32_t pe = 0; pe < it.len && !s_abort; pe++) {
+        const uint32_t m = p.mask[it.start + pe];
+        if (!m) continue;
+        for (int e = 0; e < 2; e++) {
+          uint32_t rm[2], cm[2];
+          const int np = passes<LEAF>(m, e, it.q, rm, cm);
+          for (int ps = 0; ps < np; ps++) {
+            for (int src = 0; src < p.nsrc; src++) {
+              for (int ch = 0; ch < p.chunks; ch++) {
+                if (!mbar_wait(&full[stage], phase, &s_abort)) {
+                  s_abort = 1;
+                  flag_error(p.status, DEV_TIMEOUT);
+                  break;
+                }
+                tc_fence_after();
+                const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
+#pragma unroll
+                for (int kk = 0; kk < 4; kk++) {
+                  const uint64_t da = desc_sw128(sa + kk * 32), db = desc_sw128(sb + kk * 32);
+                  if (TF32) mma_tf32(d, da, db, p.idesc, accum);
+                  else mma_f16(d, da, db, p.idesc, accum);
+                  accum = 1;
+                }
+                mma_commit(&empty[stage]);
+                nst++;
+                if (++stage == kStages) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
+              }
+            }
+          }
+        }
+      }
+      mma_commit(&accf[acc]);
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1u;
+    }
+    if (nst) atomicAdd(p.mma_stages, nst);
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int slice = warp & 3;            // TMEM lanes 32 * slice .. + 31
+    const int row = 32 * slice + lane;     // accumulator row
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (unsigned long long item = blockIdx.x; item < nitems && !s_abort; item += gridDim.x) {
+      const Item it = decode<LEAF>(p, item);
+      uint32_t touched = 0;   // quadrants (a * 2 + c) with a surviving product
+      for (uint32_t pe = 0; pe < it.len; pe++) {
+        const uint32_t m = p.mask[it.start + pe];
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if ((m >> (2 * q)) & 3u) touched |= 1u << q;
+      }
+      if (!mbar_wait(&accf[acc], acc_phase, &s_abort)) {
+        s_abort = 1;
+        flag_error(p.status, DEV_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const int a = LEAF == 64 ? row / 64 : (it.q >> 1);
+      const int r = LEAF == 64 ? row % 64 : row;
+      const int i = (int)(2 * it.I) + a;
+      double ss[2] = {0.0, 0.0};
+      bool wrote[2] = {false, false};
+#pragma unroll
+      for (int cc = 0; cc < RC; cc++) {
+        const int c = LEAF == 64 ? cc : (it.q & 1);
+        const int q = a * 2 + c;
+        const int j = (int)(2 * it.J) + c;
+        if (!((touched >> q) & 1u) || i >= p.nb || j >= p.nb) continue;   // warp-uniform
+        wrote[cc] = true;
+        float *dst = p.C + (((int64_t)i * p.nb + j) * LEAF + r) * LEAF;
+#pragma unroll
+        for (int h = 0; h < LEAF / 32; h++) {
+          uint32_t v[32];
+          const uint32_t col = (uint32_t)acc * 128u + (uint32_t)(cc * 64 + h * 32);
+          tmem_ld32(tmem + ((uint32_t)(32 * slice) << 16) + col, v);
+#pragma unroll
+          for (int x = 0; x < 32; x += 4) {
+            float4 f = make_float4(__uint_as_float(v[x]), __uint_as_float(v[x + 1]),
+                                   __uint_as_float(v[x + 2]), __uint_as_float(v[x + 3]));
+            *reinterpret_cast<float4 *>(dst + h * 32 + x) = f;
+            ss[cc] = fma((double)f.x, (double)f.x, ss[cc]);
+            ss[cc] = fma((double)f.y, (double)f.y, ss[cc]);
+            ss[cc] = fma((double)f.z, (double)f.z, ss[cc]);
+            ss[cc] = fma((double)f.w, (double)f.w, ss[cc]);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acce[acc]);
+      // squared Frobenius norms of the written blocks: rows -> warp -> fixed pair order
+#pragma unroll
+      for (int cc = 0; cc < RC; cc++) {
+        const double w = warp_sum(ss[cc]);
+        if (lane == 0) s_norm[slice][cc] = w;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (warp == 2 && lane < 4) {
+        if (LEAF == 64) {
+          const int aa = lane >> 1, c = lane & 1;
+          const int ii = (int)(2 * it.I) + aa, jj = (int)(2 * it.J) + c;
+          if (((touched >> (aa * 2 + c)) & 1u) && ii < p.nb && jj < p.nb) {
+            p.leaf_norm2C[(int64_t)ii * p.NB + jj] = s_norm[2 * aa][c] + s_norm[2 * aa + 1][c];
+            p.nzC[(int64_t)ii * p.NB + jj] = 1;
+          }
+        } else if (lane == 0) {
+          const int jj = (int)(2 * it.J) + (it.q & 1);
+          if (((touched >> it.q) & 1u) && i < p.nb && jj < p.nb) {
+            p.leaf_norm2C[(int64_t)i * p.NB + jj] =
+                ((s_norm[0][0] + s_norm[1][0]) + s_norm[2][0]) + s_norm[3][0];
+            p.nzC[(int64_t)i * p.NB + jj] = 1;
+          }
+        }
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      (void)wrote;
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1u;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (s_abort) {
+    // error path only: give copies and MMAs already issued time to land before the
+    // shared memory and TMEM are released
+    const unsigned long long t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < 200000ull) __nanosleep(1000);
+    __syncthreads();
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
+// 3-D view [leaf][row][col] of a tree's leaf copy; boxes of one 128-byte K chunk.
+bool make_map(CUtensorMap *m, const void *data, int elem, int b, int nb) {
+  auto fn = encode_fn();
+  if (!fn || !data) return false;
+  const CUtensorMapDataType dt = elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+  cuuint64_t dims[3] = {(cuuint64_t)b, (cuuint64_t)b, (cuuint64_t)nb * nb};
+  cuuint64_t strides[2] = {(cuuint64_t)b * elem, (cuuint64_t)b * b * elem};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / elem), (cuuint32_t)b, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, dt, 3, const_cast<void *>(data), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int LEAF, bool TF32>
+cudaError_t run(const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &alo, const CUtensorMap &blo,
+                const TcArgs &p, int sm_count, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kSmemBytes);
+  if (e != cudaSuccess) return e;
+  k_leaf_tc<LEAF, TF32><<<sm_count, kThreads, kSmemBytes, s>>>(a, b, alo, blo, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_tc(spamm_tree A, spamm_tree B, spamm_tree C, int prec, uint32_t *dev_status,
+                           int sm_count, cudaStream_t s) {
+  const bool tf32 = prec == SPAMM_TF32;
+  const int elem = tf32 ? 4 : 2;
+  const int row = tf32 ? CK_TF32 : prec == SPAMM_FP16 ? CK_FP16 : CK_BF16;
+  const bool bsym = (B->flags & SPAMM_SYMMETRIC) != 0;
+  const int brow = bsym ? row : row + 1;
+  const int blo = bsym ? CK_BF16LO : CK_BF16LO_T;
+  const int b = A->b;
+  CUtensorMap ma, mb, malo, mblo;
+  if (!make_map(&ma, A->copy[row], elem, b, A->nb) || !make_map(&mb, B->copy[brow], elem, b, B->nb))
+    return cudaErrorInvalidValue;
+  if (prec == SPAMM_BF16X3) {
+    if (!make_map(&malo, A->copy[CK_BF16LO], elem, b, A->nb) || !make_map(&mblo, B->copy[blo], elem, b, B->nb))
+      return cudaErrorInvalidValue;
+  } else {
+    malo = ma;
+    mblo = mb;
+  }
+  const TierList &par = C->tiers[C->kmax];
+  TcArgs p{};
+  p.gij = par.gij;
+  p.gstart = par.gstart;
+  p.glen = par.glen;
+  p.K = par.K;
+  p.mask = C->mask;
+  p.ngroups = &C->counts->ngroups[C->kmax];
+  p.cap_entries = par.cap_entries;
+  p.nzA = A->nz;
+  p.nzB = B->nz;
+  p.nb = C->nb;
+  p.NB = C->NB;
+  p.bsym = bsym;
+  p.idesc = make_idesc(tf32 ? kFmtTF32 : prec == SPAMM_FP16 ? kFmtF16 : kFmtBF16, 128, 128);
+  p.chunks = b * elem / 128;
+  p.chunk_elems = 128 / elem;
+  p.nsrc = prec == SPAMM_BF16X3 ? 3 : 1;
+  p.C = (float *)C->copy[CK_F32];
+  p.nzC = C->nz;
+  p.leaf_norm2C = C->norm2 + level_offset(C->kmax);
+  p.mma_stages = &C->counts->mma_tiles;
+  p.status = dev_status;
+  if (b == 64) return tf32 ? run<64, true>(ma, mb, malo, mblo, p, sm_count, s)
+                           : run<64, false>(ma, mb, malo, mblo, p, sm_count, s);
+  if (b == 128) return tf32 ? run<128, true>(ma, mb, malo, mblo, p, sm_count, s)
+                            : run<128, false>(ma, mb, malo, mblo, p, sm_count, s);
+  return cudaErrorInvalidValue;
 }

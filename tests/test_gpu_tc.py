@@ -1,0 +1,179 @@
+"""GPU parity of the tensor-core (tcgen05) leaf products against the CPU oracle.
+
+The cull is the FP64 one, so the triple list must equal the oracle's exactly (outside
+the near-tau band). C is compared with the oracle's SpAMM whose leaf products use the
+operands rounded to the leaf format (oracle/formats.py, from the format definitions)
+and summed in FP64: the only remaining difference is FP32 accumulation, bounded
+elementwise by K * 2^-23 * (|A| |B|)_ij, K the number of products summed into entry
+(i, j) (b per surviving k, three times that for the split BF16 form). The error
+against the plain FP64 SpAMM is reported, not asserted beyond a sanity range.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import formats as F
+from parity import compare_triples, rel_fro
+from paper_1011_3534_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SANITY = {"bf16": 3e-2, "fp16": 3e-3, "tf32": 3e-3, "bf16x3": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1011_3534_gb300 import spamm
+    return spamm
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    c = S.spamm_ctx_create(0, torch.cuda.current_stream())
+    yield c
+    S.spamm_ctx_destroy(c)
+
+
+def prec_of(S, name):
+    return S.PRECISIONS[name]
+
+
+def gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric):
+    n = A.shape[0]
+    prec = prec_of(S, prec_name)
+    fl = S.COPY_FLAG[prec] | (S.SPAMM_SYMMETRIC if symmetric else 0)
+    tA = S.spamm_tree_build(ctx, torch.from_numpy(A).cuda(), n, leaf, fl)
+    tB = tA if B is A else S.spamm_tree_build(ctx, torch.from_numpy(B).cuda(), n, leaf, fl)
+    tC = S.spamm_multiply(ctx, tA, tB, tau, prec)
+    out = dict(C=S.spamm_tree_to_dense(tC), trip=S.spamm_triples(tC), stats=S.spamm_stats(tC))
+    S.spamm_tree_free(tC)
+    if tB is not tA:
+        S.spamm_tree_free(tB)
+    S.spamm_tree_free(tA)
+    return out
+
+
+def rounded_operands(X, prec_name):
+    if prec_name == "bf16x3":
+        return F.split_bf16(X)
+    return F.round_to(X, prec_name), None
+
+
+def reference(A, B, leaf, tau, prec_name, threads):
+    """Oracle C with rounded leaf operands, |A||B| over the same triples, and per-block
+    product counts."""
+    TA, TB = oracle.Tree(A, leaf), oracle.Tree(B, leaf)
+    Ah, Al = rounded_operands(A, prec_name)
+    Bh, Bl = rounded_operands(B, prec_name)
+    T = lambda X: oracle.Tree(X, leaf)
+    if prec_name == "bf16x3":
+        tAh, tAl, tBh, tBl = T(Ah), T(Al), T(Bh), T(Bl)
+        Cref = (oracle.spamm_values(TA, TB, tAh, tBh, tau, threads)
+                + oracle.spamm_values(TA, TB, tAh, tBl, tau, threads)
+                + oracle.spamm_values(TA, TB, tAl, tBh, tau, threads))
+        Cabs = oracle.spamm_values(TA, TB, T(np.abs(Ah) + np.abs(Al)), T(np.abs(Bh) + np.abs(Bl)), tau, threads)
+    else:
+        Cref = oracle.spamm_values(TA, TB, T(Ah), T(Bh), tau, threads)
+        Cabs = oracle.spamm_values(TA, TB, T(np.abs(Ah)), T(np.abs(Bh)), tau, threads)
+    return TA, TB, Cref, Cabs
+
+
+def check(S, ctx, A, B, leaf, tau, prec_name, symmetric):
+    g = gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric)
+    thr = oracle.max_threads()
+    TA, TB, Cref, Cabs = reference(A, B, leaf, tau, prec_name, thr)
+    ref = oracle.spamm(TA, TB, tau, triples=True, product=False)
+    NB = TA.NB
+    only_g, only_o = compare_triples(g["trip"], oracle.sort_triples(ref["triples"]), NB,
+                                     TA.norm2(TA.kmax), TB.norm2(TB.kmax), tau)
+    assert not len(only_g) and not len(only_o), "near-tau flip: rerun with another tau"
+    # products summed into each output block
+    cnt = np.zeros((NB, NB), dtype=np.int64)
+    np.add.at(cnt, (ref["triples"][:, 0], ref["triples"][:, 1]), 1)
+    K = leaf * cnt * (3 if prec_name == "bf16x3" else 1) + 16
+    n = A.shape[0]
+    Kel = np.repeat(np.repeat(K, leaf, 0), leaf, 1)[:n, :n]
+    bound = Kel * 2.0 ** -23 * Cabs + 1e-300
+    viol = np.abs(g["C"] - Cref) > bound
+    assert not np.any(viol), (np.argwhere(viol)[:5], g["C"][viol][:5], Cref[viol][:5])
+    C64 = oracle.spamm(TA, TB, tau, threads=thr)["C"]
+    err = rel_fro(g["C"], C64)
+    print(f"{prec_name} leaf {leaf} n {n} tau {tau}: rel. Frobenius error vs FP64 SpAMM {err:.3e}")
+    assert err < SANITY[prec_name]
+    st = g["stats"]
+    assert st["leaf_products"] == ref["count"]
+    assert st["mma_flops"] >= st["leaf_flops"] * (3 if prec_name == "bf16x3" else 1)
+    return g
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32", "bf16x3"])
+@pytest.mark.parametrize("n,leaf,tau,kind", [
+    (1000, 64, 1e-6, "alg"),      # ragged: 1000 = 15 * 64 + 40
+    (2048, 64, 1e-8, "exp"),
+    (2100, 128, 1e-6, "alg"),
+    (60, 64, 0.0, "exp"),         # one leaf: kmax = 0
+])
+def test_tc_parity_symmetric(S, ctx, prec, n, leaf, tau, kind):
+    A = W.algebraic_decay(n, 2, 0) if kind == "alg" else W.exp_decay(n, 0.85, 1, 0)
+    check(S, ctx, A, A, leaf, tau, prec, symmetric=True)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3"])
+@pytest.mark.parametrize("leaf", [64, 128])
+def test_tc_parity_nonsymmetric(S, ctx, prec, leaf):
+    n = 1500
+    r = np.random.default_rng(9)
+    d = np.abs(np.arange(n)[:, None] - np.arange(n)[None, :])
+    A = r.uniform(-1, 1, (n, n)) * 0.9 ** d
+    B = np.triu(r.uniform(-1, 1, (n, n)) * 0.93 ** d)
+    check(S, ctx, A, B, leaf, 1e-5, prec, symmetric=False)
+
+
+def test_tc_tau_zero_dense(S, ctx):
+    # tau = 0 keeps every triple, including those of padding blocks
+    A = W.exp_decay(700, 0.9, 1, 0)
+    check(S, ctx, A, A, 64, 0.0, "bf16", symmetric=True)
+
+
+def test_tc_deterministic(S, ctx):
+    A = W.algebraic_decay(3000, 2, 0)
+    g1 = gpu_product(S, ctx, A, A, 64, 1e-8, "bf16", True)
+    g2 = gpu_product(S, ctx, A, A, 64, 1e-8, "bf16", True)
+    assert np.array_equal(g1["C"], g2["C"])
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("tau", [1e-10, 1e-8, 1e-6, 1e-4])
+def test_workload_alg8192_tc_sampled(S, ctx, prec, tau):
+    # n = 8192 algebraic decay, leaf 64, in the benchmark's launch configuration:
+    # full triple list, C on sampled output blocks against the rounded-operand oracle
+    n, leaf = 8192, 64
+    A = W.algebraic_decay(n, 2, 0)
+    g = gpu_product(S, ctx, A, A, leaf, tau, prec, True)
+    TA = oracle.Tree(A, leaf)
+    ref = oracle.spamm(TA, TA, tau, triples=True, product=False)
+    compare_triples(g["trip"], oracle.sort_triples(ref["triples"]), TA.NB, TA.norm2(TA.kmax),
+                    TA.norm2(TA.kmax), tau)
+    Ah, Al = rounded_operands(A, prec)
+    tAh = oracle.Tree(Ah, leaf)
+    tAl = oracle.Tree(Al, leaf) if Al is not None else None
+    tAbs = oracle.Tree(np.abs(Ah) + (np.abs(Al) if Al is not None else 0.0), leaf)
+    cnt = np.zeros((TA.NB, TA.NB), dtype=np.int64)
+    np.add.at(cnt, (ref["triples"][:, 0], ref["triples"][:, 1]), 1)
+    rng = np.random.default_rng(7)
+    NB = TA.NB
+    blocks = [(0, 0), (0, NB - 1), (NB - 1, NB - 1), (5, 6)] + [tuple(x) for x in rng.integers(0, NB, (12, 2))]
+    for i, j in blocks:
+        i, j = int(i), int(j)
+        if tAl is None:
+            Cref = oracle.spamm_block(TA, TA, tau, i, j, tAh, tAh)
+        else:
+            Cref = (oracle.spamm_block(TA, TA, tau, i, j, tAh, tAh) + oracle.spamm_block(TA, TA, tau, i, j, tAh, tAl)
+                    + oracle.spamm_block(TA, TA, tau, i, j, tAl, tAh))
+        Cabs = oracle.spamm_block(TA, TA, tau, i, j, tAbs, tAbs)
+        K = leaf * cnt[i, j] * (3 if tAl is not None else 1) + 16
+        got = g["C"][i * leaf:(i + 1) * leaf, j * leaf:(j + 1) * leaf]
+        assert np.all(np.abs(got - Cref) <= K * 2.0 ** -23 * Cabs + 1e-300), (i, j)

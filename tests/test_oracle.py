@@ -324,3 +324,42 @@ def test_pins_catch_planted_mistake(mutant):
     L = oracle.mutant_lib(mutant)
     assert L.oracle_mutant() == mutant
     assert _pins_fail(L)
+
+
+# ---------------------------------------------------------------- operand formats
+
+def test_format_rounding_matches_torch_on_float_inputs():
+    # on FP32-representable inputs a single rounding to BF16 / FP16 is what torch does
+    torch = pytest.importorskip("torch")
+    from oracle import formats as F
+    r = np.random.default_rng(3)
+    x = (r.standard_normal(20000) * np.exp(r.uniform(-30, 10, 20000))).astype(np.float32).astype(np.float64)
+    assert np.array_equal(F.round_to(x, "bf16"), torch.tensor(x).to(torch.bfloat16).double().numpy())
+    assert np.array_equal(F.round_to(x, "fp16"), torch.tensor(x).to(torch.float16).double().numpy())
+
+
+def test_format_rounding_hand_cases():
+    from oracle import formats as F
+    # ties go to even; just above a tie rounds up (single rounding from FP64)
+    assert F.round_to(np.array([1 + 2.0 ** -8]), "bf16")[0] == 1.0
+    assert F.round_to(np.array([1 + 3 * 2.0 ** -8]), "bf16")[0] == 1 + 2.0 ** -6
+    assert F.round_to(np.array([1 + 2.0 ** -8 + 2.0 ** -40]), "bf16")[0] == 1 + 2.0 ** -7
+    assert F.round_to(np.array([1 + 2.0 ** -11]), "tf32")[0] == 1.0
+    assert F.round_to(np.array([1 + 2.0 ** -11 + 2.0 ** -45]), "tf32")[0] == 1 + 2.0 ** -10
+    assert F.round_to(np.array([2.0 ** -25]), "fp16")[0] == 0.0           # half of the least subnormal
+    assert F.round_to(np.array([3 * 2.0 ** -25]), "fp16")[0] == 2.0 ** -23
+    assert F.round_to(np.array([65504.0]), "fp16")[0] == 65504.0
+    hi, lo = F.split_bf16(np.array([np.pi]))
+    assert abs(hi[0] + lo[0] - np.pi) < 2.0 ** -16 * np.pi
+
+
+def test_values_oracle_uses_substituted_leaves():
+    # same triple list as the plain product; leaf values from the second pair
+    A = rng_matrix(160, 31)
+    TA = oracle.Tree(A, 16)
+    T2 = oracle.Tree(2.0 * A, 16)
+    plain = oracle.spamm(TA, TA, 1e-4)["C"]
+    twice = oracle.spamm_values(TA, TA, T2, TA, 1e-4)
+    assert np.array_equal(twice, 2.0 * plain)
+    blk = oracle.spamm_block(TA, TA, 1e-4, 3, 4, T2, TA)
+    assert np.array_equal(blk, 2.0 * plain[48:64, 64:80])
