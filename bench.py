@@ -1,0 +1,378 @@
+"""SpAMM benchmark: dense-equivalent GFLOP/s of one GB300 on the algebraic-decay
+workload (n = 8192, a_ij = u_ij / (|i-j|^3 + 1), leaf 64), with leaf-GEMM TFLOP/s and
+roofline fractions.
+
+One step = the whole hot path on one input: build the quadtree of A (norms of every
+tier plus the leaf copies the precision needs, from the FP64 A resident in HBM), cull
+the product space tier by tier, and sum the surviving leaf products of C = A A into
+C's tiles and norms. Headline: tau = 1e-8, BF16 leaves with FP32 accumulation.
+A sweep over tau in {1e-10, 1e-8, 1e-6, 1e-4} and the leaf precisions reports each
+one's time and its relative Frobenius error against the FP64 SpAMM on the GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep]
+
+--impl reference times the CPU oracle (plain FP64 recursive SpAMM) on this host.
+Multi-GPU: every rank runs an independent replica (the products do not exchange data).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, LEAF, TAU = 8192, 64, 1e-8
+TAUS = (1e-10, 1e-8, 1e-6, 1e-4)
+WORKLOAD = "algebraic-decay n=8192 leaf=64 (a_ij=u_ij/(|i-j|^3+1), u=U[.5,1]*sign, seed 0)"
+METRIC = "SpAMM dense-equiv GFLOP/s & leaf-GEMM % of TC peak at fixed error vs FP64 SpAMM"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return dict(hbm=p["hbm_gbs"], bf16=p["bf16_tflops"], bf16_sus=p["bf16_tflops_sustained"],
+                    source="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, source="fallback")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(name: str):
+    """DRAM bytes per launch of `name` from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[name]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != rec["sha256_16"]:
+        return None
+    return rec["dram_bytes_per_launch"] * rec.get("scale", 1.0)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1011_3534_gb300 import spamm as S
+    from paper_1011_3534_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+    ctx = S.spamm_ctx_create(local, stream, timing=True)
+    A_host = W.algebraic_decay(N, 2, 0)
+    dA = torch.from_numpy(A_host).to(f"cuda:{local}")
+    pk = peaks()
+
+    def flags_for(prec):
+        return S.COPY_FLAG[prec] | S.SPAMM_SYMMETRIC | S.SPAMM_NO_RIGHT
+
+    def step(prec, tA, tC, tau, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        S.spamm_tree_update(tA, dA)                  # quadtree build (K1 + norm pyramid)
+        if ev is not None:
+            ev[1].record(stream)
+        tC = S.spamm_multiply(ctx, tA, tA, tau, prec, 0, tC)   # cull + leaf products
+        if ev is not None:
+            ev[2].record(stream)
+        return tC
+
+    def timed(prec, tau, steps, warmup, phases=True):
+        tA = S.spamm_tree_build(ctx, dA, N, LEAF, flags_for(prec))
+        tC = None
+        for _ in range(warmup):
+            tC = step(prec, tA, tC, tau)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        l0 = S.spamm_kernel_launches(ctx)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s in range(steps):
+            tC = step(prec, tA, tC, tau, evs[s] if phases else None)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        launches = S.spamm_kernel_launches(ctx) - l0
+        ms_total = t0.elapsed_time(t1)
+        if ws > 1:
+            tt = torch.tensor([ms_total], device=dA.device)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms_total = float(tt.item())
+        ms_build = ms_mult = None
+        if phases:
+            ms_build = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+            ms_mult = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+        st = S.spamm_stats(tC)
+        S.spamm_tree_free(tA)
+        return dict(ms=ms_total / steps, ms_build=ms_build, ms_mult=ms_mult, stats=st,
+                    launches=launches, tree=tC)
+
+    # ---- headline
+    prec = S.SPAMM_BF16
+    for _ in range(1):
+        r0 = timed(prec, TAU, 2, 1)   # allocate and warm caches
+        S.spamm_tree_free(r0["tree"])
+    with ClockSampler(local) as clk:
+        r = timed(prec, TAU, args.steps, args.warmup)
+    st = r["stats"]
+    ms = r["ms"]
+    dense_gflops = 2.0 * N ** 3 / (ms * 1e-3) / 1e9
+    value = dense_gflops * ws
+    # phase times inside the timed region (events on the library's stream)
+    ms_leaf = st["ms_leaf"]
+    ms_cull = st["ms_cull"]
+    bytes_build = 8.0 * N * N + 2.0 * N * N          # read FP64 A, write the BF16 copy
+    build_gbs = bytes_build / (r["ms_build"] * 1e-3) / 1e9
+    leaf_tflops = st["leaf_flops"] / (ms_leaf * 1e-3) / 1e12 if ms_leaf else None
+    mma_tflops = st["mma_flops"] / (ms_leaf * 1e-3) / 1e12 if ms_leaf else None
+    phases = {"build_ms": r["ms_build"], "cull_ms": ms_cull, "leaf_ms": ms_leaf,
+              "multiply_ms": r["ms_mult"]}
+    if r["ms_build"] >= (ms_leaf or 0):
+        roof = {"kernel": "k_tree_build", "bound": "hbm", "achieved": build_gbs, "peak": pk["hbm"],
+                "unit": "GB/s", "frac": build_gbs / pk["hbm"],
+                "traffic": kernel_traffic("k_tree_build"),
+                "algorithmic_bytes_per_launch": bytes_build,
+                "peak_source": pk["source"] + " hbm_gbs"}
+    else:
+        roof = {"kernel": "k_leaf_tc", "bound": "tensor", "achieved": leaf_tflops,
+                "peak": pk["bf16_sus"], "unit": "TFLOP/s", "frac": leaf_tflops / pk["bf16_sus"],
+                "traffic": kernel_traffic("k_leaf_tc"),
+                "algorithmic_flops_per_launch": st["leaf_flops"],
+                "peak_source": pk["source"] + " bf16_tflops_sustained"}
+    leaf = {"leaf_tflops": leaf_tflops, "mma_tflops": mma_tflops,
+            "frac_of_bf16_peak": (leaf_tflops / pk["bf16_sus"]) if leaf_tflops else None,
+            "leaf_products": st["leaf_products"], "leaf_flops": st["leaf_flops"],
+            "mma_flops": st["mma_flops"]}
+    S.spamm_tree_free(r["tree"])
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    A_pin = torch.from_numpy(A_host).pin_memory()
+    C_pin = torch.empty((N, N), dtype=torch.float64).pin_memory()
+    A_np, C_np = A_pin.numpy(), C_pin.numpy()
+    tA = S.spamm_tree_build(ctx, A_np, N, LEAF, flags_for(prec))
+    tC = None
+    for _ in range(max(1, args.warmup)):
+        S.spamm_tree_update(tA, A_np)
+        tC = S.spamm_multiply(ctx, tA, tA, TAU, prec, 0, tC)
+        S.spamm_tree_to_dense(tC, C_np)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 10))
+    for _ in range(e2e_steps):
+        S.spamm_tree_update(tA, A_np)        # host -> device copy of A inside
+        tC = S.spamm_multiply(ctx, tA, tA, TAU, prec, 0, tC)
+        S.spamm_tree_to_dense(tC, C_np)      # device -> host copy of C; synchronises
+    e2e_ms = (time.perf_counter() - e0) * 1e3 / e2e_steps
+    S.spamm_tree_free(tA)
+    if ws > 1:
+        tt = torch.tensor([e2e_ms], device=dA.device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    S.spamm_tree_free(tC)
+    e2e = {"value": 2.0 * N ** 3 / (e2e_ms * 1e-3) / 1e9 * ws, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": 8 * N * N, "d2h_bytes_per_step": 8 * N * N, "ms_per_step": e2e_ms}
+
+    # ---- precision and tau sweep (error vs FP64 SpAMM on the GPU)
+    sweep = []
+    if not args.no_sweep:
+        for tau in TAUS:
+            ref = None
+            for name in ("fp64", "tf32", "bf16", "bf16x3", "fp16"):
+                p = S.PRECISIONS[name]
+                rr = timed(p, tau, 3, 1)
+                Cd = torch.empty((N, N), dtype=torch.float64, device=dA.device)
+                S.spamm_tree_to_dense(rr["tree"], Cd)
+                if name == "fp64":
+                    ref = Cd
+                    err = 0.0
+                else:
+                    err = float(torch.linalg.norm(Cd - ref) / torch.linalg.norm(ref))
+                s2 = rr["stats"]
+                lt = s2["leaf_flops"] / (s2["ms_leaf"] * 1e-3) / 1e12 if s2["ms_leaf"] else None
+                sweep.append({"tau": tau, "prec": name, "ms_per_step": rr["ms"],
+                              "dense_equiv_gflops": 2.0 * N ** 3 / (rr["ms"] * 1e-3) / 1e9,
+                              "build_ms": rr["ms_build"], "cull_ms": s2["ms_cull"], "leaf_ms": s2["ms_leaf"],
+                              "leaf_tflops": lt, "leaf_products": s2["leaf_products"],
+                              "rel_fro_err_vs_fp64_spamm": err})
+                S.spamm_tree_free(rr["tree"])
+                del Cd
+            del ref
+
+    # ---- CPU oracle on this host (rank 0 only, bounded sample)
+    cpu = cpu_baseline(A_host, quick=args.no_sweep) if rank == 0 else None
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "leaf": LEAF, "tau": TAU, "precision": "bf16",
+                   "accumulate": "fp32", "l2": "inputs larger than L2 (A is 512 MiB FP64)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "e2e": e2e, "gpu_launches": r["launches"], "phases": phases, "leaf_gemm": leaf,
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "sweep": sweep,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    S.spamm_ctx_destroy(ctx)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def cpu_baseline(A_host, quick=False, budget_s=20.0):
+    """The CPU oracle (FP64 recursive SpAMM, OpenMP over output quadrants) on the host
+    cores: quadtree build + product at tau = 1e-8 on the full n = 8192 matrix, repeated
+    while inside the time budget."""
+    import oracle
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    TA = oracle.Tree(A_host, LEAF)
+    oracle.spamm(TA, TA, TAU, threads=cores)
+    dt = time.perf_counter() - t0
+    reps = 1
+    if not quick:
+        while (reps + 1) * dt < budget_s and reps < 5:
+            t1 = time.perf_counter()
+            TB = oracle.Tree(A_host, LEAF)
+            oracle.spamm(TB, TB, TAU, threads=cores)
+            dt = min(dt, time.perf_counter() - t1)
+            reps += 1
+    return {"value": 2.0 * N ** 3 / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"full n={N} product at tau={TAU} (tree build + Eq. 4 recursion, FP64), best of {reps}",
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1011_3534_gb300 import workloads as W
+    import oracle
+    A = W.algebraic_decay(N, 2, 0)
+    cores = oracle.max_threads()
+    for _ in range(args.warmup):
+        TA = oracle.Tree(A, LEAF)
+        oracle.spamm(TA, TA, TAU, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        TA = oracle.Tree(A, LEAF)
+        oracle.spamm(TA, TA, TAU, threads=cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    v = 2.0 * N ** 3 / (ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": N, "leaf": LEAF, "tau": TAU, "precision": "fp64"},
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"full n={N} product at tau={TAU} per step"},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-sweep", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

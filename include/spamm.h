@@ -130,6 +130,11 @@ SPAMM_API int64_t spamm_kernel_launches(spamm_ctx ctx);
 SPAMM_API spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t leaf,
                               int32_t flags, spamm_tree *out);
 SPAMM_API spamm_status spamm_tree_free(spamm_tree t);
+/* Rebuild tree t in place from a new n x n FP64 row-major matrix A of the same order:
+   the same leaf size and leaf copies, no allocation (a repeated build, e.g. of the
+   iterate of a purification loop). A is a device pointer unless `flags` holds
+   SPAMM_HOST_INPUT. Errors: SPAMM_EINVAL (t is a product tree, bad flags), SPAMM_ECUDA. */
+SPAMM_API spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags);
 /* Shape of a tree: order n, leaf size, padded blocks per side NB, and kmax. */
 SPAMM_API spamm_status spamm_tree_info(spamm_tree t, int64_t *n, int32_t *leaf, int32_t *nb_padded,
                              int32_t *kmax);

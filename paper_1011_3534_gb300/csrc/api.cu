@@ -275,6 +275,26 @@ spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t
   return SPAMM_OK;
 }
 
+spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags) {
+  if (!t) return SPAMM_EINVAL;
+  spamm_ctx ctx = t->ctx;
+  if (!A) return fail(ctx, SPAMM_EINVAL, "tree_update: null input");
+  if (t->is_product) return fail(ctx, SPAMM_EINVAL, "tree_update: product trees cannot be rebuilt");
+  if (flags & ~SPAMM_HOST_INPUT) return fail(ctx, SPAMM_EINVAL, "tree_update: only SPAMM_HOST_INPUT is accepted");
+  const double *src = A;
+  if (flags & SPAMM_HOST_INPUT) {
+    spamm_status st = ensure_stage(ctx, (size_t)t->n * t->n * sizeof(double));
+    if (st != SPAMM_OK) return st;
+    CK(cudaMemcpyAsync(ctx->stage, A, (size_t)t->n * t->n * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->stream), "tree_update: host to device copy");
+    src = (const double *)ctx->stage;
+  }
+  CK(launch_tree_build(t, src, ctx->stream), "tree_update: launch");
+  CK(launch_pyramid(t, ctx->stream), "tree_update: launch");
+  ctx->launches += 2 + (t->kmax >= 2 ? 1 : 0);
+  return SPAMM_OK;
+}
+
 spamm_status spamm_tree_free(spamm_tree t) {
   if (!t) return SPAMM_EINVAL;
   cudaStreamSynchronize(t->ctx->stream);

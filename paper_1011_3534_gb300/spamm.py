@@ -33,7 +33,7 @@ MAX_LEVELS = 24
 
 # Every entry point declared in include/spamm.h.
 EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_error",
-           "spamm_kernel_launches", "spamm_tree_build", "spamm_tree_free", "spamm_tree_info",
+           "spamm_kernel_launches", "spamm_tree_build", "spamm_tree_update", "spamm_tree_free", "spamm_tree_info",
            "spamm_tree_norms", "spamm_tree_to_dense", "spamm_multiply", "spamm_stats",
            "spamm_triples")
 
@@ -73,6 +73,7 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.spamm_kernel_launches.restype = _I64
     L.spamm_tree_build.argtypes = [_P, _P, _I64, _I32, _I32, ctypes.POINTER(_P)]
     L.spamm_tree_free.argtypes = [_P]
+    L.spamm_tree_update.argtypes = [_P, _P, _I32]
     L.spamm_tree_info.argtypes = [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32),
                                   ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
     L.spamm_tree_norms.argtypes = [_P, _I32, _P]
@@ -160,6 +161,13 @@ def spamm_tree_build(ctx: Ctx, A, n: int, leaf: int, flags: int) -> Tree:
     h = _P()
     ctx.check(LIB.spamm_tree_build(ctx.h, _ptr(A), n, leaf, flags, ctypes.byref(h)), "spamm_tree_build")
     return Tree(ctx, h.value)
+
+
+def spamm_tree_update(t: Tree, A) -> Tree:
+    """Rebuild t in place from A (torch CUDA tensor, or numpy host array)."""
+    flags = SPAMM_HOST_INPUT if isinstance(A, np.ndarray) else 0
+    t.ctx.check(LIB.spamm_tree_update(t.h, _ptr(A), flags), "spamm_tree_update")
+    return t
 
 
 def spamm_tree_free(t: Tree):

@@ -62,9 +62,13 @@ def rounded_operands(X, prec_name):
     return F.round_to(X, prec_name), None
 
 
+FP16_MIN_NORMAL = 2.0 ** -14
+
+
 def reference(A, B, leaf, tau, prec_name, threads):
-    """Oracle C with rounded leaf operands, |A||B| over the same triples, and per-block
-    product counts."""
+    """Oracle C with rounded leaf operands and |A||B| over the same triples. For FP16
+    also the total magnitude of the products whose two operands are both FP16
+    subnormals, which the tensor cores of this GPU do not sum exactly (measured)."""
     TA, TB = oracle.Tree(A, leaf), oracle.Tree(B, leaf)
     Ah, Al = rounded_operands(A, prec_name)
     Bh, Bl = rounded_operands(B, prec_name)
@@ -78,13 +82,17 @@ def reference(A, B, leaf, tau, prec_name, threads):
     else:
         Cref = oracle.spamm_values(TA, TB, T(Ah), T(Bh), tau, threads)
         Cabs = oracle.spamm_values(TA, TB, T(np.abs(Ah)), T(np.abs(Bh)), tau, threads)
-    return TA, TB, Cref, Cabs
+    Csub = 0.0
+    if prec_name == "fp16":
+        sub = lambda X: np.where(np.abs(X) < FP16_MIN_NORMAL, np.abs(X), 0.0)
+        Csub = oracle.spamm_values(TA, TB, T(sub(Ah)), T(sub(Bh)), tau, threads)
+    return TA, TB, Cref, Cabs + 0.0, Csub
 
 
 def check(S, ctx, A, B, leaf, tau, prec_name, symmetric):
     g = gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric)
     thr = oracle.max_threads()
-    TA, TB, Cref, Cabs = reference(A, B, leaf, tau, prec_name, thr)
+    TA, TB, Cref, Cabs, Csub = reference(A, B, leaf, tau, prec_name, thr)
     ref = oracle.spamm(TA, TB, tau, triples=True, product=False)
     NB = TA.NB
     only_g, only_o = compare_triples(g["trip"], oracle.sort_triples(ref["triples"]), NB,
@@ -96,7 +104,7 @@ def check(S, ctx, A, B, leaf, tau, prec_name, symmetric):
     K = leaf * cnt * (3 if prec_name == "bf16x3" else 1) + 16
     n = A.shape[0]
     Kel = np.repeat(np.repeat(K, leaf, 0), leaf, 1)[:n, :n]
-    bound = Kel * 2.0 ** -23 * Cabs + 1e-300
+    bound = Kel * 2.0 ** -23 * Cabs + Csub + 1e-300
     viol = np.abs(g["C"] - Cref) > bound
     assert not np.any(viol), (np.argwhere(viol)[:5], g["C"][viol][:5], Cref[viol][:5])
     C64 = oracle.spamm(TA, TB, tau, threads=thr)["C"]
