@@ -169,6 +169,35 @@ SPAMM_API spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out);
    *count receives the number of triples; SPAMM_ERANGE if it exceeds cap. */
 SPAMM_API spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, int64_t *count);
 
+/* ---- cull without device allocation ----
+   For callers that cannot allocate device memory: code running inside a CUDA graph
+   capture or a real-time loop where cudaMalloc would synchronise or fail, embedders
+   whose memory is owned by another allocator, or callers holding only raw device
+   pointers and a stream. (The paper has no counterpart to this entry point.)
+   Computes the surviving leaf triples of SpAMM(A, B) with tolerance tau from the
+   squared Frobenius norms of the leaf blocks of A and B, with the same tier-by-tier
+   cull as spamm_multiply, and allocates nothing: its working memory is one 2 MiB
+   static device array of the library, held by every GPU that loads it until exit.
+     normA2, normB2 : device, NB x NB row-major FP64 squared leaf norms (tier kmax of
+                      spamm_tree_norms, or computed by the caller); not modified
+     nb_padded      : NB, a power of two, 1 <= NB <= 128 (larger: SPAMM_ERANGE)
+     triples        : device, room for `cap` triples (i, j, k) as 3 uint32 each, written
+                      in the cull's order (output blocks in Morton order, then k
+                      ascending); beyond cap nothing is written
+     count          : device int64: the number of surviving triples (may exceed cap),
+                      or -1 if a device-side wait timed out
+     cuda_stream    : the stream all work is ordered on (a cudaStream_t; NULL = legacy)
+   The call is asynchronous on the stream. The first call on each device looks up the
+   device address of the static array (cudaGetSymbolAddress, with that device current);
+   make that first call before any stream capture. Every call on a device shares the
+   array and later calls overwrite it: calls that may overlap on the GPU (other streams,
+   other host threads) race and must be serialised by the caller.
+   Errors: SPAMM_EINVAL (null pointer, NB not a power of two, tau < 0 or not finite),
+   SPAMM_ERANGE (NB > 128), SPAMM_ECUDA (a CUDA call failed). */
+SPAMM_API spamm_status spamm_cull_noalloc(const double *normA2, const double *normB2,
+                                          int32_t nb_padded, double tau, uint32_t *triples,
+                                          int64_t cap, int64_t *count, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

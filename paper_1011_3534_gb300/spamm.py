@@ -35,7 +35,7 @@ MAX_LEVELS = 24
 EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_error",
            "spamm_kernel_launches", "spamm_tree_build", "spamm_tree_update", "spamm_tree_free", "spamm_tree_info",
            "spamm_tree_norms", "spamm_tree_to_dense", "spamm_multiply", "spamm_stats",
-           "spamm_triples")
+           "spamm_triples", "spamm_cull_noalloc")
 
 
 class SpammError(RuntimeError):
@@ -81,6 +81,7 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.spamm_multiply.argtypes = [_P, _P, _P, _D, ctypes.c_int, _I32, ctypes.POINTER(_P)]
     L.spamm_stats.argtypes = [_P, ctypes.POINTER(StatsT)]
     L.spamm_triples.argtypes = [_P, _P, _I64, ctypes.POINTER(_I64)]
+    L.spamm_cull_noalloc.argtypes = [_P, _P, _I32, _D, _P, _I64, _P, _P]
     for name in EXPORTS:
         if name not in ("spamm_last_error", "spamm_kernel_launches"):
             getattr(L, name).restype = st
@@ -218,3 +219,12 @@ def spamm_triples(C: Tree) -> np.ndarray:
     out = np.empty((max(cnt.value, 1), 3), dtype=np.uint32)
     C.ctx.check(LIB.spamm_triples(C.h, out.ctypes.data, out.shape[0], ctypes.byref(cnt)), "spamm_triples")
     return out[:cnt.value]
+
+
+def spamm_cull_noalloc(normA2, normB2, nb_padded: int, tau: float, triples, cap: int, count, stream=None):
+    """Forward to the allocation-free cull: all buffers are device tensors the caller owns."""
+    s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = LIB.spamm_cull_noalloc(_ptr(normA2), _ptr(normB2), nb_padded, float(tau),
+                                _ptr(triples) if triples is not None else None, cap, _ptr(count), s)
+    if rc != SPAMM_OK:
+        raise SpammError(rc, "spamm_cull_noalloc failed")
