@@ -265,7 +265,7 @@ spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t
   }
   cudaError_t e = launch_tree_build(t, src, ctx->stream);
   if (e == cudaSuccess) e = launch_pyramid(t, ctx->stream);
-  ctx->launches += 1 + 1 + (t->kmax >= 2 ? 1 : 0);
+  ctx->launches += 1 + pyramid_launches(t->kmax);
   if (e != cudaSuccess) {
     free_tree_memory(t);
     delete t;
@@ -291,7 +291,7 @@ spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags) {
   }
   CK(launch_tree_build(t, src, ctx->stream), "tree_update: launch");
   CK(launch_pyramid(t, ctx->stream), "tree_update: launch");
-  ctx->launches += 2 + (t->kmax >= 2 ? 1 : 0);
+  ctx->launches += 1 + pyramid_launches(t->kmax);
   return SPAMM_OK;
 }
 
@@ -424,7 +424,7 @@ spamm_status spamm_multiply(spamm_ctx ctx, spamm_tree A, spamm_tree B, double ta
   launches++;
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[2], s), "event");
   CK(launch_pyramid(Ct, s), "multiply: pyramid launch");
-  launches += 1 + (Ct->kmax >= 2 ? 1 : 0);
+  launches += pyramid_launches(Ct->kmax);
   CK(launch_finish_stats(Ct, s), "multiply: stats launch");
   launches++;
   bool want[CK_COUNT];

@@ -123,3 +123,4 @@ cudaError_t launch_finish_stats(spamm_tree C, cudaStream_t s);
 cudaError_t launch_tile_convert(spamm_tree t, cudaStream_t s);
 int64_t cull_look_words(int kmax);
 int64_t cull_bound_words(int kmax, int64_t *offsets);
+int pyramid_launches(int kmax);

@@ -54,6 +54,15 @@ struct TcArgs {
   uint32_t *status;
 };
 
+__device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
+  const float s = h + bh;
+  const float bb = s - h;
+  float err = (h - (s - bb)) + (bh - bb);
+  err += l + bl;
+  h = s + err;
+  l = err - (h - s);
+}
+
 struct Item {
   uint32_t I, J, start, len;
   int q;   // leaf 128: output quadrant a * 2 + c of the group
@@ -109,6 +118,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   __shared__ double s_norm[4][2];
+  __shared__ int4 s_desc[32][4];     // producer: passes of the 32 entries in flight
+  __shared__ int s_ndesc[32];
   constexpr int RA = LEAF == 64 ? 2 : 1;        // A leaves stacked along M
   constexpr int RC = LEAF == 64 ? 2 : 1;        // B leaves stacked along N
   constexpr uint32_t kBox = LEAF * 128;         // bytes of one leaf box (LEAF rows x 128 B)
@@ -135,153 +146,183 @@ __global__ void __launch_bounds__(kThreads, 1)
   const unsigned long long ng = *p.ngroups;
   const unsigned long long nitems = LEAF == 64 ? ng : 4ull * ng;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    tma_prefetch_desc(&mA);
-    tma_prefetch_desc(&mB);
-    if (p.nsrc == 3) {
-      tma_prefetch_desc(&mAlo);
-      tma_prefetch_desc(&mBlo);
+  if (warp == 0) {
+    // ---------------- TMA producer (warp 0) ----------------
+    // The warp reads 32 entries of the group at a time: each lane turns one entry into
+    // its (up to four) passes with the leaf coordinates of every box (zero-filled
+    // boxes point one leaf past the end), then lane 0 issues the stages in order.
+    if (lane == 0) {
+      tma_prefetch_desc(&mA);
+      tma_prefetch_desc(&mB);
+      if (p.nsrc == 3) {
+        tma_prefetch_desc(&mAlo);
+        tma_prefetch_desc(&mBlo);
+      }
     }
     const int oob = p.nb * p.nb;
     int stage = 0;
     uint32_t phase = 0;
-    for (unsigned long long item = blockIdx.x; item < nitems && !s_abort; item += gridDim.x) {
+    // loops over items and entry chunks are warp-uniform; after an abort lane 0 only
+    // skips its work, so every lane keeps the same trip counts
+    for (unsigned long long item = blockIdx.x; item < nitems; item += gridDim.x) {
       const Item it = decode<LEAF>(p, item);
-      for (uint32_t pe = 0; pe < it.len && !s_abort; pe++) {
-        const uint32_t m = p.mask[it.start + pe];
-        if (!m) continue;
-        const int K2 = 2 * (int)p.K[it.start + pe];
-        for (int e = 0; e < 2; e++) {
-          uint32_t rm[2], cm[2];
-          const int np = passes<LEAF>(m, e, it.q, rm, cm);
-          const int k = K2 + e;
-          for (int ps = 0; ps < np; ps++) {
-            for (int src = 0; src < p.nsrc; src++) {
-              const CUtensorMap *ma = src == 2 ? &mAlo : &mA;
-              const CUtensorMap *mb = src == 1 ? &mBlo : &mB;
-              for (int ch = 0; ch < p.chunks; ch++) {
-                if (!mbar_wait(&empty[stage], phase ^ 1u, &s_abort)) {
-                  s_abort = 1;
-                  flag_error(p.status, DEV_TIMEOUT);
-                  break;
-                }
-                mbar_expect_tx(&full[stage], kStageBytes);
-                const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
+      for (uint32_t p0 = 0; p0 < it.len; p0 += 32) {
+        const uint32_t pe = p0 + lane;
+        int np_all = 0;
+        if (pe < it.len) {
+          const uint32_t m = p.mask[it.start + pe];
+          const int K2 = 2 * (int)p.K[it.start + pe];
 #pragma unroll
-                for (int a = 0; a < RA; a++) {
-                  const int i = LEAF == 64 ? (int)(2 * it.I) + a : (int)(2 * it.I) + (it.q >> 1);
-                  const bool ok = ((rm[ps] >> a) & 1u) && i < p.nb && k < p.nb &&
-                                  p.nzA[(int64_t)i * p.NB + k];
-                  tma_load_3d(sa + a * kBox, ma, &full[stage], ch * p.chunk_elems, 0, ok ? i * p.nb + k : oob);
-                }
+          for (int e = 0; e < 2; e++) {
+            uint32_t rm[2], cm[2];
+            const int np = passes<LEAF>(m, e, it.q, rm, cm);
+            const int k = K2 + e;
+            for (int ps = 0; ps < np; ps++) {
+              int4 d;
+              int la[2] = {oob, oob}, lb[2] = {oob, oob};
 #pragma unroll
-                for (int c = 0; c < RC; c++) {
-                  const int j = LEAF == 64 ? (int)(2 * it.J) + c : (int)(2 * it.J) + (it.q & 1);
-                  const bool ok = ((cm[ps] >> c) & 1u) && j < p.nb && k < p.nb &&
-                                  p.nzB[(int64_t)k * p.NB + j];
-                  const int leaf = p.bsym ? j * p.nb + k : k * p.nb + j;
-                  tma_load_3d(sb + c * kBox, mb, &full[stage], ch * p.chunk_elems, 0, ok ? leaf : oob);
-                }
-                if (++stage == kStages) {
-                  stage = 0;
-                  phase ^= 1u;
+              for (int a = 0; a < RA; a++) {
+                const int i = LEAF == 64 ? (int)(2 * it.I) + a : (int)(2 * it.I) + (it.q >> 1);
+                if (((rm[ps] >> a) & 1u) && i < p.nb && k < p.nb && p.nzA[(int64_t)i * p.NB + k]) la[a] = i * p.nb + k;
+              }
+#pragma unroll
+              for (int c = 0; c < RC; c++) {
+                const int j = LEAF == 64 ? (int)(2 * it.J) + c : (int)(2 * it.J) + (it.q & 1);
+                if (((cm[ps] >> c) & 1u) && j < p.nb && k < p.nb && p.nzB[(int64_t)k * p.NB + j])
+                  lb[c] = p.bsym ? j * p.nb + k : k * p.nb + j;
+              }
+              d.x = la[0];
+              d.y = la[1];
+              d.z = lb[0];
+              d.w = lb[1];
+              s_desc[lane][np_all++] = d;
+            }
+          }
+        }
+        s_ndesc[lane] = np_all;
+        __syncwarp();
+        if (lane == 0) {
+          const int nl = (int)min(32u, it.len - p0);
+          for (int l = 0; l < nl && !s_abort; l++) {
+            for (int di = 0; di < s_ndesc[l] && !s_abort; di++) {
+              const int4 d = s_desc[l][di];
+              for (int src = 0; src < p.nsrc && !s_abort; src++) {
+                const CUtensorMap *ma = src == 2 ? &mAlo : &mA;
+                const CUtensorMap *mb = src == 1 ? &mBlo : &mB;
+                for (int ch = 0; ch < p.chunks; ch++) {
+                  if (!mbar_wait(&empty[stage], phase ^ 1u, &s_abort)) {
+                    s_abort = 1;
+                    flag_error(p.status, DEV_TIMEOUT);
+                    break;
+                  }
+                  mbar_expect_tx(&full[stage], kStageBytes);
+                  const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
+                  tma_load_3d(sa, ma, &full[stage], ch * p.chunk_elems, 0, d.x);
+                  if (RA == 2) tma_load_3d(sa + kBox, ma, &full[stage], ch * p.chunk_elems, 0, d.y);
+                  tma_load_3d(sb, mb, &full[stage], ch * p.chunk_elems, 0, d.z);
+                  if (RC == 2) tma_load_3d(sb + kBox, mb, &full[stage], ch * p.chunk_elems, 0, d.w);
+                  if (++stage == kStages) {
+                    stage = 0;
+                    phase ^= 1u;
+                  }
                 }
               }
             }
           }
         }
+        __syncwarp();
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (warp 1) ----------------
+    // The warp counts the item's stages in parallel; lane 0 issues them.
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
     unsigned long long nst = 0;
-    for (unsigned long long item = blockIdx.x; item < nitems && !s_abort; item += gridDim.x) {
+    for (unsigned long long item = blockIdx.x; item < nitems; item += gridDim.x) {
       const Item it = decode<LEAF>(p, item);
-      if (!mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort)) {
-        s_abort = 1;
-        flag_error(p.status, DEV_TIMEOUT);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t d = tmem + (uint32_t)acc * 128u;
-      uint32_t accum = 0;
-      for (uint32_t pe = 0; pe < it.len && !s_abort; pe++) {
+      int cnt = 0;
+      for (uint32_t pe = lane; pe < it.len; pe += 32) {
         const uint32_t m = p.mask[it.start + pe];
-        if (!m) continue;
-        for (int e = 0; e < 2; e++) {
-          uint32_t rm[2], cm[2];
-          const int np = passes<LEAF>(m, e, it.q, rm, cm);
-          for (int ps = 0; ps < np; ps++) {
-            for (int src = 0; src < p.nsrc; src++) {
-              for (int ch = 0; ch < p.chunks; ch++) {
-                if (!mbar_wait(&full[stage], phase, &s_abort)) {
-                  s_abort = 1;
-                  flag_error(p.status, DEV_TIMEOUT);
-                  break;
-                }
-                tc_fence_after();
-                const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
+        uint32_t rm[2], cm[2];
+        cnt += passes<LEAF>(m, 0, it.q, rm, cm) + passes<LEAF>(m, 1, it.q, rm, cm);
+      }
+      const int total = warp_sum(cnt) * p.nsrc * p.chunks;
+      if (lane == 0 && !s_abort) {
+        if (!mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort)) {
+          s_abort = 1;
+          flag_error(p.status, DEV_TIMEOUT);
+        } else {
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)acc * 128u;
+          uint32_t accum = 0;
+          for (int t = 0; t < total; t++) {
+            if (!mbar_wait(&full[stage], phase, &s_abort)) {
+              s_abort = 1;
+              flag_error(p.status, DEV_TIMEOUT);
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
 #pragma unroll
-                for (int kk = 0; kk < 4; kk++) {
-                  const uint64_t da = desc_sw128(sa + kk * 32), db = desc_sw128(sb + kk * 32);
-                  if (TF32) mma_tf32(d, da, db, p.idesc, accum);
-                  else mma_f16(d, da, db, p.idesc, accum);
-                  accum = 1;
-                }
-                mma_commit(&empty[stage]);
-                nst++;
-                if (++stage == kStages) {
-                  stage = 0;
-                  phase ^= 1u;
-                }
-              }
+            for (int kk = 0; kk < 4; kk++) {
+              const uint64_t da = desc_sw128(sa + kk * 32), db = desc_sw128(sb + kk * 32);
+              if (TF32) mma_tf32(d, da, db, p.idesc, accum);
+              else mma_f16(d, da, db, p.idesc, accum);
+              accum = 1;
+            }
+            mma_commit(&empty[stage]);
+            nst++;
+            if (++stage == kStages) {
+              stage = 0;
+              phase ^= 1u;
             }
           }
+          mma_commit(&accf[acc]);
         }
       }
-      mma_commit(&accf[acc]);
+      __syncwarp();
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
-    if (nst) atomicAdd(p.mma_stages, nst);
+    if (lane == 0 && nst) atomicAdd(p.mma_stages, nst);
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
     const int slice = warp & 3;            // TMEM lanes 32 * slice .. + 31
     const int row = 32 * slice + lane;     // accumulator row
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (unsigned long long item = blockIdx.x; item < nitems && !s_abort; item += gridDim.x) {
+    for (unsigned long long item = blockIdx.x; item < nitems; item += gridDim.x) {
       const Item it = decode<LEAF>(p, item);
       uint32_t touched = 0;   // quadrants (a * 2 + c) with a surviving product
-      for (uint32_t pe = 0; pe < it.len; pe++) {
+      for (uint32_t pe = lane; pe < it.len; pe += 32) {
         const uint32_t m = p.mask[it.start + pe];
 #pragma unroll
         for (int q = 0; q < 4; q++)
           if ((m >> (2 * q)) & 3u) touched |= 1u << q;
       }
-      if (!mbar_wait(&accf[acc], acc_phase, &s_abort)) {
+      touched = __reduce_or_sync(0xffffffffu, touched);
+      bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
+      if (!ok) {
         s_abort = 1;
         flag_error(p.status, DEV_TIMEOUT);
-        break;
       }
+      ok = __all_sync(0xffffffffu, ok);   // warp-uniform: the TMEM loads are warp-collective
+      if (!ok) touched = 0;
       tc_fence_after();
       const int a = LEAF == 64 ? row / 64 : (it.q >> 1);
       const int r = LEAF == 64 ? row % 64 : row;
       const int i = (int)(2 * it.I) + a;
-      double ss[2] = {0.0, 0.0};
-      bool wrote[2] = {false, false};
+      // squared norms in double-float: f^2 = pp + e exactly, TwoSum accumulation
+      float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
 #pragma unroll
       for (int cc = 0; cc < RC; cc++) {
         const int c = LEAF == 64 ? cc : (it.q & 1);
         const int q = a * 2 + c;
         const int j = (int)(2 * it.J) + c;
         if (!((touched >> q) & 1u) || i >= p.nb || j >= p.nb) continue;   // warp-uniform
-        wrote[cc] = true;
         float *dst = p.C + (((int64_t)i * p.nb + j) * LEAF + r) * LEAF;
 #pragma unroll
         for (int h = 0; h < LEAF / 32; h++) {
@@ -293,10 +334,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             float4 f = make_float4(__uint_as_float(v[x]), __uint_as_float(v[x + 1]),
                                    __uint_as_float(v[x + 2]), __uint_as_float(v[x + 3]));
             *reinterpret_cast<float4 *>(dst + h * 32 + x) = f;
-            ss[cc] = fma((double)f.x, (double)f.x, ss[cc]);
-            ss[cc] = fma((double)f.y, (double)f.y, ss[cc]);
-            ss[cc] = fma((double)f.z, (double)f.z, ss[cc]);
-            ss[cc] = fma((double)f.w, (double)f.w, ss[cc]);
+#pragma unroll
+            for (int z = 0; z < 4; z++) {
+              const float fv = __uint_as_float(v[x + z]);
+              const float pp = fv * fv;
+              const float e = fmaf(fv, fv, -pp);
+              const float t = sh[cc] + pp;
+              const float bb = t - sh[cc];
+              sl[cc] += ((sh[cc] - (t - bb)) + (pp - bb)) + e;
+              sh[cc] = t;
+            }
           }
         }
       }
@@ -305,8 +352,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       // squared Frobenius norms of the written blocks: rows -> warp -> fixed pair order
 #pragma unroll
       for (int cc = 0; cc < RC; cc++) {
-        const double w = warp_sum(ss[cc]);
-        if (lane == 0) s_norm[slice][cc] = w;
+        float H = sh[cc], L = sl[cc];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, H, off), l2 = __shfl_xor_sync(0xffffffffu, L, off);
+          df_add(H, L, h2, l2);
+        }
+        if (lane == 0) s_norm[slice][cc] = (double)H + (double)L;
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (warp == 2 && lane < 4) {
@@ -327,7 +379,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
-      (void)wrote;
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
