@@ -408,10 +408,6 @@ spamm_status spamm_multiply(spamm_ctx ctx, spamm_tree A, spamm_tree B, double ta
   Ct->tau = tau;
   Ct->stats_valid = false;
   cudaStream_t s = ctx->stream;
-  CK(cudaMemsetAsync(Ct->counts, 0, sizeof(DevCounts), s), "multiply: memset");
-  CK(cudaMemsetAsync(Ct->look, 0, (size_t)Ct->cap_look * 8, s), "multiply: memset");
-  CK(cudaMemsetAsync(Ct->norm2 + level_offset(Ct->kmax), 0, (size_t)Ct->NB * Ct->NB * 8, s), "multiply: memset");
-  CK(cudaMemsetAsync(Ct->nz, 0, (size_t)Ct->NB * Ct->NB, s), "multiply: memset");
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[0], s), "event");
   int launches = 0;
   CK(launch_cull(A, B, Ct, tau, ctx->dev_status, ctx->sm_count, s, &launches), "multiply: cull launch");
@@ -425,8 +421,6 @@ spamm_status spamm_multiply(spamm_ctx ctx, spamm_tree A, spamm_tree B, double ta
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[2], s), "event");
   CK(launch_pyramid(Ct, s), "multiply: pyramid launch");
   launches += pyramid_launches(Ct->kmax);
-  CK(launch_finish_stats(Ct, s), "multiply: stats launch");
-  launches++;
   bool want[CK_COUNT];
   wanted_copies(cflags & 0x01FF, want);
   bool any_copy = false;
@@ -445,6 +439,9 @@ spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out) {
   if (!out) return fail(ctx, SPAMM_EINVAL, "stats: null output");
   if (!C->is_product) return fail(ctx, SPAMM_EINVAL, "stats: not a product tree");
   if (!C->stats_valid) {
+    // the culled-bound partials of the last product are summed here, on demand
+    CK(launch_finish_stats(C, ctx->stream), "stats: reduce launch");
+    ctx->launches++;
     DevCounts h;
     CK(cudaMemcpyAsync(&h, C->counts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "stats: copy");
     spamm_status st = check_device_status(ctx);

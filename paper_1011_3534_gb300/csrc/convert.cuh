@@ -146,3 +146,50 @@ __device__ __forceinline__ uint32_t bf16_lo_bits_f32(float f, const Rounded &hi)
   }
   return round_core(sign, M, x, 63 - __clzll((long long)M), 8, -126).bits;
 }
+
+// ---- fast paths on the high and low 32-bit words of an FP64 value ----
+// Round to nearest even at bit k = 45 (BF16) or k = 42 (TF32, FP16) of the 64-bit
+// pattern: adding (2^(k-1) - 1) + (bit k) rounds the magnitude. Only the high word is
+// kept; the low word's all-ones part plus bit k carries into it exactly when the low
+// word is nonzero or bit k is set. Valid when the result is a
+// normal number of the target format; other inputs take round_f64bits.
+
+// BF16 bits, E (FP64 exponent field) in [897, 1150].
+__device__ __forceinline__ uint32_t bf16_fast(uint32_t h, uint32_t l) {
+  const uint32_t h2 = h + 0xFFFu + ((((h >> 13) & 1u) | l) != 0u ? 1u : 0u);
+  return ((h2 >> 16) & 0x8000u) | ((((h2 >> 20) & 0x7FFu) - 896u) << 7) | ((h2 >> 13) & 0x7Fu);
+}
+
+// TF32 (as FP32 bits), E in [897, 1150].
+__device__ __forceinline__ uint32_t tf32_fast(uint32_t h, uint32_t l) {
+  const uint32_t h2 = h + 0x1FFu + ((((h >> 10) & 1u) | l) != 0u ? 1u : 0u);
+  return (h2 & 0x80000000u) | ((((h2 >> 20) & 0x7FFu) - 896u) << 23) | (((h2 >> 10) & 0x3FFu) << 13);
+}
+
+// FP16 bits for FP64 exponent fields E in [985, 1038]: normal results (E >= 1009) by
+// the bias trick, overflow to infinity, subnormal results (quantum 2^-24) from the
+// high significand word with the low word as sticky bit.
+__device__ __forceinline__ uint32_t fp16_fast(uint32_t h, uint32_t l, int E) {
+  const uint32_t sign = (h >> 16) & 0x8000u;
+  if (E >= 1009) {
+    const uint32_t h2 = h + 0x1FFu + ((((h >> 10) & 1u) | l) != 0u ? 1u : 0u);
+    const uint32_t ex = ((h2 >> 20) & 0x7FFu) - 1008u;
+    if (ex >= 31u) return sign | 0x7C00u;
+    return sign | (ex << 10) | ((h2 >> 10) & 0x3FFu);
+  }
+  const uint32_t hs = (h & 0xFFFFFu) | 0x100000u;   // significand bits 52..32
+  const int s2 = 1019 - E;                          // 11 .. 34 here
+  if (s2 >= 22) return sign;                        // below half the least subnormal
+  const uint32_t r = hs >> s2, rem = hs & ((1u << s2) - 1u), half = 1u << (s2 - 1);
+  const bool up = rem > half || (rem == half && (l != 0u || (r & 1u)));
+  return sign | (r + (up ? 1u : 0u));
+}
+
+// FP32 round to nearest even from the FP64 pattern, E in [897, 1150] (normal FP32
+// results): the rounding position (bit 29) lies in the low word, so the bias is added
+// to the full 64-bit pattern.
+__device__ __forceinline__ uint32_t f32_fast(uint32_t h, uint32_t l) {
+  const uint64_t u = (((uint64_t)h << 32) | l) + 0x0FFFFFFFull + ((l >> 29) & 1u);
+  const uint32_t uh = (uint32_t)(u >> 32);
+  return (uh & 0x80000000u) | ((((uh >> 20) & 0x7FFu) - 896u) << 23) | ((uint32_t)(u >> 29) & 0x7FFFFFu);
+}

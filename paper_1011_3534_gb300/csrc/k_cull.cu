@@ -245,10 +245,24 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
   }
 }
 
-// Seeds the virtual tier -1: one group (0, 0) holding K = 0, whose only in-range
-// child is the root triple (0, 0, 0).
-__global__ void k_cull_seed(uint32_t *gij, uint32_t *gstart, uint32_t *glen, uint16_t *K,
-                            DevCounts *cnt) {
+// Prologue of a product: zeroes the counters, the look-back words and the product's
+// leaf norms / presence bytes, and seeds the virtual tier -1: one group (0, 0) holding
+// K = 0, whose only in-range child is the root triple (0, 0, 0).
+__global__ void __launch_bounds__(256) k_cull_prologue(uint32_t *gij, uint32_t *gstart, uint32_t *glen,
+                                                       uint16_t *K, DevCounts *cnt, uint64_t *look,
+                                                       int64_t nlook, double *leaf_norm2, uint8_t *nz,
+                                                       int64_t nleaves) {
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = t0; t < nlook; t += st) look[t] = 0ull;
+  if (leaf_norm2)
+    for (int64_t t = t0; t < nleaves; t += st) leaf_norm2[t] = 0.0;
+  if (nz)
+    for (int64_t t = t0; t < nleaves; t += st) nz[t] = 0;
+  if (blockIdx.x != 0) return;
+  // the counters are zeroed and seeded by block 0 alone, so no other block can race
+  uint32_t *cw = reinterpret_cast<uint32_t *>(cnt);
+  for (int t = threadIdx.x; t < (int)(sizeof(DevCounts) / 4); t += blockDim.x) cw[t] = 0u;
+  __syncthreads();
   if (threadIdx.x == 0) {
     gij[0] = 0;
     gstart[0] = 0;
@@ -288,7 +302,11 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau,
   const int kmax = A->kmax;
   DevCounts *cnt = C->counts;
   const TierList &root = C->tiers[0];
-  k_cull_seed<<<1, 32, 0, s>>>(root.gij, root.gstart, root.glen, root.K, cnt);
+  const int64_t nleaves = (int64_t)C->NB * C->NB;
+  const int64_t work = std::max<int64_t>(nleaves, C->cap_look);
+  const unsigned pg = (unsigned)std::min<int64_t>((work + 255) / 256, 1024);
+  k_cull_prologue<<<pg, 256, 0, s>>>(root.gij, root.gstart, root.glen, root.K, cnt, C->look, C->cap_look,
+                                     C->norm2 ? C->norm2 + level_offset(C->kmax) : nullptr, C->nz, nleaves);
   (*launches)++;
   int64_t look_off = 0, bound_off = 0;
   for (int l = 0; l <= kmax; l++) {

@@ -15,10 +15,10 @@
 //
 // Pipeline (one CTA, 192 threads): warp 0 issues TMA loads into a ring of 6 stages of
 // 32 KB (A 128 x 128 B, B 128 x 128 B, 128-byte swizzle, one 128-byte K chunk per stage);
-// warp 1 issues tcgen05.mma (4 K-steps of 32 bytes per stage) into one of two TMEM
+// warp 1 issues tcgen05.mma (4 K-steps of 32 bytes per stage) into one of four TMEM
 // accumulators and commits to the stage's empty barrier; warps 2-5 drain a finished
 // accumulator with tcgen05.ld, store C (FP32 tiles) and its squared Frobenius norms
-// (FP64, fixed-order sums) while the next item accumulates in the other buffer.
+// (double-float, fixed-order sums) while later items accumulate in the other buffers.
 // Every wait is bounded; a wait that runs out sets an error bit and the CTA unwinds.
 #include <cudaTypedefs.h>
 
@@ -31,7 +31,8 @@ constexpr int kStages = 6;
 constexpr int kStageA = 16384;
 constexpr int kStageBytes = 32768;
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTmemCols = 512;   // four 128-column FP32 accumulators
+constexpr int kAcc = 4;
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024;
 
 struct TcArgs {
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo,
               TcArgs p) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[2], acce[2];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[kAcc], acce[kAcc];
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   __shared__ double s_norm[4][2];
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int a = 0; a < 2; a++) {
+    for (int a = 0; a < kAcc; a++) {
       mbar_init(&accf[a], 1);
       mbar_init(&acce[a], 128);
     }
@@ -284,8 +285,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       __syncwarp();
-      acc ^= 1;
-      if (acc == 0) acc_phase ^= 1u;
+      if (++acc == kAcc) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
     }
     if (lane == 0 && nst) atomicAdd(p.mma_stages, nst);
   } else if (warp >= 2) {
@@ -379,8 +382,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
-      acc ^= 1;
-      if (acc == 0) acc_phase ^= 1u;
+      if (++acc == kAcc) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
     }
   }
   tc_fence_before();

@@ -21,26 +21,27 @@ struct BuildArgs {
   double *leaf_norm2;      // tier kmax of norm2
   uint8_t *nz;
   double *f64;             // optional copies (nullptr = not written)
+  float *f32;              // FP32 master (purification iterates)
   float *tf32, *tf32T;
   uint16_t *bf16, *bf16T, *fp16, *fp16T, *lo, *loT;
 };
 
-// Leaf-block kernel (K1). Each leaf is split into groups of 8 consecutive elements of
-// one row; a leaf is handled by TPL threads (several leaves per CTA for small leaves),
-// each thread loading its groups as 64-byte runs (four 16-byte loads, coalesced along
-// rows). The FP64 pipe is kept idle: the squared Frobenius norm is accumulated from an
-// exact FP32 hi/lo split of each element, scaled by the leaf's largest exponent, with
-// error-free (TwoSum) accumulation and a double-float reduction (relative error ~2^-46, far
-// inside the 1e-12 near-tau band), and the leaf copies are rounded in integer
-// arithmetic from the FP64 bit pattern.
+// Leaf-block kernel (K1). A leaf is read as pairs of consecutive elements of a row
+// (16-byte loads: a warp reads 512 contiguous bytes) by TPL threads, several leaves per
+// CTA for small leaves; each thread streams its pairs in rounds of four. The FP64 pipe
+// is kept idle: each round's squared norm is accumulated from an exact FP32 hi/lo split
+// of its elements scaled by the round's largest exponent, with error-free (TwoSum)
+// accumulation, rounds and threads are merged in double-float after rescaling to a
+// common exponent (relative error ~2^-46, far inside the 1e-12 near-tau band), and the
+// leaf copies are rounded in integer arithmetic on the FP64 bit pattern.
 template <int B>
 struct BuildCfg {
-  static constexpr int T = B == 128 ? 1024 : 256;   // threads per CTA
-  static constexpr int GROUPS = B * B / 8;           // 8-element groups per leaf
-  static constexpr int TPL = GROUPS < T ? GROUPS : T;
-  static constexpr int LPC = T / TPL;                // leaves per CTA
-  static constexpr int ROUNDS = GROUPS / TPL;
-  static constexpr int EPT = ROUNDS * 8;             // elements per thread
+  static constexpr int T = 256;                    // threads per CTA
+  static constexpr int PAIRS = B * B / 2;          // element pairs per leaf
+  static constexpr int TPL = PAIRS / 4 < T ? PAIRS / 4 : T;   // threads per leaf
+  static constexpr int LPC = T / TPL;              // leaves per CTA
+  static constexpr int RPT = PAIRS / TPL;          // pairs per thread
+  static constexpr int ROUNDS = RPT / 4;
 };
 
 __device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
@@ -52,112 +53,48 @@ __device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
   l = err - (h - s);
 }
 
+// 2^(2d) as a float for d <= 0 (0 when it would not be a normal float)
+__device__ __forceinline__ float pow4(int d) {
+  const int ex = 2 * d + 127;
+  return ex >= 1 ? __uint_as_float((uint32_t)ex << 23) : 0.f;
+}
+
+// Double-float accumulator (H + L) * 2^(2 (E - 1023)); E = 0 means empty.
+struct NormAcc {
+  float H = 0.f, L = 0.f;
+  int E = 0;
+  __device__ __forceinline__ void merge(float h, float l, int e) {
+    if (e == 0) return;
+    if (E == 0) { H = h; L = l; E = e; return; }
+    if (e > E) {
+      const float f = pow4(E - e);
+      H *= f;
+      L *= f;
+      E = e;
+    } else {
+      const float f = pow4(e - E);
+      h *= f;
+      l *= f;
+    }
+    df_add(H, L, h, l);
+  }
+};
+
 template <int B, bool VEC>
-__global__ void __launch_bounds__(BuildCfg<B>::T) k_tree_build(BuildArgs p) {
+__global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p) {
   using Cfg = BuildCfg<B>;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_emax[Cfg::T / 32];
-  __shared__ float s_h[Cfg::T / 32], s_l[Cfg::T / 32];
+  __shared__ float s_h[8], s_l[8];
+  __shared__ int s_e[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = threadIdx.x / Cfg::TPL, tl = threadIdx.x % Cfg::TPL;
   const int64_t leaf = (int64_t)blockIdx.x * Cfg::LPC + li;
   const bool inrange = leaf < (int64_t)p.NB * p.NB;
   const int32_t r = inrange ? (int32_t)(leaf / p.NB) : 0, c = inrange ? (int32_t)(leaf % p.NB) : 0;
   const bool stored = inrange && r < p.nb && c < p.nb;
-
-  uint64_t v[Cfg::EPT];
-  int emax = 0;
-#pragma unroll
-  for (int j = 0; j < Cfg::ROUNDS; j++) {
-    const int g = tl + Cfg::TPL * j;
-    const int row = (8 * g) / B, col0 = (8 * g) % B;
-    const int64_t gr = (int64_t)r * B + row, gc = (int64_t)c * B + col0;
-    if (stored && gr < p.n) {
-      const double *src = p.A + gr * p.n + gc;
-      if (VEC && gc + 8 <= p.n) {
-#pragma unroll
-        for (int h = 0; h < 4; h++) {
-          const double2 d = __ldcs(reinterpret_cast<const double2 *>(src) + h);
-          v[8 * j + 2 * h] = (uint64_t)__double_as_longlong(d.x);
-          v[8 * j + 2 * h + 1] = (uint64_t)__double_as_longlong(d.y);
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; e++)
-          v[8 * j + e] = gc + e < p.n ? (uint64_t)__double_as_longlong(__ldcs(src + e)) : 0ull;
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < 8; e++) v[8 * j + e] = 0ull;
-    }
-#pragma unroll
-    for (int e = 0; e < 8; e++) {
-      const int E = (int)((v[8 * j + e] >> 52) & 0x7FF);
-      emax = E > emax ? E : emax;
-    }
-  }
-  // largest exponent field of the leaf (its threads span whole warps)
-  emax = __reduce_max_sync(0xffffffffu, emax);
-  if (lane == 0) s_emax[warp] = emax;
-  __syncthreads();
-  constexpr int WPL = Cfg::TPL / 32;   // warps per leaf
-  int Emax = 0;
-#pragma unroll
-  for (int w = 0; w < WPL; w++) Emax = max(Emax, s_emax[li * WPL + w]);
-
-  // squared norm of the leaf scaled by 2^(-2 (Emax - 1023))
-  float S = 0.f, s2 = 0.f;
-  if (Emax > 0 && Emax < 0x7FF) {
-#pragma unroll
-    for (int e = 0; e < Cfg::EPT; e++) {
-      const uint64_t bits = v[e];
-      const int E = (int)((bits >> 52) & 0x7FF);
-      const int es = E - Emax;
-      if (E == 0 || es < -100) continue;   // below 2^-200 of the largest square: negligible
-      const float hi = __uint_as_float(((uint32_t)(es + 127) << 23) | (uint32_t)((bits >> 29) & 0x7FFFFFu));
-      const float lo = es >= -74 ? __uint2float_rn((uint32_t)(bits & 0x1FFFFFFFu)) *
-                                       __uint_as_float((uint32_t)(es - 52 + 127) << 23)
-                                 : 0.f;
-      const float pp = hi * hi;
-      float cc = fmaf(hi, hi, -pp);
-      cc = fmaf(2.f * hi, lo, cc);
-      cc = fmaf(lo, lo, cc);
-      // TwoSum (Knuth): S + pp = t + err exactly, whatever their magnitudes
-      const float t = S + pp;
-      const float bb = t - S;
-      const float err = (S - (t - bb)) + (pp - bb);
-      S = t;
-      s2 += err + cc;
-    }
-  }
-  float H = S, L = s2;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, H, off), l2 = __shfl_xor_sync(0xffffffffu, L, off);
-    df_add(H, L, h2, l2);
-  }
-  if (lane == 0) {
-    s_h[warp] = H;
-    s_l[warp] = L;
-  }
-  __syncthreads();
-  if (tl == 0 && inrange) {
-    if (stored) {
-      double acc = 0.0;
-      for (int w = 0; w < WPL; w++) acc += (double)s_h[li * WPL + w] + (double)s_l[li * WPL + w];
-      p.leaf_norm2[leaf] = (Emax > 0 && Emax < 0x7FF) ? ldexp(acc, 2 * (Emax - 1023))
-                                                       : (Emax == 0x7FF ? __longlong_as_double(0x7FF0000000000000ll) : 0.0);
-      p.nz[leaf] = 1;
-    } else {
-      p.leaf_norm2[leaf] = 0.0;
-      p.nz[leaf] = 0;
-    }
-  }
-  if (!stored && !(p.tf32T || p.bf16T || p.fp16T || p.loT)) return;
-
-  // leaf copies
   const int64_t tile = ((int64_t)r * p.nb + c) * (int64_t)B * B;
   const size_t bb = (size_t)B * B;
+  const bool any_t = p.tf32T || p.bf16T || p.fp16T || p.loT;
   float *s_tf32T = nullptr;
   uint16_t *s_bf16T = nullptr, *s_fp16T = nullptr, *s_loT = nullptr;
   {
@@ -167,80 +104,159 @@ __global__ void __launch_bounds__(BuildCfg<B>::T) k_tree_build(BuildArgs p) {
     if (p.fp16T) { s_fp16T = (uint16_t *)q + li * bb; q += Cfg::LPC * bb * 2; }
     if (p.loT) { s_loT = (uint16_t *)q + li * bb; q += Cfg::LPC * bb * 2; }
   }
+  NormAcc acc;
   if (stored) {
+    for (int rd = 0; rd < Cfg::ROUNDS; rd++) {
+      uint32_t hw[8], lw[8];   // high and low words of the round's 8 elements
+      int rows[4], cols[4];
 #pragma unroll
-    for (int j = 0; j < Cfg::ROUNDS; j++) {
-      const int g = tl + Cfg::TPL * j;
-      const int row = (8 * g) / B, col0 = (8 * g) % B;
-      const int64_t o = tile + (int64_t)row * B + col0;
-      if (p.f64) {
-#pragma unroll
-        for (int h = 0; h < 4; h++)
-          reinterpret_cast<double2 *>(p.f64 + o)[h] =
-              make_double2(__longlong_as_double((long long)v[8 * j + 2 * h]),
-                           __longlong_as_double((long long)v[8 * j + 2 * h + 1]));
+      for (int u = 0; u < 4; u++) {
+        const int q = tl + Cfg::TPL * (4 * rd + u);
+        rows[u] = q / (B / 2);
+        cols[u] = 2 * (q % (B / 2));
+        const int64_t gr = (int64_t)r * B + rows[u], gc = (int64_t)c * B + cols[u];
+        double2 d = make_double2(0.0, 0.0);
+        if (gr < p.n) {
+          const double *src = p.A + gr * p.n + gc;
+          if (VEC && gc + 1 < p.n) {
+            d = __ldcs(reinterpret_cast<const double2 *>(src));
+          } else {
+            if (gc < p.n) d.x = __ldcs(src);
+            if (gc + 1 < p.n) d.y = __ldcs(src + 1);
+          }
+        }
+        hw[2 * u] = (uint32_t)__double2hiint(d.x);
+        lw[2 * u] = (uint32_t)__double2loint(d.x);
+        hw[2 * u + 1] = (uint32_t)__double2hiint(d.y);
+        lw[2 * u + 1] = (uint32_t)__double2loint(d.y);
       }
-      if (p.bf16 || s_bf16T || p.lo || s_loT) {
-        uint32_t hb[8], lb[8];
+      // squared norm of the round, scaled by its largest exponent field Er
+      int Er = 0;
+#pragma unroll
+      for (int e = 0; e < 8; e++) Er = max(Er, (int)((hw[e] >> 20) & 0x7FFu));
+      if (Er > 0 && Er < 0x7FF) {
+        float S = 0.f, s2 = 0.f;
 #pragma unroll
         for (int e = 0; e < 8; e++) {
-          const Rounded h = round_f64bits(v[8 * j + e], 8, -126);
-          hb[e] = h.bits;
-          lb[e] = (p.lo || s_loT) ? bf16_lo_bits(v[8 * j + e], h) : 0u;
+          const int E = (int)((hw[e] >> 20) & 0x7FFu);
+          const int es = E - Er;
+          if (E == 0 || es < -60) continue;   // below 2^-120 of the round's largest square
+          // hi: sign-free top 24 significand bits; lo: the next 29 bits
+          const float hi = __uint_as_float(((uint32_t)(es + 127) << 23) | (((hw[e] & 0xFFFFFu) << 3) | (lw[e] >> 29)));
+          const float lo = __uint2float_rn(lw[e] & 0x1FFFFFFFu) * __uint_as_float((uint32_t)(es - 52 + 127) << 23);
+          const float pp = hi * hi;
+          float cc = fmaf(hi, hi, -pp);
+          cc = fmaf(2.f * hi, lo, cc);
+          const float t = S + pp;
+          const float tb = t - S;
+          s2 += ((S - (t - tb)) + (pp - tb)) + cc;
+          S = t;
         }
-        if (p.bf16) {
-          uint4 w;
-          w.x = (hb[0] >> 16) | (hb[1] & 0xFFFF0000u);
-          w.y = (hb[2] >> 16) | (hb[3] & 0xFFFF0000u);
-          w.z = (hb[4] >> 16) | (hb[5] & 0xFFFF0000u);
-          w.w = (hb[6] >> 16) | (hb[7] & 0xFFFF0000u);
-          *reinterpret_cast<uint4 *>(p.bf16 + o) = w;
-        }
-        if (p.lo) {
-          uint4 w;
-          w.x = (lb[0] >> 16) | (lb[1] & 0xFFFF0000u);
-          w.y = (lb[2] >> 16) | (lb[3] & 0xFFFF0000u);
-          w.z = (lb[4] >> 16) | (lb[5] & 0xFFFF0000u);
-          w.w = (lb[6] >> 16) | (lb[7] & 0xFFFF0000u);
-          *reinterpret_cast<uint4 *>(p.lo + o) = w;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; e++) {
-          if (s_bf16T) s_bf16T[(col0 + e) * B + row] = bf16_from_f32bits(hb[e]);
-          if (s_loT) s_loT[(col0 + e) * B + row] = bf16_from_f32bits(lb[e]);
-        }
+        acc.merge(S, s2, Er);
+      } else if (Er == 0x7FF) {
+        acc.merge(__uint_as_float(0x7F800000u), 0.f, 0x7FE);
       }
-      if (p.tf32 || s_tf32T) {
-        uint32_t tb[8];
+      // leaf copies of the round
 #pragma unroll
-        for (int e = 0; e < 8; e++) tb[e] = round_f64bits(v[8 * j + e], 11, -126).bits;
-        if (p.tf32) {
-          reinterpret_cast<uint4 *>(p.tf32 + o)[0] = make_uint4(tb[0], tb[1], tb[2], tb[3]);
-          reinterpret_cast<uint4 *>(p.tf32 + o)[1] = make_uint4(tb[4], tb[5], tb[6], tb[7]);
+      for (int u = 0; u < 4; u++) {
+        const int64_t o = tile + (int64_t)rows[u] * B + cols[u];
+        const uint32_t h0 = hw[2 * u], l0 = lw[2 * u], h1 = hw[2 * u + 1], l1 = lw[2 * u + 1];
+        const int E0 = (int)((h0 >> 20) & 0x7FFu), E1 = (int)((h1 >> 20) & 0x7FFu);
+        if (p.f64)
+          *reinterpret_cast<double2 *>(p.f64 + o) =
+              make_double2(__hiloint2double((int)h0, (int)l0), __hiloint2double((int)h1, (int)l1));
+        if (p.f32) {
+          const uint32_t a0 = (E0 >= 897 && E0 <= 1150) ? f32_fast(h0, l0)
+                                                       : round_f64bits(((uint64_t)h0 << 32) | l0, 24, -126).bits;
+          const uint32_t a1 = (E1 >= 897 && E1 <= 1150) ? f32_fast(h1, l1)
+                                                       : round_f64bits(((uint64_t)h1 << 32) | l1, 24, -126).bits;
+          *reinterpret_cast<uint2 *>(p.f32 + o) = make_uint2(a0, a1);
         }
-        if (s_tf32T)
-#pragma unroll
-          for (int e = 0; e < 8; e++) s_tf32T[(col0 + e) * B + row] = __uint_as_float(tb[e]);
-      }
-      if (p.fp16 || s_fp16T) {
-        uint16_t hh[8];
-#pragma unroll
-        for (int e = 0; e < 8; e++) hh[e] = fp16_from_f32bits(round_f64bits(v[8 * j + e], 11, -14).bits);
-        if (p.fp16) {
-          uint4 w;
-          w.x = hh[0] | ((uint32_t)hh[1] << 16);
-          w.y = hh[2] | ((uint32_t)hh[3] << 16);
-          w.z = hh[4] | ((uint32_t)hh[5] << 16);
-          w.w = hh[6] | ((uint32_t)hh[7] << 16);
-          *reinterpret_cast<uint4 *>(p.fp16 + o) = w;
+        if (p.bf16 || s_bf16T || p.lo || s_loT) {
+          uint32_t b0, b1;
+          Rounded r0, r1;
+          const bool need_r = p.lo || s_loT;
+          if (E0 >= 897 && E0 <= 1150 && !need_r) b0 = bf16_fast(h0, l0);
+          else { r0 = round_f64bits(((uint64_t)h0 << 32) | l0, 8, -126); b0 = r0.bits >> 16; }
+          if (E1 >= 897 && E1 <= 1150 && !need_r) b1 = bf16_fast(h1, l1);
+          else { r1 = round_f64bits(((uint64_t)h1 << 32) | l1, 8, -126); b1 = r1.bits >> 16; }
+          if (p.bf16) *reinterpret_cast<uint32_t *>(p.bf16 + o) = b0 | (b1 << 16);
+          if (s_bf16T) {
+            s_bf16T[cols[u] * B + rows[u]] = (uint16_t)b0;
+            s_bf16T[(cols[u] + 1) * B + rows[u]] = (uint16_t)b1;
+          }
+          if (need_r) {
+            const uint32_t q0 = bf16_lo_bits(((uint64_t)h0 << 32) | l0, r0) >> 16;
+            const uint32_t q1 = bf16_lo_bits(((uint64_t)h1 << 32) | l1, r1) >> 16;
+            if (p.lo) *reinterpret_cast<uint32_t *>(p.lo + o) = q0 | (q1 << 16);
+            if (s_loT) {
+              s_loT[cols[u] * B + rows[u]] = (uint16_t)q0;
+              s_loT[(cols[u] + 1) * B + rows[u]] = (uint16_t)q1;
+            }
+          }
         }
-        if (s_fp16T)
-#pragma unroll
-          for (int e = 0; e < 8; e++) s_fp16T[(col0 + e) * B + row] = hh[e];
+        if (p.tf32 || s_tf32T) {
+          const uint32_t t0 = (E0 >= 897 && E0 <= 1150) ? tf32_fast(h0, l0)
+                                                       : round_f64bits(((uint64_t)h0 << 32) | l0, 11, -126).bits;
+          const uint32_t t1 = (E1 >= 897 && E1 <= 1150) ? tf32_fast(h1, l1)
+                                                       : round_f64bits(((uint64_t)h1 << 32) | l1, 11, -126).bits;
+          if (p.tf32) *reinterpret_cast<uint2 *>(p.tf32 + o) = make_uint2(t0, t1);
+          if (s_tf32T) {
+            s_tf32T[cols[u] * B + rows[u]] = __uint_as_float(t0);
+            s_tf32T[(cols[u] + 1) * B + rows[u]] = __uint_as_float(t1);
+          }
+        }
+        if (p.fp16 || s_fp16T) {
+          const uint32_t f0 = (E0 >= 985 && E0 <= 1038) ? fp16_fast(h0, l0, E0)
+              : (uint32_t)fp16_from_f32bits(round_f64bits(((uint64_t)h0 << 32) | l0, 11, -14).bits);
+          const uint32_t f1 = (E1 >= 985 && E1 <= 1038) ? fp16_fast(h1, l1, E1)
+              : (uint32_t)fp16_from_f32bits(round_f64bits(((uint64_t)h1 << 32) | l1, 11, -14).bits);
+          if (p.fp16) *reinterpret_cast<uint32_t *>(p.fp16 + o) = f0 | (f1 << 16);
+          if (s_fp16T) {
+            s_fp16T[cols[u] * B + rows[u]] = (uint16_t)f0;
+            s_fp16T[(cols[u] + 1) * B + rows[u]] = (uint16_t)f1;
+          }
+        }
       }
     }
   }
-  if (!(p.tf32T || p.bf16T || p.fp16T || p.loT)) return;
+  // leaf norm: threads -> warp (rescale to the warp's largest exponent) -> leaf
+  const int Ew = __reduce_max_sync(0xffffffffu, acc.E);
+  float H = 0.f, L = 0.f;
+  if (acc.E) {
+    const float f = pow4(acc.E - Ew);
+    H = acc.H * f;
+    L = acc.L * f;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, H, off), l2 = __shfl_xor_sync(0xffffffffu, L, off);
+    df_add(H, L, h2, l2);
+  }
+  if (lane == 0) {
+    s_h[warp] = H;
+    s_l[warp] = L;
+    s_e[warp] = Ew;
+  }
+  __syncthreads();
+  constexpr int WPL = Cfg::TPL >= 32 ? Cfg::TPL / 32 : 1;
+  if (tl == 0 && inrange) {
+    if (stored) {
+      int Em = 0;
+      for (int w = 0; w < WPL; w++) Em = max(Em, s_e[li * WPL + w]);
+      double total = 0.0;
+      for (int w = 0; w < WPL; w++) {
+        const int ew = s_e[li * WPL + w];
+        if (ew) total += ldexp((double)s_h[li * WPL + w] + (double)s_l[li * WPL + w], 2 * (ew - Em));
+      }
+      p.leaf_norm2[leaf] = Em ? ldexp(total, 2 * (Em - 1023)) : 0.0;
+      p.nz[leaf] = 1;
+    } else {
+      p.leaf_norm2[leaf] = 0.0;
+      p.nz[leaf] = 0;
+    }
+  }
+  if (!any_t) return;
   __syncthreads();
   if (!stored) return;
   // transposed copies: shared -> global, 16-byte vectors
@@ -364,6 +380,7 @@ cudaError_t launch_tree_build(spamm_tree t, const double *A, cudaStream_t s) {
   p.leaf_norm2 = t->norm2 + level_offset(t->kmax);
   p.nz = t->nz;
   p.f64 = (double *)t->copy[CK_F64];
+  p.f32 = (float *)t->copy[CK_F32];
   p.tf32 = (float *)t->copy[CK_TF32];
   p.tf32T = (float *)t->copy[CK_TF32_T];
   p.bf16 = (uint16_t *)t->copy[CK_BF16];

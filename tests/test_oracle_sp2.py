@@ -1,0 +1,65 @@
+"""Pins of the SP2 purification oracles (CPU)."""
+import numpy as np
+import pytest
+
+from oracle import sp2 as O
+from paper_1011_3534_gb300 import workloads as W
+
+
+def tb_dense(side):
+    ip, ix, d = W.tight_binding(side)
+    n = side ** 3
+    return W.csr_to_dense(n, ip, ix, d), (ip, ix, d), n
+
+
+def test_gershgorin_matches_dense_bound():
+    H, (ip, ix, d), n = tb_dense(4)
+    lo, hi = O.gershgorin(ip, ix, d, n)
+    diag = np.diag(H)
+    rad = np.abs(H).sum(1) - np.abs(diag)
+    assert lo == pytest.approx((diag - rad).min()) and hi == pytest.approx((diag + rad).max())
+    ev = np.linalg.eigvalsh(H)
+    assert lo <= ev.min() and ev.max() <= hi
+
+
+@pytest.mark.parametrize("side", [4, 6, 8])
+def test_dense_equals_spectral(side):
+    H, (ip, ix, d), n = tb_dense(side)
+    lo, hi = O.gershgorin(ip, ix, d, n)
+    dn = O.sp2_dense(H, n / 2, 30, lo, hi)
+    sp = O.sp2_spectral(np.linalg.eigvalsh(H), n / 2, 30, lo, hi)
+    assert dn["branches"] == sp["branches"]
+    np.testing.assert_allclose(dn["traces"], sp["traces"], rtol=1e-9)
+    assert abs(dn["energy"] - sp["energy"]) <= 1e-9 * abs(sp["energy"])
+
+
+def test_gapped_spectrum_converges_to_projector():
+    # a diagonal H with a gap: SP2 drives the occupied eigenvalues to 1 and the rest to
+    # 0, so Tr X = N_occ and the energy is the sum of the N_occ lowest levels
+    eps = np.concatenate([np.linspace(-2, -1, 50), np.linspace(1, 2, 50)])
+    H = np.diag(eps)
+    r = O.sp2_dense(H, 50, 40, -2.0, 2.0)
+    assert abs(r["traces"][-1] - 50) < 1e-12
+    assert abs(r["energy"] - eps[:50].sum()) < 1e-10
+    X = r["X"]
+    assert np.abs(X @ X - X).max() < 1e-12
+
+
+def test_hand_worked_two_level():
+    # H = diag(-1, 1), N_occ = 1, interval [-1, 1]: X0 = diag(1, 0) is already the
+    # projector; Tr X0 = 1, Tr X0^2 = 1 -> |1 - 1| <= |2 - 1 - 1| ties to X^2, and the
+    # iterate never changes; E = -1
+    r = O.sp2_dense(np.diag([-1.0, 1.0]), 1.0, 5, -1.0, 1.0)
+    assert r["branches"] == [1] * 5 and r["energy"] == -1.0
+    # X0 = diag(0.75, 0.25) (interval [-2, 2]): t1 = 1, t2 = 0.625; |0.625 - 1| = 0.375
+    # vs |2 - 0.625 - 1| = 0.375: tie -> X^2 = diag(0.5625, 0.0625)
+    r = O.sp2_dense(np.diag([-1.0, 1.0]), 1.0, 1, -2.0, 2.0)
+    assert r["branches"] == [1] and r["traces"][1] == 0.625
+
+
+def test_traces_stay_in_range():
+    H, (ip, ix, d), n = tb_dense(6)
+    lo, hi = O.gershgorin(ip, ix, d, n)
+    r = O.sp2_spectral(np.linalg.eigvalsh(H), n / 2, 30, lo, hi)
+    assert all(0 <= t <= n for t in r["traces"])
+    assert abs(r["traces"][-1] - n / 2) < abs(r["traces"][0] - n / 2) + 1e-9
