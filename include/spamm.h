@@ -169,6 +169,34 @@ SPAMM_API spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out);
    *count receives the number of triples; SPAMM_ERANGE if it exceeds cap. */
 SPAMM_API spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, int64_t *count);
 
+/* ---- SP2 density-matrix purification (Sec. III: TC2 purification, energy Tr(H X)) ----
+   H is a symmetric n x n matrix given as host CSR (indptr[n+1], indices and data[nnz],
+   column indices sorted per row). X0 = (eps_max I - H) / (eps_max - eps_min) with the
+   Gershgorin bounds of H; each step s forms C = SpAMM(X, X) with tolerance tau[s] in
+   precision prec, computes t1 = Tr X and t2 = Tr C in FP64, and sets X <- C if
+   |t2 - n_occ| <= |2 t1 - t2 - n_occ| (ties to C), else X <- 2X - C. The iterate keeps
+   an FP64 master for SPAMM_FP64 and an FP32 master otherwise. After `steps` steps the
+   result holds E = Tr(H X), the trace of every iterate, the branch taken and the
+   surviving leaf products of every product. Work is ordered on the context stream;
+   the call synchronises once at the end. leaf in {16,32,64,128} for SPAMM_FP64, 64 or
+   128 for the tensor-core precisions; 0 <= steps <= SPAMM_SP2_MAX_STEPS.
+   Errors: SPAMM_EINVAL, SPAMM_EUNSUPPORTED, SPAMM_ENOMEM, SPAMM_ECUDA, SPAMM_ETIMEOUT. */
+#define SPAMM_SP2_MAX_STEPS 128
+typedef struct {
+  double energy;                                /* Tr(H X_steps) */
+  double eps_min, eps_max;                      /* Gershgorin interval of H */
+  int32_t steps;
+  double trace[SPAMM_SP2_MAX_STEPS + 1];        /* Tr X_s, s = 0 .. steps */
+  int32_t branch[SPAMM_SP2_MAX_STEPS];          /* 1: X <- X^2, 0: X <- 2X - X^2 */
+  int64_t leaf_products[SPAMM_SP2_MAX_STEPS];   /* surviving leaf triples of step s */
+  double ms;                                    /* device time of the loop (ms) */
+} spamm_sp2_result;
+
+SPAMM_API spamm_status spamm_sp2(spamm_ctx ctx, int64_t n, const int64_t *indptr,
+                                 const int64_t *indices, const double *data, double n_occ,
+                                 int32_t steps, int32_t leaf, spamm_prec prec, const double *tau,
+                                 spamm_sp2_result *out);
+
 /* ---- cull without device allocation ----
    For callers that cannot allocate device memory: code running inside a CUDA graph
    capture or a real-time loop where cudaMalloc would synchronise or fail, embedders

@@ -90,6 +90,8 @@ void free_tree_memory(spamm_tree t) {
   dfree(t->bound_part);
   dfree(t->look);
   dfree(t->counts);
+  dfree(t->plan);
+  dfree(t->items);
   for (int k = 0; k < 3; k++)
     if (t->ev[k]) cudaEventDestroy(t->ev[k]);
 }
@@ -157,6 +159,16 @@ spamm_status alloc_product_workspace(spamm_ctx ctx, spamm_tree C) {
     e = dmalloc(&C->look, (size_t)C->cap_look * 8);
   }
   if (e == cudaSuccess) e = dmalloc(&C->counts, sizeof(DevCounts));
+  if (e == cudaSuccess && (C->flags & SPAMM_INTERNAL_F32) && (C->b == 64 || C->b == 128)) {
+    // task plan of the tensor-core leaf kernel: at most 4 passes per tier kmax-1 entry at
+    // leaf 64 (two per child k), 8 at leaf 128; one item per group or per output block
+    const int64_t ent = C->tiers[C->kmax].cap_entries;
+    C->cap_plan = std::min<int64_t>(ent * (C->b == 64 ? 4 : 8), int64_t(1) << 31);
+    C->cap_items = C->tiers[C->kmax].cap_groups * (C->b == 64 ? 1 : 4);
+    e = dmalloc(&C->plan, (size_t)C->cap_plan * sizeof(int4));
+    if (e == cudaSuccess) e = dmalloc(&C->items, (size_t)C->cap_items * sizeof(uint2));
+    C->plan_mode = C->b == 64 ? 1 : 2;
+  }
   if (e == cudaSuccess && ctx->timing)
     for (int k = 0; k < 3 && e == cudaSuccess; k++) e = cudaEventCreate(&C->ev[k]);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "product workspace allocation");
@@ -191,8 +203,16 @@ spamm_status ensure_stage(spamm_ctx ctx, size_t bytes) {
 
 }  // namespace
 
-// Internal flag: the product tree keeps an FP32 master (tensor-core precisions).
-#define SPAMM_INTERNAL_F32 0x10000
+
+static int32_t COPY_FLAG_OF(spamm_prec p) {
+  switch (p) {
+    case SPAMM_TF32: return SPAMM_COPY_TF32;
+    case SPAMM_BF16: return SPAMM_COPY_BF16;
+    case SPAMM_FP16: return SPAMM_COPY_FP16;
+    case SPAMM_BF16X3: return SPAMM_COPY_BF16X3;
+    default: return SPAMM_KEEP_FP64;
+  }
+}
 
 extern "C" {
 
@@ -537,3 +557,108 @@ spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, int64_t *co
 }
 
 }  // extern "C"
+
+extern "C" spamm_status spamm_sp2(spamm_ctx ctx, int64_t n, const int64_t *indptr, const int64_t *indices,
+                                  const double *data, double n_occ, int32_t steps, int32_t leaf, spamm_prec prec,
+                                  const double *tau, spamm_sp2_result *out) {
+  if (!ctx) return SPAMM_EINVAL;
+  if (!indptr || !indices || !data || !tau || !out) return fail(ctx, SPAMM_EINVAL, "sp2: null pointer");
+  if (n < 1 || steps < 0 || steps > SPAMM_SP2_MAX_STEPS || !valid_leaf(leaf))
+    return fail(ctx, SPAMM_EINVAL, "sp2: bad n / steps / leaf");
+  if (prec < SPAMM_FP64 || prec > SPAMM_BF16X3) return fail(ctx, SPAMM_EINVAL, "sp2: unknown precision");
+  const bool tc = prec != SPAMM_FP64;
+  if (tc && leaf != 64 && leaf != 128) return fail(ctx, SPAMM_EUNSUPPORTED, "sp2: tensor-core precisions need leaf 64 or 128");
+  for (int s = 0; s < steps; s++)
+    if (!(tau[s] >= 0.0) || !std::isfinite(tau[s])) return fail(ctx, SPAMM_EINVAL, "sp2: tau[%d] invalid", s);
+  const int64_t nnz = indptr[n];
+  if (nnz < 0 || indptr[0] != 0) return fail(ctx, SPAMM_EINVAL, "sp2: bad CSR");
+  // Gershgorin interval on the host
+  double emin = INFINITY, emax = -INFINITY;
+  for (int64_t i = 0; i < n; i++) {
+    double d = 0.0, rad = 0.0;
+    for (int64_t q = indptr[i]; q < indptr[i + 1]; q++) {
+      if (indices[q] < 0 || indices[q] >= n) return fail(ctx, SPAMM_EINVAL, "sp2: column index out of range");
+      if (indices[q] == i) d += data[q];
+      else rad += std::fabs(data[q]);
+    }
+    emin = std::min(emin, d - rad);
+    emax = std::max(emax, d + rad);
+  }
+  if (!(emax > emin)) return fail(ctx, SPAMM_EINVAL, "sp2: empty spectral interval");
+  cudaStream_t s = ctx->stream;
+  int64_t *d_ip = nullptr, *d_ix = nullptr;
+  double *d_v = nullptr, *d_part = nullptr;
+  void *d_rec = nullptr;
+  spamm_tree X = nullptr, C = nullptr;
+  std::vector<unsigned char> host_rec(sp2_record_bytes());
+  spamm_status st = SPAMM_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int32_t flags = tc ? (COPY_FLAG_OF(prec) | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT)
+                           : (SPAMM_KEEP_FP64 | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT);
+  auto cleanup = [&]() {
+    if (X) { free_tree_memory(X); delete X; }
+    if (C) { free_tree_memory(C); delete C; }
+    dfree(d_ip); dfree(d_ix); dfree(d_v); dfree(d_part); dfree(d_rec);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+#define SP2CK(call, what)                                  \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) { cleanup(); return cuda_fail(ctx, _e, what); } \
+  } while (0)
+  SP2CK(dmalloc(&d_ip, (n + 1) * 8), "sp2: allocation");
+  SP2CK(dmalloc(&d_ix, std::max<int64_t>(nnz, 1) * 8), "sp2: allocation");
+  SP2CK(dmalloc(&d_v, std::max<int64_t>(nnz, 1) * 8), "sp2: allocation");
+  SP2CK(dmalloc(&d_part, ((n + 255) / 256) * 8), "sp2: allocation");
+  SP2CK(dmalloc((unsigned char **)&d_rec, sp2_record_bytes()), "sp2: allocation");
+  SP2CK(cudaMemsetAsync(d_rec, 0, sp2_record_bytes(), s), "sp2: memset");
+  SP2CK(cudaMemcpyAsync(d_ip, indptr, (n + 1) * 8, cudaMemcpyHostToDevice, s), "sp2: copy");
+  if (nnz) {
+    SP2CK(cudaMemcpyAsync(d_ix, indices, nnz * 8, cudaMemcpyHostToDevice, s), "sp2: copy");
+    SP2CK(cudaMemcpyAsync(d_v, data, nnz * 8, cudaMemcpyHostToDevice, s), "sp2: copy");
+  }
+  st = alloc_tree(ctx, n, leaf, flags, &X);
+  if (st == SPAMM_OK) st = alloc_tree(ctx, n, leaf, flags, &C);
+  if (st != SPAMM_OK) { cleanup(); return st; }
+  if (tc) {
+    const size_t elems = (size_t)X->nb * X->nb * (size_t)leaf * leaf;
+    SP2CK(dmalloc(&X->copy[CK_F32], elems * 4), "sp2: allocation");
+    SP2CK(dmalloc(&C->copy[CK_F32], elems * 4), "sp2: allocation");
+    X->flags |= SPAMM_INTERNAL_F32;
+    C->flags |= SPAMM_INTERNAL_F32;
+  }
+  st = ensure_stage(ctx, (size_t)n * n * sizeof(double));
+  if (st != SPAMM_OK) { cleanup(); return st; }
+  SP2CK(sp2_x0(n, d_ip, d_ix, d_v, emin, emax, (double *)ctx->stage, s), "sp2: X0");
+  SP2CK(launch_tree_build(X, (const double *)ctx->stage, s), "sp2: X0 tree");
+  SP2CK(launch_pyramid(X, s), "sp2: X0 pyramid");
+  SP2CK(cudaEventCreate(&e0), "sp2: event");
+  SP2CK(cudaEventCreate(&e1), "sp2: event");
+  SP2CK(cudaEventRecord(e0, s), "sp2: event");
+  for (int step = 0; step < steps; step++) {
+    spamm_tree out_tree = C;
+    st = spamm_multiply(ctx, X, X, tau[step], prec, 0, &out_tree);
+    if (st != SPAMM_OK) { cleanup(); return st; }
+    SP2CK(sp2_step_finish(X, C, n_occ, step, d_rec, s), "sp2: step");
+    std::swap(X, C);
+  }
+  SP2CK(sp2_trace_only(X, steps, d_rec, s), "sp2: trace");
+  SP2CK(sp2_energy(X, n, d_ip, d_ix, d_v, d_part, d_rec, s), "sp2: energy");
+  SP2CK(cudaEventRecord(e1, s), "sp2: event");
+  SP2CK(cudaMemcpyAsync(host_rec.data(), d_rec, sp2_record_bytes(), cudaMemcpyDeviceToHost, s), "sp2: copy");
+  st = check_device_status(ctx);
+  if (st != SPAMM_OK) { cleanup(); return st; }
+  memset(out, 0, sizeof *out);
+  sp2_read_record(host_rec.data(), steps, out);
+  out->eps_min = emin;
+  out->eps_max = emax;
+  out->steps = steps;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  out->ms = ms;
+  ctx->launches += 4 + (int64_t)steps * 5;
+  cleanup();
+  return SPAMM_OK;
+#undef SP2CK
+}

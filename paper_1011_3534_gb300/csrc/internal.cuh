@@ -15,6 +15,9 @@ enum : uint32_t {
   DEV_BADARG = 1u << 2,     // a kernel found an index outside its buffers
 };
 
+// Internal tree flag: the product tree keeps an FP32 master (tensor-core precisions).
+#define SPAMM_INTERNAL_F32 0x10000
+
 // Bounded waits give up after this many nanoseconds of %globaltimer.
 constexpr unsigned long long kSpinLimitNs = 2000000000ull;
 
@@ -76,6 +79,7 @@ struct DevCounts {                     // device-resident counters of one produc
   unsigned long long leaf_products;
   unsigned long long output_blocks;
   unsigned long long mma_tiles;        // leaf-kernel MMA tile-steps issued
+  unsigned long long npasses;          // passes of the tensor-core task plan
   unsigned int tile_ctr[SPAMM_MAX_LEVELS + 2];        // dynamic tile counters
   unsigned int work_ctr;
   double culled_bound[SPAMM_MAX_LEVELS];
@@ -102,6 +106,12 @@ struct spamm_tree_s {
   uint64_t *look = nullptr;               // look-back tile status words
   int64_t cap_look = 0;
   DevCounts *counts = nullptr;            // device
+  // task plan of the tensor-core leaf kernel (set by the last cull tier)
+  int plan_mode = 0;                      // 0 none, 1 leaf 64, 2 leaf 128
+  int4 *plan = nullptr;
+  int64_t cap_plan = 0;
+  uint2 *items = nullptr;
+  int64_t cap_items = 0;
   spamm_stats_t host_stats{};
   bool stats_valid = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -124,3 +134,11 @@ cudaError_t launch_tile_convert(spamm_tree t, cudaStream_t s);
 int64_t cull_look_words(int kmax);
 int64_t cull_bound_words(int kmax, int64_t *offsets);
 int pyramid_launches(int kmax);
+cudaError_t sp2_x0(int64_t n, const int64_t *indptr, const int64_t *indices, const double *data, double emin,
+                   double emax, double *X, cudaStream_t s);
+size_t sp2_record_bytes();
+cudaError_t sp2_step_finish(spamm_tree X, spamm_tree C, double n_occ, int step, void *rec, cudaStream_t s);
+cudaError_t sp2_trace_only(spamm_tree X, int idx, void *rec, cudaStream_t s);
+cudaError_t sp2_energy(spamm_tree X, int64_t n, const int64_t *indptr, const int64_t *indices,
+                       const double *data, double *partial, void *rec, cudaStream_t s);
+void sp2_read_record(const void *host_rec, int steps, spamm_sp2_result *out);

@@ -34,9 +34,54 @@ __device__ __forceinline__ uint64_t pack(uint64_t flag, uint64_t groups, uint64_
   return flag | ((groups & ((1ull << 31) - 1)) << 31) | (entries & kEntMask);
 }
 
+// Decoupled look-back of one tile (called by a whole warp): publishes this tile's
+// aggregates (entries, groups) and returns the exclusive prefix of all earlier tiles.
+// Waits on predecessors are bounded; a wait that runs out flags DEV_TIMEOUT.
+__device__ void tile_lookback(uint64_t *look, unsigned int tile, uint64_t agg_e, uint64_t agg_g,
+                              uint64_t &ex_e, uint64_t &ex_g, uint32_t *status) {
+  const int lane = threadIdx.x & 31;
+  ex_e = 0;
+  ex_g = 0;
+  if (tile == 0) {
+    if (lane == 0) st_release_u64(look + tile, pack(kFlagPrefix, agg_g, agg_e));
+    return;
+  }
+  if (lane == 0) st_release_u64(look + tile, pack(kFlagAgg, agg_g, agg_e));
+  int64_t base = (int64_t)tile - 1;
+  const unsigned long long t0 = globaltimer_ns();
+  bool timed_out = false;
+  for (;;) {
+    const int64_t idx = base - lane;
+    uint64_t w = idx >= 0 ? ld_acquire_u64(look + idx) : kFlagPrefix;
+    unsigned spins = 0;
+    for (;;) {   // warp-uniform: every lane leaves together
+      const bool pending = (w & kFlagMask) == 0;
+      if (!__any_sync(0xffffffffu, pending)) break;
+      if (pending) w = ld_acquire_u64(look + idx);
+      if ((++spins & 255u) == 0 && __any_sync(0xffffffffu, globaltimer_ns() - t0 > kSpinLimitNs)) {
+        timed_out = true;
+        break;
+      }
+    }
+    if (timed_out) {
+      if (lane == 0) flag_error(status, DEV_TIMEOUT);
+      break;
+    }
+    const unsigned pre = __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagPrefix);
+    const int stop = pre ? __ffs(pre) - 1 : 31;   // nearest tile with a full prefix
+    const uint64_t e = lane <= stop ? (w & kEntMask) : 0;
+    const uint64_t gg = lane <= stop ? ((w >> 31) & ((1ull << 31) - 1)) : 0;
+    ex_e += warp_sum(e);
+    ex_g += warp_sum(gg);
+    if (pre) break;
+    base -= 32;
+  }
+  if (lane == 0) st_release_u64(look + tile, pack(kFlagPrefix, ex_g + agg_g, ex_e + agg_e));
+}
+
 struct CullArgs {
   const double *nA, *nB;    // norms (not squared) of tier l, 2^l x 2^l
-  int32_t l, D, nb, final_tier;
+  int32_t l, D, nb, NB, final_tier;
   double tau;
   const uint32_t *pgij, *pgstart, *pglen;
   const uint16_t *pK;
@@ -52,7 +97,35 @@ struct CullArgs {
   unsigned long long *tested, *culled, *leaf_products, *output_blocks;
   double *bound_part;
   uint32_t *status;
+  // task plan of the tensor-core leaf kernel (last tier only)
+  int plan_mode;                 // 0: none; 1: leaf 64, one item per group (its 2 x 2 output
+                                 // blocks); 2: leaf 128, one item per output block
+  const uint8_t *nzA, *nzB;
+  int bsym;                      // B leaf (k, j) read as leaf (j, k) of a symmetric tree
+  int4 *plan;                    // per pass: leaf coordinates {A row 0, A row 1, B col 0, B col 1}
+  int64_t cap_plan;
+  uint2 *items;                  // per item: {first pass, passes | touched quadrants << 24}
+  unsigned long long *npasses;
 };
+
+// Passes of one candidate k = 2K + e of a leaf-64 item: the 2 x 2 survival pattern over
+// (a, c) taken as one outer product of a row and a column mask when it is one, else one
+// pass per row. Returns the pass count; rm/cm get the masks.
+__device__ __forceinline__ int passes64(uint32_t m, int e, uint32_t (&rm)[2], uint32_t (&cm)[2]) {
+  const uint32_t r0 = ((m >> e) & 1u) | (((m >> (2 + e)) & 1u) << 1);   // a = 0: c = 0, 1
+  const uint32_t r1 = ((m >> (4 + e)) & 1u) | (((m >> (6 + e)) & 1u) << 1);
+  if (!r0 && !r1) return 0;
+  if (!r0 || !r1 || r0 == r1) {
+    rm[0] = (r0 ? 1u : 0u) | (r1 ? 2u : 0u);
+    cm[0] = r0 | r1;
+    return 1;
+  }
+  rm[0] = 1;
+  cm[0] = r0;
+  rm[1] = 2;
+  cm[1] = r1;
+  return 2;
+}
 
 // Children of entry (I, J, K) tested at tier l: survival bits, test count, and the
 // culled norm products summed in a fixed order.
@@ -80,6 +153,103 @@ __device__ __forceinline__ uint32_t child_bits(const CullArgs &a, uint32_t I, ui
     }
   }
   return bits;
+}
+
+// Last tier: the task plan of the tensor-core leaf kernel. Items of the tile (8 groups;
+// one item per group at leaf 64, four at leaf 128) are placed after all earlier tiles
+// by the same look-back scan, each with its passes in k order (entries ascending, then
+// e, then rows): the leaf coordinates of every box the pass loads, or one past the last
+// leaf for a box that must be zero (a culled product, a padding or absent leaf).
+__device__ void final_plan(const CullArgs &a, unsigned int tile, int warp, int lane, bool has, uint32_t g,
+                           uint32_t I, uint32_t J, uint32_t start, uint32_t len, unsigned int (&npq)[4],
+                           uint32_t touched, unsigned long long ngroups, unsigned int *s_cnt,
+                           unsigned int *s_off) {
+#pragma unroll
+  for (int q = 0; q < 4; q++) npq[q] = warp_sum(npq[q]);
+  touched = __reduce_or_sync(0xffffffffu, touched);
+  if (lane < 4) s_cnt[warp * 4 + lane] = has ? npq[lane] : 0u;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned int v = s_cnt[lane];
+    const unsigned int inc = warp_inclusive_scan(v);
+    const uint64_t agg = __shfl_sync(0xffffffffu, inc, 31);
+    uint64_t ex = 0, exg = 0;
+    tile_lookback(a.look, tile, agg, 0, ex, exg, a.status);
+    s_off[lane] = (unsigned int)(ex + inc - v);
+    if (lane == 0 && (unsigned long long)(tile + 1) * 8 >= ngroups) {
+      *a.npasses = ex + agg;
+      if ((int64_t)(ex + agg) > a.cap_plan) flag_error(a.status, DEV_OVERFLOW);
+    }
+  }
+  __syncthreads();
+  if (!has) return;
+  const int oob = a.nb * a.nb;
+  if (lane == 0) {
+    if (a.plan_mode == 1) {
+      a.items[g] = make_uint2(s_off[warp * 4], npq[0] | (touched << 24));
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        a.items[4 * (uint64_t)g + q] = make_uint2(s_off[warp * 4 + q], npq[q] | (((touched >> q) & 1u) << 24));
+    }
+  }
+  unsigned int run[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) run[q] = s_off[warp * 4 + q];
+  __syncwarp();
+  for (uint32_t p0 = 0; p0 < len; p0 += 32) {
+    const uint32_t pe = p0 + lane;
+    uint32_t bits = 0;
+    int K2 = 0;
+    if (pe < len) {
+      bits = a.mask[start + pe];
+      K2 = 2 * (int)a.pK[start + pe];
+    }
+    if (a.plan_mode == 1) {
+      uint32_t rm0[2], cm0[2], rm1[2], cm1[2];
+      const int n0 = passes64(bits, 0, rm0, cm0), n1 = passes64(bits, 1, rm1, cm1);
+      const unsigned int m = (unsigned int)(n0 + n1);
+      const unsigned int inc = warp_inclusive_scan(m);
+      int64_t pos = (int64_t)run[0] + inc - m;
+      for (int e = 0; e < 2; e++) {
+        const int np = e ? n1 : n0;
+        const int k = K2 + e;
+        for (int ps = 0; ps < np; ps++) {
+          const uint32_t rmask = e ? rm1[ps] : rm0[ps], cmask = e ? cm1[ps] : cm0[ps];
+          int4 d = make_int4(oob, oob, oob, oob);
+          const int i0 = 2 * (int)I, j0 = 2 * (int)J;
+          if ((rmask & 1u) && i0 < a.nb && k < a.nb && a.nzA[(int64_t)i0 * a.NB + k]) d.x = i0 * a.nb + k;
+          if ((rmask & 2u) && i0 + 1 < a.nb && k < a.nb && a.nzA[(int64_t)(i0 + 1) * a.NB + k]) d.y = (i0 + 1) * a.nb + k;
+          if ((cmask & 1u) && j0 < a.nb && k < a.nb && a.nzB[(int64_t)k * a.NB + j0])
+            d.z = a.bsym ? j0 * a.nb + k : k * a.nb + j0;
+          if ((cmask & 2u) && j0 + 1 < a.nb && k < a.nb && a.nzB[(int64_t)k * a.NB + j0 + 1])
+            d.w = a.bsym ? (j0 + 1) * a.nb + k : k * a.nb + j0 + 1;
+          if (pos < a.cap_plan) a.plan[pos] = d;
+          pos++;
+        }
+      }
+      run[0] += __shfl_sync(0xffffffffu, inc, 31);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const uint32_t two = (bits >> (2 * q)) & 3u;
+        const unsigned int m = __popc(two);
+        const unsigned int inc = warp_inclusive_scan(m);
+        int64_t pos = (int64_t)run[q] + inc - m;
+        const int i = 2 * (int)I + (q >> 1), j = 2 * (int)J + (q & 1);
+        for (int e = 0; e < 2; e++) {
+          if (!((two >> e) & 1u)) continue;
+          const int k = K2 + e;
+          int4 d = make_int4(oob, oob, oob, oob);
+          if (i < a.nb && k < a.nb && a.nzA[(int64_t)i * a.NB + k]) d.x = i * a.nb + k;
+          if (j < a.nb && k < a.nb && a.nzB[(int64_t)k * a.NB + j]) d.z = a.bsym ? j * a.nb + k : k * a.nb + j;
+          if (pos < a.cap_plan) a.plan[pos] = d;
+          pos++;
+        }
+        run[q] += __shfl_sync(0xffffffffu, inc, 31);
+      }
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
@@ -111,6 +281,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
     }
     // pass 1: per child-quadrant counts (and, on the last tier, the masks)
     unsigned int cnt[4] = {0, 0, 0, 0};
+    unsigned int npq[4] = {0, 0, 0, 0};   // passes per item (plan)
+    uint32_t touched = 0;
     int tests = 0;
     double bound = 0.0;
     for (uint32_t p0 = 0; p0 < len; p0 += 32) {
@@ -122,7 +294,17 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
         if (a.final_tier) a.mask[start + p] = (uint8_t)bits;
       }
 #pragma unroll
-      for (int q = 0; q < 4; q++) cnt[q] += __popc((bits >> (2 * q)) & 3u);
+      for (int q = 0; q < 4; q++) {
+        cnt[q] += __popc((bits >> (2 * q)) & 3u);
+        if ((bits >> (2 * q)) & 3u) touched |= 1u << q;
+      }
+      if (a.plan_mode == 1) {
+        uint32_t rm[2], cm[2];
+        npq[0] += passes64(bits, 0, rm, cm) + passes64(bits, 1, rm, cm);
+      } else if (a.plan_mode == 2) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) npq[q] += __popc((bits >> (2 * q)) & 3u);
+      }
     }
 #pragma unroll
     for (int q = 0; q < 4; q++) cnt[q] = warp_sum(cnt[q]);
@@ -141,7 +323,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
         if (blocks) atomicAdd(a.output_blocks, (unsigned long long)blocks);
       }
     }
-    if (a.final_tier) continue;
+    if (a.final_tier) {
+      if (a.plan_mode) final_plan(a, tile, warp, lane, has, (uint32_t)g, I, J, start, len, npq, touched,
+                                  ngroups, s_cnt, s_off);
+      continue;
+    }
 
     // tile scan of the 32 child groups (warp w, quadrant q) in order
     if (lane < 4) s_cnt[warp * 4 + lane] = has ? cnt[lane] : 0u;
@@ -154,43 +340,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
       const uint64_t agg_e = __shfl_sync(0xffffffffu, inc_v, 31);
       const uint64_t agg_g = __shfl_sync(0xffffffffu, inc_f, 31);
       uint64_t ex_e = 0, ex_g = 0;
-      if (tile == 0) {
-        if (lane == 0) st_release_u64(a.look + tile, pack(kFlagPrefix, agg_g, agg_e));
-      } else {
-        if (lane == 0) st_release_u64(a.look + tile, pack(kFlagAgg, agg_g, agg_e));
-        // look back over predecessors, 32 at a time
-        int64_t base = (int64_t)tile - 1;
-        const unsigned long long t0 = globaltimer_ns();
-        bool timed_out = false;
-        for (;;) {
-          const int64_t idx = base - lane;
-          uint64_t w = idx >= 0 ? ld_acquire_u64(a.look + idx) : kFlagPrefix;
-          unsigned spins = 0;
-          for (;;) {   // warp-uniform: every lane leaves together
-            const bool pending = (w & kFlagMask) == 0;
-            if (!__any_sync(0xffffffffu, pending)) break;
-            if (pending) w = ld_acquire_u64(a.look + idx);
-            if ((++spins & 255u) == 0 &&
-                __any_sync(0xffffffffu, globaltimer_ns() - t0 > kSpinLimitNs)) {
-              timed_out = true;
-              break;
-            }
-          }
-          if (timed_out) {
-            if (lane == 0) flag_error(a.status, DEV_TIMEOUT);
-            break;
-          }
-          const unsigned pre = __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagPrefix);
-          const int stop = pre ? __ffs(pre) - 1 : 31;   // nearest tile with a full prefix
-          uint64_t e = lane <= stop ? (w & kEntMask) : 0;
-          uint64_t gg = lane <= stop ? ((w >> 31) & ((1ull << 31) - 1)) : 0;
-          ex_e += warp_sum(e);
-          ex_g += warp_sum(gg);
-          if (pre) break;
-          base -= 32;
-        }
-        if (lane == 0) st_release_u64(a.look + tile, pack(kFlagPrefix, ex_g + agg_g, ex_e + agg_e));
-      }
+      tile_lookback(a.look, tile, agg_e, agg_g, ex_e, ex_g, a.status);
       s_off[lane] = (unsigned int)(ex_e + inc_v - v);
       s_gix[lane] = (unsigned int)(ex_g + inc_f - f);
       if (lane == 0 && (unsigned long long)(tile + 1) * kWarps >= ngroups) {
@@ -316,6 +466,7 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau,
     a.l = l;
     a.D = 1 << l;
     a.nb = A->nb;
+    a.NB = A->NB;
     a.final_tier = (l == kmax);
     a.tau = tau;
     const TierList &par = C->tiers[l];
@@ -337,6 +488,14 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau,
       a.c_nentries = &cnt->nentries[l + 1];
     } else {
       a.mask = C->mask;
+      a.plan_mode = C->plan_mode;
+      a.nzA = A->nz;
+      a.nzB = B->nz;
+      a.bsym = (B->flags & SPAMM_SYMMETRIC) != 0;
+      a.plan = C->plan;
+      a.cap_plan = C->cap_plan;
+      a.items = C->items;
+      a.npasses = &cnt->npasses;
     }
     const int64_t pg = bound_groups_cap(l);
     const int64_t tiles = (pg + kWarps - 1) / kWarps;

@@ -53,6 +53,10 @@ struct TcArgs {
   double *leaf_norm2C;
   unsigned long long *mma_stages;
   uint32_t *status;
+  const int4 *plan;              // per pass: leaf coordinates of the four boxes
+  const uint2 *items;            // per item: {first pass, passes | touched << 24}
+  int64_t cap_plan;
+  const unsigned long long *nitems_dev;   // groups of the last tier list (items: x1 or x4)
 };
 
 __device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
@@ -83,32 +87,6 @@ __device__ __forceinline__ Item decode(const TcArgs &p, unsigned long long item)
   return it;
 }
 
-// Passes of candidate (mask m, e): row masks rm (bit a) and column masks cm (bit c).
-template <int LEAF>
-__device__ __forceinline__ int passes(uint32_t m, int e, int q, uint32_t (&rm)[2], uint32_t (&cm)[2]) {
-  if (LEAF == 128) {
-    if ((m >> (2 * q + e)) & 1u) {
-      rm[0] = 1;
-      cm[0] = 1;
-      return 1;
-    }
-    return 0;
-  }
-  const uint32_t r0 = ((m >> e) & 1u) | (((m >> (2 + e)) & 1u) << 1);   // a = 0: c = 0, 1
-  const uint32_t r1 = ((m >> (4 + e)) & 1u) | (((m >> (6 + e)) & 1u) << 1);   // a = 1
-  if (!r0 && !r1) return 0;
-  if (!r0 || !r1 || r0 == r1) {
-    rm[0] = (r0 ? 1u : 0u) | (r1 ? 2u : 0u);
-    cm[0] = r0 | r1;
-    return 1;
-  }
-  rm[0] = 1;
-  cm[0] = r0;
-  rm[1] = 2;
-  cm[1] = r1;
-  return 2;
-}
-
 template <int LEAF, bool TF32>
 __global__ void __launch_bounds__(kThreads, 1)
     k_leaf_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
@@ -119,8 +97,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   __shared__ double s_norm[4][2];
-  __shared__ int4 s_desc[32][4];     // producer: passes of the 32 entries in flight
-  __shared__ int s_ndesc[32];
+  __shared__ int4 s_desc[32];        // producer: the chunk of passes being issued
   constexpr int RA = LEAF == 64 ? 2 : 1;        // A leaves stacked along M
   constexpr int RC = LEAF == 64 ? 2 : 1;        // B leaves stacked along N
   constexpr uint32_t kBox = LEAF * 128;         // bytes of one leaf box (LEAF rows x 128 B)
@@ -144,14 +121,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  const unsigned long long ng = *p.ngroups;
-  const unsigned long long nitems = LEAF == 64 ? ng : 4ull * ng;
+  const unsigned long long nitems = (LEAF == 64 ? 1ull : 4ull) * (*p.nitems_dev);
+  const unsigned long long my_items =
+      nitems > blockIdx.x ? (nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0ull;
 
   if (warp == 0) {
     // ---------------- TMA producer (warp 0) ----------------
-    // The warp reads 32 entries of the group at a time: each lane turns one entry into
-    // its (up to four) passes with the leaf coordinates of every box (zero-filled
-    // boxes point one leaf past the end), then lane 0 issues the stages in order.
+    // Item metadata is loaded 32 items at a time; each item's passes are loaded 32 at a
+    // time, the next chunk while lane 0 issues the current one.
     if (lane == 0) {
       tma_prefetch_desc(&mA);
       tma_prefetch_desc(&mB);
@@ -160,53 +137,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         tma_prefetch_desc(&mBlo);
       }
     }
-    const int oob = p.nb * p.nb;
     int stage = 0;
     uint32_t phase = 0;
-    // loops over items and entry chunks are warp-uniform; after an abort lane 0 only
-    // skips its work, so every lane keeps the same trip counts
-    for (unsigned long long item = blockIdx.x; item < nitems; item += gridDim.x) {
-      const Item it = decode<LEAF>(p, item);
-      for (uint32_t p0 = 0; p0 < it.len; p0 += 32) {
-        const uint32_t pe = p0 + lane;
-        int np_all = 0;
-        if (pe < it.len) {
-          const uint32_t m = p.mask[it.start + pe];
-          const int K2 = 2 * (int)p.K[it.start + pe];
-#pragma unroll
-          for (int e = 0; e < 2; e++) {
-            uint32_t rm[2], cm[2];
-            const int np = passes<LEAF>(m, e, it.q, rm, cm);
-            const int k = K2 + e;
-            for (int ps = 0; ps < np; ps++) {
-              int4 d;
-              int la[2] = {oob, oob}, lb[2] = {oob, oob};
-#pragma unroll
-              for (int a = 0; a < RA; a++) {
-                const int i = LEAF == 64 ? (int)(2 * it.I) + a : (int)(2 * it.I) + (it.q >> 1);
-                if (((rm[ps] >> a) & 1u) && i < p.nb && k < p.nb && p.nzA[(int64_t)i * p.NB + k]) la[a] = i * p.nb + k;
-              }
-#pragma unroll
-              for (int c = 0; c < RC; c++) {
-                const int j = LEAF == 64 ? (int)(2 * it.J) + c : (int)(2 * it.J) + (it.q & 1);
-                if (((cm[ps] >> c) & 1u) && j < p.nb && k < p.nb && p.nzB[(int64_t)k * p.NB + j])
-                  lb[c] = p.bsym ? j * p.nb + k : k * p.nb + j;
-              }
-              d.x = la[0];
-              d.y = la[1];
-              d.z = lb[0];
-              d.w = lb[1];
-              s_desc[lane][np_all++] = d;
-            }
-          }
-        }
-        s_ndesc[lane] = np_all;
-        __syncwarp();
-        if (lane == 0) {
-          const int nl = (int)min(32u, it.len - p0);
-          for (int l = 0; l < nl && !s_abort; l++) {
-            for (int di = 0; di < s_ndesc[l] && !s_abort; di++) {
-              const int4 d = s_desc[l][di];
+    for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
+      const unsigned long long mine = t0 + lane;
+      const uint2 meta = mine < my_items ? p.items[blockIdx.x + mine * gridDim.x] : make_uint2(0u, 0u);
+      const int nt = (int)min(32ull, my_items - t0);
+      for (int ti = 0; ti < nt; ti++) {
+        const uint32_t first = __shfl_sync(0xffffffffu, meta.x, ti);
+        uint32_t np = __shfl_sync(0xffffffffu, meta.y, ti) & 0xFFFFFFu;
+        np = (int64_t)first >= p.cap_plan ? 0u : ((int64_t)first + np > p.cap_plan ? (uint32_t)(p.cap_plan - first) : np);   // overflowed plan
+        int4 cur = make_int4(0, 0, 0, 0);
+        if ((uint32_t)lane < np) cur = p.plan[(int64_t)first + lane];
+        for (uint32_t c0 = 0; c0 < np; c0 += 32) {
+          s_desc[lane] = cur;
+          __syncwarp();
+          if (c0 + 32 < np && c0 + 32 + lane < np) cur = p.plan[(int64_t)first + c0 + 32 + lane];
+          if (lane == 0) {
+            const int nl = (int)min(32u, np - c0);
+            for (int l = 0; l < nl && !s_abort; l++) {
+              const int4 d = s_desc[l];
               for (int src = 0; src < p.nsrc && !s_abort; src++) {
                 const CUtensorMap *ma = src == 2 ? &mAlo : &mA;
                 const CUtensorMap *mb = src == 1 ? &mBlo : &mB;
@@ -230,64 +180,64 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
           }
+          __syncwarp();
         }
-        __syncwarp();
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (warp 1) ----------------
-    // The warp counts the item's stages in parallel; lane 0 issues them.
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
     unsigned long long nst = 0;
-    for (unsigned long long item = blockIdx.x; item < nitems; item += gridDim.x) {
-      const Item it = decode<LEAF>(p, item);
-      int cnt = 0;
-      for (uint32_t pe = lane; pe < it.len; pe += 32) {
-        const uint32_t m = p.mask[it.start + pe];
-        uint32_t rm[2], cm[2];
-        cnt += passes<LEAF>(m, 0, it.q, rm, cm) + passes<LEAF>(m, 1, it.q, rm, cm);
-      }
-      const int total = warp_sum(cnt) * p.nsrc * p.chunks;
-      if (lane == 0 && !s_abort) {
-        if (!mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort)) {
-          s_abort = 1;
-          flag_error(p.status, DEV_TIMEOUT);
-        } else {
-          tc_fence_after();
-          const uint32_t d = tmem + (uint32_t)acc * 128u;
-          uint32_t accum = 0;
-          for (int t = 0; t < total; t++) {
-            if (!mbar_wait(&full[stage], phase, &s_abort)) {
-              s_abort = 1;
-              flag_error(p.status, DEV_TIMEOUT);
-              break;
-            }
+    for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
+      const unsigned long long mine = t0 + lane;
+      const uint2 meta = mine < my_items ? p.items[blockIdx.x + mine * gridDim.x] : make_uint2(0u, 0u);
+      const int nt = (int)min(32ull, my_items - t0);
+      for (int ti = 0; ti < nt; ti++) {
+        const uint32_t first = __shfl_sync(0xffffffffu, meta.x, ti);
+        uint32_t np = __shfl_sync(0xffffffffu, meta.y, ti) & 0xFFFFFFu;
+        np = (int64_t)first >= p.cap_plan ? 0u : ((int64_t)first + np > p.cap_plan ? (uint32_t)(p.cap_plan - first) : np);
+        const int total = (int)np * p.nsrc * p.chunks;
+        if (lane == 0 && !s_abort) {
+          if (!mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort)) {
+            s_abort = 1;
+            flag_error(p.status, DEV_TIMEOUT);
+          } else {
             tc_fence_after();
-            const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
+            const uint32_t d = tmem + (uint32_t)acc * 128u;
+            uint32_t accum = 0;
+            for (int t = 0; t < total; t++) {
+              if (!mbar_wait(&full[stage], phase, &s_abort)) {
+                s_abort = 1;
+                flag_error(p.status, DEV_TIMEOUT);
+                break;
+              }
+              tc_fence_after();
+              const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
 #pragma unroll
-            for (int kk = 0; kk < 4; kk++) {
-              const uint64_t da = desc_sw128(sa + kk * 32), db = desc_sw128(sb + kk * 32);
-              if (TF32) mma_tf32(d, da, db, p.idesc, accum);
-              else mma_f16(d, da, db, p.idesc, accum);
-              accum = 1;
+              for (int kk = 0; kk < 4; kk++) {
+                const uint64_t da = desc_sw128(sa + kk * 32), db = desc_sw128(sb + kk * 32);
+                if (TF32) mma_tf32(d, da, db, p.idesc, accum);
+                else mma_f16(d, da, db, p.idesc, accum);
+                accum = 1;
+              }
+              mma_commit(&empty[stage]);
+              nst++;
+              if (++stage == kStages) {
+                stage = 0;
+                phase ^= 1u;
+              }
             }
-            mma_commit(&empty[stage]);
-            nst++;
-            if (++stage == kStages) {
-              stage = 0;
-              phase ^= 1u;
-            }
+            mma_commit(&accf[acc]);
           }
-          mma_commit(&accf[acc]);
         }
-      }
-      __syncwarp();
-      if (++acc == kAcc) {
-        acc = 0;
-        acc_phase ^= 1u;
+        __syncwarp();
+        if (++acc == kAcc) {
+          acc = 0;
+          acc_phase ^= 1u;
+        }
       }
     }
     if (lane == 0 && nst) atomicAdd(p.mma_stages, nst);
@@ -297,16 +247,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = 32 * slice + lane;     // accumulator row
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (unsigned long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+    for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
+     const unsigned long long mine = t0 + lane;
+     const unsigned long long my_item = blockIdx.x + mine * gridDim.x;
+     const uint2 meta = mine < my_items ? p.items[my_item] : make_uint2(0u, 0u);
+     const int nt = (int)min(32ull, my_items - t0);
+     for (int ti = 0; ti < nt; ti++) {
+      const unsigned long long item = blockIdx.x + (t0 + ti) * gridDim.x;
       const Item it = decode<LEAF>(p, item);
-      uint32_t touched = 0;   // quadrants (a * 2 + c) with a surviving product
-      for (uint32_t pe = lane; pe < it.len; pe += 32) {
-        const uint32_t m = p.mask[it.start + pe];
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-          if ((m >> (2 * q)) & 3u) touched |= 1u << q;
-      }
-      touched = __reduce_or_sync(0xffffffffu, touched);
+      uint32_t touched = __shfl_sync(0xffffffffu, meta.y, ti) >> 24;   // output quadrants with a product
+      if (LEAF == 128) touched = touched ? (1u << it.q) : 0u;
       bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
       if (!ok) {
         s_abort = 1;
@@ -386,6 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         acc = 0;
         acc_phase ^= 1u;
       }
+     }
     }
   }
   tc_fence_before();
@@ -485,6 +436,10 @@ cudaError_t launch_leaf_tc(spamm_tree A, spamm_tree B, spamm_tree C, int prec, u
   p.leaf_norm2C = C->norm2 + level_offset(C->kmax);
   p.mma_stages = &C->counts->mma_tiles;
   p.status = dev_status;
+  p.plan = C->plan;
+  p.items = C->items;
+  p.cap_plan = C->cap_plan;
+  p.nitems_dev = &C->counts->ngroups[C->kmax];
   if (b == 64) return tf32 ? run<64, true>(ma, mb, malo, mblo, p, sm_count, s)
                            : run<64, false>(ma, mb, malo, mblo, p, sm_count, s);
   if (b == 128) return tf32 ? run<128, true>(ma, mb, malo, mblo, p, sm_count, s)

@@ -35,7 +35,7 @@ MAX_LEVELS = 24
 EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_error",
            "spamm_kernel_launches", "spamm_tree_build", "spamm_tree_update", "spamm_tree_free", "spamm_tree_info",
            "spamm_tree_norms", "spamm_tree_to_dense", "spamm_multiply", "spamm_stats",
-           "spamm_triples", "spamm_cull_noalloc")
+           "spamm_triples", "spamm_cull_noalloc", "spamm_sp2")
 
 
 class SpammError(RuntimeError):
@@ -52,6 +52,16 @@ class StatsT(ctypes.Structure):
                 ("leaf_flops", ctypes.c_double), ("dense_equiv_flops", ctypes.c_double),
                 ("mma_flops", ctypes.c_double), ("ms_cull", ctypes.c_double),
                 ("ms_leaf", ctypes.c_double), ("prec", ctypes.c_int32), ("tau", ctypes.c_double)]
+
+
+SP2_MAX_STEPS = 128
+
+
+class Sp2ResultT(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double),
+                ("steps", ctypes.c_int32), ("trace", ctypes.c_double * (SP2_MAX_STEPS + 1)),
+                ("branch", ctypes.c_int32 * SP2_MAX_STEPS), ("leaf_products", ctypes.c_int64 * SP2_MAX_STEPS),
+                ("ms", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -82,6 +92,7 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.spamm_stats.argtypes = [_P, ctypes.POINTER(StatsT)]
     L.spamm_triples.argtypes = [_P, _P, _I64, ctypes.POINTER(_I64)]
     L.spamm_cull_noalloc.argtypes = [_P, _P, _I32, _D, _P, _I64, _P, _P]
+    L.spamm_sp2.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, _I32, ctypes.c_int, _P, ctypes.POINTER(Sp2ResultT)]
     for name in EXPORTS:
         if name not in ("spamm_last_error", "spamm_kernel_launches"):
             getattr(L, name).restype = st
@@ -228,3 +239,19 @@ def spamm_cull_noalloc(normA2, normB2, nb_padded: int, tau: float, triples, cap:
                                 _ptr(triples) if triples is not None else None, cap, _ptr(count), s)
     if rc != SPAMM_OK:
         raise SpammError(rc, "spamm_cull_noalloc failed")
+
+
+def spamm_sp2(ctx: Ctx, indptr, indices, data, n_occ: float, steps: int, leaf: int, prec: int, tau) -> dict:
+    """SP2 purification of the symmetric CSR matrix H (host numpy arrays)."""
+    indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(indices, dtype=np.int64)
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    tau = np.ascontiguousarray(np.broadcast_to(np.asarray(tau, dtype=np.float64), (steps,)))
+    n = indptr.size - 1
+    r = Sp2ResultT()
+    ctx.check(LIB.spamm_sp2(ctx.h, n, indptr.ctypes.data, indices.ctypes.data, data.ctypes.data, float(n_occ),
+                            steps, leaf, int(prec), tau.ctypes.data if steps else None, ctypes.byref(r)),
+              "spamm_sp2")
+    return dict(energy=r.energy, eps_min=r.eps_min, eps_max=r.eps_max, steps=r.steps,
+                traces=list(r.trace[:steps + 1]), branches=list(r.branch[:steps]),
+                leaf_products=list(r.leaf_products[:steps]), ms=r.ms)
