@@ -79,6 +79,8 @@ typedef enum {
 #define SPAMM_COPY_BF16X3  0x0080  /* write BF16 hi and lo leaf copies */
 #define SPAMM_NO_RIGHT     0x0100  /* the tree is never a right operand: skip the
                                       transposed copies a non-symmetric tree needs */
+#define SPAMM_GRAPH        0x0200  /* spamm_multiply_batched: capture the batch into a CUDA
+                                      graph on first use and replay it afterwards */
 
 #define SPAMM_MAX_LEVELS 24
 
@@ -168,6 +170,31 @@ SPAMM_API spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out);
    (i, j, k), three uint32 per triple, into the host buffer ijk of `cap` triples.
    *count receives the number of triples; SPAMM_ERANGE if it exceeds cap. */
 SPAMM_API spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, int64_t *count);
+
+/* ---- batched products ----
+   C[p] ~ A[p] B[p] with tolerance tau[p] for p < count, every product as in
+   spamm_multiply (same precision for all; each pair of equal n and leaf; C[p] created
+   when NULL, else reused). The culls of all products run concurrently; the leaf
+   products of all tensor-core products of one leaf size run in ONE persistent launch
+   over a global work list spanning the products; the FP64 leaf kernels run per product.
+   With SPAMM_GRAPH the sequence is captured into a CUDA graph the first time a given
+   (precision, A, B, C) set is seen and replayed on later calls, the taus being read
+   from device memory; the context stream must then be a created (non-default) stream.
+   Leaf copies of the products are not produced (no SPAMM_COPY_* flags).
+   Errors: as spamm_multiply; SPAMM_EUNSUPPORTED for copy flags or graphs on the
+   default stream. */
+SPAMM_API spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *A, const spamm_tree *B,
+                                              const double *tau, int32_t count, spamm_prec prec,
+                                              int32_t flags, spamm_tree *C);
+
+/* Leaf-size autotuner: times the tree build plus the product A A at every leaf size the
+   precision supports (64 and 128 for tensor-core precisions, 16..128 for SPAMM_FP64) on
+   the n x n matrix A (device, or host with SPAMM_HOST_INPUT; SPAMM_SYMMETRIC honoured)
+   and returns the fastest in *leaf_out (and its time in *ms_out if not NULL). Results are
+   cached in the context per (ceil(log2 n), precision, decade of tau). */
+SPAMM_API spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t n, double tau,
+                                       spamm_prec prec, int32_t flags, int32_t *leaf_out,
+                                       double *ms_out);
 
 /* ---- SP2 density-matrix purification (Sec. III: TC2 purification, energy Tr(H X)) ----
    H is a symmetric n x n matrix given as host CSR (indptr[n+1], indices and data[nnz],

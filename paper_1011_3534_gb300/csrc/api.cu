@@ -92,6 +92,7 @@ void free_tree_memory(spamm_tree t) {
   dfree(t->counts);
   dfree(t->plan);
   dfree(t->items);
+  dfree(t->tc_desc_dev);
   for (int k = 0; k < 3; k++)
     if (t->ev[k]) cudaEventDestroy(t->ev[k]);
 }
@@ -240,6 +241,20 @@ spamm_status spamm_ctx_create(int device, void *cuda_stream, int32_t timing, spa
 spamm_status spamm_ctx_destroy(spamm_ctx ctx) {
   if (!ctx) return SPAMM_EINVAL;
   cudaStreamSynchronize(ctx->stream);
+  for (BatchGraph &g : ctx->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.tau_host) cudaFreeHost(g.tau_host);
+    if (g.table_host) cudaFreeHost(g.table_host);
+    if (g.tau_dev) cudaFree(g.tau_dev);
+    if (g.table_dev) cudaFree(g.table_dev);
+  }
+  for (int i = 0; i < kSideStreams; i++) {
+    if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+    if (ctx->side_ev[i]) cudaEventDestroy(ctx->side_ev[i]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
+  if (ctx->batch_dev) cudaFree(ctx->batch_dev);
   if (ctx->stage) cudaFree(ctx->stage);
   if (ctx->dev_status) cudaFree(ctx->dev_status);
   delete ctx;
@@ -366,8 +381,22 @@ spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host)
   return SPAMM_OK;
 }
 
+spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau, const double *tau_dev,
+                           spamm_prec prec, int32_t flags, spamm_tree *C);
+
 spamm_status spamm_multiply(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau,
                             spamm_prec prec, int32_t flags, spamm_tree *C) {
+  return multiply_impl(ctx, A, B, tau, nullptr, prec, flags, C);
+}
+
+}  // extern "C"
+
+// The product with tau either given on the host or read by the cull kernels from device
+// memory (tau_dev, e.g. chosen on the device by the tolerance controller).
+// Validates a product, creates or checks the output tree and its workspace, and marks it
+// as the product of (A, B, tau, prec). No device work is queued.
+spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau, spamm_prec prec,
+                             int32_t flags, spamm_tree *C) {
   if (!ctx) return SPAMM_EINVAL;
   if (!A || !B || !C) return fail(ctx, SPAMM_EINVAL, "multiply: null handle");
   if (A->n != B->n || A->b != B->b)
@@ -427,10 +456,21 @@ spamm_status spamm_multiply(spamm_ctx ctx, spamm_tree A, spamm_tree B, double ta
   Ct->prec = prec;
   Ct->tau = tau;
   Ct->stats_valid = false;
+  return SPAMM_OK;
+}
+
+spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau, const double *tau_dev,
+                           spamm_prec prec, int32_t flags, spamm_tree *C) {
+  if (!ctx) return SPAMM_EINVAL;
+  spamm_status pst = product_prepare(ctx, A, B, tau, prec, flags, C);
+  if (pst != SPAMM_OK) return pst;
+  spamm_tree Ct = *C;
+  const bool tc = prec != SPAMM_FP64;
+  const int32_t cflags = (flags & 0x01F2) | (tc ? SPAMM_INTERNAL_F32 : SPAMM_KEEP_FP64);
   cudaStream_t s = ctx->stream;
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[0], s), "event");
   int launches = 0;
-  CK(launch_cull(A, B, Ct, tau, ctx->dev_status, ctx->sm_count, s, &launches), "multiply: cull launch");
+  CK(launch_cull(A, B, Ct, tau, tau_dev, ctx->dev_status, ctx->sm_count, s, &launches), "multiply: cull launch");
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[1], s), "event");
   if (tc) {
     CK(launch_leaf_tc(A, B, Ct, prec, ctx->dev_status, ctx->sm_count, s), "multiply: leaf launch");
@@ -452,6 +492,8 @@ spamm_status spamm_multiply(spamm_ctx ctx, spamm_tree A, spamm_tree B, double ta
   ctx->launches += launches;
   return SPAMM_OK;
 }
+
+extern "C" {
 
 spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out) {
   if (!C) return SPAMM_EINVAL;

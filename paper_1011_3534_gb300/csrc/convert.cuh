@@ -193,3 +193,19 @@ __device__ __forceinline__ uint32_t f32_fast(uint32_t h, uint32_t l) {
   const uint32_t uh = (uint32_t)(u >> 32);
   return (uh & 0x80000000u) | ((((uh >> 20) & 0x7FFu) - 896u) << 23) | ((uint32_t)(u >> 29) & 0x7FFFFFu);
 }
+
+// Out-of-line rounding for the rare inputs outside a fast path's range, so the fast
+// paths stay short branches instead of predicated copies of the general code.
+static __device__ __noinline__ uint32_t slow_round_bits(uint32_t h, uint32_t l, int p, int emin) {
+  return round_f64bits(((uint64_t)h << 32) | l, p, emin).bits;
+}
+
+static __device__ __noinline__ uint32_t slow_fp16_bits(uint32_t h, uint32_t l) {
+  return fp16_from_f32bits(round_f64bits(((uint64_t)h << 32) | l, 11, -14).bits);
+}
+
+// Exact FP32 value of an integer below 2^23, on the FP32 pipe: the integer is placed in
+// the significand of 2^23 and 2^23 is subtracted.
+__device__ __forceinline__ float u23_to_float(uint32_t m) {
+  return __uint_as_float(0x4B000000u | m) - 8388608.0f;
+}

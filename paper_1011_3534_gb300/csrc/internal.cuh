@@ -4,7 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <list>
+#include <map>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/spamm.h"
 
@@ -18,11 +22,25 @@ enum : uint32_t {
 // Internal tree flag: the product tree keeps an FP32 master (tensor-core precisions).
 #define SPAMM_INTERNAL_F32 0x10000
 
+// Bytes reserved in a product tree for its tensor-core launch descriptor (host image).
+constexpr size_t kTcDescBytes = 1024;
+
 // Bounded waits give up after this many nanoseconds of %globaltimer.
 constexpr unsigned long long kSpinLimitNs = 2000000000ull;
 
 // Maximum entries of one tier's triple list (uint32 offsets, 31 bits).
 constexpr int64_t kEntryCap = int64_t(1) << 30;
+
+constexpr int kSideStreams = 8;   // concurrent per-product work of a batch
+
+struct BatchGraph {                // a captured batched product, replayed with new taus
+  std::vector<uintptr_t> key;      // precision and the trees it was captured for
+  int count = 0;
+  double *tau_host = nullptr, *tau_dev = nullptr;
+  void *table_host = nullptr, *table_dev = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+};
 
 struct spamm_ctx_s {
   int device = 0;
@@ -36,6 +54,14 @@ struct spamm_ctx_s {
   void *stage = nullptr;
   size_t stage_bytes = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // batched products
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t side_ev[kSideStreams] = {};
+  cudaEvent_t fork_ev = nullptr;
+  void *batch_host = nullptr, *batch_dev = nullptr;   // descriptor tables (pinned / device)
+  size_t batch_cap = 0;
+  std::list<BatchGraph> graphs;
+  std::map<int64_t, std::pair<int, double>> tuned;     // autotuner cache: leaf, ms
 };
 
 // Leaf copies a tree can hold. Index into spamm_tree_s::copy.
@@ -112,6 +138,9 @@ struct spamm_tree_s {
   int64_t cap_plan = 0;
   uint2 *items = nullptr;
   int64_t cap_items = 0;
+  void *tc_desc_dev = nullptr;            // device copy of the leaf kernel's descriptor
+  alignas(64) unsigned char tc_desc_host[kTcDescBytes] = {};
+  bool tc_desc_valid = false;
   spamm_stats_t host_stats{};
   bool stats_valid = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -123,7 +152,7 @@ __host__ __device__ inline int64_t level_offset(int l) { return ((int64_t(1) << 
 cudaError_t launch_tree_build(spamm_tree t, const double *A, cudaStream_t s);
 cudaError_t launch_pyramid(spamm_tree t, cudaStream_t s);
 cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s);
-cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau,
+cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, const double *tau_dev,
                         uint32_t *dev_status, int sm_count, cudaStream_t s, int *launches);
 cudaError_t launch_leaf_f64(spamm_tree A, spamm_tree B, spamm_tree C, uint32_t *dev_status,
                             int sm_count, cudaStream_t s);
@@ -142,3 +171,9 @@ cudaError_t sp2_trace_only(spamm_tree X, int idx, void *rec, cudaStream_t s);
 cudaError_t sp2_energy(spamm_tree X, int64_t n, const int64_t *indptr, const int64_t *indices,
                        const double *data, double *partial, void *rec, cudaStream_t s);
 void sp2_read_record(const void *host_rec, int steps, spamm_sp2_result *out);
+size_t tc_desc_bytes();
+cudaError_t launch_leaf_tc_batch(const spamm_tree *A, const spamm_tree *B, const spamm_tree *C, int count,
+                                 int prec, void *host_table, void *dev_table, uint32_t *dev_status, int sm_count,
+                                 cudaStream_t s);
+spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau, spamm_prec prec,
+                             int32_t flags, spamm_tree *C);

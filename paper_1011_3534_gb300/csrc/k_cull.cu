@@ -83,6 +83,7 @@ struct CullArgs {
   const double *nA, *nB;    // norms (not squared) of tier l, 2^l x 2^l
   int32_t l, D, nb, NB, final_tier;
   double tau;
+  const double *tau_dev;         // when set, tau is read from device memory at launch
   const uint32_t *pgij, *pgstart, *pglen;
   const uint16_t *pK;
   const unsigned long long *p_ngroups;
@@ -129,7 +130,7 @@ __device__ __forceinline__ int passes64(uint32_t m, int e, uint32_t (&rm)[2], ui
 
 // Children of entry (I, J, K) tested at tier l: survival bits, test count, and the
 // culled norm products summed in a fixed order.
-__device__ __forceinline__ uint32_t child_bits(const CullArgs &a, uint32_t I, uint32_t J,
+__device__ __forceinline__ uint32_t child_bits(const CullArgs &a, double tau, uint32_t I, uint32_t J,
                                                uint32_t K, int &tests, double &bound) {
   uint32_t bits = 0;
 #pragma unroll
@@ -147,7 +148,7 @@ __device__ __forceinline__ uint32_t child_bits(const CullArgs &a, uint32_t I, ui
         if (j >= (uint32_t)a.D) continue;
         const double p = na * a.nB[(int64_t)k * a.D + j];
         tests++;
-        if (p < a.tau) bound += p;
+        if (p < tau) bound += p;
         else bits |= 1u << (((ai * 2 + c) * 2) + e);
       }
     }
@@ -259,6 +260,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
   __shared__ unsigned int s_gix[kWarps * 4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long ngroups = *a.p_ngroups;
+  const double tau = a.tau_dev ? *a.tau_dev : a.tau;
 
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
       uint32_t bits = 0;
       if (p < len) {
         const uint32_t K = a.pK[start + p];
-        bits = child_bits(a, I, J, K, tests, bound);
+        bits = child_bits(a, tau, I, J, K, tests, bound);
         if (a.final_tier) a.mask[start + p] = (uint8_t)bits;
       }
 #pragma unroll
@@ -374,7 +376,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
       double dummy_b = 0.0;
       if (p < len) {
         K = a.pK[start + p];
-        bits = child_bits(a, I, J, K, dummy_t, dummy_b);
+        bits = child_bits(a, tau, I, J, K, dummy_t, dummy_b);
       }
 #pragma unroll
       for (int q = 0; q < 4; q++) {
@@ -447,7 +449,7 @@ __global__ void __launch_bounds__(256) k_bound_reduce(const double *part, const 
 // list l, at most 4^(l-1) of them, 1 for l = 0).
 static int64_t bound_groups_cap(int l) { return l == 0 ? 1 : (int64_t(1) << (2 * (l - 1))); }
 
-cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau,
+cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, const double *tau_dev,
                         uint32_t *dev_status, int sm_count, cudaStream_t s, int *launches) {
   const int kmax = A->kmax;
   DevCounts *cnt = C->counts;
@@ -469,6 +471,7 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau,
     a.NB = A->NB;
     a.final_tier = (l == kmax);
     a.tau = tau;
+    a.tau_dev = tau_dev;
     const TierList &par = C->tiers[l];
     a.pgij = par.gij;
     a.pgstart = par.gstart;

@@ -35,29 +35,32 @@ constexpr uint32_t kTmemCols = 512;   // four 128-column FP32 accumulators
 constexpr int kAcc = 4;
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024;
 
-struct TcArgs {
-  const uint32_t *gij, *gstart, *glen;
-  const uint16_t *K;
-  const uint8_t *mask;
-  const unsigned long long *ngroups;
-  int64_t cap_entries;
-  const uint8_t *nzA, *nzB;
+// One product of a launch. The table lives in device memory (64-byte aligned for the
+// tensor maps); a single product and a batch use the same kernel.
+struct __align__(64) ProdDesc {
+  CUtensorMap mA, mB, mAlo, mBlo;          // leaf copies: A rows, B (rows if symmetric, else
+                                           // transposed leaves), and the split-BF16 lows
+  const uint2 *items;                      // per item: {first pass, passes | touched << 24}
+  const int4 *plan;                        // per pass: leaf coordinates of the four boxes
+  int64_t cap_plan;
+  const uint32_t *gij;                     // groups of the last tier list: (I << 16) | J
+  const unsigned long long *ngroups;       // number of those groups (device)
+  float *C;                                // FP32 tiles of the product
+  uint8_t *nzC;
+  double *leaf_norm2C;
+  unsigned long long *mma_stages;
   int32_t nb, NB;
-  int32_t bsym;          // B leaf (k, j) is read as leaf (j, k) of a symmetric tree
+};
+
+struct TcCommon {
   uint32_t idesc;
   int32_t chunks;        // 128-byte K chunks per leaf
   int32_t chunk_elems;   // elements per chunk
   int32_t nsrc;          // 1, or 3 for the split BF16 products (hi hi, hi lo, lo hi)
-  float *C;
-  uint8_t *nzC;
-  double *leaf_norm2C;
-  unsigned long long *mma_stages;
   uint32_t *status;
-  const int4 *plan;              // per pass: leaf coordinates of the four boxes
-  const uint2 *items;            // per item: {first pass, passes | touched << 24}
-  int64_t cap_plan;
-  const unsigned long long *nitems_dev;   // groups of the last tier list (items: x1 or x4)
 };
+
+constexpr int kMaxProd = 1024;   // products per launch
 
 __device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
   const float s = h + bh;
@@ -68,39 +71,30 @@ __device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
   l = err - (h - s);
 }
 
-struct Item {
-  uint32_t I, J, start, len;
-  int q;   // leaf 128: output quadrant a * 2 + c of the group
-};
-
-template <int LEAF>
-__device__ __forceinline__ Item decode(const TcArgs &p, unsigned long long item) {
-  Item it;
-  const unsigned long long g = LEAF == 64 ? item : (item >> 2);
-  it.q = LEAF == 64 ? 0 : (int)(item & 3);
-  const uint32_t ij = p.gij[g];
-  it.I = ij >> 16;
-  it.J = ij & 0xFFFFu;
-  it.start = p.gstart[g];
-  it.len = p.glen[g];
-  if ((int64_t)it.start + it.len > p.cap_entries) it.len = 0;
-  return it;
+// Product holding global item g: offsets s_off[0..nprod] in shared memory.
+__device__ __forceinline__ int find_prod(const unsigned long long *s_off, int nprod, unsigned long long g) {
+  int lo = 0, hi = nprod;   // s_off[lo] <= g < s_off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (s_off[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
 }
 
 template <int LEAF, bool TF32>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_leaf_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-              const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo,
-              TcArgs p) {
+    k_leaf_tc(const ProdDesc *__restrict__ prods, int nprod, TcCommon cm) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[kAcc], acce[kAcc];
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   __shared__ double s_norm[4][2];
-  __shared__ int4 s_desc[32];        // producer: the chunk of passes being issued
+  __shared__ int4 s_desc[32];                    // producer: the chunk of passes being issued
+  __shared__ unsigned long long s_off[kMaxProd + 1];   // first global item of each product
   constexpr int RA = LEAF == 64 ? 2 : 1;        // A leaves stacked along M
   constexpr int RC = LEAF == 64 ? 2 : 1;        // B leaves stacked along N
   constexpr uint32_t kBox = LEAF * 128;         // bytes of one leaf box (LEAF rows x 128 B)
+  constexpr unsigned long long kPer = LEAF == 64 ? 1ull : 4ull;   // items per group
 
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -116,62 +110,77 @@ __global__ void __launch_bounds__(kThreads, 1)
     s_abort = 0;
     mbar_fence_init();
   }
+  for (int q = threadIdx.x; q < nprod; q += blockDim.x) s_off[q + 1] = kPer * (*prods[q].ngroups);
   if (warp == 1) tmem_alloc(&s_tmem, kTmemCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (threadIdx.x == 0) {   // item offsets of the products (nprod <= kMaxProd)
+    s_off[0] = 0;
+    for (int q = 1; q <= nprod; q++) s_off[q] += s_off[q - 1];
+  }
+  __syncthreads();
   const uint32_t tmem = s_tmem;
-  const unsigned long long nitems = (LEAF == 64 ? 1ull : 4ull) * (*p.nitems_dev);
+  const unsigned long long nitems = s_off[nprod];
   const unsigned long long my_items =
       nitems > blockIdx.x ? (nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0ull;
+  // item t of this CTA is global item blockIdx.x + t * gridDim.x; every role reads the
+  // metadata of 32 of its items at a time (lane l: item t0 + l)
+  auto item_meta = [&](unsigned long long t, int &prod, unsigned long long &local) -> uint2 {
+    const unsigned long long g = blockIdx.x + t * gridDim.x;
+    prod = find_prod(s_off, nprod, g);
+    local = g - s_off[prod];
+    return prods[prod].items[local];
+  };
 
   if (warp == 0) {
     // ---------------- TMA producer (warp 0) ----------------
-    // Item metadata is loaded 32 items at a time; each item's passes are loaded 32 at a
-    // time, the next chunk while lane 0 issues the current one.
-    if (lane == 0) {
-      tma_prefetch_desc(&mA);
-      tma_prefetch_desc(&mB);
-      if (p.nsrc == 3) {
-        tma_prefetch_desc(&mAlo);
-        tma_prefetch_desc(&mBlo);
-      }
+    // Each item's passes are loaded 32 at a time, the next chunk while lane 0 issues
+    // the current one.
+    if (lane == 0 && nprod == 1) {
+      tma_prefetch_desc(&prods[0].mA);
+      tma_prefetch_desc(&prods[0].mB);
     }
     int stage = 0;
     uint32_t phase = 0;
     for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
-      const unsigned long long mine = t0 + lane;
-      const uint2 meta = mine < my_items ? p.items[blockIdx.x + mine * gridDim.x] : make_uint2(0u, 0u);
+      int prod = 0;
+      unsigned long long local = 0;
+      const uint2 meta = t0 + lane < my_items ? item_meta(t0 + lane, prod, local) : make_uint2(0u, 0u);
       const int nt = (int)min(32ull, my_items - t0);
       for (int ti = 0; ti < nt; ti++) {
+        const int pr = __shfl_sync(0xffffffffu, prod, ti);
+        const ProdDesc &P = prods[pr];
         const uint32_t first = __shfl_sync(0xffffffffu, meta.x, ti);
         uint32_t np = __shfl_sync(0xffffffffu, meta.y, ti) & 0xFFFFFFu;
-        np = (int64_t)first >= p.cap_plan ? 0u : ((int64_t)first + np > p.cap_plan ? (uint32_t)(p.cap_plan - first) : np);   // overflowed plan
+        const int64_t cap = P.cap_plan;
+        np = (int64_t)first >= cap ? 0u : ((int64_t)first + np > cap ? (uint32_t)(cap - first) : np);
+        const int4 *plan = P.plan;
         int4 cur = make_int4(0, 0, 0, 0);
-        if ((uint32_t)lane < np) cur = p.plan[(int64_t)first + lane];
+        if ((uint32_t)lane < np) cur = plan[(int64_t)first + lane];
         for (uint32_t c0 = 0; c0 < np; c0 += 32) {
           s_desc[lane] = cur;
           __syncwarp();
-          if (c0 + 32 < np && c0 + 32 + lane < np) cur = p.plan[(int64_t)first + c0 + 32 + lane];
+          if (c0 + 32 < np && c0 + 32 + lane < np) cur = plan[(int64_t)first + c0 + 32 + lane];
           if (lane == 0) {
             const int nl = (int)min(32u, np - c0);
             for (int l = 0; l < nl && !s_abort; l++) {
               const int4 d = s_desc[l];
-              for (int src = 0; src < p.nsrc && !s_abort; src++) {
-                const CUtensorMap *ma = src == 2 ? &mAlo : &mA;
-                const CUtensorMap *mb = src == 1 ? &mBlo : &mB;
-                for (int ch = 0; ch < p.chunks; ch++) {
+              for (int src = 0; src < cm.nsrc && !s_abort; src++) {
+                const CUtensorMap *ma = src == 2 ? &P.mAlo : &P.mA;
+                const CUtensorMap *mb = src == 1 ? &P.mBlo : &P.mB;
+                for (int ch = 0; ch < cm.chunks; ch++) {
                   if (!mbar_wait(&empty[stage], phase ^ 1u, &s_abort)) {
                     s_abort = 1;
-                    flag_error(p.status, DEV_TIMEOUT);
+                    flag_error(cm.status, DEV_TIMEOUT);
                     break;
                   }
                   mbar_expect_tx(&full[stage], kStageBytes);
                   const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
-                  tma_load_3d(sa, ma, &full[stage], ch * p.chunk_elems, 0, d.x);
-                  if (RA == 2) tma_load_3d(sa + kBox, ma, &full[stage], ch * p.chunk_elems, 0, d.y);
-                  tma_load_3d(sb, mb, &full[stage], ch * p.chunk_elems, 0, d.z);
-                  if (RC == 2) tma_load_3d(sb + kBox, mb, &full[stage], ch * p.chunk_elems, 0, d.w);
+                  tma_load_3d(sa, ma, &full[stage], ch * cm.chunk_elems, 0, d.x);
+                  if (RA == 2) tma_load_3d(sa + kBox, ma, &full[stage], ch * cm.chunk_elems, 0, d.y);
+                  tma_load_3d(sb, mb, &full[stage], ch * cm.chunk_elems, 0, d.z);
+                  if (RC == 2) tma_load_3d(sb + kBox, mb, &full[stage], ch * cm.chunk_elems, 0, d.w);
                   if (++stage == kStages) {
                     stage = 0;
                     phase ^= 1u;
@@ -191,19 +200,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     int acc = 0;
     uint32_t acc_phase = 0;
     unsigned long long nst = 0;
+    int last_prod = -1;
     for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
-      const unsigned long long mine = t0 + lane;
-      const uint2 meta = mine < my_items ? p.items[blockIdx.x + mine * gridDim.x] : make_uint2(0u, 0u);
+      int prod = 0;
+      unsigned long long local = 0;
+      const uint2 meta = t0 + lane < my_items ? item_meta(t0 + lane, prod, local) : make_uint2(0u, 0u);
       const int nt = (int)min(32ull, my_items - t0);
       for (int ti = 0; ti < nt; ti++) {
+        const int pr = __shfl_sync(0xffffffffu, prod, ti);
         const uint32_t first = __shfl_sync(0xffffffffu, meta.x, ti);
         uint32_t np = __shfl_sync(0xffffffffu, meta.y, ti) & 0xFFFFFFu;
-        np = (int64_t)first >= p.cap_plan ? 0u : ((int64_t)first + np > p.cap_plan ? (uint32_t)(p.cap_plan - first) : np);
-        const int total = (int)np * p.nsrc * p.chunks;
+        const int64_t cap = prods[pr].cap_plan;
+        np = (int64_t)first >= cap ? 0u : ((int64_t)first + np > cap ? (uint32_t)(cap - first) : np);
+        const int total = (int)np * cm.nsrc * cm.chunks;
+        if (lane == 0 && pr != last_prod) {
+          // stage counts are kept per product: flush this CTA's count of the previous one
+          if (last_prod >= 0 && nst) atomicAdd(prods[last_prod].mma_stages, nst);
+          nst = 0;
+          last_prod = pr;
+        }
         if (lane == 0 && !s_abort) {
           if (!mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort)) {
             s_abort = 1;
-            flag_error(p.status, DEV_TIMEOUT);
+            flag_error(cm.status, DEV_TIMEOUT);
           } else {
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)acc * 128u;
@@ -211,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int t = 0; t < total; t++) {
               if (!mbar_wait(&full[stage], phase, &s_abort)) {
                 s_abort = 1;
-                flag_error(p.status, DEV_TIMEOUT);
+                flag_error(cm.status, DEV_TIMEOUT);
                 break;
               }
               tc_fence_after();
@@ -219,8 +238,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int kk = 0; kk < 4; kk++) {
                 const uint64_t da = desc_sw128(sa + kk * 32), db = desc_sw128(sb + kk * 32);
-                if (TF32) mma_tf32(d, da, db, p.idesc, accum);
-                else mma_f16(d, da, db, p.idesc, accum);
+                if (TF32) mma_tf32(d, da, db, cm.idesc, accum);
+                else mma_f16(d, da, db, cm.idesc, accum);
                 accum = 1;
               }
               mma_commit(&empty[stage]);
@@ -240,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    if (lane == 0 && nst) atomicAdd(p.mma_stages, nst);
+    if (lane == 0 && last_prod >= 0 && nst) atomicAdd(prods[last_prod].mma_stages, nst);
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
     const int slice = warp & 3;            // TMEM lanes 32 * slice .. + 31
@@ -248,95 +267,98 @@ __global__ void __launch_bounds__(kThreads, 1)
     int acc = 0;
     uint32_t acc_phase = 0;
     for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
-     const unsigned long long mine = t0 + lane;
-     const unsigned long long my_item = blockIdx.x + mine * gridDim.x;
-     const uint2 meta = mine < my_items ? p.items[my_item] : make_uint2(0u, 0u);
-     const int nt = (int)min(32ull, my_items - t0);
-     for (int ti = 0; ti < nt; ti++) {
-      const unsigned long long item = blockIdx.x + (t0 + ti) * gridDim.x;
-      const Item it = decode<LEAF>(p, item);
-      uint32_t touched = __shfl_sync(0xffffffffu, meta.y, ti) >> 24;   // output quadrants with a product
-      if (LEAF == 128) touched = touched ? (1u << it.q) : 0u;
-      bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
-      if (!ok) {
-        s_abort = 1;
-        flag_error(p.status, DEV_TIMEOUT);
-      }
-      ok = __all_sync(0xffffffffu, ok);   // warp-uniform: the TMEM loads are warp-collective
-      if (!ok) touched = 0;
-      tc_fence_after();
-      const int a = LEAF == 64 ? row / 64 : (it.q >> 1);
-      const int r = LEAF == 64 ? row % 64 : row;
-      const int i = (int)(2 * it.I) + a;
-      // squared norms in double-float: f^2 = pp + e exactly, TwoSum accumulation
-      float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
+      int prod = 0;
+      unsigned long long local = 0;
+      const uint2 meta = t0 + lane < my_items ? item_meta(t0 + lane, prod, local) : make_uint2(0u, 0u);
+      const uint32_t ij_l = t0 + lane < my_items ? prods[prod].gij[LEAF == 64 ? local : (local >> 2)] : 0u;
+      const int nt = (int)min(32ull, my_items - t0);
+      for (int ti = 0; ti < nt; ti++) {
+        const int pr = __shfl_sync(0xffffffffu, prod, ti);
+        const ProdDesc &P = prods[pr];
+        const uint32_t ij = __shfl_sync(0xffffffffu, ij_l, ti);
+        const int qd = LEAF == 64 ? 0 : (int)(__shfl_sync(0xffffffffu, (uint32_t)local, ti) & 3u);
+        const uint32_t I = ij >> 16, J = ij & 0xFFFFu;
+        uint32_t touched = __shfl_sync(0xffffffffu, meta.y, ti) >> 24;   // quadrants with a product
+        if (LEAF == 128) touched = touched ? (1u << qd) : 0u;
+        bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
+        if (!ok) {
+          s_abort = 1;
+          flag_error(cm.status, DEV_TIMEOUT);
+        }
+        ok = __all_sync(0xffffffffu, ok);   // warp-uniform: the TMEM loads are warp-collective
+        if (!ok) touched = 0;
+        tc_fence_after();
+        const int a = LEAF == 64 ? row / 64 : (qd >> 1);
+        const int r = LEAF == 64 ? row % 64 : row;
+        const int i = (int)(2 * I) + a;
+        // squared norms in double-float: f^2 = pp + e exactly, TwoSum accumulation
+        float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
 #pragma unroll
-      for (int cc = 0; cc < RC; cc++) {
-        const int c = LEAF == 64 ? cc : (it.q & 1);
-        const int q = a * 2 + c;
-        const int j = (int)(2 * it.J) + c;
-        if (!((touched >> q) & 1u) || i >= p.nb || j >= p.nb) continue;   // warp-uniform
-        float *dst = p.C + (((int64_t)i * p.nb + j) * LEAF + r) * LEAF;
+        for (int cc = 0; cc < RC; cc++) {
+          const int c = LEAF == 64 ? cc : (qd & 1);
+          const int q = a * 2 + c;
+          const int j = (int)(2 * J) + c;
+          if (!((touched >> q) & 1u) || i >= P.nb || j >= P.nb) continue;   // warp-uniform
+          float *dst = P.C + (((int64_t)i * P.nb + j) * LEAF + r) * LEAF;
 #pragma unroll
-        for (int h = 0; h < LEAF / 32; h++) {
-          uint32_t v[32];
-          const uint32_t col = (uint32_t)acc * 128u + (uint32_t)(cc * 64 + h * 32);
-          tmem_ld32(tmem + ((uint32_t)(32 * slice) << 16) + col, v);
+          for (int h = 0; h < LEAF / 32; h++) {
+            uint32_t v[32];
+            const uint32_t col = (uint32_t)acc * 128u + (uint32_t)(cc * 64 + h * 32);
+            tmem_ld32(tmem + ((uint32_t)(32 * slice) << 16) + col, v);
 #pragma unroll
-          for (int x = 0; x < 32; x += 4) {
-            float4 f = make_float4(__uint_as_float(v[x]), __uint_as_float(v[x + 1]),
-                                   __uint_as_float(v[x + 2]), __uint_as_float(v[x + 3]));
-            *reinterpret_cast<float4 *>(dst + h * 32 + x) = f;
+            for (int x = 0; x < 32; x += 4) {
+              float4 f = make_float4(__uint_as_float(v[x]), __uint_as_float(v[x + 1]),
+                                     __uint_as_float(v[x + 2]), __uint_as_float(v[x + 3]));
+              *reinterpret_cast<float4 *>(dst + h * 32 + x) = f;
 #pragma unroll
-            for (int z = 0; z < 4; z++) {
-              const float fv = __uint_as_float(v[x + z]);
-              const float pp = fv * fv;
-              const float e = fmaf(fv, fv, -pp);
-              const float t = sh[cc] + pp;
-              const float bb = t - sh[cc];
-              sl[cc] += ((sh[cc] - (t - bb)) + (pp - bb)) + e;
-              sh[cc] = t;
+              for (int z = 0; z < 4; z++) {
+                const float fv = __uint_as_float(v[x + z]);
+                const float pp = fv * fv;
+                const float e = fmaf(fv, fv, -pp);
+                const float t = sh[cc] + pp;
+                const float bb = t - sh[cc];
+                sl[cc] += ((sh[cc] - (t - bb)) + (pp - bb)) + e;
+                sh[cc] = t;
+              }
             }
           }
         }
-      }
-      tc_fence_before();
-      mbar_arrive(&acce[acc]);
-      // squared Frobenius norms of the written blocks: rows -> warp -> fixed pair order
+        tc_fence_before();
+        mbar_arrive(&acce[acc]);
+        // squared Frobenius norms of the written blocks: rows -> warp -> fixed pair order
 #pragma unroll
-      for (int cc = 0; cc < RC; cc++) {
-        float H = sh[cc], L = sl[cc];
+        for (int cc = 0; cc < RC; cc++) {
+          float H = sh[cc], L = sl[cc];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          const float h2 = __shfl_xor_sync(0xffffffffu, H, off), l2 = __shfl_xor_sync(0xffffffffu, L, off);
-          df_add(H, L, h2, l2);
-        }
-        if (lane == 0) s_norm[slice][cc] = (double)H + (double)L;
-      }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (warp == 2 && lane < 4) {
-        if (LEAF == 64) {
-          const int aa = lane >> 1, c = lane & 1;
-          const int ii = (int)(2 * it.I) + aa, jj = (int)(2 * it.J) + c;
-          if (((touched >> (aa * 2 + c)) & 1u) && ii < p.nb && jj < p.nb) {
-            p.leaf_norm2C[(int64_t)ii * p.NB + jj] = s_norm[2 * aa][c] + s_norm[2 * aa + 1][c];
-            p.nzC[(int64_t)ii * p.NB + jj] = 1;
+          for (int off = 16; off > 0; off >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, H, off), l2 = __shfl_xor_sync(0xffffffffu, L, off);
+            df_add(H, L, h2, l2);
           }
-        } else if (lane == 0) {
-          const int jj = (int)(2 * it.J) + (it.q & 1);
-          if (((touched >> it.q) & 1u) && i < p.nb && jj < p.nb) {
-            p.leaf_norm2C[(int64_t)i * p.NB + jj] =
-                ((s_norm[0][0] + s_norm[1][0]) + s_norm[2][0]) + s_norm[3][0];
-            p.nzC[(int64_t)i * p.NB + jj] = 1;
+          if (lane == 0) s_norm[slice][cc] = (double)H + (double)L;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (warp == 2 && lane < 4) {
+          if (LEAF == 64) {
+            const int aa = lane >> 1, c = lane & 1;
+            const int ii = (int)(2 * I) + aa, jj = (int)(2 * J) + c;
+            if (((touched >> (aa * 2 + c)) & 1u) && ii < P.nb && jj < P.nb) {
+              P.leaf_norm2C[(int64_t)ii * P.NB + jj] = s_norm[2 * aa][c] + s_norm[2 * aa + 1][c];
+              P.nzC[(int64_t)ii * P.NB + jj] = 1;
+            }
+          } else if (lane == 0) {
+            const int jj = (int)(2 * J) + (qd & 1);
+            if (((touched >> qd) & 1u) && i < P.nb && jj < P.nb) {
+              P.leaf_norm2C[(int64_t)i * P.NB + jj] = ((s_norm[0][0] + s_norm[1][0]) + s_norm[2][0]) + s_norm[3][0];
+              P.nzC[(int64_t)i * P.NB + jj] = 1;
+            }
           }
         }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (++acc == kAcc) {
+          acc = 0;
+          acc_phase ^= 1u;
+        }
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (++acc == kAcc) {
-        acc = 0;
-        acc_phase ^= 1u;
-      }
-     }
     }
   }
   tc_fence_before();
@@ -383,66 +405,102 @@ bool make_map(CUtensorMap *m, const void *data, int elem, int b, int nb) {
 }
 
 template <int LEAF, bool TF32>
-cudaError_t run(const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &alo, const CUtensorMap &blo,
-                const TcArgs &p, int sm_count, cudaStream_t s) {
+cudaError_t run(const ProdDesc *table, int nprod, const TcCommon &cm, int sm_count, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kSmemBytes);
   if (e != cudaSuccess) return e;
-  k_leaf_tc<LEAF, TF32><<<sm_count, kThreads, kSmemBytes, s>>>(a, b, alo, blo, p);
+  k_leaf_tc<LEAF, TF32><<<sm_count, kThreads, kSmemBytes, s>>>(table, nprod, cm);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-cudaError_t launch_leaf_tc(spamm_tree A, spamm_tree B, spamm_tree C, int prec, uint32_t *dev_status,
-                           int sm_count, cudaStream_t s) {
+// Host image of one product's descriptor.
+bool fill_desc(ProdDesc *d, spamm_tree A, spamm_tree B, spamm_tree C, int prec) {
   const bool tf32 = prec == SPAMM_TF32;
   const int elem = tf32 ? 4 : 2;
   const int row = tf32 ? CK_TF32 : prec == SPAMM_FP16 ? CK_FP16 : CK_BF16;
   const bool bsym = (B->flags & SPAMM_SYMMETRIC) != 0;
   const int brow = bsym ? row : row + 1;
   const int blo = bsym ? CK_BF16LO : CK_BF16LO_T;
-  const int b = A->b;
-  CUtensorMap ma, mb, malo, mblo;
-  if (!make_map(&ma, A->copy[row], elem, b, A->nb) || !make_map(&mb, B->copy[brow], elem, b, B->nb))
-    return cudaErrorInvalidValue;
+  memset(d, 0, sizeof *d);
+  if (!make_map(&d->mA, A->copy[row], elem, A->b, A->nb) || !make_map(&d->mB, B->copy[brow], elem, B->b, B->nb))
+    return false;
   if (prec == SPAMM_BF16X3) {
-    if (!make_map(&malo, A->copy[CK_BF16LO], elem, b, A->nb) || !make_map(&mblo, B->copy[blo], elem, b, B->nb))
-      return cudaErrorInvalidValue;
+    if (!make_map(&d->mAlo, A->copy[CK_BF16LO], elem, A->b, A->nb) || !make_map(&d->mBlo, B->copy[blo], elem, B->b, B->nb))
+      return false;
   } else {
-    malo = ma;
-    mblo = mb;
+    d->mAlo = d->mA;
+    d->mBlo = d->mB;
   }
-  const TierList &par = C->tiers[C->kmax];
-  TcArgs p{};
-  p.gij = par.gij;
-  p.gstart = par.gstart;
-  p.glen = par.glen;
-  p.K = par.K;
-  p.mask = C->mask;
-  p.ngroups = &C->counts->ngroups[C->kmax];
-  p.cap_entries = par.cap_entries;
-  p.nzA = A->nz;
-  p.nzB = B->nz;
-  p.nb = C->nb;
-  p.NB = C->NB;
-  p.bsym = bsym;
-  p.idesc = make_idesc(tf32 ? kFmtTF32 : prec == SPAMM_FP16 ? kFmtF16 : kFmtBF16, 128, 128);
-  p.chunks = b * elem / 128;
-  p.chunk_elems = 128 / elem;
-  p.nsrc = prec == SPAMM_BF16X3 ? 3 : 1;
-  p.C = (float *)C->copy[CK_F32];
-  p.nzC = C->nz;
-  p.leaf_norm2C = C->norm2 + level_offset(C->kmax);
-  p.mma_stages = &C->counts->mma_tiles;
-  p.status = dev_status;
-  p.plan = C->plan;
-  p.items = C->items;
-  p.cap_plan = C->cap_plan;
-  p.nitems_dev = &C->counts->ngroups[C->kmax];
-  if (b == 64) return tf32 ? run<64, true>(ma, mb, malo, mblo, p, sm_count, s)
-                           : run<64, false>(ma, mb, malo, mblo, p, sm_count, s);
-  if (b == 128) return tf32 ? run<128, true>(ma, mb, malo, mblo, p, sm_count, s)
-                            : run<128, false>(ma, mb, malo, mblo, p, sm_count, s);
+  d->items = C->items;
+  d->plan = C->plan;
+  d->cap_plan = C->cap_plan;
+  d->gij = C->tiers[C->kmax].gij;
+  d->ngroups = &C->counts->ngroups[C->kmax];
+  d->C = (float *)C->copy[CK_F32];
+  d->nzC = C->nz;
+  d->leaf_norm2C = C->norm2 + level_offset(C->kmax);
+  d->mma_stages = &C->counts->mma_tiles;
+  d->nb = C->nb;
+  d->NB = C->NB;
+  return true;
+}
+
+TcCommon common_of(int prec, int b, uint32_t *status) {
+  const bool tf32 = prec == SPAMM_TF32;
+  const int elem = tf32 ? 4 : 2;
+  TcCommon cm{};
+  cm.idesc = make_idesc(tf32 ? kFmtTF32 : prec == SPAMM_FP16 ? kFmtF16 : kFmtBF16, 128, 128);
+  cm.chunks = b * elem / 128;
+  cm.chunk_elems = 128 / elem;
+  cm.nsrc = prec == SPAMM_BF16X3 ? 3 : 1;
+  cm.status = status;
+  return cm;
+}
+
+cudaError_t run_table(const ProdDesc *table, int nprod, int b, int prec, uint32_t *status, int sm_count,
+                      cudaStream_t s) {
+  const TcCommon cm = common_of(prec, b, status);
+  const bool tf32 = prec == SPAMM_TF32;
+  if (b == 64) return tf32 ? run<64, true>(table, nprod, cm, sm_count, s) : run<64, false>(table, nprod, cm, sm_count, s);
+  if (b == 128) return tf32 ? run<128, true>(table, nprod, cm, sm_count, s) : run<128, false>(table, nprod, cm, sm_count, s);
   return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+static_assert(sizeof(ProdDesc) <= kTcDescBytes, "descriptor storage of a tree");
+
+size_t tc_desc_bytes() { return sizeof(ProdDesc); }
+
+cudaError_t launch_leaf_tc(spamm_tree A, spamm_tree B, spamm_tree C, int prec, uint32_t *dev_status,
+                           int sm_count, cudaStream_t s) {
+  ProdDesc d;
+  if (!fill_desc(&d, A, B, C, prec)) return cudaErrorInvalidValue;
+  if (!C->tc_desc_dev) {
+    cudaError_t e = cudaMalloc(&C->tc_desc_dev, sizeof(ProdDesc));
+    if (e != cudaSuccess) return e;
+    C->tc_desc_valid = false;
+  }
+  // upload only when the descriptor changed (other operands or a new tree)
+  if (!C->tc_desc_valid || memcmp(C->tc_desc_host, &d, sizeof d) != 0) {
+    memcpy(C->tc_desc_host, &d, sizeof d);
+    cudaError_t e = cudaMemcpyAsync(C->tc_desc_dev, C->tc_desc_host, sizeof d, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    C->tc_desc_valid = true;
+  }
+  return run_table((const ProdDesc *)C->tc_desc_dev, 1, C->b, prec, dev_status, sm_count, s);
+}
+
+// One launch over several products (same leaf size and precision): host descriptors
+// are written to `host_table` (pinned, count entries) and copied to `dev_table`.
+cudaError_t launch_leaf_tc_batch(const spamm_tree *A, const spamm_tree *B, const spamm_tree *C, int count,
+                                 int prec, void *host_table, void *dev_table, uint32_t *dev_status, int sm_count,
+                                 cudaStream_t s) {
+  if (count < 1 || count > kMaxProd) return cudaErrorInvalidValue;
+  ProdDesc *h = (ProdDesc *)host_table;
+  for (int q = 0; q < count; q++)
+    if (!fill_desc(&h[q], A[q], B[q], C[q], prec)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(dev_table, h, sizeof(ProdDesc) * count, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return run_table((const ProdDesc *)dev_table, count, C[0]->b, prec, dev_status, sm_count, s);
 }

@@ -141,9 +141,11 @@ __global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p) {
           const int E = (int)((hw[e] >> 20) & 0x7FFu);
           const int es = E - Er;
           if (E == 0 || es < -60) continue;   // below 2^-120 of the round's largest square
-          // hi: sign-free top 24 significand bits; lo: the next 29 bits
+          // hi: sign-free top 24 significand bits; lo: the bits below
           const float hi = __uint_as_float(((uint32_t)(es + 127) << 23) | (((hw[e] & 0xFFFFFu) << 3) | (lw[e] >> 29)));
-          const float lo = __uint2float_rn(lw[e] & 0x1FFFFFFFu) * __uint_as_float((uint32_t)(es - 52 + 127) << 23);
+          // (the next 23 bits, as an exact FP32 integer: their last 6 bits' share of the
+          // square is below 2^-46)
+          const float lo = u23_to_float((lw[e] >> 6) & 0x7FFFFFu) * __uint_as_float((uint32_t)(es - 46 + 127) << 23);
           const float pp = hi * hi;
           float cc = fmaf(hi, hi, -pp);
           cc = fmaf(2.f * hi, lo, cc);

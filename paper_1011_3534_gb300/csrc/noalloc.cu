@@ -172,7 +172,7 @@ extern "C" SPAMM_API spamm_status spamm_cull_noalloc(const double *normA2, const
   if (e == cudaSuccess) e = launch_pyramid(&A, s);
   if (e == cudaSuccess) e = launch_pyramid(&B, s);
   int launches = 0;
-  if (e == cudaSuccess) e = launch_cull(&A, &B, &C, tau, status, sms, s, &launches);
+  if (e == cudaSuccess) e = launch_cull(&A, &B, &C, tau, nullptr, status, sms, s, &launches);
   if (e == cudaSuccess) {
     k_expand_triples<<<1, 1024, 0, s>>>(C.tiers[kmax].gij, C.tiers[kmax].gstart, C.tiers[kmax].K, C.mask,
                                          C.counts, kmax, triples, cap, count, status);

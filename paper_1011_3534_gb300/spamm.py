@@ -27,6 +27,7 @@ SPAMM_COPY_BF16 = 0x0020
 SPAMM_COPY_FP16 = 0x0040
 SPAMM_COPY_BF16X3 = 0x0080
 SPAMM_NO_RIGHT = 0x0100
+SPAMM_GRAPH = 0x0200
 COPY_FLAG = {SPAMM_FP64: SPAMM_KEEP_FP64, SPAMM_TF32: SPAMM_COPY_TF32, SPAMM_BF16: SPAMM_COPY_BF16,
              SPAMM_FP16: SPAMM_COPY_FP16, SPAMM_BF16X3: SPAMM_COPY_BF16X3}
 MAX_LEVELS = 24
@@ -35,7 +36,8 @@ MAX_LEVELS = 24
 EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_error",
            "spamm_kernel_launches", "spamm_tree_build", "spamm_tree_update", "spamm_tree_free", "spamm_tree_info",
            "spamm_tree_norms", "spamm_tree_to_dense", "spamm_multiply", "spamm_stats",
-           "spamm_triples", "spamm_cull_noalloc", "spamm_sp2")
+           "spamm_triples", "spamm_cull_noalloc", "spamm_sp2", "spamm_multiply_batched",
+           "spamm_tune_leaf")
 
 
 class SpammError(RuntimeError):
@@ -92,6 +94,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.spamm_stats.argtypes = [_P, ctypes.POINTER(StatsT)]
     L.spamm_triples.argtypes = [_P, _P, _I64, ctypes.POINTER(_I64)]
     L.spamm_cull_noalloc.argtypes = [_P, _P, _I32, _D, _P, _I64, _P, _P]
+    L.spamm_multiply_batched.argtypes = [_P, _P, _P, _P, _I32, ctypes.c_int, _I32, _P]
+    L.spamm_tune_leaf.argtypes = [_P, _P, _I64, _D, ctypes.c_int, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_D)]
     L.spamm_sp2.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, _I32, ctypes.c_int, _P, ctypes.POINTER(Sp2ResultT)]
     for name in EXPORTS:
         if name not in ("spamm_last_error", "spamm_kernel_launches"):
@@ -255,3 +259,27 @@ def spamm_sp2(ctx: Ctx, indptr, indices, data, n_occ: float, steps: int, leaf: i
     return dict(energy=r.energy, eps_min=r.eps_min, eps_max=r.eps_max, steps=r.steps,
                 traces=list(r.trace[:steps + 1]), branches=list(r.branch[:steps]),
                 leaf_products=list(r.leaf_products[:steps]), ms=r.ms)
+
+
+def spamm_multiply_batched(ctx: Ctx, A: list, B: list, tau, prec: int, flags: int = 0, C: list | None = None) -> list:
+    """C[p] ~ A[p] B[p] with tolerance tau[p]; returns the list of product trees."""
+    count = len(A)
+    pa = (ctypes.c_void_p * count)(*[t.h for t in A])
+    pb = (ctypes.c_void_p * count)(*[t.h for t in B])
+    pc = (ctypes.c_void_p * count)(*[(c.h if c is not None else None) for c in (C or [None] * count)])
+    tv = np.ascontiguousarray(np.broadcast_to(np.asarray(tau, dtype=np.float64), (count,)))
+    ctx.check(LIB.spamm_multiply_batched(ctx.h, ctypes.addressof(pa), ctypes.addressof(pb), tv.ctypes.data, count,
+                                         int(prec), flags, ctypes.addressof(pc)), "spamm_multiply_batched")
+    if C is not None:
+        return C
+    return [Tree(ctx, pc[p]) for p in range(count)]
+
+
+def spamm_tune_leaf(ctx: Ctx, A, n: int, tau: float, prec: int, flags: int = 0) -> tuple[int, float]:
+    """Fastest leaf size for the product A A (A: torch CUDA tensor or numpy host array)."""
+    if isinstance(A, np.ndarray):
+        flags |= SPAMM_HOST_INPUT
+    leaf, ms = _I32(), _D()
+    ctx.check(LIB.spamm_tune_leaf(ctx.h, _ptr(A), n, float(tau), int(prec), flags, ctypes.byref(leaf),
+                                  ctypes.byref(ms)), "spamm_tune_leaf")
+    return leaf.value, ms.value

@@ -1,0 +1,96 @@
+"""Batched products (one persistent tensor-core launch over all products, optionally a
+CUDA graph) against the single-product path, and the leaf-size autotuner.
+
+Each product of a batch runs the same per-item arithmetic in the same order as when it
+is multiplied alone, so its C must be identical bit for bit; the triple lists equal.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from parity import compare_triples
+from paper_1011_3534_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1011_3534_gb300 import spamm
+    return spamm
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    st = torch.cuda.Stream()
+    c = S.spamm_ctx_create(0, st)
+    c.stream = st
+    yield c
+    S.spamm_ctx_destroy(c)
+
+
+def batch_inputs(count, seed=3):
+    shapes = W.batched_shapes(count=count, lo=512, hi=3072, seed=seed)
+    return [W.batched_matrix(m, n, lam, seed=seed) for m, (n, lam) in enumerate(shapes)]
+
+
+def build(S, ctx, mats, leaves, prec):
+    fl = S.COPY_FLAG[prec] | S.SPAMM_SYMMETRIC | (S.SPAMM_NO_RIGHT if prec != S.SPAMM_FP64 else 0)
+    with torch.cuda.stream(ctx.stream):
+        return [S.spamm_tree_build(ctx, torch.from_numpy(M).cuda(), M.shape[0], b, fl) for M, b in zip(mats, leaves)]
+
+
+@pytest.mark.parametrize("prec_name", ["bf16", "bf16x3", "fp64"])
+def test_batched_equals_single(S, ctx, prec_name):
+    prec = S.PRECISIONS[prec_name]
+    mats = batch_inputs(12)
+    leaves = [64 if i % 3 else 128 for i in range(len(mats))] if prec != S.SPAMM_FP64 else [32, 64] * 6
+    trees = build(S, ctx, mats, leaves, prec)
+    taus = [1e-7 * (1 + (i % 4)) for i in range(len(mats))]
+    Cb = S.spamm_multiply_batched(ctx, trees, trees, taus, prec)
+    for p, (t, tau) in enumerate(zip(trees, taus)):
+        Cs = S.spamm_multiply(ctx, t, t, tau, prec)
+        assert np.array_equal(S.spamm_triples(Cb[p]), S.spamm_triples(Cs)), p
+        assert np.array_equal(S.spamm_tree_to_dense(Cb[p]), S.spamm_tree_to_dense(Cs)), p
+        sb, ss = S.spamm_stats(Cb[p]), S.spamm_stats(Cs)
+        assert sb["leaf_products"] == ss["leaf_products"] and sb["mma_flops"] == ss["mma_flops"]
+        S.spamm_tree_free(Cs)
+    # the triples are the oracle's (one product checked against the CPU)
+    T = oracle.Tree(mats[0], leaves[0])
+    ref = oracle.spamm(T, T, taus[0], triples=True, product=False)
+    compare_triples(S.spamm_triples(Cb[0]), oracle.sort_triples(ref["triples"]), T.NB, T.norm2(T.kmax),
+                    T.norm2(T.kmax), taus[0])
+    for t in Cb + trees:
+        S.spamm_tree_free(t)
+
+
+def test_batched_graph_replay(S, ctx):
+    prec = S.SPAMM_BF16
+    mats = batch_inputs(8, seed=5)
+    trees = build(S, ctx, mats, [64] * len(mats), prec)
+    C = None
+    for tau in (1e-7, 1e-5, 1e-7):
+        taus = [tau] * len(mats)
+        C = S.spamm_multiply_batched(ctx, trees, trees, taus, prec, S.SPAMM_GRAPH, C)
+        for p, t in enumerate(trees):
+            Cs = S.spamm_multiply(ctx, t, t, tau, prec)
+            assert np.array_equal(S.spamm_tree_to_dense(C[p]), S.spamm_tree_to_dense(Cs)), (tau, p)
+            assert S.spamm_stats(C[p])["leaf_products"] == S.spamm_stats(Cs)["leaf_products"]
+            S.spamm_tree_free(Cs)
+    for t in C + trees:
+        S.spamm_tree_free(t)
+
+
+def test_tuner_picks_a_supported_leaf(S, ctx):
+    M = W.batched_matrix(0, 2048, 0.85)
+    with torch.cuda.stream(ctx.stream):
+        d = torch.from_numpy(M).cuda()
+        leaf, ms = S.spamm_tune_leaf(ctx, d, 2048, 1e-7, S.SPAMM_BF16, S.SPAMM_SYMMETRIC)
+        assert leaf in (64, 128) and ms > 0
+        leaf2, ms2 = S.spamm_tune_leaf(ctx, d, 2048, 1e-7, S.SPAMM_BF16, S.SPAMM_SYMMETRIC)
+        assert (leaf2, ms2) == (leaf, ms)   # cached
+        leaf3, _ = S.spamm_tune_leaf(ctx, d, 2048, 1e-7, S.SPAMM_FP64, S.SPAMM_SYMMETRIC)
+        assert leaf3 in (16, 32, 64, 128)
