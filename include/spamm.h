@@ -63,8 +63,10 @@ typedef enum {
   SPAMM_TF32 = 1,    /* operands rounded to TF32, FP32 accumulation (tensor cores) */
   SPAMM_BF16 = 2,    /* operands rounded to BF16, FP32 accumulation (tensor cores) */
   SPAMM_FP16 = 3,    /* operands rounded to FP16, FP32 accumulation (tensor cores) */
-  SPAMM_BF16X3 = 4   /* split BF16: a = hi + lo, hi = bf16(a), lo = bf16(a - hi);
+  SPAMM_BF16X3 = 4,  /* split BF16: a = hi + lo, hi = bf16(a), lo = bf16(a - hi);
                         A B ~ Ahi Bhi + Ahi Blo + Alo Bhi, FP32 accumulation */
+  SPAMM_TF32X3 = 5   /* split TF32, the same three products of hi = tf32(a),
+                        lo = tf32(a - hi): about 22 significant bits of each operand */
 } spamm_prec;
 
 /* ---- flags of spamm_tree_build and spamm_multiply ---- */
@@ -81,6 +83,7 @@ typedef enum {
                                       transposed copies a non-symmetric tree needs */
 #define SPAMM_GRAPH        0x0200  /* spamm_multiply_batched: capture the batch into a CUDA
                                       graph on first use and replay it afterwards */
+#define SPAMM_COPY_TF32X3  0x0400  /* write TF32 hi and lo leaf copies */
 
 #define SPAMM_MAX_LEVELS 24
 
@@ -99,7 +102,7 @@ typedef struct {
   double dense_equiv_flops;                /* 2 n^3 */
   double mma_flops;                        /* flops issued by the leaf kernel, counting
                                               zero-filled operand halves and the three
-                                              products of SPAMM_BF16X3 */
+                                              products of the split precisions */
   double ms_cull;                          /* phase times (ms), when the context was made
                                               with timing on; else 0 */
   double ms_leaf;
@@ -196,6 +199,55 @@ SPAMM_API spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t n
                                        spamm_prec prec, int32_t flags, int32_t *leaf_out,
                                        double *ms_out);
 
+/* ---- learned tolerance controller ----
+   (The paper has no counterpart: it fixes tau by hand, Sec. III.) A small network
+   predicts log10 of a product's relative Frobenius error from features of the
+   operands' norm trees and tau; the controller picks, per product, the largest tau on a
+   grid whose prediction meets an error budget. The network is a perceptron with two
+   tanh hidden layers, trained on the GPU by the library's own forward, backward and
+   Adam kernels (FP32, fixed-order reductions). Parameters are one float vector:
+   W1 (hidden x inputs, row-major), b1, W2 (hidden x hidden), b2, W3 (1 x hidden), b3.
+   All arrays of these calls are host arrays; calls synchronise the context stream. */
+typedef struct spamm_mlp_s *spamm_mlp;
+#define SPAMM_MLP_FEATURES 68   /* per operand: 16-bin decade histograms of the block norms
+                                   of its leaf tier and the tier above, as fractions of
+                                   nonzero blocks; then (log10 tau - log10 ||A||_F -
+                                   log10 ||B||_F) / 8, (log10 ||A||_F + log10 ||B||_F) / 8,
+                                   and the nonzero-leaf fractions of A and B */
+/* Network with `inputs` (1..128) and `hidden` (1..64) units, weights drawn
+   U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed), biases 0. */
+SPAMM_API spamm_status spamm_mlp_create(spamm_ctx ctx, int32_t inputs, int32_t hidden, uint64_t seed,
+                                        spamm_mlp *out);
+SPAMM_API spamm_status spamm_mlp_free(spamm_mlp m);
+SPAMM_API int32_t spamm_mlp_num_params(spamm_mlp m);
+SPAMM_API spamm_status spamm_mlp_get_params(spamm_mlp m, float *out, int32_t cap);
+/* Set the parameters (count == spamm_mlp_num_params) and reset the Adam state. */
+SPAMM_API spamm_status spamm_mlp_set_params(spamm_mlp m, const float *in, int32_t count);
+/* y[N] = network(X[N x inputs]). */
+SPAMM_API spamm_status spamm_mlp_forward(spamm_mlp m, const float *X, int32_t N, float *y);
+/* Loss (1/2N) sum (y_hat - y)^2 and its gradient grad[num_params] (either may be NULL). */
+SPAMM_API spamm_status spamm_mlp_gradient(spamm_mlp m, const float *X, const float *y, int32_t N,
+                                          float *grad, float *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on N samples. */
+SPAMM_API spamm_status spamm_mlp_adam_step(spamm_mlp m, const float *X, const float *y, int32_t N,
+                                           float lr, float *loss);
+/* One Adam step with the caller's gradient grad[num_params]. */
+SPAMM_API spamm_status spamm_mlp_adam_apply(spamm_mlp m, const float *grad, float lr);
+/* `epochs` passes of mini-batch Adam over a SplitMix64(seed) permutation per epoch;
+   *final_loss gets the full-data loss at the end. */
+SPAMM_API spamm_status spamm_mlp_train(spamm_mlp m, const float *X, const float *y, int32_t N,
+                                       int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                                       float *final_loss);
+/* Features of the product A B at tolerance tau > 0 (SPAMM_MLP_FEATURES floats). */
+SPAMM_API spamm_status spamm_features(spamm_tree A, spamm_tree B, double tau, float *out);
+/* Largest tau on the grid of 37 values log-spaced over [tau_min, tau_max] whose predicted
+   relative error is <= err_budget (tau_min when none is). */
+SPAMM_API spamm_status spamm_tau_select(spamm_mlp m, spamm_tree A, spamm_tree B, double err_budget,
+                                        double tau_min, double tau_max, double *tau_out);
+/* ||X - Y||_F and ||Y||_F of two trees of equal n and leaf (FP64 or FP32 tiles). */
+SPAMM_API spamm_status spamm_tree_distance(spamm_tree X, spamm_tree Y, double *diff_fro,
+                                           double *ref_fro);
+
 /* ---- SP2 density-matrix purification (Sec. III: TC2 purification, energy Tr(H X)) ----
    H is a symmetric n x n matrix given as host CSR (indptr[n+1], indices and data[nnz],
    column indices sorted per row). X0 = (eps_max I - H) / (eps_max - eps_min) with the
@@ -216,6 +268,8 @@ typedef struct {
   double trace[SPAMM_SP2_MAX_STEPS + 1];        /* Tr X_s, s = 0 .. steps */
   int32_t branch[SPAMM_SP2_MAX_STEPS];          /* 1: X <- X^2, 0: X <- 2X - X^2 */
   int64_t leaf_products[SPAMM_SP2_MAX_STEPS];   /* surviving leaf triples of step s */
+  double tau[SPAMM_SP2_MAX_STEPS];              /* tolerance of step s (given, or chosen
+                                                   by the controller) */
   double ms;                                    /* device time of the loop (ms) */
 } spamm_sp2_result;
 
@@ -223,6 +277,32 @@ SPAMM_API spamm_status spamm_sp2(spamm_ctx ctx, int64_t n, const int64_t *indptr
                                  const int64_t *indices, const double *data, double n_occ,
                                  int32_t steps, int32_t leaf, spamm_prec prec, const double *tau,
                                  spamm_sp2_result *out);
+
+/* The same loop one step at a time. spamm_sp2_begin validates H, forms X0 and its tree
+   (errors as above; *out owns device memory until spamm_sp2_end). spamm_sp2_step queues
+   one step with tolerance tau; spamm_sp2_step_learned queues one step whose tolerance
+   the controller m chooses on the device from the features of X (spamm_tau_select's
+   rule: budget and grid [tau_min, tau_max]), without a host round trip. Both are
+   asynchronous on the context stream; more than SPAMM_SP2_MAX_STEPS steps give
+   SPAMM_ERANGE. spamm_sp2_iterate lends the current iterate X as a tree (valid until
+   the next step or the end; the caller must not free it), e.g. to record features and
+   errors for training. spamm_sp2_end computes E, fills *out (may be NULL), and frees
+   the run whatever the status. */
+typedef struct spamm_sp2_s *spamm_sp2_run;
+SPAMM_API spamm_status spamm_sp2_begin(spamm_ctx ctx, int64_t n, const int64_t *indptr,
+                                       const int64_t *indices, const double *data, double n_occ,
+                                       int32_t leaf, spamm_prec prec, spamm_sp2_run *out);
+SPAMM_API spamm_status spamm_sp2_step(spamm_sp2_run r, double tau);
+SPAMM_API spamm_status spamm_sp2_step_learned(spamm_sp2_run r, spamm_mlp m, double err_budget,
+                                              double tau_min, double tau_max);
+SPAMM_API spamm_status spamm_sp2_iterate(spamm_sp2_run r, spamm_tree *X);
+SPAMM_API spamm_status spamm_sp2_end(spamm_sp2_run r, spamm_sp2_result *out);
+/* spamm_sp2 with every step's tolerance chosen by the controller. */
+SPAMM_API spamm_status spamm_sp2_learned(spamm_ctx ctx, int64_t n, const int64_t *indptr,
+                                         const int64_t *indices, const double *data,
+                                         double n_occ, int32_t steps, int32_t leaf,
+                                         spamm_prec prec, spamm_mlp m, double err_budget,
+                                         double tau_min, double tau_max, spamm_sp2_result *out);
 
 /* ---- cull without device allocation ----
    For callers that cannot allocate device memory: code running inside a CUDA graph

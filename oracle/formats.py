@@ -4,8 +4,9 @@ Written from the format definitions: a binary floating-point format with p signi
 bits and minimum normal exponent emin represents x as a multiple of the quantum
 2^(max(E, emin) - p + 1), E = floor(log2 |x|); round to nearest, ties to even (IEEE 754).
   BF16: p = 8,  emin = -126    FP16: p = 11, emin = -14    TF32: p = 11, emin = -126
-Overflow is not handled (the workloads stay far inside every range). The split BF16
-pair of a value is hi = bf16(x), lo = bf16(x - hi).
+Overflow is not handled (the workloads stay far inside every range). The split pair of
+a value in a format is hi = fmt(x), lo = fmt(x - hi) (x - hi is exact in FP64: both are
+multiples of the unit in the last place of x).
 """
 import numpy as np
 
@@ -21,7 +22,11 @@ def round_to(x: np.ndarray, fmt: str) -> np.ndarray:
     return np.rint(x / q) * q                # rint: round half to even
 
 
-def split_bf16(x: np.ndarray):
-    hi = round_to(x, "bf16")
-    lo = round_to(x - hi, "bf16")
+def split(x: np.ndarray, fmt: str):
+    hi = round_to(x, fmt)
+    lo = round_to(np.asarray(x, dtype=np.float64) - hi, fmt)
     return hi, lo
+
+
+def split_bf16(x: np.ndarray):
+    return split(x, "bf16")

@@ -63,6 +63,12 @@ void wanted_copies(int32_t flags, bool want[CK_COUNT]) {
     want[CK_BF16_T] = right_t;
     want[CK_BF16LO_T] = right_t;
   }
+  if (flags & SPAMM_COPY_TF32X3) {
+    want[CK_TF32] = true;
+    want[CK_TF32LO] = true;
+    want[CK_TF32_T] = right_t;
+    want[CK_TF32LO_T] = right_t;
+  }
 }
 
 void shape(int64_t n, int32_t b, int32_t *nb, int32_t *NB, int32_t *kmax) {
@@ -211,6 +217,7 @@ static int32_t COPY_FLAG_OF(spamm_prec p) {
     case SPAMM_BF16: return SPAMM_COPY_BF16;
     case SPAMM_FP16: return SPAMM_COPY_FP16;
     case SPAMM_BF16X3: return SPAMM_COPY_BF16X3;
+    case SPAMM_TF32X3: return SPAMM_COPY_TF32X3;
     default: return SPAMM_KEEP_FP64;
   }
 }
@@ -276,7 +283,7 @@ spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t
   if (!A || !out) return fail(ctx, SPAMM_EINVAL, "tree_build: null pointer");
   if (n < 1) return fail(ctx, SPAMM_EINVAL, "tree_build: n = %lld < 1", (long long)n);
   if (!valid_leaf(leaf)) return fail(ctx, SPAMM_EINVAL, "tree_build: leaf %d not in {16,32,64,128}", leaf);
-  if (flags & ~0x01FF) return fail(ctx, SPAMM_EINVAL, "tree_build: unknown flag bits 0x%x", flags);
+  if (flags & ~kTreeFlags) return fail(ctx, SPAMM_EINVAL, "tree_build: unknown flag bits 0x%x", flags);
   *out = nullptr;
   spamm_tree t = nullptr;
   spamm_status st = alloc_tree(ctx, n, leaf, flags, &t);
@@ -403,29 +410,30 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
     return fail(ctx, SPAMM_EINVAL, "multiply: operands differ (n %lld/%lld, leaf %d/%d)",
                 (long long)A->n, (long long)B->n, A->b, B->b);
   if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(ctx, SPAMM_EINVAL, "multiply: tau must be finite and >= 0");
-  if (flags & ~0x01F6) return fail(ctx, SPAMM_EINVAL, "multiply: unknown flag bits 0x%x", flags);
+  if (flags & ~(kTreeFlags & ~SPAMM_HOST_INPUT)) return fail(ctx, SPAMM_EINVAL, "multiply: unknown flag bits 0x%x", flags);
   const bool tc = prec != SPAMM_FP64;
-  if (prec < SPAMM_FP64 || prec > SPAMM_BF16X3) return fail(ctx, SPAMM_EINVAL, "multiply: unknown precision %d", (int)prec);
+  if (prec < SPAMM_FP64 || prec > SPAMM_TF32X3) return fail(ctx, SPAMM_EINVAL, "multiply: unknown precision %d", (int)prec);
   if (!tc) {
     if (!A->copy[CK_F64] || !B->copy[CK_F64])
       return fail(ctx, SPAMM_EINVAL, "multiply: SPAMM_FP64 needs SPAMM_KEEP_FP64 operands");
   } else {
     if (A->b != 64 && A->b != 128)
       return fail(ctx, SPAMM_EUNSUPPORTED, "multiply: tensor-core precisions need leaf 64 or 128");
-    int row = prec == SPAMM_TF32 ? CK_TF32 : prec == SPAMM_FP16 ? CK_FP16 : CK_BF16;
+    int row = tf32_prec(prec) ? CK_TF32 : prec == SPAMM_FP16 ? CK_FP16 : CK_BF16;
     int rowT = row + 1;
-    if (!A->copy[row] || (prec == SPAMM_BF16X3 && !A->copy[CK_BF16LO]))
+    const int lo = prec == SPAMM_TF32X3 ? CK_TF32LO : CK_BF16LO;
+    if (!A->copy[row] || (split_prec(prec) && !A->copy[lo]))
       return fail(ctx, SPAMM_EINVAL, "multiply: left operand lacks the leaf copy for this precision");
     const bool bsym = (B->flags & SPAMM_SYMMETRIC) != 0;
     if (bsym ? !B->copy[row] : !B->copy[rowT])
       return fail(ctx, SPAMM_EINVAL, "multiply: right operand lacks the leaf copy for this precision");
-    if (prec == SPAMM_BF16X3 && (bsym ? !B->copy[CK_BF16LO] : !B->copy[CK_BF16LO_T]))
-      return fail(ctx, SPAMM_EINVAL, "multiply: right operand lacks the BF16 lo copy");
+    if (split_prec(prec) && (bsym ? !B->copy[lo] : !B->copy[lo + 1]))
+      return fail(ctx, SPAMM_EINVAL, "multiply: right operand lacks the lo copy of the split");
   }
   spamm_tree Ct = *C;
-  const int32_t cflags = (flags & 0x01F2) | (tc ? SPAMM_INTERNAL_F32 : SPAMM_KEEP_FP64);
+  const int32_t cflags = (flags & (kLowCopyFlags | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT)) | (tc ? SPAMM_INTERNAL_F32 : SPAMM_KEEP_FP64);
   if (!Ct) {
-    spamm_status st = alloc_tree(ctx, A->n, A->b, cflags & 0x01FF, &Ct);
+    spamm_status st = alloc_tree(ctx, A->n, A->b, cflags & kTreeFlags, &Ct);
     if (st != SPAMM_OK) return st;
     if (tc) {
       cudaError_t e = dmalloc(&Ct->copy[CK_F32], (size_t)Ct->nb * Ct->nb * Ct->b * Ct->b * 4);
@@ -440,7 +448,7 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
     if (Ct == A || Ct == B) return fail(ctx, SPAMM_EINVAL, "multiply: output aliases an operand");
     if (Ct->n != A->n || Ct->b != A->b) return fail(ctx, SPAMM_EINVAL, "multiply: reused output has another shape");
     bool want[CK_COUNT];
-    wanted_copies(cflags & 0x01FF, want);
+    wanted_copies(cflags & kTreeFlags, want);
     for (int k = 0; k < CK_COUNT; k++)
       if (want[k] && !Ct->copy[k]) return fail(ctx, SPAMM_EINVAL, "multiply: reused output lacks a requested copy");
     if (tc ? !Ct->copy[CK_F32] : !Ct->copy[CK_F64])
@@ -466,7 +474,7 @@ spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau
   if (pst != SPAMM_OK) return pst;
   spamm_tree Ct = *C;
   const bool tc = prec != SPAMM_FP64;
-  const int32_t cflags = (flags & 0x01F2) | (tc ? SPAMM_INTERNAL_F32 : SPAMM_KEEP_FP64);
+  const int32_t cflags = (flags & (kLowCopyFlags | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT)) | (tc ? SPAMM_INTERNAL_F32 : SPAMM_KEEP_FP64);
   cudaStream_t s = ctx->stream;
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[0], s), "event");
   int launches = 0;
@@ -482,7 +490,7 @@ spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau
   CK(launch_pyramid(Ct, s), "multiply: pyramid launch");
   launches += pyramid_launches(Ct->kmax);
   bool want[CK_COUNT];
-  wanted_copies(cflags & 0x01FF, want);
+  wanted_copies(cflags & kTreeFlags, want);
   bool any_copy = false;
   for (int k = CK_TF32; k < CK_COUNT; k++) any_copy |= want[k];
   if (any_copy) {
@@ -524,7 +532,7 @@ spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out) {
     S.leaf_flops = 2.0 * b * b * b * (double)h.leaf_products;
     S.dense_equiv_flops = 2.0 * (double)C->n * (double)C->n * (double)C->n;
     // tensor-core kernel: one stage = a 128 x 128 x (128-byte K chunk) MMA chain
-    const double chunk_k = C->prec == SPAMM_TF32 ? 32.0 : 64.0;
+    const double chunk_k = tf32_prec(C->prec) ? 32.0 : 64.0;
     S.mma_flops = C->prec == SPAMM_FP64 ? S.leaf_flops : (double)h.mma_tiles * 2.0 * 128.0 * 128.0 * chunk_k;
     S.prec = C->prec;
     S.tau = C->tau;
@@ -600,23 +608,52 @@ spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, int64_t *co
 
 }  // extern "C"
 
-extern "C" spamm_status spamm_sp2(spamm_ctx ctx, int64_t n, const int64_t *indptr, const int64_t *indices,
-                                  const double *data, double n_occ, int32_t steps, int32_t leaf, spamm_prec prec,
-                                  const double *tau, spamm_sp2_result *out) {
+// ---- SP2 purification: a run object stepping on the context stream ----
+struct spamm_sp2_s {
+  spamm_ctx ctx = nullptr;
+  int64_t n = 0, nnz = 0;
+  double n_occ = 0, emin = 0, emax = 0;
+  spamm_prec prec = SPAMM_FP64;
+  int steps = 0;
+  int64_t *d_ip = nullptr, *d_ix = nullptr;
+  double *d_v = nullptr, *d_part = nullptr;
+  void *d_rec = nullptr;
+  float *d_feat = nullptr;
+  spamm_tree X = nullptr, C = nullptr;
+  double tau_host[SPAMM_SP2_MAX_STEPS] = {};
+  bool learned[SPAMM_SP2_MAX_STEPS] = {};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+namespace {
+
+void sp2_release(spamm_sp2_run r) {
+  if (!r) return;
+  if (r->X) { free_tree_memory(r->X); delete r->X; }
+  if (r->C) { free_tree_memory(r->C); delete r->C; }
+  dfree(r->d_ip); dfree(r->d_ix); dfree(r->d_v); dfree(r->d_part); dfree(r->d_rec); dfree(r->d_feat);
+  if (r->e0) cudaEventDestroy(r->e0);
+  if (r->e1) cudaEventDestroy(r->e1);
+  delete r;
+}
+
+}  // namespace
+
+extern "C" spamm_status spamm_sp2_begin(spamm_ctx ctx, int64_t n, const int64_t *indptr, const int64_t *indices,
+                                        const double *data, double n_occ, int32_t leaf, spamm_prec prec,
+                                        spamm_sp2_run *out) {
   if (!ctx) return SPAMM_EINVAL;
-  if (!indptr || !indices || !data || !tau || !out) return fail(ctx, SPAMM_EINVAL, "sp2: null pointer");
-  if (n < 1 || steps < 0 || steps > SPAMM_SP2_MAX_STEPS || !valid_leaf(leaf))
-    return fail(ctx, SPAMM_EINVAL, "sp2: bad n / steps / leaf");
-  if (prec < SPAMM_FP64 || prec > SPAMM_BF16X3) return fail(ctx, SPAMM_EINVAL, "sp2: unknown precision");
+  if (!indptr || !indices || !data || !out) return fail(ctx, SPAMM_EINVAL, "sp2: null pointer");
+  if (n < 1 || !valid_leaf(leaf)) return fail(ctx, SPAMM_EINVAL, "sp2: bad n / leaf");
+  if (prec < SPAMM_FP64 || prec > SPAMM_TF32X3) return fail(ctx, SPAMM_EINVAL, "sp2: unknown precision");
   const bool tc = prec != SPAMM_FP64;
   if (tc && leaf != 64 && leaf != 128) return fail(ctx, SPAMM_EUNSUPPORTED, "sp2: tensor-core precisions need leaf 64 or 128");
-  for (int s = 0; s < steps; s++)
-    if (!(tau[s] >= 0.0) || !std::isfinite(tau[s])) return fail(ctx, SPAMM_EINVAL, "sp2: tau[%d] invalid", s);
   const int64_t nnz = indptr[n];
   if (nnz < 0 || indptr[0] != 0) return fail(ctx, SPAMM_EINVAL, "sp2: bad CSR");
   // Gershgorin interval on the host
   double emin = INFINITY, emax = -INFINITY;
   for (int64_t i = 0; i < n; i++) {
+    if (indptr[i + 1] < indptr[i]) return fail(ctx, SPAMM_EINVAL, "sp2: bad CSR");
     double d = 0.0, rad = 0.0;
     for (int64_t q = indptr[i]; q < indptr[i + 1]; q++) {
       if (indices[q] < 0 || indices[q] >= n) return fail(ctx, SPAMM_EINVAL, "sp2: column index out of range");
@@ -627,80 +664,172 @@ extern "C" spamm_status spamm_sp2(spamm_ctx ctx, int64_t n, const int64_t *indpt
     emax = std::max(emax, d + rad);
   }
   if (!(emax > emin)) return fail(ctx, SPAMM_EINVAL, "sp2: empty spectral interval");
+  spamm_sp2_run r = new (std::nothrow) spamm_sp2_s();
+  if (!r) return SPAMM_ENOMEM;
+  r->ctx = ctx;
+  r->n = n;
+  r->nnz = nnz;
+  r->n_occ = n_occ;
+  r->emin = emin;
+  r->emax = emax;
+  r->prec = prec;
   cudaStream_t s = ctx->stream;
-  int64_t *d_ip = nullptr, *d_ix = nullptr;
-  double *d_v = nullptr, *d_part = nullptr;
-  void *d_rec = nullptr;
-  spamm_tree X = nullptr, C = nullptr;
-  std::vector<unsigned char> host_rec(sp2_record_bytes());
-  spamm_status st = SPAMM_OK;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
   const int32_t flags = tc ? (COPY_FLAG_OF(prec) | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT)
                            : (SPAMM_KEEP_FP64 | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT);
-  auto cleanup = [&]() {
-    if (X) { free_tree_memory(X); delete X; }
-    if (C) { free_tree_memory(C); delete C; }
-    dfree(d_ip); dfree(d_ix); dfree(d_v); dfree(d_part); dfree(d_rec);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-  };
 #define SP2CK(call, what)                                  \
   do {                                                     \
     cudaError_t _e = (call);                               \
-    if (_e != cudaSuccess) { cleanup(); return cuda_fail(ctx, _e, what); } \
+    if (_e != cudaSuccess) { sp2_release(r); return cuda_fail(ctx, _e, what); } \
   } while (0)
-  SP2CK(dmalloc(&d_ip, (n + 1) * 8), "sp2: allocation");
-  SP2CK(dmalloc(&d_ix, std::max<int64_t>(nnz, 1) * 8), "sp2: allocation");
-  SP2CK(dmalloc(&d_v, std::max<int64_t>(nnz, 1) * 8), "sp2: allocation");
-  SP2CK(dmalloc(&d_part, ((n + 255) / 256) * 8), "sp2: allocation");
-  SP2CK(dmalloc((unsigned char **)&d_rec, sp2_record_bytes()), "sp2: allocation");
-  SP2CK(cudaMemsetAsync(d_rec, 0, sp2_record_bytes(), s), "sp2: memset");
-  SP2CK(cudaMemcpyAsync(d_ip, indptr, (n + 1) * 8, cudaMemcpyHostToDevice, s), "sp2: copy");
+  SP2CK(dmalloc(&r->d_ip, (n + 1) * 8), "sp2: allocation");
+  SP2CK(dmalloc(&r->d_ix, std::max<int64_t>(nnz, 1) * 8), "sp2: allocation");
+  SP2CK(dmalloc(&r->d_v, std::max<int64_t>(nnz, 1) * 8), "sp2: allocation");
+  SP2CK(dmalloc(&r->d_part, ((n + 255) / 256) * 8), "sp2: allocation");
+  SP2CK(dmalloc((unsigned char **)&r->d_rec, sp2_record_bytes()), "sp2: allocation");
+  SP2CK(dmalloc(&r->d_feat, sizeof(float) * kTreeFeatures), "sp2: allocation");
+  SP2CK(cudaMemsetAsync(r->d_rec, 0, sp2_record_bytes(), s), "sp2: memset");
+  SP2CK(cudaMemcpyAsync(r->d_ip, indptr, (n + 1) * 8, cudaMemcpyHostToDevice, s), "sp2: copy");
   if (nnz) {
-    SP2CK(cudaMemcpyAsync(d_ix, indices, nnz * 8, cudaMemcpyHostToDevice, s), "sp2: copy");
-    SP2CK(cudaMemcpyAsync(d_v, data, nnz * 8, cudaMemcpyHostToDevice, s), "sp2: copy");
+    SP2CK(cudaMemcpyAsync(r->d_ix, indices, nnz * 8, cudaMemcpyHostToDevice, s), "sp2: copy");
+    SP2CK(cudaMemcpyAsync(r->d_v, data, nnz * 8, cudaMemcpyHostToDevice, s), "sp2: copy");
   }
-  st = alloc_tree(ctx, n, leaf, flags, &X);
-  if (st == SPAMM_OK) st = alloc_tree(ctx, n, leaf, flags, &C);
-  if (st != SPAMM_OK) { cleanup(); return st; }
+  spamm_status st = alloc_tree(ctx, n, leaf, flags, &r->X);
+  if (st == SPAMM_OK) st = alloc_tree(ctx, n, leaf, flags, &r->C);
+  if (st != SPAMM_OK) { sp2_release(r); return st; }
   if (tc) {
-    const size_t elems = (size_t)X->nb * X->nb * (size_t)leaf * leaf;
-    SP2CK(dmalloc(&X->copy[CK_F32], elems * 4), "sp2: allocation");
-    SP2CK(dmalloc(&C->copy[CK_F32], elems * 4), "sp2: allocation");
-    X->flags |= SPAMM_INTERNAL_F32;
-    C->flags |= SPAMM_INTERNAL_F32;
+    const size_t elems = (size_t)r->X->nb * r->X->nb * (size_t)leaf * leaf;
+    SP2CK(dmalloc(&r->X->copy[CK_F32], elems * 4), "sp2: allocation");
+    SP2CK(dmalloc(&r->C->copy[CK_F32], elems * 4), "sp2: allocation");
+    r->X->flags |= SPAMM_INTERNAL_F32;
+    r->C->flags |= SPAMM_INTERNAL_F32;
   }
   st = ensure_stage(ctx, (size_t)n * n * sizeof(double));
-  if (st != SPAMM_OK) { cleanup(); return st; }
-  SP2CK(sp2_x0(n, d_ip, d_ix, d_v, emin, emax, (double *)ctx->stage, s), "sp2: X0");
-  SP2CK(launch_tree_build(X, (const double *)ctx->stage, s), "sp2: X0 tree");
-  SP2CK(launch_pyramid(X, s), "sp2: X0 pyramid");
-  SP2CK(cudaEventCreate(&e0), "sp2: event");
-  SP2CK(cudaEventCreate(&e1), "sp2: event");
-  SP2CK(cudaEventRecord(e0, s), "sp2: event");
-  for (int step = 0; step < steps; step++) {
-    spamm_tree out_tree = C;
-    st = spamm_multiply(ctx, X, X, tau[step], prec, 0, &out_tree);
-    if (st != SPAMM_OK) { cleanup(); return st; }
-    SP2CK(sp2_step_finish(X, C, n_occ, step, d_rec, s), "sp2: step");
-    std::swap(X, C);
-  }
-  SP2CK(sp2_trace_only(X, steps, d_rec, s), "sp2: trace");
-  SP2CK(sp2_energy(X, n, d_ip, d_ix, d_v, d_part, d_rec, s), "sp2: energy");
-  SP2CK(cudaEventRecord(e1, s), "sp2: event");
-  SP2CK(cudaMemcpyAsync(host_rec.data(), d_rec, sp2_record_bytes(), cudaMemcpyDeviceToHost, s), "sp2: copy");
-  st = check_device_status(ctx);
-  if (st != SPAMM_OK) { cleanup(); return st; }
-  memset(out, 0, sizeof *out);
-  sp2_read_record(host_rec.data(), steps, out);
-  out->eps_min = emin;
-  out->eps_max = emax;
-  out->steps = steps;
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  out->ms = ms;
-  ctx->launches += 4 + (int64_t)steps * 5;
-  cleanup();
-  return SPAMM_OK;
+  if (st != SPAMM_OK) { sp2_release(r); return st; }
+  SP2CK(sp2_x0(n, r->d_ip, r->d_ix, r->d_v, emin, emax, (double *)ctx->stage, s), "sp2: X0");
+  SP2CK(launch_tree_build(r->X, (const double *)ctx->stage, s), "sp2: X0 tree");
+  SP2CK(launch_pyramid(r->X, s), "sp2: X0 pyramid");
+  SP2CK(cudaEventCreate(&r->e0), "sp2: event");
+  SP2CK(cudaEventCreate(&r->e1), "sp2: event");
+  SP2CK(cudaEventRecord(r->e0, s), "sp2: event");
 #undef SP2CK
+  ctx->launches += 2 + pyramid_launches(r->X->kmax);
+  *out = r;
+  return SPAMM_OK;
+}
+
+namespace {
+
+// One step with tau on the host, or read from the record slot the controller wrote.
+spamm_status sp2_advance(spamm_sp2_run r, double tau, bool from_record) {
+  spamm_ctx ctx = r->ctx;
+  const int step = r->steps;
+  spamm_tree out_tree = r->C;
+  const double *tau_dev = from_record ? sp2_tau_slot(r->d_rec, step) : nullptr;
+  spamm_status st = multiply_impl(ctx, r->X, r->X, from_record ? 0.0 : tau, tau_dev, r->prec, 0, &out_tree);
+  if (st != SPAMM_OK) return st;
+  CK(sp2_step_finish(r->X, r->C, r->n_occ, step, r->d_rec, ctx->stream), "sp2: step");
+  ctx->launches += 3 + pyramid_launches(r->C->kmax);
+  r->tau_host[step] = tau;
+  r->learned[step] = from_record;
+  std::swap(r->X, r->C);
+  r->steps++;
+  return SPAMM_OK;
+}
+
+}  // namespace
+
+extern "C" spamm_status spamm_sp2_step(spamm_sp2_run r, double tau) {
+  if (!r) return SPAMM_EINVAL;
+  if (r->steps >= SPAMM_SP2_MAX_STEPS) return fail(r->ctx, SPAMM_ERANGE, "sp2: more than %d steps", SPAMM_SP2_MAX_STEPS);
+  if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(r->ctx, SPAMM_EINVAL, "sp2: tau invalid");
+  return sp2_advance(r, tau, false);
+}
+
+extern "C" spamm_status spamm_sp2_step_learned(spamm_sp2_run r, spamm_mlp m, double err_budget, double tau_min,
+                                               double tau_max) {
+  if (!r || !m) return SPAMM_EINVAL;
+  spamm_ctx ctx = r->ctx;
+  if (r->steps >= SPAMM_SP2_MAX_STEPS) return fail(ctx, SPAMM_ERANGE, "sp2: more than %d steps", SPAMM_SP2_MAX_STEPS);
+  if (!(err_budget > 0.0) || !(tau_min > 0.0) || !(tau_max >= tau_min) || !std::isfinite(tau_max))
+    return fail(ctx, SPAMM_EINVAL, "sp2: bad budget or tau range");
+  if (mlp_inputs(m) != SPAMM_MLP_FEATURES) return fail(ctx, SPAMM_EINVAL, "sp2: network has the wrong input width");
+  cudaStream_t s = ctx->stream;
+  CK(launch_feat_hist(r->X, r->d_feat, s), "sp2: features");
+  CK(launch_tau_select(m, r->d_feat, r->d_feat, std::log10(err_budget), std::log10(tau_min), std::log10(tau_max), 37,
+                       sp2_tau_slot(r->d_rec, r->steps), s),
+     "sp2: tau selection");
+  ctx->launches += 2;
+  return sp2_advance(r, 0.0, true);
+}
+
+extern "C" spamm_status spamm_sp2_iterate(spamm_sp2_run r, spamm_tree *X) {
+  if (!r || !X) return SPAMM_EINVAL;
+  *X = r->X;
+  return SPAMM_OK;
+}
+
+extern "C" spamm_status spamm_sp2_end(spamm_sp2_run r, spamm_sp2_result *out) {
+  if (!r) return SPAMM_EINVAL;
+  spamm_ctx ctx = r->ctx;
+  cudaStream_t s = ctx->stream;
+  std::vector<unsigned char> host_rec(sp2_record_bytes());
+  spamm_status st = SPAMM_OK;
+  cudaError_t e = sp2_trace_only(r->X, r->steps, r->d_rec, s);
+  if (e == cudaSuccess) e = sp2_energy(r->X, r->n, r->d_ip, r->d_ix, r->d_v, r->d_part, r->d_rec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(r->e1, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_rec.data(), r->d_rec, sp2_record_bytes(), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) st = cuda_fail(ctx, e, "sp2: finish");
+  if (st == SPAMM_OK) st = check_device_status(ctx);
+  if (st == SPAMM_OK && out) {
+    memset(out, 0, sizeof *out);
+    sp2_read_record(host_rec.data(), r->steps, out);
+    for (int q = 0; q < r->steps; q++)
+      if (!r->learned[q]) out->tau[q] = r->tau_host[q];
+    out->eps_min = r->emin;
+    out->eps_max = r->emax;
+    out->steps = r->steps;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r->e0, r->e1);
+    out->ms = ms;
+  }
+  ctx->launches += 3;
+  sp2_release(r);
+  return st;
+}
+
+extern "C" spamm_status spamm_sp2(spamm_ctx ctx, int64_t n, const int64_t *indptr, const int64_t *indices,
+                                  const double *data, double n_occ, int32_t steps, int32_t leaf, spamm_prec prec,
+                                  const double *tau, spamm_sp2_result *out) {
+  if (!ctx) return SPAMM_EINVAL;
+  if (!tau || !out) return fail(ctx, SPAMM_EINVAL, "sp2: null pointer");
+  if (steps < 0 || steps > SPAMM_SP2_MAX_STEPS) return fail(ctx, SPAMM_EINVAL, "sp2: bad steps");
+  for (int q = 0; q < steps; q++)
+    if (!(tau[q] >= 0.0) || !std::isfinite(tau[q])) return fail(ctx, SPAMM_EINVAL, "sp2: tau[%d] invalid", q);
+  spamm_sp2_run r = nullptr;
+  spamm_status st = spamm_sp2_begin(ctx, n, indptr, indices, data, n_occ, leaf, prec, &r);
+  if (st != SPAMM_OK) return st;
+  for (int q = 0; q < steps && st == SPAMM_OK; q++) st = spamm_sp2_step(r, tau[q]);
+  if (st != SPAMM_OK) {
+    spamm_sp2_end(r, nullptr);
+    return st;
+  }
+  return spamm_sp2_end(r, out);
+}
+
+extern "C" spamm_status spamm_sp2_learned(spamm_ctx ctx, int64_t n, const int64_t *indptr, const int64_t *indices,
+                                          const double *data, double n_occ, int32_t steps, int32_t leaf,
+                                          spamm_prec prec, spamm_mlp m, double err_budget, double tau_min,
+                                          double tau_max, spamm_sp2_result *out) {
+  if (!ctx) return SPAMM_EINVAL;
+  if (!m || !out) return fail(ctx, SPAMM_EINVAL, "sp2: null pointer");
+  if (steps < 0 || steps > SPAMM_SP2_MAX_STEPS) return fail(ctx, SPAMM_EINVAL, "sp2: bad steps");
+  spamm_sp2_run r = nullptr;
+  spamm_status st = spamm_sp2_begin(ctx, n, indptr, indices, data, n_occ, leaf, prec, &r);
+  if (st != SPAMM_OK) return st;
+  for (int q = 0; q < steps && st == SPAMM_OK; q++) st = spamm_sp2_step_learned(r, m, err_budget, tau_min, tau_max);
+  if (st != SPAMM_OK) {
+    spamm_sp2_end(r, nullptr);
+    return st;
+  }
+  return spamm_sp2_end(r, out);
 }

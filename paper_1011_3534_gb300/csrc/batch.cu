@@ -134,13 +134,13 @@ extern "C" spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *
                                                spamm_tree *C) {
   if (!ctx) return SPAMM_EINVAL;
   if (!A || !B || !tau || !C || count < 1) return bfail(ctx, SPAMM_EINVAL, "batched: bad arguments");
-  if (flags & ~(0x01F2 | SPAMM_GRAPH)) return bfail(ctx, SPAMM_EINVAL, "batched: unknown flag bits");
-  if (flags & 0x01F0) return bfail(ctx, SPAMM_EUNSUPPORTED, "batched: leaf copies of the products are not produced");
+  if (flags & ~(kLowCopyFlags | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT | SPAMM_GRAPH)) return bfail(ctx, SPAMM_EINVAL, "batched: unknown flag bits");
+  if (flags & kLowCopyFlags) return bfail(ctx, SPAMM_EUNSUPPORTED, "batched: leaf copies of the products are not produced");
   spamm_status st = ensure_side_streams(ctx);
   if (st != SPAMM_OK) return st;
   // every product validated, created or checked, workspace allocated (before any capture)
   for (int p = 0; p < count; p++) {
-    st = product_prepare(ctx, A[p], B[p], tau[p], prec, flags & 0x01F2, &C[p]);
+    st = product_prepare(ctx, A[p], B[p], tau[p], prec, flags & (SPAMM_SYMMETRIC | SPAMM_NO_RIGHT), &C[p]);
     if (st != SPAMM_OK) return st;
   }
   st = ensure_batch_tables(ctx, count);
@@ -226,7 +226,8 @@ extern "C" spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t 
   const bool tc = prec != SPAMM_FP64;
   std::vector<int> cand = tc ? std::vector<int>{64, 128} : std::vector<int>{16, 32, 64, 128};
   const int32_t copy = tc ? (prec == SPAMM_TF32 ? SPAMM_COPY_TF32 : prec == SPAMM_FP16 ? SPAMM_COPY_FP16
-                             : prec == SPAMM_BF16X3 ? SPAMM_COPY_BF16X3 : SPAMM_COPY_BF16)
+                             : prec == SPAMM_BF16X3 ? SPAMM_COPY_BF16X3
+                             : prec == SPAMM_TF32X3 ? SPAMM_COPY_TF32X3 : SPAMM_COPY_BF16)
                           : SPAMM_KEEP_FP64;
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0), "tune: event");

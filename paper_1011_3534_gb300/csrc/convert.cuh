@@ -74,14 +74,14 @@ __device__ __forceinline__ Rounded round_f64bits(uint64_t bits, int p, int emin)
   return round_core(sign, sig, E - 1075, 52, p, emin);
 }
 
-// The low half of the split BF16 pair: bf16(x - hi), hi = bf16(x), from the exact
-// integer remainder of the significand.
-__device__ __forceinline__ uint32_t bf16_lo_bits(uint64_t bits, const Rounded &hi) {
+// The low part of a split pair: fmt(x - hi), hi = fmt(x), from the exact integer
+// remainder of the significand, rounded to p significant bits (8: BF16, 11: TF32).
+__device__ __forceinline__ uint32_t split_lo_bits(uint64_t bits, const Rounded &hi, int p) {
   const int E = (int)((bits >> 52) & 0x7FF);
   if (E == 0 || E == 0x7FF) return 0;
   const uint64_t sig = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
   const int x = E - 1075;
-  const int shift = hi.q - x;                        // >= 45
+  const int shift = hi.q - x;                        // >= 42
   int64_t R = (int64_t)sig;
   if (shift < 64) R -= (int64_t)((uint64_t)hi.r << shift);
   if (R == 0) return 0;
@@ -91,8 +91,10 @@ __device__ __forceinline__ uint32_t bf16_lo_bits(uint64_t bits, const Rounded &h
     sign ^= 0x80000000u;
     M = (uint64_t)(-R);
   }
-  return round_core(sign, M, x, 63 - __clzll((long long)M), 8, -126).bits;
+  return round_core(sign, M, x, 63 - __clzll((long long)M), p, -126).bits;
 }
+
+__device__ __forceinline__ uint32_t bf16_lo_bits(uint64_t bits, const Rounded &hi) { return split_lo_bits(bits, hi, 8); }
 
 __device__ __forceinline__ uint16_t bf16_from_f32bits(uint32_t b) { return (uint16_t)(b >> 16); }
 
@@ -127,7 +129,7 @@ __device__ __forceinline__ Rounded round_f32(float f, int p, int emin) {
   return round_core(sign, (u & 0x7FFFFFu) | 0x800000u, E - 150, 23, p, emin);
 }
 
-__device__ __forceinline__ uint32_t bf16_lo_bits_f32(float f, const Rounded &hi) {
+__device__ __forceinline__ uint32_t split_lo_bits_f32(float f, const Rounded &hi, int p) {
   const uint32_t u = __float_as_uint(f);
   const int E = (int)((u >> 23) & 0xFF);
   if (E == 0xFF || (u & 0x7FFFFFFFu) == 0) return 0;
@@ -144,8 +146,10 @@ __device__ __forceinline__ uint32_t bf16_lo_bits_f32(float f, const Rounded &hi)
     sign ^= 0x80000000u;
     M = (uint64_t)(-R);
   }
-  return round_core(sign, M, x, 63 - __clzll((long long)M), 8, -126).bits;
+  return round_core(sign, M, x, 63 - __clzll((long long)M), p, -126).bits;
 }
+
+__device__ __forceinline__ uint32_t bf16_lo_bits_f32(float f, const Rounded &hi) { return split_lo_bits_f32(f, hi, 8); }
 
 // ---- fast paths on the high and low 32-bit words of an FP64 value ----
 // Round to nearest even at bit k = 45 (BF16) or k = 42 (TF32, FP16) of the 64-bit

@@ -21,6 +21,13 @@ enum : uint32_t {
 
 // Internal tree flag: the product tree keeps an FP32 master (tensor-core precisions).
 #define SPAMM_INTERNAL_F32 0x10000
+// flag groups of the public API
+constexpr int32_t kCopyFlags = SPAMM_KEEP_FP64 | SPAMM_COPY_TF32 | SPAMM_COPY_BF16 | SPAMM_COPY_FP16 |
+                               SPAMM_COPY_BF16X3 | SPAMM_COPY_TF32X3;
+constexpr int32_t kTreeFlags = SPAMM_HOST_INPUT | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT | kCopyFlags;
+constexpr int32_t kLowCopyFlags = kCopyFlags & ~SPAMM_KEEP_FP64;
+inline bool split_prec(int prec) { return prec == SPAMM_BF16X3 || prec == SPAMM_TF32X3; }
+inline bool tf32_prec(int prec) { return prec == SPAMM_TF32 || prec == SPAMM_TF32X3; }
 
 // Bytes reserved in a product tree for its tensor-core launch descriptor (host image).
 constexpr size_t kTcDescBytes = 1024;
@@ -76,13 +83,15 @@ enum CopyKind : int {
   CK_FP16_T,
   CK_BF16LO,      // low half of the BF16 split
   CK_BF16LO_T,
+  CK_TF32LO,      // low part of the TF32 split, in FP32 storage
+  CK_TF32LO_T,
   CK_COUNT
 };
 
 inline int copy_elem_bytes(int ck) {
   switch (ck) {
     case CK_F64: return 8;
-    case CK_F32: case CK_TF32: case CK_TF32_T: return 4;
+    case CK_F32: case CK_TF32: case CK_TF32_T: case CK_TF32LO: case CK_TF32LO_T: return 4;
     default: return 2;
   }
 }
@@ -171,9 +180,15 @@ cudaError_t sp2_trace_only(spamm_tree X, int idx, void *rec, cudaStream_t s);
 cudaError_t sp2_energy(spamm_tree X, int64_t n, const int64_t *indptr, const int64_t *indices,
                        const double *data, double *partial, void *rec, cudaStream_t s);
 void sp2_read_record(const void *host_rec, int steps, spamm_sp2_result *out);
+double *sp2_tau_slot(void *rec, int step);   // device address of the record's tau of a step
+constexpr int kTreeFeatures = 34;            // per-tree part of the controller's features
 size_t tc_desc_bytes();
 cudaError_t launch_leaf_tc_batch(const spamm_tree *A, const spamm_tree *B, const spamm_tree *C, int count,
                                  int prec, void *host_table, void *dev_table, uint32_t *dev_status, int sm_count,
                                  cudaStream_t s);
 spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau, spamm_prec prec,
                              int32_t flags, spamm_tree *C);
+cudaError_t launch_feat_hist(spamm_tree t, float *out, cudaStream_t s);
+cudaError_t launch_tau_select(spamm_mlp mm, const float *fa, const float *fb, double log10_budget, double lt_min,
+                              double lt_max, int G, double *tau_out, cudaStream_t s);
+int mlp_inputs(spamm_mlp mm);

@@ -39,7 +39,7 @@ constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024;
 // tensor maps); a single product and a batch use the same kernel.
 struct __align__(64) ProdDesc {
   CUtensorMap mA, mB, mAlo, mBlo;          // leaf copies: A rows, B (rows if symmetric, else
-                                           // transposed leaves), and the split-BF16 lows
+                                           // transposed leaves), and the lows of a split
   const uint2 *items;                      // per item: {first pass, passes | touched << 24}
   const int4 *plan;                        // per pass: leaf coordinates of the four boxes
   int64_t cap_plan;
@@ -56,7 +56,7 @@ struct TcCommon {
   uint32_t idesc;
   int32_t chunks;        // 128-byte K chunks per leaf
   int32_t chunk_elems;   // elements per chunk
-  int32_t nsrc;          // 1, or 3 for the split BF16 products (hi hi, hi lo, lo hi)
+  int32_t nsrc;          // 1, or 3 for the split products (hi hi, hi lo, lo hi)
   uint32_t *status;
 };
 
@@ -81,7 +81,7 @@ __device__ __forceinline__ int find_prod(const unsigned long long *s_off, int np
   return lo;
 }
 
-template <int LEAF, bool TF32>
+template <int LEAF, bool TF32, bool PERPASS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_leaf_tc(const ProdDesc *__restrict__ prods, int nprod, TcCommon cm) {
   extern __shared__ uint8_t smem_raw[];
@@ -166,7 +166,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int nl = (int)min(32u, np - c0);
             for (int l = 0; l < nl && !s_abort; l++) {
               const int4 d = s_desc[l];
-              for (int src = 0; src < cm.nsrc && !s_abort; src++) {
+              for (int si = 0; si < cm.nsrc && !s_abort; si++) {
+                // split forms: hi lo, lo hi, then hi hi, so the small products are summed
+                // before the accumulator holds the large one
+                const int src = cm.nsrc == 3 ? (si + 1) % 3 : 0;
                 const CUtensorMap *ma = src == 2 ? &P.mAlo : &P.mA;
                 const CUtensorMap *mb = src == 1 ? &P.mBlo : &P.mB;
                 for (int ch = 0; ch < cm.chunks; ch++) {
@@ -219,7 +222,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           nst = 0;
           last_prod = pr;
         }
-        if (lane == 0 && !s_abort) {
+        // one accumulator per item, or (PERPASS) a fresh one for every pass
+        const int chains = PERPASS ? (int)np : 1;
+        const int per_chain = PERPASS ? cm.nsrc * cm.chunks : total;
+        for (int p = 0; p < chains && lane == 0 && !s_abort; p++) {
           if (!mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort)) {
             s_abort = 1;
             flag_error(cm.status, DEV_TIMEOUT);
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)acc * 128u;
             uint32_t accum = 0;
-            for (int t = 0; t < total; t++) {
+            for (int t = 0; t < per_chain; t++) {
               if (!mbar_wait(&full[stage], phase, &s_abort)) {
                 s_abort = 1;
                 flag_error(cm.status, DEV_TIMEOUT);
@@ -251,9 +257,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             mma_commit(&accf[acc]);
           }
+          if (PERPASS && ++acc == kAcc) {
+            acc = 0;
+            acc_phase ^= 1u;
+          }
         }
         __syncwarp();
-        if (++acc == kAcc) {
+        if (!PERPASS && ++acc == kAcc) {
           acc = 0;
           acc_phase ^= 1u;
         }
@@ -280,14 +290,53 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t I = ij >> 16, J = ij & 0xFFFFu;
         uint32_t touched = __shfl_sync(0xffffffffu, meta.y, ti) >> 24;   // quadrants with a product
         if (LEAF == 128) touched = touched ? (1u << qd) : 0u;
-        bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
-        if (!ok) {
-          s_abort = 1;
-          flag_error(cm.status, DEV_TIMEOUT);
+        // PERPASS: the passes arrive one accumulator each and are summed here in FP32
+        // (round to nearest) in the order of the plan
+        float run[128];
+        if (PERPASS) {
+          const uint32_t first = __shfl_sync(0xffffffffu, meta.x, ti);
+          uint32_t np = __shfl_sync(0xffffffffu, meta.y, ti) & 0xFFFFFFu;
+          const int64_t cap = P.cap_plan;
+          np = (int64_t)first >= cap ? 0u : ((int64_t)first + np > cap ? (uint32_t)(cap - first) : np);
+#pragma unroll
+          for (int x = 0; x < 128; x++) run[x] = 0.f;
+          bool all_ok = true;
+          for (uint32_t p = 0; p < np; p++) {
+            bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
+            if (!ok) {
+              s_abort = 1;
+              flag_error(cm.status, DEV_TIMEOUT);
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            all_ok = all_ok && ok;
+            if (ok) {
+              tc_fence_after();
+#pragma unroll
+              for (int h = 0; h < 4; h++) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * slice) << 16) + (uint32_t)acc * 128u + (uint32_t)(h * 32), v);
+#pragma unroll
+                for (int x = 0; x < 32; x++) run[h * 32 + x] += __uint_as_float(v[x]);
+              }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[acc]);
+            if (++acc == kAcc) {
+              acc = 0;
+              acc_phase ^= 1u;
+            }
+          }
+          if (!all_ok) touched = 0;
+        } else {
+          bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
+          if (!ok) {
+            s_abort = 1;
+            flag_error(cm.status, DEV_TIMEOUT);
+          }
+          ok = __all_sync(0xffffffffu, ok);   // warp-uniform: the TMEM loads are warp-collective
+          if (!ok) touched = 0;
+          tc_fence_after();
         }
-        ok = __all_sync(0xffffffffu, ok);   // warp-uniform: the TMEM loads are warp-collective
-        if (!ok) touched = 0;
-        tc_fence_after();
         const int a = LEAF == 64 ? row / 64 : (qd >> 1);
         const int r = LEAF == 64 ? row % 64 : row;
         const int i = (int)(2 * I) + a;
@@ -303,8 +352,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int h = 0; h < LEAF / 32; h++) {
             uint32_t v[32];
-            const uint32_t col = (uint32_t)acc * 128u + (uint32_t)(cc * 64 + h * 32);
-            tmem_ld32(tmem + ((uint32_t)(32 * slice) << 16) + col, v);
+            if (PERPASS) {
+#pragma unroll
+              for (int x = 0; x < 32; x++) v[x] = __float_as_uint(run[cc * 64 + h * 32 + x]);
+            } else {
+              const uint32_t col = (uint32_t)acc * 128u + (uint32_t)(cc * 64 + h * 32);
+              tmem_ld32(tmem + ((uint32_t)(32 * slice) << 16) + col, v);
+            }
 #pragma unroll
             for (int x = 0; x < 32; x += 4) {
               float4 f = make_float4(__uint_as_float(v[x]), __uint_as_float(v[x + 1]),
@@ -323,8 +377,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-        tc_fence_before();
-        mbar_arrive(&acce[acc]);
+        if (!PERPASS) {
+          tc_fence_before();
+          mbar_arrive(&acce[acc]);
+        }
         // squared Frobenius norms of the written blocks: rows -> warp -> fixed pair order
 #pragma unroll
         for (int cc = 0; cc < RC; cc++) {
@@ -354,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (++acc == kAcc) {
+        if (!PERPASS && ++acc == kAcc) {
           acc = 0;
           acc_phase ^= 1u;
         }
@@ -404,28 +460,29 @@ bool make_map(CUtensorMap *m, const void *data, int elem, int b, int nb) {
   return r == CUDA_SUCCESS;
 }
 
-template <int LEAF, bool TF32>
+template <int LEAF, bool TF32, bool PERPASS>
 cudaError_t run(const ProdDesc *table, int nprod, const TcCommon &cm, int sm_count, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, TF32, PERPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kSmemBytes);
   if (e != cudaSuccess) return e;
-  k_leaf_tc<LEAF, TF32><<<sm_count, kThreads, kSmemBytes, s>>>(table, nprod, cm);
+  k_leaf_tc<LEAF, TF32, PERPASS><<<sm_count, kThreads, kSmemBytes, s>>>(table, nprod, cm);
   return cudaGetLastError();
 }
 
 // Host image of one product's descriptor.
 bool fill_desc(ProdDesc *d, spamm_tree A, spamm_tree B, spamm_tree C, int prec) {
-  const bool tf32 = prec == SPAMM_TF32;
+  const bool tf32 = tf32_prec(prec);
   const int elem = tf32 ? 4 : 2;
   const int row = tf32 ? CK_TF32 : prec == SPAMM_FP16 ? CK_FP16 : CK_BF16;
   const bool bsym = (B->flags & SPAMM_SYMMETRIC) != 0;
   const int brow = bsym ? row : row + 1;
-  const int blo = bsym ? CK_BF16LO : CK_BF16LO_T;
+  const int alo = tf32 ? CK_TF32LO : CK_BF16LO;
+  const int blo = bsym ? alo : alo + 1;
   memset(d, 0, sizeof *d);
   if (!make_map(&d->mA, A->copy[row], elem, A->b, A->nb) || !make_map(&d->mB, B->copy[brow], elem, B->b, B->nb))
     return false;
-  if (prec == SPAMM_BF16X3) {
-    if (!make_map(&d->mAlo, A->copy[CK_BF16LO], elem, A->b, A->nb) || !make_map(&d->mBlo, B->copy[blo], elem, B->b, B->nb))
+  if (split_prec(prec)) {
+    if (!make_map(&d->mAlo, A->copy[alo], elem, A->b, A->nb) || !make_map(&d->mBlo, B->copy[blo], elem, B->b, B->nb))
       return false;
   } else {
     d->mAlo = d->mA;
@@ -446,13 +503,13 @@ bool fill_desc(ProdDesc *d, spamm_tree A, spamm_tree B, spamm_tree C, int prec) 
 }
 
 TcCommon common_of(int prec, int b, uint32_t *status) {
-  const bool tf32 = prec == SPAMM_TF32;
+  const bool tf32 = tf32_prec(prec);
   const int elem = tf32 ? 4 : 2;
   TcCommon cm{};
   cm.idesc = make_idesc(tf32 ? kFmtTF32 : prec == SPAMM_FP16 ? kFmtF16 : kFmtBF16, 128, 128);
   cm.chunks = b * elem / 128;
   cm.chunk_elems = 128 / elem;
-  cm.nsrc = prec == SPAMM_BF16X3 ? 3 : 1;
+  cm.nsrc = split_prec(prec) ? 3 : 1;
   cm.status = status;
   return cm;
 }
@@ -460,9 +517,15 @@ TcCommon common_of(int prec, int b, uint32_t *status) {
 cudaError_t run_table(const ProdDesc *table, int nprod, int b, int prec, uint32_t *status, int sm_count,
                       cudaStream_t s) {
   const TcCommon cm = common_of(prec, b, status);
-  const bool tf32 = prec == SPAMM_TF32;
-  if (b == 64) return tf32 ? run<64, true>(table, nprod, cm, sm_count, s) : run<64, false>(table, nprod, cm, sm_count, s);
-  if (b == 128) return tf32 ? run<128, true>(table, nprod, cm, sm_count, s) : run<128, false>(table, nprod, cm, sm_count, s);
+  const bool tf32 = tf32_prec(prec), pp = split_prec(prec);
+  if (b == 64) {
+    if (pp) return tf32 ? run<64, true, true>(table, nprod, cm, sm_count, s) : run<64, false, true>(table, nprod, cm, sm_count, s);
+    return tf32 ? run<64, true, false>(table, nprod, cm, sm_count, s) : run<64, false, false>(table, nprod, cm, sm_count, s);
+  }
+  if (b == 128) {
+    if (pp) return tf32 ? run<128, true, true>(table, nprod, cm, sm_count, s) : run<128, false, true>(table, nprod, cm, sm_count, s);
+    return tf32 ? run<128, true, false>(table, nprod, cm, sm_count, s) : run<128, false, false>(table, nprod, cm, sm_count, s);
+  }
   return cudaErrorInvalidValue;
 }
 

@@ -22,7 +22,7 @@ struct BuildArgs {
   uint8_t *nz;
   double *f64;             // optional copies (nullptr = not written)
   float *f32;              // FP32 master (purification iterates)
-  float *tf32, *tf32T;
+  float *tf32, *tf32T, *tlo, *tloT;   // TF32 and the low part of the TF32 split
   uint16_t *bf16, *bf16T, *fp16, *fp16T, *lo, *loT;
 };
 
@@ -94,12 +94,13 @@ __global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p) {
   const bool stored = inrange && r < p.nb && c < p.nb;
   const int64_t tile = ((int64_t)r * p.nb + c) * (int64_t)B * B;
   const size_t bb = (size_t)B * B;
-  const bool any_t = p.tf32T || p.bf16T || p.fp16T || p.loT;
-  float *s_tf32T = nullptr;
+  const bool any_t = p.tf32T || p.bf16T || p.fp16T || p.loT || p.tloT;
+  float *s_tf32T = nullptr, *s_tloT = nullptr;
   uint16_t *s_bf16T = nullptr, *s_fp16T = nullptr, *s_loT = nullptr;
   {
     unsigned char *q = smem;
     if (p.tf32T) { s_tf32T = (float *)q + li * bb; q += Cfg::LPC * bb * 4; }
+    if (p.tloT) { s_tloT = (float *)q + li * bb; q += Cfg::LPC * bb * 4; }
     if (p.bf16T) { s_bf16T = (uint16_t *)q + li * bb; q += Cfg::LPC * bb * 2; }
     if (p.fp16T) { s_fp16T = (uint16_t *)q + li * bb; q += Cfg::LPC * bb * 2; }
     if (p.loT) { s_loT = (uint16_t *)q + li * bb; q += Cfg::LPC * bb * 2; }
@@ -197,11 +198,26 @@ __global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p) {
             }
           }
         }
-        if (p.tf32 || s_tf32T) {
-          const uint32_t t0 = (E0 >= 897 && E0 <= 1150) ? tf32_fast(h0, l0)
-                                                       : round_f64bits(((uint64_t)h0 << 32) | l0, 11, -126).bits;
-          const uint32_t t1 = (E1 >= 897 && E1 <= 1150) ? tf32_fast(h1, l1)
-                                                       : round_f64bits(((uint64_t)h1 << 32) | l1, 11, -126).bits;
+        if (p.tf32 || s_tf32T || p.tlo || s_tloT) {
+          uint32_t t0, t1;
+          if (p.tlo || s_tloT) {
+            const Rounded r0 = round_f64bits(((uint64_t)h0 << 32) | l0, 11, -126);
+            const Rounded r1 = round_f64bits(((uint64_t)h1 << 32) | l1, 11, -126);
+            t0 = r0.bits;
+            t1 = r1.bits;
+            const uint32_t q0 = split_lo_bits(((uint64_t)h0 << 32) | l0, r0, 11);
+            const uint32_t q1 = split_lo_bits(((uint64_t)h1 << 32) | l1, r1, 11);
+            if (p.tlo) *reinterpret_cast<uint2 *>(p.tlo + o) = make_uint2(q0, q1);
+            if (s_tloT) {
+              s_tloT[cols[u] * B + rows[u]] = __uint_as_float(q0);
+              s_tloT[(cols[u] + 1) * B + rows[u]] = __uint_as_float(q1);
+            }
+          } else {
+            t0 = (E0 >= 897 && E0 <= 1150) ? tf32_fast(h0, l0)
+                                           : round_f64bits(((uint64_t)h0 << 32) | l0, 11, -126).bits;
+            t1 = (E1 >= 897 && E1 <= 1150) ? tf32_fast(h1, l1)
+                                           : round_f64bits(((uint64_t)h1 << 32) | l1, 11, -126).bits;
+          }
           if (p.tf32) *reinterpret_cast<uint2 *>(p.tf32 + o) = make_uint2(t0, t1);
           if (s_tf32T) {
             s_tf32T[cols[u] * B + rows[u]] = __uint_as_float(t0);
@@ -265,6 +281,9 @@ __global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p) {
   if (s_tf32T)
     for (int q = tl; q < (int)(bb / 4); q += Cfg::TPL)
       reinterpret_cast<float4 *>(p.tf32T + tile)[q] = reinterpret_cast<const float4 *>(s_tf32T)[q];
+  if (s_tloT)
+    for (int q = tl; q < (int)(bb / 4); q += Cfg::TPL)
+      reinterpret_cast<float4 *>(p.tloT + tile)[q] = reinterpret_cast<const float4 *>(s_tloT)[q];
   if (s_bf16T)
     for (int q = tl; q < (int)(bb / 8); q += Cfg::TPL)
       reinterpret_cast<uint4 *>(p.bf16T + tile)[q] = reinterpret_cast<const uint4 *>(s_bf16T)[q];
@@ -385,6 +404,8 @@ cudaError_t launch_tree_build(spamm_tree t, const double *A, cudaStream_t s) {
   p.f32 = (float *)t->copy[CK_F32];
   p.tf32 = (float *)t->copy[CK_TF32];
   p.tf32T = (float *)t->copy[CK_TF32_T];
+  p.tlo = (float *)t->copy[CK_TF32LO];
+  p.tloT = (float *)t->copy[CK_TF32LO_T];
   p.bf16 = (uint16_t *)t->copy[CK_BF16];
   p.bf16T = (uint16_t *)t->copy[CK_BF16_T];
   p.fp16 = (uint16_t *)t->copy[CK_FP16];
@@ -394,6 +415,7 @@ cudaError_t launch_tree_build(spamm_tree t, const double *A, cudaStream_t s) {
   size_t per_leaf = 0;
   const size_t bb = (size_t)t->b * t->b;
   if (p.tf32T) per_leaf += bb * 4;
+  if (p.tloT) per_leaf += bb * 4;
   if (p.bf16T) per_leaf += bb * 2;
   if (p.fp16T) per_leaf += bb * 2;
   if (p.loT) per_leaf += bb * 2;
@@ -442,7 +464,7 @@ struct ConvertArgs {
   int src_f64;
   const uint8_t *nz;
   int32_t b, nb, NB;
-  float *tf32, *tf32T;
+  float *tf32, *tf32T, *tlo, *tloT;
   uint16_t *bf16, *bf16T, *fp16, *fp16T, *lo, *loT;
 };
 
@@ -453,11 +475,12 @@ __global__ void __launch_bounds__(256) k_tile_convert(ConvertArgs p) {
   const int32_t r = (int32_t)(leaf / p.nb), c = (int32_t)(leaf % p.nb);
   if (!p.nz[(int64_t)r * p.NB + c]) return;   // never read: zero blocks load as zero fill
   const int64_t tile = leaf * (int64_t)b * b;
-  float *s_tf32T = nullptr;
+  float *s_tf32T = nullptr, *s_tloT = nullptr;
   uint16_t *s_bf16T = nullptr, *s_fp16T = nullptr, *s_loT = nullptr;
   {
     unsigned char *q = smem;
     if (p.tf32T) { s_tf32T = (float *)q; q += (size_t)b * b * 4; }
+    if (p.tloT) { s_tloT = (float *)q; q += (size_t)b * b * 4; }
     if (p.bf16T) { s_bf16T = (uint16_t *)q; q += (size_t)b * b * 2; }
     if (p.fp16T) { s_fp16T = (uint16_t *)q; q += (size_t)b * b * 2; }
     if (p.loT) { s_loT = (uint16_t *)q; q += (size_t)b * b * 2; }
@@ -466,22 +489,27 @@ __global__ void __launch_bounds__(256) k_tile_convert(ConvertArgs p) {
   for (int32_t e = threadIdx.x; e < bb; e += blockDim.x) {
     const int32_t row = e / b, col = e % b;
     Rounded hb, tb, fb;
-    uint32_t lb = 0;
+    uint32_t lb = 0, tl = 0;
+    const bool want_tlo = p.tlo || s_tloT;
     if (p.src_f64) {
       const uint64_t bits = (uint64_t)__double_as_longlong(((const double *)p.src)[tile + e]);
       hb = round_f64bits(bits, 8, -126);
       tb = round_f64bits(bits, 11, -126);
       fb = round_f64bits(bits, 11, -14);
       if (p.lo || s_loT) lb = bf16_lo_bits(bits, hb);
+      if (want_tlo) tl = split_lo_bits(bits, tb, 11);
     } else {
       const float f = ((const float *)p.src)[tile + e];
       hb = round_f32(f, 8, -126);
       tb = round_f32(f, 11, -126);
       fb = round_f32(f, 11, -14);
       if (p.lo || s_loT) lb = bf16_lo_bits_f32(f, hb);
+      if (want_tlo) tl = split_lo_bits_f32(f, tb, 11);
     }
     if (p.tf32) p.tf32[tile + e] = __uint_as_float(tb.bits);
     if (s_tf32T) s_tf32T[col * b + row] = __uint_as_float(tb.bits);
+    if (p.tlo) p.tlo[tile + e] = __uint_as_float(tl);
+    if (s_tloT) s_tloT[col * b + row] = __uint_as_float(tl);
     if (p.bf16) p.bf16[tile + e] = bf16_from_f32bits(hb.bits);
     if (s_bf16T) s_bf16T[col * b + row] = bf16_from_f32bits(hb.bits);
     if (p.lo) p.lo[tile + e] = bf16_from_f32bits(lb);
@@ -495,6 +523,7 @@ __global__ void __launch_bounds__(256) k_tile_convert(ConvertArgs p) {
   __syncthreads();
   for (int32_t e = threadIdx.x; e < bb; e += blockDim.x) {
     if (s_tf32T) p.tf32T[tile + e] = s_tf32T[e];
+    if (s_tloT) p.tloT[tile + e] = s_tloT[e];
     if (s_bf16T) p.bf16T[tile + e] = s_bf16T[e];
     if (s_fp16T) p.fp16T[tile + e] = s_fp16T[e];
     if (s_loT) p.loT[tile + e] = s_loT[e];
@@ -514,17 +543,20 @@ cudaError_t launch_tile_convert(spamm_tree t, cudaStream_t s) {
   p.NB = t->NB;
   p.tf32 = (float *)t->copy[CK_TF32];
   p.tf32T = (float *)t->copy[CK_TF32_T];
+  p.tlo = (float *)t->copy[CK_TF32LO];
+  p.tloT = (float *)t->copy[CK_TF32LO_T];
   p.bf16 = (uint16_t *)t->copy[CK_BF16];
   p.bf16T = (uint16_t *)t->copy[CK_BF16_T];
   p.fp16 = (uint16_t *)t->copy[CK_FP16];
   p.fp16T = (uint16_t *)t->copy[CK_FP16_T];
   p.lo = (uint16_t *)t->copy[CK_BF16LO];
   p.loT = (uint16_t *)t->copy[CK_BF16LO_T];
-  if (!p.tf32 && !p.tf32T && !p.bf16 && !p.bf16T && !p.fp16 && !p.fp16T && !p.lo && !p.loT)
+  if (!p.tf32 && !p.tf32T && !p.bf16 && !p.bf16T && !p.fp16 && !p.fp16T && !p.lo && !p.loT && !p.tlo && !p.tloT)
     return cudaSuccess;
   size_t sm = 0;
   const size_t bb = (size_t)t->b * t->b;
   if (p.tf32T) sm += bb * 4;
+  if (p.tloT) sm += bb * 4;
   if (p.bf16T) sm += bb * 2;
   if (p.fp16T) sm += bb * 2;
   if (p.loT) sm += bb * 2;

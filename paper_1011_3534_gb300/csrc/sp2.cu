@@ -21,6 +21,7 @@ struct StepRec {        // device record of a solve
   double trace2[SPAMM_SP2_MAX_STEPS + 1];
   int32_t branch[SPAMM_SP2_MAX_STEPS + 1];
   unsigned long long leaf_products[SPAMM_SP2_MAX_STEPS];
+  double tau[SPAMM_SP2_MAX_STEPS];   // tolerances chosen on the device (learned steps)
   double energy;
 };
 
@@ -88,7 +89,7 @@ struct UpdArgs {
   int32_t b, nb, NB;
   const StepRec *rec;
   int step;
-  float *tf32;
+  float *tf32, *tlo;
   uint16_t *bf16, *lo, *fp16;
 };
 
@@ -139,25 +140,28 @@ __global__ void __launch_bounds__(256) k_sp2_update(UpdArgs p) {
       sl += ((sh - (t - tb)) + (pp - tb)) + er;
       sh = t;
     }
-    if (p.bf16 || p.lo || p.tf32 || p.fp16) {
+    if (p.bf16 || p.lo || p.tf32 || p.tlo || p.fp16) {
       Rounded h, t32, f16;
-      uint32_t lo = 0;
+      uint32_t lo = 0, tl = 0;
       if (sizeof(T) == 8) {
         const uint64_t bits = (uint64_t)__double_as_longlong((double)v);
         h = round_f64bits(bits, 8, -126);
         if (p.lo) lo = bf16_lo_bits(bits, h);
-        if (p.tf32) t32 = round_f64bits(bits, 11, -126);
+        if (p.tf32 || p.tlo) t32 = round_f64bits(bits, 11, -126);
+        if (p.tlo) tl = split_lo_bits(bits, t32, 11);
         if (p.fp16) f16 = round_f64bits(bits, 11, -14);
       } else {
         const float f = (float)v;
         h = round_f32(f, 8, -126);
         if (p.lo) lo = bf16_lo_bits_f32(f, h);
-        if (p.tf32) t32 = round_f32(f, 11, -126);
+        if (p.tf32 || p.tlo) t32 = round_f32(f, 11, -126);
+        if (p.tlo) tl = split_lo_bits_f32(f, t32, 11);
         if (p.fp16) f16 = round_f32(f, 11, -14);
       }
       if (p.bf16) p.bf16[base + e] = bf16_from_f32bits(h.bits);
       if (p.lo) p.lo[base + e] = bf16_from_f32bits(lo);
       if (p.tf32) p.tf32[base + e] = __uint_as_float(t32.bits);
+      if (p.tlo) p.tlo[base + e] = __uint_as_float(tl);
       if (p.fp16) p.fp16[base + e] = fp16_from_f32bits(f16.bits);
     }
   }
@@ -259,6 +263,7 @@ cudaError_t sp2_step_finish(spamm_tree X, spamm_tree C, double n_occ, int step, 
   u.rec = rec;
   u.step = step;
   u.tf32 = (float *)C->copy[CK_TF32];
+  u.tlo = (float *)C->copy[CK_TF32LO];
   u.bf16 = (uint16_t *)C->copy[CK_BF16];
   u.lo = (uint16_t *)C->copy[CK_BF16LO];
   u.fp16 = (uint16_t *)C->copy[CK_FP16];
@@ -304,5 +309,8 @@ void sp2_read_record(const void *host_rec, int steps, spamm_sp2_result *out) {
   for (int s = 0; s < steps; s++) {
     out->branch[s] = r->branch[s];
     out->leaf_products[s] = (int64_t)r->leaf_products[s];
+    out->tau[s] = r->tau[s];
   }
 }
+
+double *sp2_tau_slot(void *rec, int step) { return &((StepRec *)rec)->tau[step]; }

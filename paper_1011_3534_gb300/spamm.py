@@ -15,9 +15,9 @@ import numpy as np
 from . import build as _build
 
 SPAMM_OK, SPAMM_EINVAL, SPAMM_ENOMEM, SPAMM_ECUDA, SPAMM_ERANGE, SPAMM_ETIMEOUT, SPAMM_EUNSUPPORTED = range(7)
-SPAMM_FP64, SPAMM_TF32, SPAMM_BF16, SPAMM_FP16, SPAMM_BF16X3 = range(5)
+SPAMM_FP64, SPAMM_TF32, SPAMM_BF16, SPAMM_FP16, SPAMM_BF16X3, SPAMM_TF32X3 = range(6)
 PRECISIONS = {"fp64": SPAMM_FP64, "tf32": SPAMM_TF32, "bf16": SPAMM_BF16, "fp16": SPAMM_FP16,
-              "bf16x3": SPAMM_BF16X3}
+              "bf16x3": SPAMM_BF16X3, "tf32x3": SPAMM_TF32X3}
 
 SPAMM_HOST_INPUT = 0x0001
 SPAMM_SYMMETRIC = 0x0002
@@ -28,8 +28,10 @@ SPAMM_COPY_FP16 = 0x0040
 SPAMM_COPY_BF16X3 = 0x0080
 SPAMM_NO_RIGHT = 0x0100
 SPAMM_GRAPH = 0x0200
+SPAMM_COPY_TF32X3 = 0x0400
 COPY_FLAG = {SPAMM_FP64: SPAMM_KEEP_FP64, SPAMM_TF32: SPAMM_COPY_TF32, SPAMM_BF16: SPAMM_COPY_BF16,
-             SPAMM_FP16: SPAMM_COPY_FP16, SPAMM_BF16X3: SPAMM_COPY_BF16X3}
+             SPAMM_FP16: SPAMM_COPY_FP16, SPAMM_BF16X3: SPAMM_COPY_BF16X3, SPAMM_TF32X3: SPAMM_COPY_TF32X3}
+MLP_FEATURES = 68
 MAX_LEVELS = 24
 
 # Every entry point declared in include/spamm.h.
@@ -37,7 +39,11 @@ EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_er
            "spamm_kernel_launches", "spamm_tree_build", "spamm_tree_update", "spamm_tree_free", "spamm_tree_info",
            "spamm_tree_norms", "spamm_tree_to_dense", "spamm_multiply", "spamm_stats",
            "spamm_triples", "spamm_cull_noalloc", "spamm_sp2", "spamm_multiply_batched",
-           "spamm_tune_leaf")
+           "spamm_tune_leaf", "spamm_mlp_create", "spamm_mlp_free", "spamm_mlp_num_params",
+           "spamm_mlp_get_params", "spamm_mlp_set_params", "spamm_mlp_forward", "spamm_mlp_gradient",
+           "spamm_mlp_adam_step", "spamm_mlp_adam_apply", "spamm_mlp_train", "spamm_features", "spamm_tau_select",
+           "spamm_tree_distance", "spamm_sp2_begin", "spamm_sp2_step", "spamm_sp2_step_learned",
+           "spamm_sp2_iterate", "spamm_sp2_end", "spamm_sp2_learned")
 
 
 class SpammError(RuntimeError):
@@ -63,7 +69,7 @@ class Sp2ResultT(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double),
                 ("steps", ctypes.c_int32), ("trace", ctypes.c_double * (SP2_MAX_STEPS + 1)),
                 ("branch", ctypes.c_int32 * SP2_MAX_STEPS), ("leaf_products", ctypes.c_int64 * SP2_MAX_STEPS),
-                ("ms", ctypes.c_double)]
+                ("tau", ctypes.c_double * SP2_MAX_STEPS), ("ms", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -97,9 +103,30 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.spamm_multiply_batched.argtypes = [_P, _P, _P, _P, _I32, ctypes.c_int, _I32, _P]
     L.spamm_tune_leaf.argtypes = [_P, _P, _I64, _D, ctypes.c_int, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_D)]
     L.spamm_sp2.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, _I32, ctypes.c_int, _P, ctypes.POINTER(Sp2ResultT)]
+    L.spamm_sp2_learned.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, _I32, ctypes.c_int, _P, _D, _D, _D,
+                                    ctypes.POINTER(Sp2ResultT)]
+    L.spamm_sp2_begin.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, ctypes.c_int, ctypes.POINTER(_P)]
+    L.spamm_sp2_step.argtypes = [_P, _D]
+    L.spamm_sp2_step_learned.argtypes = [_P, _P, _D, _D, _D]
+    L.spamm_sp2_iterate.argtypes = [_P, ctypes.POINTER(_P)]
+    L.spamm_sp2_end.argtypes = [_P, ctypes.POINTER(Sp2ResultT)]
+    L.spamm_mlp_create.argtypes = [_P, _I32, _I32, ctypes.c_uint64, ctypes.POINTER(_P)]
+    L.spamm_mlp_free.argtypes = [_P]
+    L.spamm_mlp_num_params.argtypes = [_P]
+    L.spamm_mlp_get_params.argtypes = [_P, _P, _I32]
+    L.spamm_mlp_set_params.argtypes = [_P, _P, _I32]
+    L.spamm_mlp_forward.argtypes = [_P, _P, _I32, _P]
+    L.spamm_mlp_gradient.argtypes = [_P, _P, _P, _I32, _P, _P]
+    L.spamm_mlp_adam_step.argtypes = [_P, _P, _P, _I32, ctypes.c_float, _P]
+    L.spamm_mlp_adam_apply.argtypes = [_P, _P, ctypes.c_float]
+    L.spamm_mlp_train.argtypes = [_P, _P, _P, _I32, _I32, _I32, ctypes.c_float, ctypes.c_uint64, _P]
+    L.spamm_features.argtypes = [_P, _P, _D, _P]
+    L.spamm_tau_select.argtypes = [_P, _P, _P, _D, _D, _D, ctypes.POINTER(_D)]
+    L.spamm_tree_distance.argtypes = [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]
     for name in EXPORTS:
-        if name not in ("spamm_last_error", "spamm_kernel_launches"):
+        if name not in ("spamm_last_error", "spamm_kernel_launches", "spamm_mlp_num_params"):
             getattr(L, name).restype = st
+    L.spamm_mlp_num_params.restype = _I32
     return L
 
 
@@ -256,9 +283,142 @@ def spamm_sp2(ctx: Ctx, indptr, indices, data, n_occ: float, steps: int, leaf: i
     ctx.check(LIB.spamm_sp2(ctx.h, n, indptr.ctypes.data, indices.ctypes.data, data.ctypes.data, float(n_occ),
                             steps, leaf, int(prec), tau.ctypes.data if steps else None, ctypes.byref(r)),
               "spamm_sp2")
-    return dict(energy=r.energy, eps_min=r.eps_min, eps_max=r.eps_max, steps=r.steps,
-                traces=list(r.trace[:steps + 1]), branches=list(r.branch[:steps]),
-                leaf_products=list(r.leaf_products[:steps]), ms=r.ms)
+    return _sp2_dict(r)
+
+
+def _sp2_dict(r: Sp2ResultT) -> dict:
+    k = r.steps
+    return dict(energy=r.energy, eps_min=r.eps_min, eps_max=r.eps_max, steps=k,
+                traces=list(r.trace[:k + 1]), branches=list(r.branch[:k]),
+                leaf_products=list(r.leaf_products[:k]), taus=list(r.tau[:k]), ms=r.ms)
+
+
+def _csr(indptr, indices, data):
+    return (np.ascontiguousarray(indptr, dtype=np.int64), np.ascontiguousarray(indices, dtype=np.int64),
+            np.ascontiguousarray(data, dtype=np.float64))
+
+
+def spamm_sp2_learned(ctx: Ctx, indptr, indices, data, n_occ: float, steps: int, leaf: int, prec: int,
+                      mlp: "Mlp", err_budget: float, tau_min: float, tau_max: float) -> dict:
+    """SP2 with every step's tolerance chosen on the device by the controller."""
+    ip, ix, dv = _csr(indptr, indices, data)
+    r = Sp2ResultT()
+    ctx.check(LIB.spamm_sp2_learned(ctx.h, ip.size - 1, ip.ctypes.data, ix.ctypes.data, dv.ctypes.data,
+                                    float(n_occ), steps, leaf, int(prec), mlp.h, float(err_budget),
+                                    float(tau_min), float(tau_max), ctypes.byref(r)), "spamm_sp2_learned")
+    return _sp2_dict(r)
+
+
+class Sp2Run:
+    """spamm_sp2_begin .. spamm_sp2_end: the SP2 loop one step at a time."""
+
+    def __init__(self, ctx: Ctx, indptr, indices, data, n_occ: float, leaf: int, prec: int):
+        self.ctx = ctx
+        ip, ix, dv = _csr(indptr, indices, data)
+        h = _P()
+        ctx.check(LIB.spamm_sp2_begin(ctx.h, ip.size - 1, ip.ctypes.data, ix.ctypes.data, dv.ctypes.data,
+                                      float(n_occ), leaf, int(prec), ctypes.byref(h)), "spamm_sp2_begin")
+        self.h = h.value
+
+    def step(self, tau: float):
+        self.ctx.check(LIB.spamm_sp2_step(self.h, float(tau)), "spamm_sp2_step")
+
+    def step_learned(self, mlp: "Mlp", err_budget: float, tau_min: float, tau_max: float):
+        self.ctx.check(LIB.spamm_sp2_step_learned(self.h, mlp.h, float(err_budget), float(tau_min), float(tau_max)),
+                       "spamm_sp2_step_learned")
+
+    def iterate(self) -> Tree:
+        """The current iterate (borrowed: valid until the next step or end; never freed here)."""
+        x = _P()
+        self.ctx.check(LIB.spamm_sp2_iterate(self.h, ctypes.byref(x)), "spamm_sp2_iterate")
+        return Tree(self.ctx, x.value)
+
+    def end(self) -> dict:
+        r = Sp2ResultT()
+        h, self.h = self.h, None
+        self.ctx.check(LIB.spamm_sp2_end(h, ctypes.byref(r)), "spamm_sp2_end")
+        return _sp2_dict(r)
+
+
+# ---- tolerance controller ----
+class Mlp:
+    def __init__(self, ctx: Ctx, inputs: int, hidden: int, seed: int = 0):
+        self.ctx = ctx
+        h = _P()
+        ctx.check(LIB.spamm_mlp_create(ctx.h, inputs, hidden, seed, ctypes.byref(h)), "spamm_mlp_create")
+        self.h = h.value
+        self.inputs, self.hidden = inputs, hidden
+        self.P = LIB.spamm_mlp_num_params(self.h)
+
+    def free(self):
+        if self.h:
+            LIB.spamm_mlp_free(self.h)
+            self.h = None
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.P, dtype=np.float32)
+        self.ctx.check(LIB.spamm_mlp_get_params(self.h, out.ctypes.data, self.P), "spamm_mlp_get_params")
+        return out
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        self.ctx.check(LIB.spamm_mlp_set_params(self.h, th.ctypes.data, th.size), "spamm_mlp_set_params")
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.empty(X.shape[0], dtype=np.float32)
+        self.ctx.check(LIB.spamm_mlp_forward(self.h, X.ctypes.data, X.shape[0], y.ctypes.data), "spamm_mlp_forward")
+        return y
+
+    def gradient(self, X, y) -> tuple[float, np.ndarray]:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        g = np.empty(self.P, dtype=np.float32)
+        L = np.zeros(1, dtype=np.float32)
+        self.ctx.check(LIB.spamm_mlp_gradient(self.h, X.ctypes.data, y.ctypes.data, X.shape[0], g.ctypes.data,
+                                              L.ctypes.data), "spamm_mlp_gradient")
+        return float(L[0]), g
+
+    def adam_step(self, X, y, lr: float) -> float:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        L = np.zeros(1, dtype=np.float32)
+        self.ctx.check(LIB.spamm_mlp_adam_step(self.h, X.ctypes.data, y.ctypes.data, X.shape[0], float(lr),
+                                               L.ctypes.data), "spamm_mlp_adam_step")
+        return float(L[0])
+
+    def adam_apply(self, grad, lr: float):
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        assert g.size == self.P
+        self.ctx.check(LIB.spamm_mlp_adam_apply(self.h, g.ctypes.data, float(lr)), "spamm_mlp_adam_apply")
+
+    def train(self, X, y, epochs: int, batch: int, lr: float, seed: int = 0) -> float:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        L = np.zeros(1, dtype=np.float32)
+        self.ctx.check(LIB.spamm_mlp_train(self.h, X.ctypes.data, y.ctypes.data, X.shape[0], epochs, batch,
+                                           float(lr), seed, L.ctypes.data), "spamm_mlp_train")
+        return float(L[0])
+
+
+def spamm_features(A: Tree, B: Tree, tau: float) -> np.ndarray:
+    out = np.empty(MLP_FEATURES, dtype=np.float32)
+    A.ctx.check(LIB.spamm_features(A.h, B.h, float(tau), out.ctypes.data), "spamm_features")
+    return out
+
+
+def spamm_tau_select(mlp: Mlp, A: Tree, B: Tree, err_budget: float, tau_min: float, tau_max: float) -> float:
+    t = _D()
+    A.ctx.check(LIB.spamm_tau_select(mlp.h, A.h, B.h, float(err_budget), float(tau_min), float(tau_max),
+                                     ctypes.byref(t)), "spamm_tau_select")
+    return t.value
+
+
+def spamm_tree_distance(X: Tree, Y: Tree) -> tuple[float, float]:
+    """(||X - Y||_F, ||Y||_F)."""
+    d, r = _D(), _D()
+    X.ctx.check(LIB.spamm_tree_distance(X.h, Y.h, ctypes.byref(d), ctypes.byref(r)), "spamm_tree_distance")
+    return d.value, r.value
 
 
 def spamm_multiply_batched(ctx: Ctx, A: list, B: list, tau, prec: int, flags: int = 0, C: list | None = None) -> list:

@@ -51,7 +51,7 @@ def test_sp2_fp64_tau0_matches_dense(S, ctx, side, leaf):
     assert all(lp == NB ** 3 for lp in g["leaf_products"])   # tau = 0 keeps every triple
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-5), ("tf32", 1e-3), ("bf16", 1e-2)])
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-6), ("bf16x3", 1e-5), ("tf32", 1e-3), ("bf16", 1e-2)])
 def test_sp2_tensor_core_energy(S, ctx, prec, tol):
     (ip, ix, d), H, n, lo, hi = system(10)
     ref = O.sp2_dense(H, n / 2, 30, lo, hi)
@@ -74,3 +74,36 @@ def test_sp2_tau_positive_and_spectral_oracle(S, ctx):
         print(f"SP2 fp64 tau={tau:g}: relative energy error {err:.3e}, leaf products {sum(g['leaf_products'])}")
         assert err < 1e3 * tau
         assert sum(g["leaf_products"]) < sum(g0["leaf_products"])
+
+
+def test_sp2_stepwise_run_equals_one_shot(S, ctx):
+    # the run object queues the same kernels in the same order: identical results
+    (ip, ix, d), H, n, lo, hi = system(10)
+    taus = [1e-9 * (1 + (k % 3)) for k in range(25)]
+    one = S.spamm_sp2(ctx, ip, ix, d, n / 2, 25, 64, S.SPAMM_TF32X3, np.array(taus))
+    run = S.Sp2Run(ctx, ip, ix, d, n / 2, 64, S.SPAMM_TF32X3)
+    for k, t in enumerate(taus):
+        run.step(t)
+        X = run.iterate()
+        assert X.n == n and X.leaf == 64
+    two = run.end()
+    assert two["energy"] == one["energy"] and two["traces"] == one["traces"]
+    assert two["branches"] == one["branches"] and two["leaf_products"] == one["leaf_products"]
+    assert two["taus"] == taus
+
+
+def test_sp2_learned_with_constant_network_equals_fixed_tau(S, ctx):
+    # a network predicting log10 error -7 everywhere: with budget 1e-6 every step takes
+    # tau_max, with budget 1e-8 every step tau_min; each must equal the fixed-tau loop
+    (ip, ix, d), H, n, lo, hi = system(10)
+    m = S.Mlp(ctx, S.MLP_FEATURES, 8, seed=0)
+    z = np.zeros(m.P, dtype=np.float32)
+    z[-1] = -7.0
+    m.set_params(z)
+    for budget, tau in ((1e-6, 1e-5), (1e-8, 1e-9)):
+        g = S.spamm_sp2_learned(ctx, ip, ix, d, n / 2, 20, 64, S.SPAMM_BF16X3, m, budget, 1e-9, 1e-5)
+        f = S.spamm_sp2(ctx, ip, ix, d, n / 2, 20, 64, S.SPAMM_BF16X3, tau)
+        assert all(abs(t / tau - 1) < 1e-12 for t in g["taus"])
+        assert g["energy"] == f["energy"] and g["branches"] == f["branches"]
+        assert g["leaf_products"] == f["leaf_products"]
+    m.free()

@@ -5,7 +5,7 @@ the near-tau band). C is compared with the oracle's SpAMM whose leaf products us
 operands rounded to the leaf format (oracle/formats.py, from the format definitions)
 and summed in FP64: the only remaining difference is FP32 accumulation, bounded
 elementwise by K * 2^-23 * (|A| |B|)_ij, K the number of products summed into entry
-(i, j) (b per surviving k, three times that for the split BF16 form). The error
+(i, j) (b per surviving k, three times that for the split forms). The error
 against the plain FP64 SpAMM is reported, not asserted beyond a sanity range.
 """
 import numpy as np
@@ -19,7 +19,8 @@ from paper_1011_3534_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-SANITY = {"bf16": 3e-2, "fp16": 3e-3, "tf32": 3e-3, "bf16x3": 1e-4}
+SANITY = {"bf16": 3e-2, "fp16": 3e-3, "tf32": 3e-3, "bf16x3": 1e-4, "tf32x3": 1e-5}
+SPLIT = {"bf16x3": "bf16", "tf32x3": "tf32"}
 
 
 @pytest.fixture(scope="module")
@@ -57,8 +58,8 @@ def gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric):
 
 
 def rounded_operands(X, prec_name):
-    if prec_name == "bf16x3":
-        return F.split_bf16(X)
+    if prec_name in SPLIT:
+        return F.split(X, SPLIT[prec_name])
     return F.round_to(X, prec_name), None
 
 
@@ -73,7 +74,7 @@ def reference(A, B, leaf, tau, prec_name, threads):
     Ah, Al = rounded_operands(A, prec_name)
     Bh, Bl = rounded_operands(B, prec_name)
     T = lambda X: oracle.Tree(X, leaf)
-    if prec_name == "bf16x3":
+    if prec_name in SPLIT:
         tAh, tAl, tBh, tBl = T(Ah), T(Al), T(Bh), T(Bl)
         Cref = (oracle.spamm_values(TA, TB, tAh, tBh, tau, threads)
                 + oracle.spamm_values(TA, TB, tAh, tBl, tau, threads)
@@ -101,7 +102,7 @@ def check(S, ctx, A, B, leaf, tau, prec_name, symmetric):
     # products summed into each output block
     cnt = np.zeros((NB, NB), dtype=np.int64)
     np.add.at(cnt, (ref["triples"][:, 0], ref["triples"][:, 1]), 1)
-    K = leaf * cnt * (3 if prec_name == "bf16x3" else 1) + 16
+    K = leaf * cnt * (3 if prec_name in SPLIT else 1) + 16
     n = A.shape[0]
     Kel = np.repeat(np.repeat(K, leaf, 0), leaf, 1)[:n, :n]
     bound = Kel * 2.0 ** -23 * Cabs + Csub + 1e-300
@@ -113,11 +114,11 @@ def check(S, ctx, A, B, leaf, tau, prec_name, symmetric):
     assert err < SANITY[prec_name]
     st = g["stats"]
     assert st["leaf_products"] == ref["count"]
-    assert st["mma_flops"] >= st["leaf_flops"] * (3 if prec_name == "bf16x3" else 1)
+    assert st["mma_flops"] >= st["leaf_flops"] * (3 if prec_name in SPLIT else 1)
     return g
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32", "bf16x3", "tf32x3"])
 @pytest.mark.parametrize("n,leaf,tau,kind", [
     (1000, 64, 1e-6, "alg"),      # ragged: 1000 = 15 * 64 + 40
     (2048, 64, 1e-8, "exp"),
@@ -129,7 +130,7 @@ def test_tc_parity_symmetric(S, ctx, prec, n, leaf, tau, kind):
     check(S, ctx, A, A, leaf, tau, prec, symmetric=True)
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3", "tf32x3"])
 @pytest.mark.parametrize("leaf", [64, 128])
 def test_tc_parity_nonsymmetric(S, ctx, prec, leaf):
     n = 1500
@@ -153,7 +154,7 @@ def test_tc_deterministic(S, ctx):
     assert np.array_equal(g1["C"], g2["C"])
 
 
-@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3", "tf32x3"])
 @pytest.mark.parametrize("tau", [1e-10, 1e-8, 1e-6, 1e-4])
 def test_workload_alg8192_tc_sampled(S, ctx, prec, tau):
     # n = 8192 algebraic decay, leaf 64, in the benchmark's launch configuration:

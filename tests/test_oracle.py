@@ -351,6 +351,14 @@ def test_format_rounding_hand_cases():
     assert F.round_to(np.array([65504.0]), "fp16")[0] == 65504.0
     hi, lo = F.split_bf16(np.array([np.pi]))
     assert abs(hi[0] + lo[0] - np.pi) < 2.0 ** -16 * np.pi
+    # TF32 split: 1 + 2^-11 + 2^-30 lies just above the tie between 1 and 1 + 2^-10, so
+    # hi = 1 + 2^-10 and the remainder -2^-11 + 2^-30 rounds to -2^-11 in 11 bits
+    hi, lo = F.split(np.array([1 + 2.0 ** -11 + 2.0 ** -30]), "tf32")
+    assert hi[0] == 1 + 2.0 ** -10 and lo[0] == -2.0 ** -11
+    x = np.random.default_rng(5).normal(size=1000) * 10.0 ** np.random.default_rng(6).uniform(-20, 20, 1000)
+    hi, lo = F.split(x, "tf32")
+    assert np.all(np.abs(hi + lo - x) <= 2.0 ** -22 * np.abs(x))
+    assert np.array_equal(F.round_to(hi, "tf32"), hi) and np.array_equal(F.round_to(lo, "tf32"), lo)
 
 
 def test_values_oracle_uses_substituted_leaves():
