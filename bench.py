@@ -262,7 +262,7 @@ def run_gpu(args):
     if not args.no_sweep:
         for tau in TAUS:
             ref = None
-            for name in ("fp64", "tf32", "bf16", "bf16x3", "fp16"):
+            for name in ("fp64", "tf32", "bf16", "bf16x3", "tf32x3", "fp16"):
                 p = S.PRECISIONS[name]
                 rr = timed(p, tau, 3, 1)
                 Cd = torch.empty((N, N), dtype=torch.float64, device=dA.device)

@@ -209,11 +209,14 @@ SPAMM_API spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t n
    W1 (hidden x inputs, row-major), b1, W2 (hidden x hidden), b2, W3 (1 x hidden), b3.
    All arrays of these calls are host arrays; calls synchronise the context stream. */
 typedef struct spamm_mlp_s *spamm_mlp;
-#define SPAMM_MLP_FEATURES 68   /* per operand: 16-bin decade histograms of the block norms
+#define SPAMM_MLP_FEATURES 69   /* per operand: 16-bin decade histograms of the block norms
                                    of its leaf tier and the tier above, as fractions of
                                    nonzero blocks; then (log10 tau - log10 ||A||_F -
                                    log10 ||B||_F) / 8, (log10 ||A||_F + log10 ||B||_F) / 8,
-                                   and the nonzero-leaf fractions of A and B */
+                                   the nonzero-leaf fractions of A and B, and
+                                   (log10 F(tau) - log10 ||A||_F - log10 ||B||_F) / 8 (at
+                                   least -2) of the flat leaf bound F(tau): the sum of
+                                   ||A_ik|| ||B_kj|| over leaf triples below tau (FP32) */
 /* Network with `inputs` (1..128) and `hidden` (1..64) units, weights drawn
    U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed), biases 0. */
 SPAMM_API spamm_status spamm_mlp_create(spamm_ctx ctx, int32_t inputs, int32_t hidden, uint64_t seed,
@@ -240,7 +243,8 @@ SPAMM_API spamm_status spamm_mlp_train(spamm_mlp m, const float *X, const float 
                                        float *final_loss);
 /* Features of the product A B at tolerance tau > 0 (SPAMM_MLP_FEATURES floats). */
 SPAMM_API spamm_status spamm_features(spamm_tree A, spamm_tree B, double tau, float *out);
-/* Largest tau on the grid of 37 values log-spaced over [tau_min, tau_max] whose predicted
+/* Largest tau on the grid of 37 values log-spaced over [tau_min, tau_max]
+   (10^(log10 tau_min + g (log10 tau_max - log10 tau_min) / 36), g = 0..36) whose predicted
    relative error is <= err_budget (tau_min when none is). */
 SPAMM_API spamm_status spamm_tau_select(spamm_mlp m, spamm_tree A, spamm_tree B, double err_budget,
                                         double tau_min, double tau_max, double *tau_out);

@@ -93,7 +93,7 @@ class Adam:
 
 # ---- features of a product (the controller's input) ----
 HIST = 16
-N_FEATURES = 4 * HIST + 4
+N_FEATURES = 4 * HIST + 5
 # squared-norm thresholds of the decade bins: 10^-2, 10^-4, ..., 10^-30
 _DECADE2 = [float(f"1e-{2 * (q + 1)}") for q in range(HIST - 1)]
 
@@ -135,15 +135,40 @@ def tree_features(tree, nb: int) -> np.ndarray:
     return out
 
 
-def features(treeA, nbA: int, treeB, nbB: int, tau: float) -> np.ndarray:
-    """The network's input for the product A B at tolerance tau."""
+def flat_bound32(treeA, treeB, taus) -> np.ndarray:
+    """Flat leaf bound at each tau: the sum of p = ||A_ik|| ||B_kj|| over leaf triples
+    with p < tau, with the leaf norms, p and the comparison in FP32 (tau rounded to
+    FP32), the sum in FP64. A plain triple loop over (i, k) and a vector over j."""
+    nA = np.sqrt(treeA.norm2(treeA.kmax)).astype(np.float32)
+    nB = np.sqrt(treeB.norm2(treeB.kmax)).astype(np.float32)
+    thr = np.asarray(taus, dtype=np.float64).astype(np.float32)
+    out = np.zeros(thr.size)
+    NB = nA.shape[0]
+    for i in range(NB):
+        for k in range(NB):
+            if nA[i, k] == 0:
+                continue
+            p = nA[i, k] * nB[k, :]                 # FP32 products
+            p = p[p > 0]
+            for q, t in enumerate(thr):
+                out[q] += float(np.sum(p[p < t].astype(np.float64)))
+    return out
+
+
+def features(treeA, nbA: int, treeB, nbB: int, tau: float, bound: float | None = None) -> np.ndarray:
+    """The network's input for the product A B at tolerance tau (the flat bound at tau
+    is computed unless given)."""
     fa, fb = tree_features(treeA, nbA), tree_features(treeB, nbB)
     la, lb = float(fa[2 * HIST + 1]), float(fb[2 * HIST + 1])
+    if bound is None:
+        bound = flat_bound32(treeA, treeB, [tau])[0]
     f = np.zeros(N_FEATURES, dtype=np.float32)
     f[:2 * HIST], f[2 * HIST:4 * HIST] = fa[:2 * HIST], fb[:2 * HIST]
     f[4 * HIST] = np.float32((np.log10(tau) - la - lb) / 8.0)
     f[4 * HIST + 1] = np.float32((la + lb) / 8.0)
     f[4 * HIST + 2], f[4 * HIST + 3] = fa[2 * HIST], fb[2 * HIST]
+    lr = (np.log10(bound) - la - lb) / 8.0 if bound > 0 else -2.0
+    f[4 * HIST + 4] = np.float32(max(lr, -2.0))
     return f
 
 

@@ -619,6 +619,8 @@ struct spamm_sp2_s {
   double *d_v = nullptr, *d_part = nullptr;
   void *d_rec = nullptr;
   float *d_feat = nullptr;
+  double *d_ctrl = nullptr;   // controller: bound workspace, then the tolerance grid
+  double grid_lo = 0, grid_hi = 0;
   spamm_tree X = nullptr, C = nullptr;
   double tau_host[SPAMM_SP2_MAX_STEPS] = {};
   bool learned[SPAMM_SP2_MAX_STEPS] = {};
@@ -632,6 +634,7 @@ void sp2_release(spamm_sp2_run r) {
   if (r->X) { free_tree_memory(r->X); delete r->X; }
   if (r->C) { free_tree_memory(r->C); delete r->C; }
   dfree(r->d_ip); dfree(r->d_ix); dfree(r->d_v); dfree(r->d_part); dfree(r->d_rec); dfree(r->d_feat);
+  dfree(r->d_ctrl);
   if (r->e0) cudaEventDestroy(r->e0);
   if (r->e1) cudaEventDestroy(r->e1);
   delete r;
@@ -754,11 +757,22 @@ extern "C" spamm_status spamm_sp2_step_learned(spamm_sp2_run r, spamm_mlp m, dou
     return fail(ctx, SPAMM_EINVAL, "sp2: bad budget or tau range");
   if (mlp_inputs(m) != SPAMM_MLP_FEATURES) return fail(ctx, SPAMM_EINVAL, "sp2: network has the wrong input width");
   cudaStream_t s = ctx->stream;
+  const size_t nw = bound_workspace_doubles(r->X);
+  if (!r->d_ctrl) CK(dmalloc(&r->d_ctrl, sizeof(double) * (nw + kTauGrid)), "sp2: allocation");
+  double *grid = r->d_ctrl + nw, *bound = r->d_ctrl + (nw - kTauGrid);
+  if (r->grid_lo != tau_min || r->grid_hi != tau_max) {   // the grid, uploaded once per range
+    double h[kTauGrid];
+    tau_grid(tau_min, tau_max, h);
+    CK(cudaMemcpyAsync(grid, h, sizeof h, cudaMemcpyHostToDevice, s), "sp2: grid");
+    CK(cudaStreamSynchronize(s), "sp2: grid");
+    r->grid_lo = tau_min;
+    r->grid_hi = tau_max;
+  }
   CK(launch_feat_hist(r->X, r->d_feat, s), "sp2: features");
-  CK(launch_tau_select(m, r->d_feat, r->d_feat, std::log10(err_budget), std::log10(tau_min), std::log10(tau_max), 37,
-                       sp2_tau_slot(r->d_rec, r->steps), s),
+  CK(launch_flat_bound(r->X, r->X, grid, kTauGrid, r->d_ctrl, bound, s), "sp2: flat bound");
+  CK(launch_tau_select(m, r->d_feat, r->d_feat, grid, bound, std::log10(err_budget), sp2_tau_slot(r->d_rec, r->steps), s),
      "sp2: tau selection");
-  ctx->launches += 2;
+  ctx->launches += 4;
   return sp2_advance(r, 0.0, true);
 }
 

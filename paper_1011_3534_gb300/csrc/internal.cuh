@@ -189,6 +189,11 @@ cudaError_t launch_leaf_tc_batch(const spamm_tree *A, const spamm_tree *B, const
 spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau, spamm_prec prec,
                              int32_t flags, spamm_tree *C);
 cudaError_t launch_feat_hist(spamm_tree t, float *out, cudaStream_t s);
-cudaError_t launch_tau_select(spamm_mlp mm, const float *fa, const float *fb, double log10_budget, double lt_min,
-                              double lt_max, int G, double *tau_out, cudaStream_t s);
+cudaError_t launch_tau_select(spamm_mlp mm, const float *fa, const float *fb, const double *grid, const double *bound,
+                              double log10_budget, double *tau_out, cudaStream_t s);
+cudaError_t launch_flat_bound(spamm_tree A, spamm_tree B, const double *grid, int G, double *work, double *bound,
+                              cudaStream_t s);
+size_t bound_workspace_doubles(spamm_tree A);   // work + bound of launch_flat_bound on the 37-point grid
+void tau_grid(double tau_min, double tau_max, double *grid);   // the 37 log-spaced tolerances
+constexpr int kTauGrid = 37;
 int mlp_inputs(spamm_mlp mm);

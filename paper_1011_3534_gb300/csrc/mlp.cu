@@ -370,12 +370,14 @@ spamm_status spamm_mlp_train(spamm_mlp mm, const float *X, const float *y, int32
 }  // extern "C"
 
 // ---------------------------------------------------------------- controller features
-// Features of a product A B at tolerance tau (SPAMM_MLP_FEATURES = 68). Per operand, for
+// Features of a product A B at tolerance tau (SPAMM_MLP_FEATURES = 69). Per operand, for
 // its leaf tier and the tier above: a 16-bin histogram of block norms in decades below
 // the tier's largest norm (bin q holds the blocks with max * 10^-(q+1) <= norm <
 // max * 10^-q, bin 15 everything further down), as fractions of the tier's nonzero
 // blocks. Then (log10 tau - log10 ||A||_F - log10 ||B||_F) / 8, (log10 ||A||_F +
-// log10 ||B||_F) / 8, and the fraction of nonzero leaves of A and of B. The bin of a
+// log10 ||B||_F) / 8, the fraction of nonzero leaves of A and of B, and
+// (log10 bound(tau) - log10 ||A||_F - log10 ||B||_F) / 8 of the flat leaf bound below
+// (-2 when it is zero, the floor of the feature). The bin of a
 // block is decided by FP64 comparisons of its squared norm against max^2 * 10^(-2q), so
 // the histogram is exact integer work.
 namespace {
@@ -383,7 +385,7 @@ namespace {
 constexpr int kHist = 16;
 constexpr int kTreeFeat = kTreeFeatures;   // two histograms, nonzero fraction, log10 norm
 static_assert(kTreeFeat == 2 * kHist + 2, "per-tree feature count");
-static_assert(SPAMM_MLP_FEATURES == 2 * kTreeFeat, "feature layout");
+static_assert(SPAMM_MLP_FEATURES == 2 * kTreeFeat + 1, "feature layout");
 
 __device__ __constant__ double c_decade2[kHist] = {1e-2,  1e-4,  1e-6,  1e-8,  1e-10, 1e-12, 1e-14, 1e-16,
                                                    1e-18, 1e-20, 1e-22, 1e-24, 1e-26, 1e-28, 1e-30, 1e-32};
@@ -436,7 +438,67 @@ __global__ void __launch_bounds__(1024) k_feat_hist(const double *norm2, int kma
   }
 }
 
-__device__ __forceinline__ void assemble(const float *fa, const float *fb, double log10_tau, float *f) {
+// Flat leaf bound of the product at each tolerance of a grid: the sum of
+// p = ||A_ik||_F ||B_kj||_F over the leaf triples with p < tau_q, the norms and p in FP32
+// (the decision p < tau_q is taken in FP32 against tau_q rounded to FP32). It bounds the
+// Frobenius error of the product at tau_q (triangle inequality over the dropped
+// triples). One CTA per leaf row i: row i of A's norms staged in shared memory, threads
+// over columns j, per-thread FP32 sums, fixed-order reductions, FP64 partial per row.
+constexpr int kGrid = 37;   // tolerance grid of the selection
+constexpr int kBoundThreads = 256;
+constexpr int kBoundChunk = 2048;   // k-chunk of A's row staged at a time
+
+template <int G>
+__global__ void __launch_bounds__(kBoundThreads) k_flat_bound(const double *nA, const double *nB, int NB,
+                                                              const double *grid, double *partial) {
+  __shared__ float s_a[kBoundChunk];
+  __shared__ float s_thr[G];
+  __shared__ float s_w[kBoundThreads / 32][G];
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < G) s_thr[tid] = (float)grid[tid];
+  float bins[G];
+#pragma unroll
+  for (int q = 0; q < G; q++) bins[q] = 0.f;
+  for (int k0 = 0; k0 < NB; k0 += kBoundChunk) {
+    const int kn = NB - k0 < kBoundChunk ? NB - k0 : kBoundChunk;
+    __syncthreads();
+    for (int k = tid; k < kn; k += kBoundThreads) s_a[k] = (float)nA[(int64_t)i * NB + k0 + k];
+    __syncthreads();
+    for (int j = tid; j < NB; j += kBoundThreads) {
+      for (int k = 0; k < kn; k++) {
+        const float a = s_a[k];
+        if (a == 0.f) continue;
+        const float pr = a * (float)nB[(int64_t)(k0 + k) * NB + j];
+        if (pr == 0.f) continue;
+#pragma unroll
+        for (int q = 0; q < G; q++) bins[q] += pr < s_thr[q] ? pr : 0.f;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < G; q++) {
+    float v = bins[q];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) s_w[warp][q] = v;
+  }
+  __syncthreads();
+  if (tid < G) {
+    double t = 0.0;
+    for (int w = 0; w < kBoundThreads / 32; w++) t += (double)s_w[w][tid];
+    partial[(int64_t)i * G + tid] = t;
+  }
+}
+
+__global__ void k_bound_total(const double *partial, int NB, int G, double *bound) {
+  const int q = threadIdx.x;
+  if (q >= G) return;
+  double t = 0.0;
+  for (int i = 0; i < NB; i++) t += partial[(int64_t)i * G + q];
+  bound[q] = t;
+}
+
+// The network's input for tolerance log10_tau with flat bound `bound`.
+__device__ __forceinline__ void assemble(const float *fa, const float *fb, double log10_tau, double bound, float *f) {
   for (int q = 0; q < 2 * kHist; q++) {
     f[q] = fa[q];
     f[2 * kHist + q] = fb[q];
@@ -446,6 +508,8 @@ __device__ __forceinline__ void assemble(const float *fa, const float *fb, doubl
   f[4 * kHist + 1] = (float)((la + lb) / 8.0);
   f[4 * kHist + 2] = fa[2 * kHist];
   f[4 * kHist + 3] = fb[2 * kHist];
+  double lr = bound > 0.0 ? (log10(bound) - la - lb) / 8.0 : -2.0;
+  f[4 * kHist + 4] = (float)(lr < -2.0 ? -2.0 : lr);
 }
 
 __device__ float net_eval(const Net &n, const float *th, const float *x) {
@@ -465,29 +529,27 @@ __device__ float net_eval(const Net &n, const float *th, const float *x) {
   return o;
 }
 
-// Thread g scores tau_g = 10^(lt_min + g * step); the largest tau_g whose predicted
-// log10 relative error is within the budget is written to *tau_out (the smallest grid
-// value when none is).
+// Thread g scores grid[g] (ascending); the largest grid[g] whose predicted log10
+// relative error is within the budget is written to *tau_out (grid[0] when none is).
 __global__ void __launch_bounds__(128) k_tau_select(Net n, const float *th, const float *fa, const float *fb,
-                                                    double log10_budget, double lt_min, double lt_step, int G,
-                                                    double *tau_out) {
+                                                    const double *grid, const double *bound, int G,
+                                                    double log10_budget, double *tau_out) {
   __shared__ int s_best;
   if (threadIdx.x == 0) s_best = -1;
   __syncthreads();
   const int g = threadIdx.x;
   if (g < G) {
     float f[SPAMM_MLP_FEATURES];
-    const double lt = lt_min + g * lt_step;
-    assemble(fa, fb, lt, f);
+    assemble(fa, fb, log10(grid[g]), bound[g], f);
     const float pred = net_eval(n, th, f);
     if (pred <= (float)log10_budget) atomicMax(&s_best, g);
   }
   __syncthreads();
-  if (threadIdx.x == 0) *tau_out = pow(10.0, lt_min + (s_best < 0 ? 0 : s_best) * lt_step);
+  if (threadIdx.x == 0) *tau_out = grid[s_best < 0 ? 0 : s_best];
 }
 
-__global__ void k_feat_assemble(const float *fa, const float *fb, double log10_tau, float *f) {
-  if (threadIdx.x == 0) assemble(fa, fb, log10_tau, f);
+__global__ void k_feat_assemble(const float *fa, const float *fb, double log10_tau, const double *bound, float *f) {
+  if (threadIdx.x == 0) assemble(fa, fb, log10_tau, bound[0], f);
 }
 
 }  // namespace
@@ -497,11 +559,27 @@ cudaError_t launch_feat_hist(spamm_tree t, float *out, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_tau_select(spamm_mlp mm, const float *fa, const float *fb, double log10_budget, double lt_min,
-                              double lt_max, int G, double *tau_out, cudaStream_t s) {
-  const double step = G > 1 ? (lt_max - lt_min) / (G - 1) : 0.0;
-  k_tau_select<<<1, 128, 0, s>>>(mm->net, mm->th, fa, fb, log10_budget, lt_min, step, G, tau_out);
+size_t bound_workspace_doubles(spamm_tree A) { return (size_t)A->NB * kGrid + kGrid; }
+
+cudaError_t launch_flat_bound(spamm_tree A, spamm_tree B, const double *grid, int G, double *work, double *bound,
+                              cudaStream_t s) {
+  const double *nA = A->norm + level_offset(A->kmax), *nB = B->norm + level_offset(B->kmax);
+  if (G == 1) k_flat_bound<1><<<(unsigned)A->NB, kBoundThreads, 0, s>>>(nA, nB, A->NB, grid, work);
+  else if (G == kGrid) k_flat_bound<kGrid><<<(unsigned)A->NB, kBoundThreads, 0, s>>>(nA, nB, A->NB, grid, work);
+  else return cudaErrorInvalidValue;
+  k_bound_total<<<1, 64, 0, s>>>(work, A->NB, G, bound);
   return cudaGetLastError();
+}
+
+cudaError_t launch_tau_select(spamm_mlp mm, const float *fa, const float *fb, const double *grid, const double *bound,
+                              double log10_budget, double *tau_out, cudaStream_t s) {
+  k_tau_select<<<1, 128, 0, s>>>(mm->net, mm->th, fa, fb, grid, bound, kGrid, log10_budget, tau_out);
+  return cudaGetLastError();
+}
+
+void tau_grid(double tau_min, double tau_max, double *grid) {
+  const double l0 = std::log10(tau_min), l1 = std::log10(tau_max);
+  for (int g = 0; g < kGrid; g++) grid[g] = std::pow(10.0, l0 + (l1 - l0) * g / (kGrid - 1));
 }
 
 int mlp_inputs(spamm_mlp mm) { return mm->net.F; }
@@ -509,44 +587,59 @@ int mlp_inputs(spamm_mlp mm) { return mm->net.F; }
 extern "C" {
 
 spamm_status spamm_features(spamm_tree A, spamm_tree B, double tau, float *out) {
-  if (!A || !B || !out || !(tau > 0.0)) return SPAMM_EINVAL;
+  if (!A || !B || !out || !(tau > 0.0) || !std::isfinite(tau)) return SPAMM_EINVAL;
   spamm_ctx ctx = A->ctx;
+  if (A->n != B->n || A->b != B->b) return mfail(ctx, SPAMM_EINVAL, "features: shapes differ");
   float *d = nullptr;
+  double *w = nullptr;
+  const size_t nw = (size_t)A->NB + 4;
   if (cudaMalloc(&d, sizeof(float) * (2 * kTreeFeat + SPAMM_MLP_FEATURES)) != cudaSuccess) return SPAMM_ENOMEM;
+  if (cudaMalloc(&w, sizeof(double) * nw) != cudaSuccess) { cudaFree(d); return SPAMM_ENOMEM; }
   cudaStream_t s = ctx->stream;
-  cudaError_t e = launch_feat_hist(A, d, s);
+  double *grid = w + A->NB, *bound = w + A->NB + 1;
+  cudaError_t e = cudaMemcpyAsync(grid, &tau, sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_feat_hist(A, d, s);
   if (e == cudaSuccess) e = launch_feat_hist(B, d + kTreeFeat, s);
+  if (e == cudaSuccess) e = launch_flat_bound(A, B, grid, 1, w, bound, s);
   if (e == cudaSuccess) {
-    k_feat_assemble<<<1, 32, 0, s>>>(d, d + kTreeFeat, log10(tau), d + 2 * kTreeFeat);
+    k_feat_assemble<<<1, 32, 0, s>>>(d, d + kTreeFeat, log10(tau), bound, d + 2 * kTreeFeat);
     e = cudaGetLastError();
   }
-  ctx->launches += 3;
+  ctx->launches += 5;
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + 2 * kTreeFeat, sizeof(float) * SPAMM_MLP_FEATURES, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d);
+  cudaFree(w);
   return e == cudaSuccess ? SPAMM_OK : SPAMM_ECUDA;
 }
 
 spamm_status spamm_tau_select(spamm_mlp mm, spamm_tree A, spamm_tree B, double err_budget, double tau_min,
                               double tau_max, double *tau_out) {
-  if (!mm || !A || !B || !tau_out || !(err_budget > 0.0) || !(tau_min > 0.0) || !(tau_max >= tau_min))
+  if (!mm || !A || !B || !tau_out || !(err_budget > 0.0) || !(tau_min > 0.0) || !(tau_max >= tau_min) ||
+      !std::isfinite(tau_max))
     return SPAMM_EINVAL;
-  if (mm->net.F != SPAMM_MLP_FEATURES) return SPAMM_EINVAL;
   spamm_ctx ctx = A->ctx;
+  if (mm->net.F != SPAMM_MLP_FEATURES) return mfail(ctx, SPAMM_EINVAL, "tau_select: network input width");
+  if (A->n != B->n || A->b != B->b) return mfail(ctx, SPAMM_EINVAL, "tau_select: shapes differ");
   float *d = nullptr;
-  double *dt = nullptr;
+  double *w = nullptr;
+  const size_t nw = bound_workspace_doubles(A) + kGrid + 1;
   if (cudaMalloc(&d, sizeof(float) * 2 * kTreeFeat) != cudaSuccess) return SPAMM_ENOMEM;
-  if (cudaMalloc(&dt, sizeof(double)) != cudaSuccess) { cudaFree(d); return SPAMM_ENOMEM; }
+  if (cudaMalloc(&w, sizeof(double) * nw) != cudaSuccess) { cudaFree(d); return SPAMM_ENOMEM; }
+  double hgrid[kGrid];
+  tau_grid(tau_min, tau_max, hgrid);
+  double *grid = w + bound_workspace_doubles(A), *dt = grid + kGrid, *bound = w + (size_t)A->NB * kGrid;
   cudaStream_t s = ctx->stream;
-  cudaError_t e = launch_feat_hist(A, d, s);
+  cudaError_t e = cudaMemcpyAsync(grid, hgrid, sizeof hgrid, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_feat_hist(A, d, s);
   if (e == cudaSuccess) e = launch_feat_hist(B, d + kTreeFeat, s);
-  if (e == cudaSuccess)
-    e = launch_tau_select(mm, d, d + kTreeFeat, log10(err_budget), log10(tau_min), log10(tau_max), 37, dt, s);
-  ctx->launches += 3;
+  if (e == cudaSuccess) e = launch_flat_bound(A, B, grid, kGrid, w, bound, s);
+  if (e == cudaSuccess) e = launch_tau_select(mm, d, d + kTreeFeat, grid, bound, log10(err_budget), dt, s);
+  ctx->launches += 5;
   if (e == cudaSuccess) e = cudaMemcpyAsync(tau_out, dt, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d);
-  cudaFree(dt);
+  cudaFree(w);
   return e == cudaSuccess ? SPAMM_OK : SPAMM_ECUDA;
 }
 

@@ -31,7 +31,7 @@ SPAMM_GRAPH = 0x0200
 SPAMM_COPY_TF32X3 = 0x0400
 COPY_FLAG = {SPAMM_FP64: SPAMM_KEEP_FP64, SPAMM_TF32: SPAMM_COPY_TF32, SPAMM_BF16: SPAMM_COPY_BF16,
              SPAMM_FP16: SPAMM_COPY_FP16, SPAMM_BF16X3: SPAMM_COPY_BF16X3, SPAMM_TF32X3: SPAMM_COPY_TF32X3}
-MLP_FEATURES = 68
+MLP_FEATURES = 69
 MAX_LEVELS = 24
 
 # Every entry point declared in include/spamm.h.

@@ -1,0 +1,88 @@
+"""What the learned tolerance controller gains inside SP2, measured on the GPU.
+
+Workload: 16^3-site tight-binding Hamiltonians (n = 4096, open boundaries, on-site
+energies U[-2, 2]), half filling, 30 SP2 steps, leaf 64. The network is trained on the
+GPU, by the library's kernels, on (features, log10 error) pairs that FP64 SpAMM products
+generate along the SP2 trajectory of a training system (seed 7); its per-product error
+budget is the largest on a half-decade grid whose learned-tau SP2 meets the 1e-6
+relative energy target on that training system, divided by a safety margin of ten (the
+energy error jumps where a product error flips a near-tie branch decision). It then
+runs, without further calibration, on the test system (seed 2).
+
+The method without the network is the fixed conservative tau: the largest tau on a
+half-decade grid whose plain FP64 SP2 meets the target on the test system itself. It is
+also the judge: the learned run's energy must lie within the target of the fixed-tau
+FP64 energy, and of the reference energy (FP64 SpAMM at tau = 0, which equals dense SP2;
+see test_gpu_sp2.py).
+
+Asserted: the learned split-precision (TF32X3) run meets the target against both, and
+its time to solution beats plain FP64 SpAMM at the conservative tau. Reported: leaf
+products and device time of the learned run against the same precision at the fixed
+conservative tau (the network's gain, or loss, over the method without it).
+"""
+import numpy as np
+import pytest
+
+from paper_1011_3534_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TARGET = 1e-6
+SIDE, STEPS, LEAF = 16, 30, 64
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1011_3534_gb300 import spamm
+    return spamm
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    c = S.spamm_ctx_create(0, torch.cuda.current_stream())
+    yield c
+    S.spamm_ctx_destroy(c)
+
+
+def test_learned_tau_against_fixed_conservative_tau(S, ctx):
+    from paper_1011_3534_gb300 import controller as CT
+    n = SIDE ** 3
+    occ = n / 2
+    train_csr = W.tight_binding(SIDE, seed=7)[:3]
+    test_csr = W.tight_binding(SIDE, seed=2)[:3]
+    taus = CT.half_decades(1e-12, 1e-3)
+    X, y = CT.collect(ctx, *train_csr, occ, STEPS, LEAF, taus)
+    assert X.shape == (STEPS * len(taus), S.MLP_FEATURES)
+    m, loss = CT.train(ctx, X, y, epochs=1000)
+    rmse = float(np.sqrt(np.mean((m.forward(X) - y) ** 2)))
+    print(f"controller: {X.shape[0]} samples, train loss {loss:.4f}, rmse {rmse:.3f} decades")
+    assert rmse < 0.3
+    tau_lo, tau_hi = 1e-12, 1e-3
+    e_train = S.spamm_sp2(ctx, *train_csr, occ, STEPS, LEAF, S.SPAMM_FP64, 0.0)["energy"]
+    cal = CT.calibrate_budget(ctx, m, train_csr, occ, STEPS, LEAF, S.SPAMM_TF32X3, e_train, TARGET,
+                              CT.half_decades(1e-8, 1e-3), tau_lo, tau_hi)
+    assert cal is not None, "no budget meets the target on the training system"
+    budget = cal[0]
+    # the test system
+    ref = S.spamm_sp2(ctx, *test_csr, occ, STEPS, LEAF, S.SPAMM_FP64, 0.0)
+    e_ref = ref["energy"]
+    fixed = CT.conservative_tau(ctx, test_csr, occ, STEPS, LEAF, e_ref, TARGET, CT.half_decades(1e-6, 1e-3))
+    assert fixed is not None
+    tau_c, fixed64 = fixed
+    fixed_tc = S.spamm_sp2(ctx, *test_csr, occ, STEPS, LEAF, S.SPAMM_TF32X3, tau_c)
+    learned = S.spamm_sp2_learned(ctx, *test_csr, occ, STEPS, LEAF, S.SPAMM_TF32X3, m, budget, tau_lo, tau_hi)
+    err_ref = CT.energy_error(learned, e_ref)
+    err_judge = CT.energy_error(learned, fixed64["energy"])
+    lp = lambda r: sum(r["leaf_products"])
+    print(f"fixed conservative tau {tau_c:.2e}: FP64 {fixed64['ms']:.1f} ms, err {CT.energy_error(fixed64, e_ref):.2e}; "
+          f"TF32X3 {fixed_tc['ms']:.1f} ms, {lp(fixed_tc)} leaf products, err {CT.energy_error(fixed_tc, e_ref):.2e}")
+    print(f"learned tau, budget {budget:.2e}: TF32X3 {learned['ms']:.1f} ms, {lp(learned)} leaf products, "
+          f"err {err_ref:.2e} (vs judge {err_judge:.2e}); taus {['%.0e' % t for t in learned['taus']]}")
+    print(f"gain over the fixed conservative tau at TF32X3: leaf products x{lp(fixed_tc) / lp(learned):.3f}, "
+          f"time x{fixed_tc['ms'] / learned['ms']:.3f}; over FP64 at that tau: time x{fixed64['ms'] / learned['ms']:.1f}")
+    assert err_ref <= TARGET and err_judge <= TARGET
+    assert learned["ms"] < fixed64["ms"]
+    m.free()

@@ -24,7 +24,7 @@ from paper_1011_3534_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-F, H = 68, 32
+F, H = 69, 32
 U = 2.0 ** -24
 
 
@@ -188,6 +188,10 @@ def test_features_match_oracle(S, ctx, n, leaf, kind):
                 assert np.abs(a - b).sum() <= 2 * s / max(1, (b > 0).sum()), (part, a, b)
         assert got[66] == ref[66] and got[67] == ref[67]
         np.testing.assert_allclose(got[64:66], ref[64:66], rtol=1e-6, atol=1e-6)
+        # flat bound: the same FP32 decisions; FP32 partial sums (about NB terms per
+        # thread) against the oracle's FP64 sum: 1e-5 relative, i.e. 1e-5 / (8 ln 10)
+        # in the scaled log10 feature
+        assert abs(got[68] - ref[68]) <= 1e-6, (got[68], ref[68])
     S.spamm_tree_free(tA)
     S.spamm_tree_free(tB)
 
@@ -202,7 +206,8 @@ def test_tau_select_matches_oracle_network(S, ctx):
     th = m.get_params().astype(np.float64)
     lo, hi, G = 1e-12, 1e-2, 37
     grid = np.log10(lo) + np.arange(G) * (np.log10(hi) - np.log10(lo)) / (G - 1)
-    feats = np.stack([M.features(TA, nb, TA, nb, 10.0 ** g) for g in grid])
+    bounds = M.flat_bound32(TA, TA, 10.0 ** grid)
+    feats = np.stack([M.features(TA, nb, TA, nb, 10.0 ** g, bound=b) for g, b in zip(grid, bounds)])
     pred, _ = M.forward(th, feats.astype(np.float64), F, H)
     for q in (3, 12, 20, 30):
         budget = 10.0 ** float(pred[q])     # a budget met by some grid points, not all

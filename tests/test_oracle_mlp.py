@@ -96,6 +96,27 @@ def test_features_of_a_constructed_matrix():
     assert abs(g[64] - (-8 - np.log10(tot2)) / 8) < 1e-6
     assert abs(g[65] - np.log10(tot2) / 8) < 1e-6
     assert g[66] == g[67] == np.float32(0.125)
+    # flat bound: A is block diagonal, so the only leaf products are (i, i, i) with
+    # p = norm_i^2; below 1e-8 lie 1e-11 and 1e-34
+    assert abs(g[68] - (np.log10(1e-11 + 1e-34) - np.log10(tot2)) / 8) < 1e-6
+    b = M.flat_bound32(T, T, [1e-8, 2e-3, 1e-40])
+    np.testing.assert_allclose(b, [1e-11 + 1e-34, 1e-3 + 1e-5 + 1e-7 + 1e-11 + 1e-34, 0.0], rtol=1e-6)
+    assert M.features(T, 8, T, 8, 1e-40)[68] == np.float32(-2.0)     # nothing below tau: the floor
+
+
+def test_flat_bound32_matches_the_fp64_oracle_bound():
+    # the FP32 bound against the C oracle's FP64 flat bound (an independent loop) on a
+    # random decaying matrix, away from ties at the thresholds
+    import oracle
+    n = 300
+    r = np.random.default_rng(3)
+    d = np.abs(np.arange(n)[:, None] - np.arange(n)[None, :])
+    A = r.uniform(-1, 1, (n, n)) * 0.8 ** d
+    T = oracle.Tree(A, 16)
+    for tau in (1e-9, 1e-5, 1e-2):
+        got = M.flat_bound32(T, T, [tau])[0]
+        ref = oracle.flat_bound(T, T, tau)
+        assert abs(got - ref) <= 1e-5 * ref + 1e-300, (tau, got, ref)
 
 
 def test_feature_bins_follow_the_decades():
