@@ -1,6 +1,7 @@
 // Internal declarations of the SpAMM CUDA library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 

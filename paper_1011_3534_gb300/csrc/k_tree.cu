@@ -80,6 +80,130 @@ struct NormAcc {
   }
 };
 
+// Squared norm (into acc) and leaf copies of one round: the 8 elements of 4 pairs
+// (row rows[u], columns cols[u] and cols[u] + 1 of the leaf at element offset `tile`),
+// given as the high and low words of their FP64 patterns. Transposed copies go to
+// shared-memory leaf images (nullptr: not written).
+template <int B>
+__device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const uint32_t (&hw)[8],
+                                         const uint32_t (&lw)[8], const int (&rows)[4], const int (&cols)[4],
+                                         NormAcc &acc, float *s_tf32T, float *s_tloT, uint16_t *s_bf16T,
+                                         uint16_t *s_fp16T, uint16_t *s_loT) {
+  // squared norm of the round, scaled by its largest exponent field Er
+  int Er = 0;
+#pragma unroll
+  for (int e = 0; e < 8; e++) Er = max(Er, (int)((hw[e] >> 20) & 0x7FFu));
+  if (Er > 0 && Er < 0x7FF) {
+    float S = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+      const int E = (int)((hw[e] >> 20) & 0x7FFu);
+      const int es = E - Er;
+      if (E == 0 || es < -60) continue;   // below 2^-120 of the round's largest square
+      // hi: sign-free top 24 significand bits; lo: the bits below
+      const float hi = __uint_as_float(((uint32_t)(es + 127) << 23) | (((hw[e] & 0xFFFFFu) << 3) | (lw[e] >> 29)));
+      // (the next 23 bits, as an exact FP32 integer: their last 6 bits' share of the
+      // square is below 2^-46)
+      const float lo = u23_to_float((lw[e] >> 6) & 0x7FFFFFu) * __uint_as_float((uint32_t)(es - 46 + 127) << 23);
+      const float pp = hi * hi;
+      float cc = fmaf(hi, hi, -pp);
+      cc = fmaf(2.f * hi, lo, cc);
+      const float t = S + pp;
+      const float tb = t - S;
+      s2 += ((S - (t - tb)) + (pp - tb)) + cc;
+      S = t;
+    }
+    acc.merge(S, s2, Er);
+  } else if (Er == 0x7FF) {
+    acc.merge(__uint_as_float(0x7F800000u), 0.f, 0x7FE);
+  }
+  // leaf copies of the round
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const int64_t o = tile + (int64_t)rows[u] * B + cols[u];
+    const uint32_t h0 = hw[2 * u], l0 = lw[2 * u], h1 = hw[2 * u + 1], l1 = lw[2 * u + 1];
+    const int E0 = (int)((h0 >> 20) & 0x7FFu), E1 = (int)((h1 >> 20) & 0x7FFu);
+    if (p.f64)
+      *reinterpret_cast<double2 *>(p.f64 + o) =
+          make_double2(__hiloint2double((int)h0, (int)l0), __hiloint2double((int)h1, (int)l1));
+    if (p.f32) {
+      const uint32_t a0 = (E0 >= 897 && E0 <= 1150) ? f32_fast(h0, l0)
+                                                   : round_f64bits(((uint64_t)h0 << 32) | l0, 24, -126).bits;
+      const uint32_t a1 = (E1 >= 897 && E1 <= 1150) ? f32_fast(h1, l1)
+                                                   : round_f64bits(((uint64_t)h1 << 32) | l1, 24, -126).bits;
+      *reinterpret_cast<uint2 *>(p.f32 + o) = make_uint2(a0, a1);
+    }
+    if (p.bf16 || s_bf16T || p.lo || s_loT) {
+      uint32_t b0, b1;
+      Rounded r0, r1;
+      const bool need_r = p.lo || s_loT;
+      if (E0 >= 897 && E0 <= 1150 && !need_r) b0 = bf16_fast(h0, l0);
+      else { r0 = round_f64bits(((uint64_t)h0 << 32) | l0, 8, -126); b0 = r0.bits >> 16; }
+      if (E1 >= 897 && E1 <= 1150 && !need_r) b1 = bf16_fast(h1, l1);
+      else { r1 = round_f64bits(((uint64_t)h1 << 32) | l1, 8, -126); b1 = r1.bits >> 16; }
+      if (p.bf16) *reinterpret_cast<uint32_t *>(p.bf16 + o) = b0 | (b1 << 16);
+      if (s_bf16T) {
+        s_bf16T[cols[u] * B + rows[u]] = (uint16_t)b0;
+        s_bf16T[(cols[u] + 1) * B + rows[u]] = (uint16_t)b1;
+      }
+      if (need_r) {
+        const uint32_t q0 = bf16_lo_bits(((uint64_t)h0 << 32) | l0, r0) >> 16;
+        const uint32_t q1 = bf16_lo_bits(((uint64_t)h1 << 32) | l1, r1) >> 16;
+        if (p.lo) *reinterpret_cast<uint32_t *>(p.lo + o) = q0 | (q1 << 16);
+        if (s_loT) {
+          s_loT[cols[u] * B + rows[u]] = (uint16_t)q0;
+          s_loT[(cols[u] + 1) * B + rows[u]] = (uint16_t)q1;
+        }
+      }
+    }
+    if (p.tf32 || s_tf32T || p.tlo || s_tloT) {
+      uint32_t t0, t1;
+      if (p.tlo || s_tloT) {
+        const Rounded r0 = round_f64bits(((uint64_t)h0 << 32) | l0, 11, -126);
+        const Rounded r1 = round_f64bits(((uint64_t)h1 << 32) | l1, 11, -126);
+        t0 = r0.bits;
+        t1 = r1.bits;
+        const uint32_t q0 = split_lo_bits(((uint64_t)h0 << 32) | l0, r0, 11);
+        const uint32_t q1 = split_lo_bits(((uint64_t)h1 << 32) | l1, r1, 11);
+        if (p.tlo) *reinterpret_cast<uint2 *>(p.tlo + o) = make_uint2(q0, q1);
+        if (s_tloT) {
+          s_tloT[cols[u] * B + rows[u]] = __uint_as_float(q0);
+          s_tloT[(cols[u] + 1) * B + rows[u]] = __uint_as_float(q1);
+        }
+      } else {
+        t0 = (E0 >= 897 && E0 <= 1150) ? tf32_fast(h0, l0)
+                                       : round_f64bits(((uint64_t)h0 << 32) | l0, 11, -126).bits;
+        t1 = (E1 >= 897 && E1 <= 1150) ? tf32_fast(h1, l1)
+                                       : round_f64bits(((uint64_t)h1 << 32) | l1, 11, -126).bits;
+      }
+      if (p.tf32) *reinterpret_cast<uint2 *>(p.tf32 + o) = make_uint2(t0, t1);
+      if (s_tf32T) {
+        s_tf32T[cols[u] * B + rows[u]] = __uint_as_float(t0);
+        s_tf32T[(cols[u] + 1) * B + rows[u]] = __uint_as_float(t1);
+      }
+    }
+    if (p.fp16 || s_fp16T) {
+      const uint32_t f0 = (E0 >= 985 && E0 <= 1038) ? fp16_fast(h0, l0, E0)
+          : (uint32_t)fp16_from_f32bits(round_f64bits(((uint64_t)h0 << 32) | l0, 11, -14).bits);
+      const uint32_t f1 = (E1 >= 985 && E1 <= 1038) ? fp16_fast(h1, l1, E1)
+          : (uint32_t)fp16_from_f32bits(round_f64bits(((uint64_t)h1 << 32) | l1, 11, -14).bits);
+      if (p.fp16) *reinterpret_cast<uint32_t *>(p.fp16 + o) = f0 | (f1 << 16);
+      if (s_fp16T) {
+        s_fp16T[cols[u] * B + rows[u]] = (uint16_t)f0;
+        s_fp16T[(cols[u] + 1) * B + rows[u]] = (uint16_t)f1;
+      }
+    }
+  }
+}
+
+// The squared norm of a leaf from its warps' double-float partials (each scaled by
+// 2^(-2 (e - 1023))): merged in order in double-float, converted to FP64 once.
+__device__ __forceinline__ double merge_warps(const float *h, const float *l, const int *e, int count) {
+  NormAcc m;
+  for (int w = 0; w < count; w++) m.merge(h[w], l[w], e[w]);
+  return m.E ? ldexp((double)m.H + (double)m.L, 2 * (m.E - 1023)) : 0.0;
+}
+
 template <int B, bool VEC>
 __global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p) {
   using Cfg = BuildCfg<B>;
@@ -131,111 +255,7 @@ __global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p) {
         hw[2 * u + 1] = (uint32_t)__double2hiint(d.y);
         lw[2 * u + 1] = (uint32_t)__double2loint(d.y);
       }
-      // squared norm of the round, scaled by its largest exponent field Er
-      int Er = 0;
-#pragma unroll
-      for (int e = 0; e < 8; e++) Er = max(Er, (int)((hw[e] >> 20) & 0x7FFu));
-      if (Er > 0 && Er < 0x7FF) {
-        float S = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int e = 0; e < 8; e++) {
-          const int E = (int)((hw[e] >> 20) & 0x7FFu);
-          const int es = E - Er;
-          if (E == 0 || es < -60) continue;   // below 2^-120 of the round's largest square
-          // hi: sign-free top 24 significand bits; lo: the bits below
-          const float hi = __uint_as_float(((uint32_t)(es + 127) << 23) | (((hw[e] & 0xFFFFFu) << 3) | (lw[e] >> 29)));
-          // (the next 23 bits, as an exact FP32 integer: their last 6 bits' share of the
-          // square is below 2^-46)
-          const float lo = u23_to_float((lw[e] >> 6) & 0x7FFFFFu) * __uint_as_float((uint32_t)(es - 46 + 127) << 23);
-          const float pp = hi * hi;
-          float cc = fmaf(hi, hi, -pp);
-          cc = fmaf(2.f * hi, lo, cc);
-          const float t = S + pp;
-          const float tb = t - S;
-          s2 += ((S - (t - tb)) + (pp - tb)) + cc;
-          S = t;
-        }
-        acc.merge(S, s2, Er);
-      } else if (Er == 0x7FF) {
-        acc.merge(__uint_as_float(0x7F800000u), 0.f, 0x7FE);
-      }
-      // leaf copies of the round
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int64_t o = tile + (int64_t)rows[u] * B + cols[u];
-        const uint32_t h0 = hw[2 * u], l0 = lw[2 * u], h1 = hw[2 * u + 1], l1 = lw[2 * u + 1];
-        const int E0 = (int)((h0 >> 20) & 0x7FFu), E1 = (int)((h1 >> 20) & 0x7FFu);
-        if (p.f64)
-          *reinterpret_cast<double2 *>(p.f64 + o) =
-              make_double2(__hiloint2double((int)h0, (int)l0), __hiloint2double((int)h1, (int)l1));
-        if (p.f32) {
-          const uint32_t a0 = (E0 >= 897 && E0 <= 1150) ? f32_fast(h0, l0)
-                                                       : round_f64bits(((uint64_t)h0 << 32) | l0, 24, -126).bits;
-          const uint32_t a1 = (E1 >= 897 && E1 <= 1150) ? f32_fast(h1, l1)
-                                                       : round_f64bits(((uint64_t)h1 << 32) | l1, 24, -126).bits;
-          *reinterpret_cast<uint2 *>(p.f32 + o) = make_uint2(a0, a1);
-        }
-        if (p.bf16 || s_bf16T || p.lo || s_loT) {
-          uint32_t b0, b1;
-          Rounded r0, r1;
-          const bool need_r = p.lo || s_loT;
-          if (E0 >= 897 && E0 <= 1150 && !need_r) b0 = bf16_fast(h0, l0);
-          else { r0 = round_f64bits(((uint64_t)h0 << 32) | l0, 8, -126); b0 = r0.bits >> 16; }
-          if (E1 >= 897 && E1 <= 1150 && !need_r) b1 = bf16_fast(h1, l1);
-          else { r1 = round_f64bits(((uint64_t)h1 << 32) | l1, 8, -126); b1 = r1.bits >> 16; }
-          if (p.bf16) *reinterpret_cast<uint32_t *>(p.bf16 + o) = b0 | (b1 << 16);
-          if (s_bf16T) {
-            s_bf16T[cols[u] * B + rows[u]] = (uint16_t)b0;
-            s_bf16T[(cols[u] + 1) * B + rows[u]] = (uint16_t)b1;
-          }
-          if (need_r) {
-            const uint32_t q0 = bf16_lo_bits(((uint64_t)h0 << 32) | l0, r0) >> 16;
-            const uint32_t q1 = bf16_lo_bits(((uint64_t)h1 << 32) | l1, r1) >> 16;
-            if (p.lo) *reinterpret_cast<uint32_t *>(p.lo + o) = q0 | (q1 << 16);
-            if (s_loT) {
-              s_loT[cols[u] * B + rows[u]] = (uint16_t)q0;
-              s_loT[(cols[u] + 1) * B + rows[u]] = (uint16_t)q1;
-            }
-          }
-        }
-        if (p.tf32 || s_tf32T || p.tlo || s_tloT) {
-          uint32_t t0, t1;
-          if (p.tlo || s_tloT) {
-            const Rounded r0 = round_f64bits(((uint64_t)h0 << 32) | l0, 11, -126);
-            const Rounded r1 = round_f64bits(((uint64_t)h1 << 32) | l1, 11, -126);
-            t0 = r0.bits;
-            t1 = r1.bits;
-            const uint32_t q0 = split_lo_bits(((uint64_t)h0 << 32) | l0, r0, 11);
-            const uint32_t q1 = split_lo_bits(((uint64_t)h1 << 32) | l1, r1, 11);
-            if (p.tlo) *reinterpret_cast<uint2 *>(p.tlo + o) = make_uint2(q0, q1);
-            if (s_tloT) {
-              s_tloT[cols[u] * B + rows[u]] = __uint_as_float(q0);
-              s_tloT[(cols[u] + 1) * B + rows[u]] = __uint_as_float(q1);
-            }
-          } else {
-            t0 = (E0 >= 897 && E0 <= 1150) ? tf32_fast(h0, l0)
-                                           : round_f64bits(((uint64_t)h0 << 32) | l0, 11, -126).bits;
-            t1 = (E1 >= 897 && E1 <= 1150) ? tf32_fast(h1, l1)
-                                           : round_f64bits(((uint64_t)h1 << 32) | l1, 11, -126).bits;
-          }
-          if (p.tf32) *reinterpret_cast<uint2 *>(p.tf32 + o) = make_uint2(t0, t1);
-          if (s_tf32T) {
-            s_tf32T[cols[u] * B + rows[u]] = __uint_as_float(t0);
-            s_tf32T[(cols[u] + 1) * B + rows[u]] = __uint_as_float(t1);
-          }
-        }
-        if (p.fp16 || s_fp16T) {
-          const uint32_t f0 = (E0 >= 985 && E0 <= 1038) ? fp16_fast(h0, l0, E0)
-              : (uint32_t)fp16_from_f32bits(round_f64bits(((uint64_t)h0 << 32) | l0, 11, -14).bits);
-          const uint32_t f1 = (E1 >= 985 && E1 <= 1038) ? fp16_fast(h1, l1, E1)
-              : (uint32_t)fp16_from_f32bits(round_f64bits(((uint64_t)h1 << 32) | l1, 11, -14).bits);
-          if (p.fp16) *reinterpret_cast<uint32_t *>(p.fp16 + o) = f0 | (f1 << 16);
-          if (s_fp16T) {
-            s_fp16T[cols[u] * B + rows[u]] = (uint16_t)f0;
-            s_fp16T[(cols[u] + 1) * B + rows[u]] = (uint16_t)f1;
-          }
-        }
-      }
+      k1_round<B>(p, tile, hw, lw, rows, cols, acc, s_tf32T, s_tloT, s_bf16T, s_fp16T, s_loT);
     }
   }
   // leaf norm: threads -> warp (rescale to the warp's largest exponent) -> leaf
@@ -260,14 +280,7 @@ __global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p) {
   constexpr int WPL = Cfg::TPL >= 32 ? Cfg::TPL / 32 : 1;
   if (tl == 0 && inrange) {
     if (stored) {
-      int Em = 0;
-      for (int w = 0; w < WPL; w++) Em = max(Em, s_e[li * WPL + w]);
-      double total = 0.0;
-      for (int w = 0; w < WPL; w++) {
-        const int ew = s_e[li * WPL + w];
-        if (ew) total += ldexp((double)s_h[li * WPL + w] + (double)s_l[li * WPL + w], 2 * (ew - Em));
-      }
-      p.leaf_norm2[leaf] = Em ? ldexp(total, 2 * (Em - 1023)) : 0.0;
+      p.leaf_norm2[leaf] = merge_warps(s_h + li * WPL, s_l + li * WPL, s_e + li * WPL, WPL);
       p.nz[leaf] = 1;
     } else {
       p.leaf_norm2[leaf] = 0.0;

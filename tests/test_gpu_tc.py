@@ -186,3 +186,22 @@ def test_workload_alg8192_tc_sampled(S, ctx, prec, tau):
         K = leaf * cnt[i, j] * (3 if tAl is not None else 1) + 16
         got = g["C"][i * leaf:(i + 1) * leaf, j * leaf:(j + 1) * leaf]
         assert np.all(np.abs(got - Cref) <= K * 2.0 ** -23 * Cabs + 1e-300), (i, j)
+
+
+@pytest.mark.parametrize("n", [4096, 1000, 130])
+def test_symmetric_and_transposed_layouts_agree(S, ctx, n):
+    # a symmetric operand declared symmetric (one copy serves both roles) and the same
+    # operand with transposed copies for the right role: identical norms, and identical
+    # products from the two operand layouts
+    A = W.algebraic_decay(n, 2, 0)
+    dA = torch.from_numpy(A).cuda()
+    f = S.COPY_FLAG[S.SPAMM_BF16X3]
+    t1 = S.spamm_tree_build(ctx, dA, n, 64, f | S.SPAMM_SYMMETRIC)
+    t2 = S.spamm_tree_build(ctx, dA, n, 64, f)
+    for l in range(t1.kmax + 1):
+        assert np.array_equal(S.spamm_tree_norms(t1, l), S.spamm_tree_norms(t2, l)), l
+    c1 = S.spamm_multiply(ctx, t1, t1, 1e-7, S.SPAMM_BF16X3)
+    c2 = S.spamm_multiply(ctx, t2, t2, 1e-7, S.SPAMM_BF16X3)
+    assert np.array_equal(S.spamm_tree_to_dense(c1), S.spamm_tree_to_dense(c2))
+    for t in (c1, c2, t1, t2):
+        S.spamm_tree_free(t)
