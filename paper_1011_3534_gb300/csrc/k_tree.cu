@@ -80,6 +80,26 @@ struct NormAcc {
   }
 };
 
+
+// BF16 pair of two FP64 values with FP32-normal results (exponent fields 897..1150):
+// each value truncated to FP32 with the discarded low bits folded into the last bit
+// (sticky), then the hardware FP32 -> BF16x2 round to nearest even. The sticky bit
+// turns an FP64 value just above a BF16 tie into one above the tie in FP32 too, and is
+// far below the BF16 rounding position otherwise, so the result is the correctly
+// rounded BF16 of the FP64 value.
+__device__ __forceinline__ uint32_t trunc_f32_sticky(uint32_t h, uint32_t l) {
+  return (h & 0x80000000u) | ((((h & 0x7FFFFFFFu) - (896u << 20)) << 3) | (l >> 29)) |
+         ((l & 0x1FFFFFFFu) != 0u ? 1u : 0u);
+}
+
+__device__ __forceinline__ uint32_t bf16x2_fast(uint32_t h0, uint32_t l0, uint32_t h1, uint32_t l1) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;"
+      : "=r"(r)
+      : "f"(__uint_as_float(trunc_f32_sticky(h1, l1))), "f"(__uint_as_float(trunc_f32_sticky(h0, l0))));
+  return r;   // element 0 in the low half
+}
+
 // Squared norm (into acc) and leaf copies of one round: the 8 elements of 4 pairs
 // (row rows[u], columns cols[u] and cols[u] + 1 of the leaf at element offset `tile`),
 // given as the high and low words of their FP64 patterns. Transposed copies go to
@@ -128,19 +148,30 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
           make_double2(__hiloint2double((int)h0, (int)l0), __hiloint2double((int)h1, (int)l1));
     if (p.f32) {
       const uint32_t a0 = (E0 >= 897 && E0 <= 1150) ? f32_fast(h0, l0)
-                                                   : round_f64bits(((uint64_t)h0 << 32) | l0, 24, -126).bits;
+                                                   : slow_round_bits(h0, l0, 24, -126);
       const uint32_t a1 = (E1 >= 897 && E1 <= 1150) ? f32_fast(h1, l1)
-                                                   : round_f64bits(((uint64_t)h1 << 32) | l1, 24, -126).bits;
+                                                   : slow_round_bits(h1, l1, 24, -126);
       *reinterpret_cast<uint2 *>(p.f32 + o) = make_uint2(a0, a1);
     }
     if (p.bf16 || s_bf16T || p.lo || s_loT) {
       uint32_t b0, b1;
       Rounded r0, r1;
       const bool need_r = p.lo || s_loT;
-      if (E0 >= 897 && E0 <= 1150 && !need_r) b0 = bf16_fast(h0, l0);
-      else { r0 = round_f64bits(((uint64_t)h0 << 32) | l0, 8, -126); b0 = r0.bits >> 16; }
-      if (E1 >= 897 && E1 <= 1150 && !need_r) b1 = bf16_fast(h1, l1);
-      else { r1 = round_f64bits(((uint64_t)h1 << 32) | l1, 8, -126); b1 = r1.bits >> 16; }
+      if (need_r) {   // the split needs the rounded significands
+        r0 = round_f64bits(((uint64_t)h0 << 32) | l0, 8, -126);
+        r1 = round_f64bits(((uint64_t)h1 << 32) | l1, 8, -126);
+        b0 = r0.bits >> 16;
+        b1 = r1.bits >> 16;
+      } else {
+        if (E0 >= 897 && E0 <= 1150 && E1 >= 897 && E1 <= 1150) {
+          const uint32_t pk = bf16x2_fast(h0, l0, h1, l1);
+          b0 = pk & 0xFFFFu;
+          b1 = pk >> 16;
+        } else {   // out of the FP32-normal range: out of line
+          b0 = (E0 >= 897 && E0 <= 1150) ? bf16_fast(h0, l0) : (slow_round_bits(h0, l0, 8, -126) >> 16);
+          b1 = (E1 >= 897 && E1 <= 1150) ? bf16_fast(h1, l1) : (slow_round_bits(h1, l1, 8, -126) >> 16);
+        }
+      }
       if (p.bf16) *reinterpret_cast<uint32_t *>(p.bf16 + o) = b0 | (b1 << 16);
       if (s_bf16T) {
         s_bf16T[cols[u] * B + rows[u]] = (uint16_t)b0;
@@ -172,9 +203,9 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
         }
       } else {
         t0 = (E0 >= 897 && E0 <= 1150) ? tf32_fast(h0, l0)
-                                       : round_f64bits(((uint64_t)h0 << 32) | l0, 11, -126).bits;
+                                       : slow_round_bits(h0, l0, 11, -126);
         t1 = (E1 >= 897 && E1 <= 1150) ? tf32_fast(h1, l1)
-                                       : round_f64bits(((uint64_t)h1 << 32) | l1, 11, -126).bits;
+                                       : slow_round_bits(h1, l1, 11, -126);
       }
       if (p.tf32) *reinterpret_cast<uint2 *>(p.tf32 + o) = make_uint2(t0, t1);
       if (s_tf32T) {
@@ -184,9 +215,9 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
     }
     if (p.fp16 || s_fp16T) {
       const uint32_t f0 = (E0 >= 985 && E0 <= 1038) ? fp16_fast(h0, l0, E0)
-          : (uint32_t)fp16_from_f32bits(round_f64bits(((uint64_t)h0 << 32) | l0, 11, -14).bits);
+          : slow_fp16_bits(h0, l0);
       const uint32_t f1 = (E1 >= 985 && E1 <= 1038) ? fp16_fast(h1, l1, E1)
-          : (uint32_t)fp16_from_f32bits(round_f64bits(((uint64_t)h1 << 32) | l1, 11, -14).bits);
+          : slow_fp16_bits(h1, l1);
       if (p.fp16) *reinterpret_cast<uint32_t *>(p.fp16 + o) = f0 | (f1 << 16);
       if (s_fp16T) {
         s_fp16T[cols[u] * B + rows[u]] = (uint16_t)f0;
@@ -194,6 +225,32 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
       }
     }
   }
+}
+
+// Leaf copies a kernel instance writes: one bit per output. The instance for kAllCopies
+// checks every pointer at run time; the specialised instances (the copy sets of the
+// common symmetric operands) compile only their own outputs, which keeps the kernel
+// small enough for the instruction cache.
+constexpr uint32_t kF64 = 1u << 0, kF32 = 1u << 1, kTF32 = 1u << 2, kTF32T = 1u << 3, kTLO = 1u << 4,
+                   kTLOT = 1u << 5, kBF16 = 1u << 6, kBF16T = 1u << 7, kLO = 1u << 8, kLOT = 1u << 9,
+                   kFP16 = 1u << 10, kFP16T = 1u << 11, kAllCopies = (1u << 12) - 1;
+
+template <uint32_t M>
+__device__ __forceinline__ BuildArgs masked(const BuildArgs &in) {
+  BuildArgs p = in;
+  if (!(M & kF64)) p.f64 = nullptr;
+  if (!(M & kF32)) p.f32 = nullptr;
+  if (!(M & kTF32)) p.tf32 = nullptr;
+  if (!(M & kTF32T)) p.tf32T = nullptr;
+  if (!(M & kTLO)) p.tlo = nullptr;
+  if (!(M & kTLOT)) p.tloT = nullptr;
+  if (!(M & kBF16)) p.bf16 = nullptr;
+  if (!(M & kBF16T)) p.bf16T = nullptr;
+  if (!(M & kLO)) p.lo = nullptr;
+  if (!(M & kLOT)) p.loT = nullptr;
+  if (!(M & kFP16)) p.fp16 = nullptr;
+  if (!(M & kFP16T)) p.fp16T = nullptr;
+  return p;
 }
 
 // The squared norm of a leaf from its warps' double-float partials (each scaled by
@@ -204,8 +261,9 @@ __device__ __forceinline__ double merge_warps(const float *h, const float *l, co
   return m.E ? ldexp((double)m.H + (double)m.L, 2 * (m.E - 1023)) : 0.0;
 }
 
-template <int B, bool VEC>
-__global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p) {
+template <int B, bool VEC, uint32_t M>
+__global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p_in) {
+  const BuildArgs p = masked<M>(p_in);
   using Cfg = BuildCfg<B>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float s_h[8], s_l[8];
@@ -388,19 +446,40 @@ __global__ void k_to_dense(const T *tiles, const uint8_t *nz, int64_t n, int32_t
 
 }  // namespace
 
-template <int B>
-static cudaError_t run_build(const BuildArgs &p, size_t bytes_per_leaf_T, bool vec, cudaStream_t s) {
+template <int B, bool VEC, uint32_t M>
+static cudaError_t run_build_m(const BuildArgs &p, size_t sm, cudaStream_t s) {
   using Cfg = BuildCfg<B>;
-  const size_t sm = bytes_per_leaf_T * Cfg::LPC;
   const int64_t leaves = (int64_t)p.NB * p.NB;
   const unsigned grid = (unsigned)((leaves + Cfg::LPC - 1) / Cfg::LPC);
-  auto k = vec ? k_tree_build<B, true> : k_tree_build<B, false>;
+  auto k = k_tree_build<B, VEC, M>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
   k<<<grid, Cfg::T, sm, s>>>(p);
   return cudaGetLastError();
+}
+
+template <int B>
+static cudaError_t run_build(const BuildArgs &p, size_t bytes_per_leaf_T, bool vec, cudaStream_t s) {
+  using Cfg = BuildCfg<B>;
+  const size_t sm = bytes_per_leaf_T * Cfg::LPC;
+  const uint32_t m = (p.f64 ? kF64 : 0u) | (p.f32 ? kF32 : 0u) | (p.tf32 ? kTF32 : 0u) | (p.tf32T ? kTF32T : 0u) |
+                     (p.tlo ? kTLO : 0u) | (p.tloT ? kTLOT : 0u) | (p.bf16 ? kBF16 : 0u) | (p.bf16T ? kBF16T : 0u) |
+                     (p.lo ? kLO : 0u) | (p.loT ? kLOT : 0u) | (p.fp16 ? kFP16 : 0u) | (p.fp16T ? kFP16T : 0u);
+  if constexpr (B == 64 || B == 128) {
+    if (vec) switch (m) {
+      case 0: return run_build_m<B, true, 0>(p, sm, s);
+      case kF64: return run_build_m<B, true, kF64>(p, sm, s);
+      case kBF16: return run_build_m<B, true, kBF16>(p, sm, s);
+      case kBF16 | kLO: return run_build_m<B, true, kBF16 | kLO>(p, sm, s);
+      case kTF32: return run_build_m<B, true, kTF32>(p, sm, s);
+      case kTF32 | kTLO: return run_build_m<B, true, kTF32 | kTLO>(p, sm, s);
+      case kFP16: return run_build_m<B, true, kFP16>(p, sm, s);
+      default: break;
+    }
+  }
+  return vec ? run_build_m<B, true, kAllCopies>(p, sm, s) : run_build_m<B, false, kAllCopies>(p, sm, s);
 }
 
 cudaError_t launch_tree_build(spamm_tree t, const double *A, cudaStream_t s) {
