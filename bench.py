@@ -10,9 +10,15 @@ A sweep over tau in {1e-10, 1e-8, 1e-6, 1e-4} and the leaf precisions reports ea
 one's time and its relative Frobenius error against the FP64 SpAMM on the GPU.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep]
+                  [--config alg8192 | lattice32768 | batched256 | sp2-32768]
 
 --impl reference times the CPU oracle (plain FP64 recursive SpAMM) on this host.
 Multi-GPU: every rank runs an independent replica (the products do not exchange data).
+The other --config values measure the remaining workloads once, one JSON line each:
+lattice32768 (n = 32768 physical-distance decay, FP16/BF16 leaves, leaf 64/128, three
+tau), batched256 (256 exponential-decay matrices of uneven n in one launch under a CUDA
+graph), sp2-32768 (SP2 on 32^3 tight-binding sites: fixed conservative tau in FP64
+against the learned controller with split-TF32 leaves).
 """
 from __future__ import annotations
 
@@ -358,6 +364,192 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ other workloads
+
+def _events_ms(stream, fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _line(config, value, ms, dtype, extra):
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "ms_per_step": ms,
+            "config": config}
+    line.update(extra)
+    print(json.dumps(line))
+
+
+def run_lattice(args):
+    """n = 32768 physical-distance decay: each (leaf, precision, tau) timed as build +
+    multiply from the resident FP64 matrix; errors against FP64 SpAMM on the GPU."""
+    import torch
+    from paper_1011_3534_gb300 import spamm as S
+    from paper_1011_3534_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    ctx = S.spamm_ctx_create(0, stream, timing=True)
+    A = torch.from_numpy(W.physical_decay(16, 8, 1.2, 0.1, 3, 1)).cuda()
+    n = A.shape[0]
+    rows = []
+    with ClockSampler(0) as clk:
+        for leaf in (64, 128):
+            for tau in (1e-8, 1e-6, 1e-4):
+                ref = None
+                for name in ("fp64", "bf16", "fp16"):
+                    if name == "fp64" and tau == 1e-8:
+                        continue   # 4.6e13 FP64 flop: the error of this tau is not measured
+                    p = S.PRECISIONS[name]
+                    t = S.spamm_tree_build(ctx, A, n, leaf, S.COPY_FLAG[p] | S.SPAMM_SYMMETRIC | S.SPAMM_NO_RIGHT)
+                    box = {}
+
+                    def one():
+                        S.spamm_tree_update(t, A)
+                        box["c"] = S.spamm_multiply(ctx, t, t, tau, p, 0, box.get("c"))
+                    ms = _events_ms(stream, one, 1 if name == "fp64" else args.steps, 1 if name == "fp64" else 3)
+                    st = S.spamm_stats(box["c"])
+                    Cd = torch.empty((n, n), dtype=torch.float64, device=A.device)
+                    S.spamm_tree_to_dense(box["c"], Cd)
+                    if name == "fp64":
+                        ref, err = Cd, 0.0
+                    else:
+                        err = float(torch.linalg.norm(Cd - ref) / torch.linalg.norm(ref)) if ref is not None else None
+                        del Cd
+                    rows.append({"leaf": leaf, "tau": tau, "prec": name, "ms_per_step": ms,
+                                 "dense_equiv_gflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+                                 "leaf_ms": st["ms_leaf"], "cull_ms": st["ms_cull"],
+                                 "leaf_tflops": st["leaf_flops"] / (st["ms_leaf"] * 1e-3) / 1e12 if st["ms_leaf"] else None,
+                                 "mma_tflops": st["mma_flops"] / (st["ms_leaf"] * 1e-3) / 1e12 if st["ms_leaf"] else None,
+                                 "leaf_products": st["leaf_products"], "rel_fro_err_vs_fp64_spamm": err})
+                    S.spamm_tree_free(box["c"])
+                    S.spamm_tree_free(t)
+                del ref
+    head = max((r for r in rows if r["prec"] != "fp64"), key=lambda r: r["dense_equiv_gflops"])
+    _line({"workload": "physical-distance decay n=32768 (16^3 jittered lattice, 8 per site, exp(-1.2 r) N(0,1), seed 1)",
+           "n": n, "leaf": head["leaf"], "tau": head["tau"], "precision": head["prec"], "accumulate": "fp32",
+           "l2": "inputs larger than L2 (A is 8 GiB FP64)"},
+          head["dense_equiv_gflops"], head["ms_per_step"], head["prec"],
+          {"sweep": rows, "clocks": clk.summary()})
+    S.spamm_ctx_destroy(ctx)
+
+
+def run_batched(args):
+    """256 symmetric exponential-decay matrices, n log-uniform in [512, 8192], tau = 1e-7,
+    BF16 leaves: one step builds the 256 trees and runs the batched product (culls on
+    side streams, one tensor-core launch per leaf size) from a CUDA graph."""
+    import torch
+    from paper_1011_3534_gb300 import spamm as S
+    from paper_1011_3534_gb300 import workloads as W
+    shapes = W.batched_shapes()
+    tau, prec = 1e-7, S.SPAMM_BF16
+    mats = [torch.from_numpy(W.batched_matrix(m, nm, lam)).cuda() for m, (nm, lam) in enumerate(shapes)]
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()   # graph capture needs a stream of its own
+    ctx = S.spamm_ctx_create(0, stream)
+    mid = sorted(range(len(shapes)), key=lambda m: shapes[m][0])[len(shapes) // 2]
+    leaf, _ = S.spamm_tune_leaf(ctx, mats[mid], shapes[mid][0], tau, prec)
+    fl = S.COPY_FLAG[prec] | S.SPAMM_SYMMETRIC | S.SPAMM_NO_RIGHT
+    trees = [S.spamm_tree_build(ctx, X, X.shape[0], leaf, fl) for X in mats]
+    dense = sum(2.0 * nm ** 3 for nm, _ in shapes)
+    taus = np.full(len(trees), tau)
+    box = {}
+
+    def product_graph():
+        box["C"] = S.spamm_multiply_batched(ctx, trees, trees, taus, prec, S.SPAMM_GRAPH, box.get("C"))
+
+    def step():
+        for t, X in zip(trees, mats):
+            S.spamm_tree_update(t, X)
+        product_graph()
+
+    def singles():
+        box["C1"] = [S.spamm_multiply(ctx, t, t, tau, prec, 0, c) for t, c in zip(trees, box.get("C1") or [None] * len(trees))]
+
+    with ClockSampler(0) as clk:
+        ms_step = _events_ms(stream, step, args.steps, args.warmup)
+        ms_graph = _events_ms(stream, product_graph, args.steps, args.warmup)
+        ms_single = _events_ms(stream, singles, args.steps, args.warmup)
+    lp = sum(S.spamm_stats(c)["leaf_products"] for c in box["C"])
+    _line({"workload": "256 exponential-decay matrices, n log-uniform [512, 8192], lambda U[0.7, 0.95], seed 3",
+           "matrices": len(shapes), "sum_n2": int(sum(nm * nm for nm, _ in shapes)), "leaf": leaf, "tau": tau,
+           "precision": "bf16", "accumulate": "fp32", "graph": True, "l2": "inputs larger than L2"},
+          dense / (ms_step * 1e-3) / 1e9, ms_step, "bf16",
+          {"batched_product_ms": ms_graph, "batched_product_dense_equiv_gflops": dense / (ms_graph * 1e-3) / 1e9,
+           "one_launch_per_product_ms": ms_single, "leaf_products": lp,
+           "leaf_tflops_over_product": lp * 2.0 * leaf ** 3 / (ms_graph * 1e-3) / 1e12, "clocks": clk.summary()})
+    for c in box["C"] + box["C1"]:
+        S.spamm_tree_free(c)
+    for t in trees:
+        S.spamm_tree_free(t)
+    S.spamm_ctx_destroy(ctx)
+
+
+def run_sp2(args):
+    """SP2 on 32^3 tight-binding sites (n = 32768, 30 steps, leaf 64). Reference energy:
+    split-TF32 SpAMM at tau = 1e-8 (at 16^3 split TF32 at tau = 0 is within 4e-7 of dense
+    FP64 SP2; dense FP64 SP2 at this size is 2e15 flop, about half an hour on this
+    GPU's FP64 pipe). The fixed conservative tau is the largest of a half-decade grid
+    whose split-TF32 SP2 meets the 1e-6 target against that reference; plain FP64
+    SpAMM runs at it (the method without the controller, and its judge). The controller
+    is trained and its budget calibrated on a 16^3 system (seed 7) and applied here
+    without further calibration."""
+    import torch
+    from paper_1011_3534_gb300 import spamm as S
+    from paper_1011_3534_gb300 import controller as CT
+    from paper_1011_3534_gb300 import workloads as W
+    ctx = S.spamm_ctx_create(0, torch.cuda.current_stream())
+    steps, leaf, target = 30, 64, 1e-6
+    small = W.tight_binding(16, seed=7)[:3]
+    ns = 16 ** 3
+    X, y = CT.collect(ctx, *small, ns / 2, steps, leaf, CT.half_decades(1e-12, 1e-3))
+    m, loss = CT.train(ctx, X, y, epochs=1000)
+    e_small = S.spamm_sp2(ctx, *small, ns / 2, steps, leaf, S.SPAMM_FP64, 0.0)["energy"]
+    cal = CT.calibrate_budget(ctx, m, small, ns / 2, steps, leaf, S.SPAMM_TF32X3, e_small, target,
+                              CT.half_decades(1e-8, 1e-3), 1e-12, 1e-3)
+    budget = cal[0]
+    big = W.tight_binding(32, seed=2)[:3]
+    n = 32 ** 3
+    with ClockSampler(0) as clk:
+        ref = S.spamm_sp2(ctx, *big, n / 2, steps, leaf, S.SPAMM_TF32X3, 1e-8)
+        e_ref = ref["energy"]
+        grid = {}
+        for tau in CT.half_decades(1e-6, 1e-3):
+            grid[tau] = S.spamm_sp2(ctx, *big, n / 2, steps, leaf, S.SPAMM_TF32X3, tau)
+        ok = [t for t, r in grid.items() if CT.energy_error(r, e_ref) <= target]
+        tau_c = max(t for t in ok if all(CT.energy_error(grid[u], e_ref) <= target for u in grid if u <= t)) if ok else 1e-6
+        fixed_tc = grid[tau_c]
+        fixed64 = S.spamm_sp2(ctx, *big, n / 2, steps, leaf, S.SPAMM_FP64, tau_c)
+        learned = S.spamm_sp2_learned(ctx, *big, n / 2, steps, leaf, S.SPAMM_TF32X3, m, budget, 1e-12, 1e-3)
+    dense = steps * 2.0 * n ** 3
+    err = lambda r: CT.energy_error(r, e_ref)
+    lp = lambda r: int(sum(r["leaf_products"]))
+    _line({"workload": "SP2, 3-D tight binding on 32^3 sites (open boundaries, on-site U[-2,2], seed 2), "
+                       "half filling, 30 steps", "n": n, "leaf": leaf, "precision": "tf32x3 (learned tau)",
+           "accumulate": "fp32 per pass", "tau_fixed": tau_c, "error_budget": budget,
+           "reference": "tf32x3 SpAMM SP2 at tau=1e-8"},
+          dense / (learned["ms"] * 1e-3) / 1e9, learned["ms"], "tf32x3",
+          {"time_to_solution_ms": {"fp64_fixed_tau": fixed64["ms"], "tf32x3_fixed_tau": fixed_tc["ms"],
+                                   "tf32x3_learned_tau": learned["ms"], "tf32x3_reference": ref["ms"]},
+           "energy_rel_err_vs_reference": {"fp64_fixed_tau": err(fixed64), "tf32x3_fixed_tau": err(fixed_tc),
+                                           "tf32x3_learned_tau": err(learned),
+                                           "tf32x3_grid": {f"{t:.2e}": err(r) for t, r in grid.items()}},
+           "judge_rel_diff_learned_vs_fp64_fixed_tau": abs(learned["energy"] - fixed64["energy"]) / abs(fixed64["energy"]),
+           "branches_equal_to_reference": {"fp64_fixed_tau": fixed64["branches"] == ref["branches"],
+                                           "tf32x3_learned_tau": learned["branches"] == ref["branches"]},
+           "leaf_products": {"fp64_fixed_tau": lp(fixed64), "tf32x3_fixed_tau": lp(fixed_tc),
+                             "tf32x3_learned_tau": lp(learned), "tf32x3_reference": lp(ref)},
+           "learned_taus": learned["taus"], "controller_train_loss": loss, "clocks": clk.summary()})
+    m.free()
+    S.spamm_ctx_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,11 +557,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--config", default="alg8192", choices=["alg8192", "lattice32768", "batched256", "sp2-32768"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "lattice32768":
+        run_lattice(args)
+    elif args.config == "batched256":
+        run_batched(args)
+    elif args.config == "sp2-32768":
+        run_sp2(args)
     else:
         run_gpu(args)
 
