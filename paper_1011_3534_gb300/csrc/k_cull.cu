@@ -397,6 +397,164 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
   }
 }
 
+// The upper tiers in one CTA. Tiers 0..T (T < k_max, at most kTopTiers of them) hold
+// at most 4^(T-1) parent groups and 8^T entries, far too little work for a launch per
+// tier: a single CTA runs the same expansion as k_cull_tier tier after tier with the
+// lists in shared memory (a warp per parent group, entries 32 at a time, the same
+// per-lane order, so the counters and the per-group culled bounds are the same values),
+// and writes only the tier-T list and the counters of tiers 0..T.
+constexpr int kTopTiers = 5;                 // tiers 0..4
+constexpr int kTopGroups = 256;              // groups of the tier-4 list (4^4)
+constexpr int kTopEntries = 4096;            // entries of the tier-4 list (8^4)
+constexpr int kTopThreads = 1024;
+
+struct TopArgs {
+  const double *nA[kTopTiers], *nB[kTopTiers];   // tier norms (not squared)
+  int64_t bound_off[kTopTiers];                  // this tier's block of bound_part
+  int32_t T;                                     // last tier run here
+  double tau;
+  const double *tau_dev;
+  uint32_t *gij, *gstart, *glen;                 // the tier-T list (C->tiers[T + 1])
+  uint16_t *K;
+  int64_t cap_groups, cap_entries;
+  DevCounts *cnt;
+  double *bound_part;
+  uint32_t *status;
+};
+
+__global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
+  __shared__ uint32_t s_gij[2][kTopGroups], s_gstart[2][kTopGroups], s_glen[2][kTopGroups];
+  __shared__ uint16_t s_K[2][kTopEntries];
+  __shared__ uint8_t s_bits[kTopEntries];
+  __shared__ uint32_t s_cnt[kTopGroups], s_off[kTopGroups + 1], s_gix[kTopGroups + 1];
+  __shared__ unsigned long long s_tested, s_surv;
+  __shared__ uint32_t s_ng, s_ne;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kTopThreads / 32;
+  const double tau = t.tau_dev ? *t.tau_dev : t.tau;
+  if (threadIdx.x == 0) {   // tier -1: one group (0, 0) holding K = 0
+    s_gij[0][0] = 0;
+    s_gstart[0][0] = 0;
+    s_glen[0][0] = 1;
+    s_K[0][0] = 0;
+    s_ng = 1;
+    s_ne = 1;
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int l = 0; l <= t.T; l++) {
+    CullArgs a{};
+    a.nA = t.nA[l];
+    a.nB = t.nB[l];
+    a.D = 1 << l;
+    const uint32_t ng = s_ng;
+    const int nx = cur ^ 1;
+    if (threadIdx.x == 0) {
+      s_tested = 0;
+      s_surv = 0;
+    }
+    __syncthreads();
+    // pass 1: survival bits, per child-quadrant counts, tests and culled bounds
+    for (uint32_t g = warp; g < ng; g += nw) {
+      const uint32_t ij = s_gij[cur][g], I = ij >> 16, J = ij & 0xFFFFu;
+      const uint32_t start = s_gstart[cur][g], len = s_glen[cur][g];
+      unsigned int cq[4] = {0, 0, 0, 0};
+      int tests = 0;
+      double bound = 0.0;
+      for (uint32_t p0 = 0; p0 < len; p0 += 32) {
+        const uint32_t p = p0 + lane;
+        uint32_t bits = 0;
+        if (p < len) {
+          bits = child_bits(a, tau, I, J, s_K[cur][start + p], tests, bound);
+          s_bits[start + p] = (uint8_t)bits;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) cq[q] += __popc((bits >> (2 * q)) & 3u);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) cq[q] = warp_sum(cq[q]);
+      tests = warp_sum(tests);
+      bound = warp_sum(bound);
+      if (lane < 4) s_cnt[4 * g + lane] = cq[lane];
+      if (lane == 0) {
+        t.bound_part[t.bound_off[l] + g] = bound;
+        atomicAdd(&s_tested, (unsigned long long)tests);
+        atomicAdd(&s_surv, (unsigned long long)(cq[0] + cq[1] + cq[2] + cq[3]));
+      }
+    }
+    __syncthreads();
+    // child groups (parent group, quadrant) in order: entry offsets and group indices
+    if (warp == 0) {
+      uint32_t base_e = 0, base_g = 0;
+      for (uint32_t c0 = 0; c0 < 4 * ng; c0 += 32) {
+        const uint32_t c = c0 + lane;
+        const uint32_t v = c < 4 * ng ? s_cnt[c] : 0u, f = v ? 1u : 0u;
+        const uint32_t iv = warp_inclusive_scan(v), ifl = warp_inclusive_scan(f);
+        if (c < 4 * ng) {
+          s_off[c] = base_e + iv - v;
+          s_gix[c] = base_g + ifl - f;
+        }
+        base_e += __shfl_sync(0xffffffffu, iv, 31);
+        base_g += __shfl_sync(0xffffffffu, ifl, 31);
+      }
+      if (lane == 0) {
+        s_ne = base_e;
+        s_ng = base_g;
+        t.cnt->ngroups[l + 1] = base_g;
+        t.cnt->nentries[l + 1] = base_e;
+        t.cnt->tested[l] = s_tested;
+        t.cnt->culled[l] = s_tested - s_surv;
+        if (base_e > (uint32_t)kTopEntries || base_g > (uint32_t)kTopGroups) flag_error(t.status, DEV_OVERFLOW);
+      }
+    }
+    __syncthreads();
+    // pass 2: child group records and entries
+    for (uint32_t g = warp; g < ng; g += nw) {
+      const uint32_t ij = s_gij[cur][g], I = ij >> 16, J = ij & 0xFFFFu;
+      const uint32_t start = s_gstart[cur][g], len = s_glen[cur][g];
+      if (lane < 4 && s_cnt[4 * g + lane]) {
+        const uint32_t gi = s_gix[4 * g + lane];
+        if (gi < (uint32_t)kTopGroups) {
+          s_gij[nx][gi] = ((2 * I + (lane >> 1)) << 16) | (2 * J + (lane & 1));
+          s_gstart[nx][gi] = s_off[4 * g + lane];
+          s_glen[nx][gi] = s_cnt[4 * g + lane];
+        }
+      }
+      unsigned int run[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) run[q] = s_off[4 * g + q];
+      for (uint32_t p0 = 0; p0 < len; p0 += 32) {
+        const uint32_t p = p0 + lane;
+        const uint32_t bits = p < len ? s_bits[start + p] : 0u;
+        const uint32_t K = p < len ? s_K[cur][start + p] : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const uint32_t two = (bits >> (2 * q)) & 3u;
+          const unsigned int m = __popc(two);
+          const unsigned int inc = warp_inclusive_scan(m);
+          unsigned int pos = run[q] + inc - m;
+          if ((two & 1u) && pos < (unsigned)kTopEntries) s_K[nx][pos++] = (uint16_t)(2 * K);
+          if ((two & 2u) && pos < (unsigned)kTopEntries) s_K[nx][pos] = (uint16_t)(2 * K + 1);
+          run[q] += __shfl_sync(0xffffffffu, inc, 31);
+        }
+      }
+    }
+    __syncthreads();
+    cur = nx;
+  }
+  // the tier-T list, for the launch of tier T + 1
+  const uint32_t ng = s_ng < (uint32_t)kTopGroups ? s_ng : (uint32_t)kTopGroups;
+  const uint32_t ne = s_ne < (uint32_t)kTopEntries ? s_ne : (uint32_t)kTopEntries;
+  for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
+    if ((int64_t)g < t.cap_groups) {
+      t.gij[g] = s_gij[cur][g];
+      t.gstart[g] = s_gstart[cur][g];
+      t.glen[g] = s_glen[cur][g];
+    }
+  }
+  for (uint32_t e = threadIdx.x; e < ne; e += blockDim.x)
+    if ((int64_t)e < t.cap_entries) t.K[e] = s_K[cur][e];
+}
+
 // Prologue of a product: zeroes the counters, the look-back words and the product's
 // leaf norms / presence bytes, and seeds the virtual tier -1: one group (0, 0) holding
 // K = 0, whose only in-range child is the root triple (0, 0, 0).
@@ -461,7 +619,34 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
                                      C->norm2 ? C->norm2 + level_offset(C->kmax) : nullptr, C->nz, nleaves);
   (*launches)++;
   int64_t look_off = 0, bound_off = 0;
-  for (int l = 0; l <= kmax; l++) {
+  int l0 = 0;   // first tier launched on its own
+  if (kmax >= 2) {
+    TopArgs ta{};
+    ta.T = std::min(kTopTiers, kmax) - 1;   // the last tier always runs in k_cull_tier
+    for (int l = 0; l <= ta.T; l++) {
+      ta.nA[l] = A->norm + level_offset(l);
+      ta.nB[l] = B->norm + level_offset(l);
+      ta.bound_off[l] = bound_off;
+      look_off += (bound_groups_cap(l) + kWarps - 1) / kWarps;
+      bound_off += bound_groups_cap(l);
+    }
+    ta.tau = tau;
+    ta.tau_dev = tau_dev;
+    const TierList &out = C->tiers[ta.T + 1];
+    ta.gij = out.gij;
+    ta.gstart = out.gstart;
+    ta.glen = out.glen;
+    ta.K = out.K;
+    ta.cap_groups = out.cap_groups;
+    ta.cap_entries = out.cap_entries;
+    ta.cnt = cnt;
+    ta.bound_part = C->bound_part;
+    ta.status = dev_status;
+    k_cull_top<<<1, kTopThreads, 0, s>>>(ta);
+    (*launches)++;
+    l0 = ta.T + 1;
+  }
+  for (int l = l0; l <= kmax; l++) {
     CullArgs a{};
     a.nA = A->norm + level_offset(l);
     a.nB = B->norm + level_offset(l);
