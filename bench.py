@@ -5,7 +5,9 @@ roofline fractions.
 One step = the whole hot path on one input: build the quadtree of A (norms of every
 tier plus the leaf copies the precision needs, from the FP64 A resident in HBM), cull
 the product space tier by tier, and sum the surviving leaf products of C = A A into
-C's tiles and norms. Headline: tau = 1e-8, BF16 leaves with FP32 accumulation.
+C's tiles and norms. A is symmetric, so C is: the output blocks i <= j are culled and
+multiplied and the blocks i > j written as their transposes (SPAMM_SYM_PRODUCT).
+Headline: tau = 1e-8, BF16 leaves with FP32 accumulation.
 A sweep over tau in {1e-10, 1e-8, 1e-6, 1e-4} and the leaf precisions reports each
 one's time and its relative Frobenius error against the FP64 SpAMM on the GPU.
 
@@ -151,6 +153,8 @@ def run_gpu(args):
     dA = torch.from_numpy(A_host).to(f"cuda:{local}")
     pk = peaks()
 
+    SYMP = S.SPAMM_SYM_PRODUCT   # A is symmetric: blocks i <= j multiplied, C_ji = C_ij^T
+
     def flags_for(prec):
         return S.COPY_FLAG[prec] | S.SPAMM_SYMMETRIC | S.SPAMM_NO_RIGHT
 
@@ -160,7 +164,7 @@ def run_gpu(args):
         S.spamm_tree_update(tA, dA)                  # quadtree build (K1 + norm pyramid)
         if ev is not None:
             ev[1].record(stream)
-        tC = S.spamm_multiply(ctx, tA, tA, tau, prec, 0, tC)   # cull + leaf products
+        tC = S.spamm_multiply(ctx, tA, tA, tau, prec, SYMP, tC)   # cull + leaf products (+ mirror)
         if ev is not None:
             ev[2].record(stream)
         return tC
@@ -244,14 +248,14 @@ def run_gpu(args):
     tC = None
     for _ in range(max(1, args.warmup)):
         S.spamm_tree_update(tA, A_np)
-        tC = S.spamm_multiply(ctx, tA, tA, TAU, prec, 0, tC)
+        tC = S.spamm_multiply(ctx, tA, tA, TAU, prec, SYMP, tC)
         S.spamm_tree_to_dense(tC, C_np)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 10))
     for _ in range(e2e_steps):
         S.spamm_tree_update(tA, A_np)        # host -> device copy of A inside
-        tC = S.spamm_multiply(ctx, tA, tA, TAU, prec, 0, tC)
+        tC = S.spamm_multiply(ctx, tA, tA, TAU, prec, SYMP, tC)
         S.spamm_tree_to_dense(tC, C_np)      # device -> host copy of C; synchronises
     e2e_ms = (time.perf_counter() - e0) * 1e3 / e2e_steps
     S.spamm_tree_free(tA)
@@ -298,7 +302,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "leaf": LEAF, "tau": TAU, "precision": "bf16",
-                   "accumulate": "fp32", "l2": "inputs larger than L2 (A is 512 MiB FP64)",
+                   "accumulate": "fp32", "product": "symmetric (blocks i <= j multiplied, i > j mirrored)",
+                   "l2": "inputs larger than L2 (A is 512 MiB FP64)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": e2e, "gpu_launches": r["launches"], "phases": phases, "leaf_gemm": leaf,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "sweep": sweep,
@@ -412,7 +417,7 @@ def run_lattice(args):
 
                     def one():
                         S.spamm_tree_update(t, A)
-                        box["c"] = S.spamm_multiply(ctx, t, t, tau, p, 0, box.get("c"))
+                        box["c"] = S.spamm_multiply(ctx, t, t, tau, p, S.SPAMM_SYM_PRODUCT, box.get("c"))
                     ms = _events_ms(stream, one, 1 if name == "fp64" else args.steps, 1 if name == "fp64" else 3)
                     st = S.spamm_stats(box["c"])
                     Cd = torch.empty((n, n), dtype=torch.float64, device=A.device)

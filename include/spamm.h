@@ -84,6 +84,13 @@ typedef enum {
 #define SPAMM_GRAPH        0x0200  /* spamm_multiply_batched: capture the batch into a CUDA
                                       graph on first use and replay it afterwards */
 #define SPAMM_COPY_TF32X3  0x0400  /* write TF32 hi and lo leaf copies */
+#define SPAMM_SYM_PRODUCT  0x0800  /* spamm_multiply of a symmetric tree by itself (B == A,
+                                      built with SPAMM_SYMMETRIC): C = A A is symmetric, so
+                                      only the output blocks i <= j are culled and
+                                      multiplied, and C_ji is written as C_ij^T. The norm
+                                      trees of symmetric trees are kept transpose-consistent
+                                      (||A_ki|| = ||A_ik|| bit for bit), so the surviving
+                                      triples are the mirror images of each other */
 
 #define SPAMM_MAX_LEVELS 24
 
@@ -96,7 +103,9 @@ typedef struct {
   int64_t culled[SPAMM_MAX_LEVELS];        /* tests that dropped the sub-product */
   double culled_bound[SPAMM_MAX_LEVELS];   /* sum of ||A^k|| ||B^k|| over the dropped ones;
                                               their total bounds ||C~ - AB||_F (Eq. 3) */
-  int64_t leaf_products;                   /* surviving leaf triples (i, j, k) */
+  int64_t leaf_products;                   /* surviving leaf triples (i, j, k) multiplied */
+  int64_t mirrored_products;               /* surviving triples of blocks i > j obtained by
+                                              mirroring (SPAMM_SYM_PRODUCT; else 0) */
   int64_t output_blocks;                   /* output leaf blocks with a surviving k */
   double leaf_flops;                       /* 2 b^3 leaf_products */
   double dense_equiv_flops;                /* 2 n^3 */
@@ -257,7 +266,8 @@ SPAMM_API spamm_status spamm_tree_distance(spamm_tree X, spamm_tree Y, double *d
    column indices sorted per row). X0 = (eps_max I - H) / (eps_max - eps_min) with the
    Gershgorin bounds of H; each step s forms C = SpAMM(X, X) with tolerance tau[s] in
    precision prec, computes t1 = Tr X and t2 = Tr C in FP64, and sets X <- C if
-   |t2 - n_occ| <= |2 t1 - t2 - n_occ| (ties to C), else X <- 2X - C. The iterate keeps
+   |t2 - n_occ| <= |2 t1 - t2 - n_occ| (ties to C), else X <- 2X - C; every product is
+   a SPAMM_SYM_PRODUCT (X is symmetric). The iterate keeps
    an FP64 master for SPAMM_FP64 and an FP32 master otherwise. After `steps` steps the
    result holds E = Tr(H X), the trace of every iterate, the branch taken and the
    surviving leaf products of every product. Work is ordered on the context stream;
@@ -271,7 +281,8 @@ typedef struct {
   int32_t steps;
   double trace[SPAMM_SP2_MAX_STEPS + 1];        /* Tr X_s, s = 0 .. steps */
   int32_t branch[SPAMM_SP2_MAX_STEPS];          /* 1: X <- X^2, 0: X <- 2X - X^2 */
-  int64_t leaf_products[SPAMM_SP2_MAX_STEPS];   /* surviving leaf triples of step s */
+  int64_t leaf_products[SPAMM_SP2_MAX_STEPS];   /* leaf triples multiplied at step s (the
+                                                   products are symmetric: blocks i <= j) */
   double tau[SPAMM_SP2_MAX_STEPS];              /* tolerance of step s (given, or chosen
                                                    by the controller) */
   double ms;                                    /* device time of the loop (ms) */

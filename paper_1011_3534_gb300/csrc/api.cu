@@ -254,12 +254,14 @@ spamm_status spamm_ctx_destroy(spamm_ctx ctx) {
     if (g.table_host) cudaFreeHost(g.table_host);
     if (g.tau_dev) cudaFree(g.tau_dev);
     if (g.table_dev) cudaFree(g.table_dev);
+    if (g.tau_copied) cudaEventDestroy(g.tau_copied);
   }
   for (int i = 0; i < kSideStreams; i++) {
     if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
     if (ctx->side_ev[i]) cudaEventDestroy(ctx->side_ev[i]);
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->batch_copied) cudaEventDestroy(ctx->batch_copied);
   if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
   if (ctx->batch_dev) cudaFree(ctx->batch_dev);
   if (ctx->stage) cudaFree(ctx->stage);
@@ -307,7 +309,8 @@ spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t
   }
   cudaError_t e = launch_tree_build(t, src, ctx->stream);
   if (e == cudaSuccess) e = launch_pyramid(t, ctx->stream);
-  ctx->launches += 1 + pyramid_launches(t->kmax);
+  if (e == cudaSuccess && (flags & SPAMM_SYMMETRIC)) e = launch_sym_norms(t, ctx->stream);
+  ctx->launches += 1 + pyramid_launches(t->kmax) + ((t->flags & SPAMM_SYMMETRIC) ? 1 : 0);
   if (e != cudaSuccess) {
     free_tree_memory(t);
     delete t;
@@ -333,7 +336,8 @@ spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags) {
   }
   CK(launch_tree_build(t, src, ctx->stream), "tree_update: launch");
   CK(launch_pyramid(t, ctx->stream), "tree_update: launch");
-  ctx->launches += 1 + pyramid_launches(t->kmax);
+  if (t->flags & SPAMM_SYMMETRIC) CK(launch_sym_norms(t, ctx->stream), "tree_update: launch");
+  ctx->launches += 1 + pyramid_launches(t->kmax) + ((t->flags & SPAMM_SYMMETRIC) ? 1 : 0);
   return SPAMM_OK;
 }
 
@@ -410,7 +414,11 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
     return fail(ctx, SPAMM_EINVAL, "multiply: operands differ (n %lld/%lld, leaf %d/%d)",
                 (long long)A->n, (long long)B->n, A->b, B->b);
   if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(ctx, SPAMM_EINVAL, "multiply: tau must be finite and >= 0");
-  if (flags & ~(kTreeFlags & ~SPAMM_HOST_INPUT)) return fail(ctx, SPAMM_EINVAL, "multiply: unknown flag bits 0x%x", flags);
+  if (flags & ~((kTreeFlags & ~SPAMM_HOST_INPUT) | SPAMM_SYM_PRODUCT))
+    return fail(ctx, SPAMM_EINVAL, "multiply: unknown flag bits 0x%x", flags);
+  const bool symp = (flags & SPAMM_SYM_PRODUCT) != 0;
+  if (symp && (A != B || !(A->flags & SPAMM_SYMMETRIC)))
+    return fail(ctx, SPAMM_EINVAL, "multiply: SPAMM_SYM_PRODUCT needs B == A built with SPAMM_SYMMETRIC");
   const bool tc = prec != SPAMM_FP64;
   if (prec < SPAMM_FP64 || prec > SPAMM_TF32X3) return fail(ctx, SPAMM_EINVAL, "multiply: unknown precision %d", (int)prec);
   if (!tc) {
@@ -431,7 +439,8 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
       return fail(ctx, SPAMM_EINVAL, "multiply: right operand lacks the lo copy of the split");
   }
   spamm_tree Ct = *C;
-  const int32_t cflags = (flags & (kLowCopyFlags | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT)) | (tc ? SPAMM_INTERNAL_F32 : SPAMM_KEEP_FP64);
+  const int32_t cflags = (flags & (kLowCopyFlags | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT)) | (symp ? SPAMM_SYMMETRIC : 0) |
+                         (tc ? SPAMM_INTERNAL_F32 : SPAMM_KEEP_FP64);
   if (!Ct) {
     spamm_status st = alloc_tree(ctx, A->n, A->b, cflags & kTreeFlags, &Ct);
     if (st != SPAMM_OK) return st;
@@ -461,6 +470,8 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
   }
   *C = Ct;
   Ct->is_product = true;
+  Ct->sym_product = symp;
+  if (symp) Ct->flags |= SPAMM_SYMMETRIC;
   Ct->prec = prec;
   Ct->tau = tau;
   Ct->stats_valid = false;
@@ -487,8 +498,16 @@ spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau
   }
   launches++;
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[2], s), "event");
+  if (Ct->sym_product) {
+    CK(launch_mirror(Ct, s), "multiply: mirror launch");
+    launches++;
+  }
   CK(launch_pyramid(Ct, s), "multiply: pyramid launch");
   launches += pyramid_launches(Ct->kmax);
+  if (Ct->flags & SPAMM_SYMMETRIC) {
+    CK(launch_sym_norms(Ct, s), "multiply: norm symmetrisation");
+    launches++;
+  }
   bool want[CK_COUNT];
   wanted_copies(cflags & kTreeFlags, want);
   bool any_copy = false;
@@ -527,6 +546,7 @@ spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out) {
       S.culled_bound[l] = h.culled_bound[l];
     }
     S.leaf_products = (int64_t)h.leaf_products;
+    S.mirrored_products = (int64_t)h.mirror_products;
     S.output_blocks = (int64_t)h.output_blocks;
     const double b = C->b;
     S.leaf_flops = 2.0 * b * b * b * (double)h.leaf_products;
@@ -561,7 +581,8 @@ spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, int64_t *co
   const TierList &T = C->tiers[C->kmax];
   const int64_t ng = (int64_t)h.ngroups[C->kmax];
   const int64_t ne = (int64_t)h.nentries[C->kmax];
-  *count = (int64_t)h.leaf_products;
+  // a symmetric product lists the mirror (j, i, k) of every triple of a block i < j
+  *count = (int64_t)h.leaf_products + (C->sym_product ? (int64_t)h.mirror_products : 0);
   if (!ijk) return SPAMM_OK;
   if (*count > cap) return fail(ctx, SPAMM_ERANGE, "triples: %lld needed, cap %lld", (long long)*count, (long long)cap);
   std::vector<uint32_t> gij(ng), gs(ng), gl(ng);
@@ -591,6 +612,7 @@ spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, int64_t *co
           const uint64_t a = (q >> 2) & 1, c = (q >> 1) & 1, ee = q & 1;
           const uint64_t i = 2 * I + a, j = 2 * J + c, k = 2 * (uint64_t)K[e] + ee;
           keys.push_back((i << (2 * sh)) | (j << sh) | k);
+          if (C->sym_product && i < j) keys.push_back((j << (2 * sh)) | (i << sh) | k);
         }
     }
   }
@@ -711,11 +733,12 @@ extern "C" spamm_status spamm_sp2_begin(spamm_ctx ctx, int64_t n, const int64_t 
   SP2CK(sp2_x0(n, r->d_ip, r->d_ix, r->d_v, emin, emax, (double *)ctx->stage, s), "sp2: X0");
   SP2CK(launch_tree_build(r->X, (const double *)ctx->stage, s), "sp2: X0 tree");
   SP2CK(launch_pyramid(r->X, s), "sp2: X0 pyramid");
+  SP2CK(launch_sym_norms(r->X, s), "sp2: X0 norms");
   SP2CK(cudaEventCreate(&r->e0), "sp2: event");
   SP2CK(cudaEventCreate(&r->e1), "sp2: event");
   SP2CK(cudaEventRecord(r->e0, s), "sp2: event");
 #undef SP2CK
-  ctx->launches += 2 + pyramid_launches(r->X->kmax);
+  ctx->launches += 3 + pyramid_launches(r->X->kmax);
   *out = r;
   return SPAMM_OK;
 }
@@ -728,10 +751,11 @@ spamm_status sp2_advance(spamm_sp2_run r, double tau, bool from_record) {
   const int step = r->steps;
   spamm_tree out_tree = r->C;
   const double *tau_dev = from_record ? sp2_tau_slot(r->d_rec, step) : nullptr;
-  spamm_status st = multiply_impl(ctx, r->X, r->X, from_record ? 0.0 : tau, tau_dev, r->prec, 0, &out_tree);
+  spamm_status st = multiply_impl(ctx, r->X, r->X, from_record ? 0.0 : tau, tau_dev, r->prec, SPAMM_SYM_PRODUCT,
+                                  &out_tree);
   if (st != SPAMM_OK) return st;
   CK(sp2_step_finish(r->X, r->C, r->n_occ, step, r->d_rec, ctx->stream), "sp2: step");
-  ctx->launches += 3 + pyramid_launches(r->C->kmax);
+  ctx->launches += 4 + pyramid_launches(r->C->kmax);
   r->tau_host[step] = tau;
   r->learned[step] = from_record;
   std::swap(r->X, r->C);

@@ -40,6 +40,7 @@ spamm_status ensure_side_streams(spamm_ctx ctx) {
     BCK(cudaEventCreateWithFlags(&ctx->side_ev[i], cudaEventDisableTiming), "side event");
   }
   BCK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "fork event");
+  BCK(cudaEventCreateWithFlags(&ctx->batch_copied, cudaEventDisableTiming), "batch table event");
   return SPAMM_OK;
 }
 
@@ -79,7 +80,7 @@ spamm_status ensure_batch_tables(spamm_ctx ctx, int count) {
 // size, FP64 leaf kernels, pyramids (side streams). tau_dev may be null (host taus).
 static spamm_status batch_sequence(spamm_ctx ctx, const spamm_tree *A, const spamm_tree *B, const double *tau,
                                    const double *tau_dev, int count, spamm_prec prec, spamm_tree *C,
-                                   void *host_table, void *dev_table) {
+                                   void *host_table, void *dev_table, cudaEvent_t copied) {
   const bool tc = prec != SPAMM_FP64;
   const int used = std::min(count, kSideStreams);
   spamm_status st = fork(ctx, used);
@@ -94,7 +95,10 @@ static spamm_status batch_sequence(spamm_ctx ctx, const spamm_tree *A, const spa
   st = join(ctx, used);
   if (st != SPAMM_OK) return st;
   if (tc) {
-    // one persistent launch per leaf size over all products of that size
+    // one persistent launch per leaf size over all products of that size; the
+    // descriptors of all launches go over in one copy
+    struct Chunk { size_t off; int m, leaf; };
+    std::vector<Chunk> chunks;
     size_t off = 0;
     for (int leaf : {64, 128}) {
       std::vector<spamm_tree> a, b, c;
@@ -106,13 +110,20 @@ static spamm_status batch_sequence(spamm_ctx ctx, const spamm_tree *A, const spa
         }
       for (size_t s0 = 0; s0 < c.size(); s0 += 1024) {
         const int m = (int)std::min<size_t>(1024, c.size() - s0);
-        BCK(launch_leaf_tc_batch(a.data() + s0, b.data() + s0, c.data() + s0, m, prec,
-                                 (unsigned char *)host_table + off, (unsigned char *)dev_table + off,
-                                 ctx->dev_status, ctx->sm_count, ctx->stream),
-            "batch: leaf launch");
+        BCK(fill_leaf_tc_table(a.data() + s0, b.data() + s0, c.data() + s0, m, prec,
+                               (unsigned char *)host_table + off),
+            "batch: descriptors");
+        chunks.push_back({off, m, leaf});
         off += tc_desc_bytes() * m;
-        ctx->launches++;
       }
+    }
+    BCK(cudaMemcpyAsync(dev_table, host_table, off, cudaMemcpyHostToDevice, ctx->stream), "batch: descriptors");
+    if (copied) BCK(cudaEventRecord(copied, ctx->stream), "batch: descriptors");
+    for (const Chunk &k : chunks) {
+      BCK(launch_leaf_tc_table((unsigned char *)dev_table + k.off, k.m, k.leaf, prec, ctx->dev_status, ctx->sm_count,
+                               ctx->stream),
+          "batch: leaf launch");
+      ctx->launches++;
     }
   } else {
     for (int p = 0; p < count; p++) {
@@ -145,8 +156,12 @@ extern "C" spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *
   }
   st = ensure_batch_tables(ctx, count);
   if (st != SPAMM_OK) return st;
-  if (!(flags & SPAMM_GRAPH))
-    return batch_sequence(ctx, A, B, tau, nullptr, count, prec, C, ctx->batch_host, ctx->batch_dev);
+  if (!(flags & SPAMM_GRAPH)) {
+    // the pinned table is rewritten only after the previous call's copy out of it ran
+    BCK(cudaEventSynchronize(ctx->batch_copied), "batched: descriptor table");
+    return batch_sequence(ctx, A, B, tau, nullptr, count, prec, C, ctx->batch_host, ctx->batch_dev,
+                          ctx->batch_copied);
+  }
 
   // CUDA graph: one per (precision, trees) set, replayed with fresh taus
   std::vector<uintptr_t> key;
@@ -169,10 +184,12 @@ extern "C" spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *
     BCK(cudaMalloc(&g->tau_dev, sizeof(double) * count), "batched: graph taus");
     BCK(cudaMallocHost(&g->table_host, tc_desc_bytes() * count), "batched: graph table");
     BCK(cudaMalloc(&g->table_dev, tc_desc_bytes() * count), "batched: graph table");
+    BCK(cudaEventCreateWithFlags(&g->tau_copied, cudaEventDisableTiming), "batched: graph taus");
     cudaGraph_t graph = nullptr;
     BCK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "batched: capture");
     const int64_t l0 = ctx->launches;
-    st = batch_sequence(ctx, A, B, nullptr, g->tau_dev, count, prec, C, g->table_host, g->table_dev);
+    // the captured copy reads table_host at every replay; it is written once, here
+    st = batch_sequence(ctx, A, B, nullptr, g->tau_dev, count, prec, C, g->table_host, g->table_dev, nullptr);
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
     if (st != SPAMM_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -192,9 +209,11 @@ extern "C" spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *
       return bcuda(ctx, e, "batched: instantiate");
     }
   }
+  BCK(cudaEventSynchronize(g->tau_copied), "batched: taus");   // the previous replay's taus were copied
   memcpy(g->tau_host, tau, sizeof(double) * count);
   BCK(cudaMemcpyAsync(g->tau_dev, g->tau_host, sizeof(double) * count, cudaMemcpyHostToDevice, ctx->stream),
       "batched: taus");
+  BCK(cudaEventRecord(g->tau_copied, ctx->stream), "batched: taus");
   BCK(cudaGraphLaunch(g->exec, ctx->stream), "batched: graph launch");
   ctx->launches += g->launches;
   for (int p = 0; p < count; p++) {

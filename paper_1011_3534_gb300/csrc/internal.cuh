@@ -48,6 +48,7 @@ struct BatchGraph {                // a captured batched product, replayed with 
   void *table_host = nullptr, *table_dev = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
+  cudaEvent_t tau_copied = nullptr;   // the last copy out of tau_host has run
 };
 
 struct spamm_ctx_s {
@@ -67,6 +68,7 @@ struct spamm_ctx_s {
   cudaEvent_t side_ev[kSideStreams] = {};
   cudaEvent_t fork_ev = nullptr;
   void *batch_host = nullptr, *batch_dev = nullptr;   // descriptor tables (pinned / device)
+  cudaEvent_t batch_copied = nullptr;   // the last copy out of batch_host has run
   size_t batch_cap = 0;
   std::list<BatchGraph> graphs;
   std::map<int64_t, std::pair<int, double>> tuned;     // autotuner cache: leaf, ms
@@ -113,6 +115,7 @@ struct DevCounts {                     // device-resident counters of one produc
   unsigned long long tested[SPAMM_MAX_LEVELS];
   unsigned long long culled[SPAMM_MAX_LEVELS];
   unsigned long long leaf_products;
+  unsigned long long mirror_products;  // triples of blocks i < j (mirrored to j > i)
   unsigned long long output_blocks;
   unsigned long long mma_tiles;        // leaf-kernel MMA tile-steps issued
   unsigned long long npasses;          // passes of the tensor-core task plan
@@ -132,6 +135,7 @@ struct spamm_tree_s {
   void *copy[CK_COUNT] = {};
   // product trees
   bool is_product = false;
+  bool sym_product = false;               // C = A A of a symmetric A, blocks i <= j computed
   int32_t prec = 0;
   double tau = 0;
   TierList tiers[SPAMM_MAX_LEVELS + 1];   // tiers[l + 1] lists tier l; tiers[0] the virtual root
@@ -161,6 +165,8 @@ __host__ __device__ inline int64_t level_offset(int l) { return ((int64_t(1) << 
 // ---- launchers (each returns a cudaError_t from the launch) ----
 cudaError_t launch_tree_build(spamm_tree t, const double *A, cudaStream_t s);
 cudaError_t launch_pyramid(spamm_tree t, cudaStream_t s);
+cudaError_t launch_sym_norms(spamm_tree t, cudaStream_t s);    // lower triangles := upper, every tier
+cudaError_t launch_mirror(spamm_tree C, cudaStream_t s);       // C_ji := C_ij^T for i < j
 cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s);
 cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, const double *tau_dev,
                         uint32_t *dev_status, int sm_count, cudaStream_t s, int *launches);
@@ -184,9 +190,12 @@ void sp2_read_record(const void *host_rec, int steps, spamm_sp2_result *out);
 double *sp2_tau_slot(void *rec, int step);   // device address of the record's tau of a step
 constexpr int kTreeFeatures = 34;            // per-tree part of the controller's features
 size_t tc_desc_bytes();
-cudaError_t launch_leaf_tc_batch(const spamm_tree *A, const spamm_tree *B, const spamm_tree *C, int count,
-                                 int prec, void *host_table, void *dev_table, uint32_t *dev_status, int sm_count,
-                                 cudaStream_t s);
+// Batched tensor-core products: host descriptors of `count` products (same leaf size
+// and precision) written to `host_table`, then one launch over a device copy of them.
+cudaError_t fill_leaf_tc_table(const spamm_tree *A, const spamm_tree *B, const spamm_tree *C, int count, int prec,
+                               void *host_table);
+cudaError_t launch_leaf_tc_table(const void *dev_table, int count, int b, int prec, uint32_t *dev_status,
+                                 int sm_count, cudaStream_t s);
 spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau, spamm_prec prec,
                              int32_t flags, spamm_tree *C);
 cudaError_t launch_feat_hist(spamm_tree t, float *out, cudaStream_t s);

@@ -82,6 +82,7 @@ __device__ void tile_lookback(uint64_t *look, unsigned int tile, uint64_t agg_e,
 struct CullArgs {
   const double *nA, *nB;    // norms (not squared) of tier l, 2^l x 2^l
   int32_t l, D, nb, NB, final_tier;
+  int32_t sym;              // symmetric product: output blocks below the diagonal are skipped
   double tau;
   const double *tau_dev;         // when set, tau is read from device memory at launch
   const uint32_t *pgij, *pgstart, *pglen;
@@ -95,7 +96,7 @@ struct CullArgs {
   uint8_t *mask;
   uint64_t *look;
   unsigned int *tile_ctr;
-  unsigned long long *tested, *culled, *leaf_products, *output_blocks;
+  unsigned long long *tested, *culled, *leaf_products, *output_blocks, *mirror_products;
   double *bound_part;
   uint32_t *status;
   // task plan of the tensor-core leaf kernel (last tier only)
@@ -146,6 +147,7 @@ __device__ __forceinline__ uint32_t child_bits(const CullArgs &a, double tau, ui
       for (int c = 0; c < 2; c++) {
         const uint32_t j = 2 * J + c;
         if (j >= (uint32_t)a.D) continue;
+        if (a.sym && i > j) continue;   // below the diagonal: the mirror of (j, i)
         const double p = na * a.nB[(int64_t)k * a.D + j];
         tests++;
         if (p < tau) bound += p;
@@ -319,10 +321,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
       a.bound_part[g] = bound;
       if (a.final_tier) {
         atomicAdd(a.leaf_products, (unsigned long long)surv);
-        unsigned int blocks = 0;
-        for (int q = 0; q < 4; q++)
-          if (cnt[q] && 2 * I + (q >> 1) < (uint32_t)a.nb && 2 * J + (q & 1) < (uint32_t)a.nb) blocks++;
+        unsigned int blocks = 0, mir = 0;
+        for (int q = 0; q < 4; q++) {
+          const uint32_t bi = 2 * I + (q >> 1), bj = 2 * J + (q & 1);
+          if (cnt[q] && bi < (uint32_t)a.nb && bj < (uint32_t)a.nb) blocks += (a.sym && bi < bj) ? 2 : 1;
+          if (a.sym && bi < bj) mir += cnt[q];
+        }
         if (blocks) atomicAdd(a.output_blocks, (unsigned long long)blocks);
+        if (mir) atomicAdd(a.mirror_products, (unsigned long long)mir);
       }
     }
     if (a.final_tier) {
@@ -412,6 +418,7 @@ struct TopArgs {
   const double *nA[kTopTiers], *nB[kTopTiers];   // tier norms (not squared)
   int64_t bound_off[kTopTiers];                  // this tier's block of bound_part
   int32_t T;                                     // last tier run here
+  int32_t sym;                                   // symmetric product
   double tau;
   const double *tau_dev;
   uint32_t *gij, *gstart, *glen;                 // the tier-T list (C->tiers[T + 1])
@@ -446,6 +453,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
     a.nA = t.nA[l];
     a.nB = t.nB[l];
     a.D = 1 << l;
+    a.sym = t.sym;
     const uint32_t ng = s_ng;
     const int nx = cur ^ 1;
     if (threadIdx.x == 0) {
@@ -632,6 +640,7 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
     }
     ta.tau = tau;
     ta.tau_dev = tau_dev;
+    ta.sym = C->sym_product ? 1 : 0;
     const TierList &out = C->tiers[ta.T + 1];
     ta.gij = out.gij;
     ta.gstart = out.gstart;
@@ -655,6 +664,7 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
     a.nb = A->nb;
     a.NB = A->NB;
     a.final_tier = (l == kmax);
+    a.sym = C->sym_product ? 1 : 0;
     a.tau = tau;
     a.tau_dev = tau_dev;
     const TierList &par = C->tiers[l];
@@ -693,6 +703,7 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
     a.culled = &cnt->culled[l];
     a.leaf_products = &cnt->leaf_products;
     a.output_blocks = &cnt->output_blocks;
+    a.mirror_products = &cnt->mirror_products;
     a.bound_part = C->bound_part + bound_off;
     a.status = dev_status;
     look_off += tiles;

@@ -554,16 +554,20 @@ cudaError_t launch_leaf_tc(spamm_tree A, spamm_tree B, spamm_tree C, int prec, u
   return run_table((const ProdDesc *)C->tc_desc_dev, 1, C->b, prec, dev_status, sm_count, s);
 }
 
-// One launch over several products (same leaf size and precision): host descriptors
-// are written to `host_table` (pinned, count entries) and copied to `dev_table`.
-cudaError_t launch_leaf_tc_batch(const spamm_tree *A, const spamm_tree *B, const spamm_tree *C, int count,
-                                 int prec, void *host_table, void *dev_table, uint32_t *dev_status, int sm_count,
-                                 cudaStream_t s) {
+// Batched products: host descriptors of `count` products (same leaf size and
+// precision) are written to `host_table` (pinned); the caller copies them to a device
+// table and launches over it.
+cudaError_t fill_leaf_tc_table(const spamm_tree *A, const spamm_tree *B, const spamm_tree *C, int count, int prec,
+                               void *host_table) {
   if (count < 1 || count > kMaxProd) return cudaErrorInvalidValue;
   ProdDesc *h = (ProdDesc *)host_table;
   for (int q = 0; q < count; q++)
     if (!fill_desc(&h[q], A[q], B[q], C[q], prec)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemcpyAsync(dev_table, h, sizeof(ProdDesc) * count, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
-  return run_table((const ProdDesc *)dev_table, count, C[0]->b, prec, dev_status, sm_count, s);
+  return cudaSuccess;
+}
+
+cudaError_t launch_leaf_tc_table(const void *dev_table, int count, int b, int prec, uint32_t *dev_status,
+                                 int sm_count, cudaStream_t s) {
+  if (count < 1 || count > kMaxProd) return cudaErrorInvalidValue;
+  return run_table((const ProdDesc *)dev_table, count, b, prec, dev_status, sm_count, s);
 }

@@ -9,6 +9,8 @@
 //   norm2, norm : every tier l = 0..kmax as a 2^l x 2^l row-major FP64 grid at offset
 //                 (4^l - 1) / 3; norm = sqrt(norm2).
 //   nz          : NB x NB bytes, 1 where the leaf's tile storage holds the block.
+#include <type_traits>
+
 #include "convert.cuh"
 #include "internal.cuh"
 
@@ -532,6 +534,110 @@ cudaError_t launch_pyramid(spamm_tree t, cudaStream_t s) {
 
 // kernels launch_pyramid issues for a tree of this depth
 int pyramid_launches(int kmax) { return 1 + (kmax - kPyrL - 1 >= 0 ? 1 : 0); }
+
+// Transpose-consistent norm tree of a symmetric matrix: on every tier, the entries below
+// the diagonal are copies of their mirror images above it. The leaf norms of A_ik and
+// A_ki are sums of the same squares in different orders, so they may differ in the last
+// bit; copying makes every cull decision of (i, j, k) and (j, i, k) the same. A parent
+// stays at least as large as each child (it sums the upper children, whose copies the
+// lower children are), so the hierarchical cull still equals the flat leaf test.
+__global__ void __launch_bounds__(256) k_sym_norms(double *norm2, double *norm, int32_t kmax) {
+  const int64_t total = level_offset(kmax + 1);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int l = 0;
+    while (level_offset(l + 1) <= t) l++;
+    const int64_t D = int64_t(1) << l, loc = t - level_offset(l), i = loc / D, k = loc % D;
+    if (i > k) {
+      const int64_t src = level_offset(l) + k * D + i;
+      norm2[t] = norm2[src];
+      norm[t] = norm[src];
+    }
+  }
+}
+
+cudaError_t launch_sym_norms(spamm_tree t, cudaStream_t s) {
+  const int64_t total = level_offset(t->kmax + 1);
+  const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 1024);
+  k_sym_norms<<<grid, 256, 0, s>>>(t->norm2, t->norm, t->kmax);
+  return cudaGetLastError();
+}
+
+// C_ji := C_ij^T for every stored block i < j of a symmetric product (master tiles,
+// squared leaf norm, presence byte). Work item w is sub-tile w % S (E x E elements,
+// S = (b / E)^2) of block w / S in row-major block order; a CTA of 256 threads moves one
+// sub-tile per iteration with 16-byte loads and stores (V elements each) through a
+// padded shared-memory tile. Items of blocks on or below the diagonal, or absent, are
+// skipped.
+template <typename T, int E, int V>
+__global__ void __launch_bounds__(256) k_mirror(T *tiles, uint8_t *nz, double *leaf_norm2, int32_t b, int32_t nb,
+                                                int32_t NB) {
+  static_assert((E * E) % (256 * V) == 0, "whole vectors per thread");
+  constexpr int VR = E / V;                     // vectors per tile row
+  constexpr int PER = E * E / (256 * V);        // vectors per thread
+  constexpr int RSTEP = 256 / VR;               // tile rows covered by one pass of the CTA
+  using Vec = typename std::conditional<V * sizeof(T) == 16, uint4,
+              typename std::conditional<V * sizeof(T) == 8, uint2, uint32_t>::type>::type;
+  __shared__ T s[E][E + 1];
+  const int sub = b / E, S = sub * sub;
+  const int vc = threadIdx.x % VR, vr = threadIdx.x / VR;
+  const int64_t items = (int64_t)nb * nb * S;
+  for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    const int64_t t = w / S;
+    const int q = (int)(w % S);
+    const int32_t i = (int32_t)(t / nb), j = (int32_t)(t % nb);
+    const int64_t uij = (int64_t)i * NB + j, uji = (int64_t)j * NB + i;
+    if (i >= j || !nz[uij]) continue;   // block-uniform; an absent lower block stays absent
+    const int r0 = (q / sub) * E, c0 = (q % sub) * E;   // sub-tile origin in block (i, j)
+    const T *src = tiles + ((int64_t)i * nb + j) * b * b;
+    T *dst = tiles + ((int64_t)j * nb + i) * b * b;
+    __syncthreads();   // the previous item's reads of s are done
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+      const int y = vr + k * RSTEP;
+      union { Vec v; T e[V]; } u;
+      u.v = *reinterpret_cast<const Vec *>(src + (int64_t)(r0 + y) * b + c0 + vc * V);
+#pragma unroll
+      for (int e = 0; e < V; e++) s[y][vc * V + e] = u.e[e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+      const int y = vr + k * RSTEP;   // row c0 + y of block (j, i) = column c0 + y of (i, j)
+      union { Vec v; T e[V]; } u;
+#pragma unroll
+      for (int e = 0; e < V; e++) u.e[e] = s[vc * V + e][y];
+      *reinterpret_cast<Vec *>(dst + (int64_t)(c0 + y) * b + r0 + vc * V) = u.v;
+    }
+    if (q == 0 && threadIdx.x == 0) {
+      leaf_norm2[uji] = leaf_norm2[uij];
+      nz[uji] = 1;
+    }
+  }
+}
+
+template <typename T, int E, int V>
+static void run_mirror(spamm_tree C, T *tiles, double *ln2, cudaStream_t s) {
+  const int64_t S = (C->b / E) * (C->b / E);
+  const unsigned grid = (unsigned)std::min<int64_t>((int64_t)C->nb * C->nb * S, (int64_t)C->ctx->sm_count * 8);
+  k_mirror<T, E, V><<<grid, 256, 0, s>>>(tiles, C->nz, ln2, C->b, C->nb, C->NB);
+}
+
+cudaError_t launch_mirror(spamm_tree C, cudaStream_t s) {
+  double *ln2 = C->norm2 + level_offset(C->kmax);
+  if (C->copy[CK_F64]) {
+    double *t = (double *)C->copy[CK_F64];
+    if (C->b >= 32) run_mirror<double, 32, 2>(C, t, ln2, s);
+    else if (C->b == 16) run_mirror<double, 16, 1>(C, t, ln2, s);
+    else return cudaErrorInvalidValue;
+  } else if (C->copy[CK_F32]) {
+    float *t = (float *)C->copy[CK_F32];
+    if (C->b >= 64) run_mirror<float, 64, 4>(C, t, ln2, s);
+    else return cudaErrorInvalidValue;
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s) {
   const int64_t total = t->n * t->n;

@@ -29,6 +29,7 @@ SPAMM_COPY_BF16X3 = 0x0080
 SPAMM_NO_RIGHT = 0x0100
 SPAMM_GRAPH = 0x0200
 SPAMM_COPY_TF32X3 = 0x0400
+SPAMM_SYM_PRODUCT = 0x0800
 COPY_FLAG = {SPAMM_FP64: SPAMM_KEEP_FP64, SPAMM_TF32: SPAMM_COPY_TF32, SPAMM_BF16: SPAMM_COPY_BF16,
              SPAMM_FP16: SPAMM_COPY_FP16, SPAMM_BF16X3: SPAMM_COPY_BF16X3, SPAMM_TF32X3: SPAMM_COPY_TF32X3}
 MLP_FEATURES = 69
@@ -56,7 +57,8 @@ class StatsT(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("leaf", ctypes.c_int32), ("n", ctypes.c_int64),
                 ("tested", ctypes.c_int64 * MAX_LEVELS), ("culled", ctypes.c_int64 * MAX_LEVELS),
                 ("culled_bound", ctypes.c_double * MAX_LEVELS),
-                ("leaf_products", ctypes.c_int64), ("output_blocks", ctypes.c_int64),
+                ("leaf_products", ctypes.c_int64), ("mirrored_products", ctypes.c_int64),
+                ("output_blocks", ctypes.c_int64),
                 ("leaf_flops", ctypes.c_double), ("dense_equiv_flops", ctypes.c_double),
                 ("mma_flops", ctypes.c_double), ("ms_cull", ctypes.c_double),
                 ("ms_leaf", ctypes.c_double), ("prec", ctypes.c_int32), ("tau", ctypes.c_double)]
@@ -249,6 +251,7 @@ def spamm_stats(C: Tree) -> dict:
     L = s.levels
     return dict(levels=L, leaf=s.leaf, n=s.n, tested=list(s.tested[:L]), culled=list(s.culled[:L]),
                 culled_bound=list(s.culled_bound[:L]), leaf_products=s.leaf_products,
+                mirrored_products=s.mirrored_products,
                 output_blocks=s.output_blocks, leaf_flops=s.leaf_flops,
                 dense_equiv_flops=s.dense_equiv_flops, mma_flops=s.mma_flops, ms_cull=s.ms_cull,
                 ms_leaf=s.ms_leaf, prec=s.prec, tau=s.tau)

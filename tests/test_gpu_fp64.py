@@ -192,3 +192,34 @@ def test_workload_alg8192_fp64_sampled(S, ctx, tau):
         got = g["C"][i * leaf:(i + 1) * leaf, j * leaf:(j + 1) * leaf]
         d = np.linalg.norm(got - ref)
         assert d <= 1e-12 * max(np.linalg.norm(ref), 1e-300) or d == 0, (i, j, d)
+
+
+@pytest.mark.parametrize("n,leaf,tau,kind", [(1000, 32, 1e-8, "exp"), (3000, 64, 1e-8, "alg"), (1536, 16, 1e-4, "rand"),
+                                             (2048, 64, 0.0, "exp")])
+def test_fp64_symmetric_product(S, ctx, n, leaf, tau, kind):
+    # SPAMM_SYM_PRODUCT: blocks i <= j multiplied, the rest mirrored; same triples (with
+    # the transpose-consistent norms of a symmetric tree) and C within 1e-12 of the oracle
+    A = {"exp": lambda: W.exp_decay(n, 0.85, 1, 0), "alg": lambda: W.algebraic_decay(n, 2, 0),
+         "rand": lambda: rng_matrix(n, 5, 0.9, sym=True)}[kind]()
+    fl = S.SPAMM_KEEP_FP64 | S.SPAMM_SYMMETRIC
+    tA = S.spamm_tree_build(ctx, torch.from_numpy(A).cuda(), n, leaf, fl)
+    tC = S.spamm_multiply(ctx, tA, tA, tau, S.SPAMM_FP64, S.SPAMM_SYM_PRODUCT)
+    C, trip, st = S.spamm_tree_to_dense(tC), S.spamm_triples(tC), S.spamm_stats(tC)
+    norms = [S.spamm_tree_norms(tA, l) for l in range(tA.kmax + 1)]
+    normsC = [S.spamm_tree_norms(tC, l) for l in range(tC.kmax + 1)]
+    S.spamm_tree_free(tC)
+    S.spamm_tree_free(tA)
+    for nl in norms + normsC:
+        assert np.array_equal(nl, nl.T)
+    check_pyramid_monotone(norms)
+    check_pyramid_monotone(normsC)
+    assert np.array_equal(C, C.T)
+    TA = oracle.Tree(A, leaf)
+    ref = oracle.spamm(TA, TA, tau, triples=True, product=False)
+    only_g, only_o = compare_triples(trip, oracle.sort_triples(ref["triples"]), TA.NB, TA.norm2(TA.kmax),
+                                     TA.norm2(TA.kmax), tau)
+    assert st["leaf_products"] + st["mirrored_products"] == ref["count"] + len(only_g) - len(only_o)
+    assert st["mirrored_products"] <= st["leaf_products"]
+    Cref = oracle.spamm(TA, TA, tau, threads=oracle.max_threads())["C"]
+    Cref = adjust_for_band(Cref, A, A, leaf, TA.NB, only_g, only_o)
+    assert rel_fro(C, Cref) <= 1e-12

@@ -48,7 +48,8 @@ def test_sp2_fp64_tau0_matches_dense(S, ctx, side, leaf):
     assert abs(g["energy"] - ref["energy"]) <= 1e-12 * abs(ref["energy"])
     nb = -(-n // leaf)
     NB = 1 << (nb - 1).bit_length()
-    assert all(lp == NB ** 3 for lp in g["leaf_products"])   # tau = 0 keeps every triple
+    # tau = 0 keeps every triple; the symmetric products multiply the blocks i <= j
+    assert all(lp == NB * NB * (NB + 1) // 2 for lp in g["leaf_products"])
 
 
 @pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-6), ("bf16x3", 1e-5), ("tf32", 1e-3), ("bf16", 1e-2)])

@@ -42,14 +42,15 @@ def prec_of(S, name):
     return S.PRECISIONS[name]
 
 
-def gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric):
+def gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product=False):
     n = A.shape[0]
     prec = prec_of(S, prec_name)
     fl = S.COPY_FLAG[prec] | (S.SPAMM_SYMMETRIC if symmetric else 0)
     tA = S.spamm_tree_build(ctx, torch.from_numpy(A).cuda(), n, leaf, fl)
     tB = tA if B is A else S.spamm_tree_build(ctx, torch.from_numpy(B).cuda(), n, leaf, fl)
-    tC = S.spamm_multiply(ctx, tA, tB, tau, prec)
-    out = dict(C=S.spamm_tree_to_dense(tC), trip=S.spamm_triples(tC), stats=S.spamm_stats(tC))
+    tC = S.spamm_multiply(ctx, tA, tB, tau, prec, S.SPAMM_SYM_PRODUCT if sym_product else 0)
+    out = dict(C=S.spamm_tree_to_dense(tC), trip=S.spamm_triples(tC), stats=S.spamm_stats(tC),
+               norms=[S.spamm_tree_norms(tA, l) for l in range(tA.kmax + 1)])
     S.spamm_tree_free(tC)
     if tB is not tA:
         S.spamm_tree_free(tB)
@@ -90,8 +91,8 @@ def reference(A, B, leaf, tau, prec_name, threads):
     return TA, TB, Cref, Cabs + 0.0, Csub
 
 
-def check(S, ctx, A, B, leaf, tau, prec_name, symmetric):
-    g = gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric)
+def check(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product=False):
+    g = gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product)
     thr = oracle.max_threads()
     TA, TB, Cref, Cabs, Csub = reference(A, B, leaf, tau, prec_name, thr)
     ref = oracle.spamm(TA, TB, tau, triples=True, product=False)
@@ -113,7 +114,7 @@ def check(S, ctx, A, B, leaf, tau, prec_name, symmetric):
     print(f"{prec_name} leaf {leaf} n {n} tau {tau}: rel. Frobenius error vs FP64 SpAMM {err:.3e}")
     assert err < SANITY[prec_name]
     st = g["stats"]
-    assert st["leaf_products"] == ref["count"]
+    assert st["leaf_products"] + st["mirrored_products"] == ref["count"]
     assert st["mma_flops"] >= st["leaf_flops"] * (3 if prec_name in SPLIT else 1)
     return g
 
@@ -141,6 +142,32 @@ def test_tc_parity_nonsymmetric(S, ctx, prec, leaf):
     check(S, ctx, A, B, leaf, 1e-5, prec, symmetric=False)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "tf32x3", "fp16"])
+@pytest.mark.parametrize("n,leaf,tau,kind", [(1000, 64, 1e-6, "alg"), (2100, 128, 1e-6, "alg"), (2048, 64, 1e-8, "exp"),
+                                             (60, 64, 0.0, "exp")])
+def test_tc_symmetric_product(S, ctx, prec, n, leaf, tau, kind):
+    # blocks i <= j multiplied, i > j mirrored: the full triple list, C against the
+    # oracle, C symmetric bit for bit, and the norm tree transpose-consistent
+    A = W.algebraic_decay(n, 2, 0) if kind == "alg" else W.exp_decay(n, 0.85, 1, 0)
+    g = check(S, ctx, A, A, leaf, tau, prec, symmetric=True, sym_product=True)
+    # mirrored blocks are exact transposes; a diagonal block is computed, and is exactly
+    # symmetric in the plain formats (the products A_ir A_is are the same numbers),
+    # while the split forms sum hi lo and lo hi in separate passes
+    C = g["C"]
+    blk = np.arange(n) // leaf
+    diag = blk[:, None] == blk[None, :]
+    asym = np.abs(C - C.T)
+    assert not np.any(asym[~diag])
+    if prec in SPLIT:
+        assert np.all(asym[diag] <= 2.0 ** -20 * np.abs(C).max())
+    else:
+        assert not np.any(asym[diag])
+    for nl in g["norms"]:
+        assert np.array_equal(nl, nl.T)
+    if n > 100:
+        assert g["stats"]["mirrored_products"] > 0 and g["stats"]["leaf_products"] < g["stats"]["leaf_products"] + g["stats"]["mirrored_products"]
+
+
 def test_tc_tau_zero_dense(S, ctx):
     # tau = 0 keeps every triple, including those of padding blocks
     A = W.exp_decay(700, 0.9, 1, 0)
@@ -161,7 +188,7 @@ def test_workload_alg8192_tc_sampled(S, ctx, prec, tau):
     # full triple list, C on sampled output blocks against the rounded-operand oracle
     n, leaf = 8192, 64
     A = W.algebraic_decay(n, 2, 0)
-    g = gpu_product(S, ctx, A, A, leaf, tau, prec, True)
+    g = gpu_product(S, ctx, A, A, leaf, tau, prec, True, sym_product=True)
     TA = oracle.Tree(A, leaf)
     ref = oracle.spamm(TA, TA, tau, triples=True, product=False)
     compare_triples(g["trip"], oracle.sort_triples(ref["triples"]), TA.NB, TA.norm2(TA.kmax),
@@ -191,15 +218,16 @@ def test_workload_alg8192_tc_sampled(S, ctx, prec, tau):
 @pytest.mark.parametrize("n", [4096, 1000, 130])
 def test_symmetric_and_transposed_layouts_agree(S, ctx, n):
     # a symmetric operand declared symmetric (one copy serves both roles) and the same
-    # operand with transposed copies for the right role: identical norms, and identical
-    # products from the two operand layouts
+    # operand with transposed copies for the right role: identical norms on and above the
+    # diagonal, and identical products from the two operand layouts
     A = W.algebraic_decay(n, 2, 0)
     dA = torch.from_numpy(A).cuda()
     f = S.COPY_FLAG[S.SPAMM_BF16X3]
     t1 = S.spamm_tree_build(ctx, dA, n, 64, f | S.SPAMM_SYMMETRIC)
     t2 = S.spamm_tree_build(ctx, dA, n, 64, f)
-    for l in range(t1.kmax + 1):
-        assert np.array_equal(S.spamm_tree_norms(t1, l), S.spamm_tree_norms(t2, l)), l
+    for l in range(t1.kmax + 1):   # on and above the diagonal (a symmetric tree mirrors the rest)
+        up = np.triu(np.ones((1 << l, 1 << l), dtype=bool))
+        assert np.array_equal(S.spamm_tree_norms(t1, l)[up], S.spamm_tree_norms(t2, l)[up]), l
     c1 = S.spamm_multiply(ctx, t1, t1, 1e-7, S.SPAMM_BF16X3)
     c2 = S.spamm_multiply(ctx, t2, t2, 1e-7, S.SPAMM_BF16X3)
     assert np.array_equal(S.spamm_tree_to_dense(c1), S.spamm_tree_to_dense(c2))
