@@ -149,6 +149,13 @@ SPAMM_API spamm_status spamm_tree_free(spamm_tree t);
    iterate of a purification loop). A is a device pointer unless `flags` holds
    SPAMM_HOST_INPUT. Errors: SPAMM_EINVAL (t is a product tree, bad flags), SPAMM_ECUDA. */
 SPAMM_API spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags);
+/* Mean device time in milliseconds of the leaf-block kernel (quadtree leaves, leaf
+   norms and leaf copies; Eq. 1 and the norms of Sec. III) over the builds and updates
+   of t since the previous call (the last 64 at most), from CUDA events recorded on the
+   context's stream around each launch when the context was created with timing != 0.
+   Waits for those launches to finish, then starts a new count.
+   Errors: SPAMM_EINVAL (null argument, or no timed build since the last call), SPAMM_ECUDA. */
+SPAMM_API spamm_status spamm_tree_build_ms(spamm_tree t, float *ms);
 /* Shape of a tree: order n, leaf size, padded blocks per side NB, and kmax. */
 SPAMM_API spamm_status spamm_tree_info(spamm_tree t, int64_t *n, int32_t *leaf, int32_t *nb_padded,
                              int32_t *kmax);

@@ -101,6 +101,9 @@ void free_tree_memory(spamm_tree t) {
   dfree(t->tc_desc_dev);
   for (int k = 0; k < 3; k++)
     if (t->ev[k]) cudaEventDestroy(t->ev[k]);
+  for (int q = 0; q < kBuildEvents; q++)
+    for (int k = 0; k < 2; k++)
+      if (t->ev_build[q][k]) cudaEventDestroy(t->ev_build[q][k]);
 }
 
 spamm_status alloc_tree(spamm_ctx ctx, int64_t n, int32_t b, int32_t flags, spamm_tree *out) {
@@ -279,6 +282,24 @@ const char *spamm_last_error(spamm_ctx ctx) { return ctx ? ctx->err.c_str() : "n
 
 int64_t spamm_kernel_launches(spamm_ctx ctx) { return ctx ? ctx->launches : -1; }
 
+// The leaf-block kernel, bracketed by the next event pair of the tree's ring on a
+// timing context.
+static cudaError_t timed_tree_build(spamm_tree t, const double *src, cudaStream_t s) {
+  if (!t->ctx->timing) return launch_tree_build(t, src, s);
+  cudaEvent_t *ev = t->ev_build[t->build_pos];
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; k++)
+    if (!ev[k]) e = cudaEventCreate(&ev[k]);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess) e = launch_tree_build(t, src, s);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+  if (e == cudaSuccess) {
+    t->build_pos = (t->build_pos + 1) % kBuildEvents;
+    t->build_count = std::min(t->build_count + 1, kBuildEvents);
+  }
+  return e;
+}
+
 spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t leaf,
                               int32_t flags, spamm_tree *out) {
   if (!ctx) return SPAMM_EINVAL;
@@ -307,7 +328,7 @@ spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t
     }
     src = (const double *)ctx->stage;
   }
-  cudaError_t e = launch_tree_build(t, src, ctx->stream);
+  cudaError_t e = timed_tree_build(t, src, ctx->stream);
   if (e == cudaSuccess) e = launch_pyramid(t, ctx->stream);
   if (e == cudaSuccess && (flags & SPAMM_SYMMETRIC)) e = launch_sym_norms(t, ctx->stream);
   ctx->launches += 1 + pyramid_launches(t->kmax) + ((t->flags & SPAMM_SYMMETRIC) ? 1 : 0);
@@ -334,7 +355,7 @@ spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags) {
                        ctx->stream), "tree_update: host to device copy");
     src = (const double *)ctx->stage;
   }
-  CK(launch_tree_build(t, src, ctx->stream), "tree_update: launch");
+  CK(timed_tree_build(t, src, ctx->stream), "tree_update: launch");
   CK(launch_pyramid(t, ctx->stream), "tree_update: launch");
   if (t->flags & SPAMM_SYMMETRIC) CK(launch_sym_norms(t, ctx->stream), "tree_update: launch");
   ctx->launches += 1 + pyramid_launches(t->kmax) + ((t->flags & SPAMM_SYMMETRIC) ? 1 : 0);
@@ -346,6 +367,24 @@ spamm_status spamm_tree_free(spamm_tree t) {
   cudaStreamSynchronize(t->ctx->stream);
   free_tree_memory(t);
   delete t;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_tree_build_ms(spamm_tree t, float *ms) {
+  if (!t) return SPAMM_EINVAL;
+  spamm_ctx ctx = t->ctx;
+  if (!ms) return fail(ctx, SPAMM_EINVAL, "tree_build_ms: null output");
+  if (t->build_count == 0) return fail(ctx, SPAMM_EINVAL, "tree_build_ms: no timed build of this tree since the last read");
+  double sum = 0.0;
+  for (int k = 1; k <= t->build_count; k++) {
+    cudaEvent_t *ev = t->ev_build[(t->build_pos - k + kBuildEvents) % kBuildEvents];
+    float one = 0.f;
+    CK(cudaEventSynchronize(ev[1]), "tree_build_ms: event");
+    CK(cudaEventElapsedTime(&one, ev[0], ev[1]), "tree_build_ms: event");
+    sum += one;
+  }
+  *ms = (float)(sum / t->build_count);
+  t->build_count = 0;
   return SPAMM_OK;
 }
 

@@ -32,6 +32,7 @@ inline bool tf32_prec(int prec) { return prec == SPAMM_TF32 || prec == SPAMM_TF3
 
 // Bytes reserved in a product tree for its tensor-core launch descriptor (host image).
 constexpr size_t kTcDescBytes = 1024;
+constexpr int kBuildEvents = 64;
 
 // Bounded waits give up after this many nanoseconds of %globaltimer.
 constexpr unsigned long long kSpinLimitNs = 2000000000ull;
@@ -158,6 +159,10 @@ struct spamm_tree_s {
   spamm_stats_t host_stats{};
   bool stats_valid = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  // timing contexts: event pairs around the leaf-block kernel of the last kBuildEvents
+  // builds (a ring), and how many were recorded since spamm_tree_build_ms last read them
+  cudaEvent_t ev_build[kBuildEvents][2] = {};
+  int build_pos = 0, build_count = 0;
 };
 
 __host__ __device__ inline int64_t level_offset(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }

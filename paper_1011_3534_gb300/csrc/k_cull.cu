@@ -413,6 +413,7 @@ constexpr int kTopTiers = 5;                 // tiers 0..4
 constexpr int kTopGroups = 256;              // groups of the tier-4 list (4^4)
 constexpr int kTopEntries = 4096;            // entries of the tier-4 list (8^4)
 constexpr int kTopThreads = 1024;
+constexpr int kTopNorms = ((1 << (2 * kTopTiers)) - 1) / 3;   // norms of tiers 0..4 per operand
 
 struct TopArgs {
   const double *nA[kTopTiers], *nB[kTopTiers];   // tier norms (not squared)
@@ -436,8 +437,16 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
   __shared__ uint32_t s_cnt[kTopGroups], s_off[kTopGroups + 1], s_gix[kTopGroups + 1];
   __shared__ unsigned long long s_tested, s_surv;
   __shared__ uint32_t s_ng, s_ne;
+  __shared__ double s_nA[kTopNorms], s_nB[kTopNorms];   // the tier norms, read once
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kTopThreads / 32;
   const double tau = t.tau_dev ? *t.tau_dev : t.tau;
+  for (int l = 0; l <= t.T; l++) {
+    const int64_t off = level_offset(l);
+    for (int q = threadIdx.x; q < (1 << (2 * l)); q += blockDim.x) {
+      s_nA[off + q] = t.nA[l][q];
+      s_nB[off + q] = t.nB[l][q];
+    }
+  }
   if (threadIdx.x == 0) {   // tier -1: one group (0, 0) holding K = 0
     s_gij[0][0] = 0;
     s_gstart[0][0] = 0;
@@ -450,8 +459,8 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
   int cur = 0;
   for (int l = 0; l <= t.T; l++) {
     CullArgs a{};
-    a.nA = t.nA[l];
-    a.nB = t.nB[l];
+    a.nA = s_nA + level_offset(l);
+    a.nB = s_nB + level_offset(l);
     a.D = 1 << l;
     a.sym = t.sym;
     const uint32_t ng = s_ng;

@@ -38,7 +38,9 @@ struct BuildArgs {
 // leaf copies are rounded in integer arithmetic on the FP64 bit pattern.
 template <int B>
 struct BuildCfg {
-  static constexpr int T = 256;                    // threads per CTA
+  // threads per CTA: a 64 x 64 leaf gets 128 threads, so that each streams four rounds
+  // and the leaf's coordinates stay CTA-uniform
+  static constexpr int T = B == 64 ? 128 : 256;
   static constexpr int PAIRS = B * B / 2;          // element pairs per leaf
   static constexpr int TPL = PAIRS / 4 < T ? PAIRS / 4 : T;   // threads per leaf
   static constexpr int LPC = T / TPL;              // leaves per CTA
@@ -116,7 +118,9 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
 #pragma unroll
   for (int e = 0; e < 8; e++) Er = max(Er, (int)((hw[e] >> 20) & 0x7FFu));
   if (Er > 0 && Er < 0x7FF) {
-    float S = 0.f, s2 = 0.f;
+    // two independent double-float sums (even and odd elements) halve the dependency
+    // chain; they are joined once per round
+    float S[2] = {0.f, 0.f}, s2[2] = {0.f, 0.f};
 #pragma unroll
     for (int e = 0; e < 8; e++) {
       const int E = (int)((hw[e] >> 20) & 0x7FFu);
@@ -130,12 +134,14 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
       const float pp = hi * hi;
       float cc = fmaf(hi, hi, -pp);
       cc = fmaf(2.f * hi, lo, cc);
-      const float t = S + pp;
-      const float tb = t - S;
-      s2 += ((S - (t - tb)) + (pp - tb)) + cc;
-      S = t;
+      float &Sx = S[e & 1], &sx = s2[e & 1];
+      const float t = Sx + pp;
+      const float tb = t - Sx;
+      sx += ((Sx - (t - tb)) + (pp - tb)) + cc;
+      Sx = t;
     }
-    acc.merge(S, s2, Er);
+    df_add(S[0], s2[0], S[1], s2[1]);
+    acc.merge(S[0], s2[0], Er);
   } else if (Er == 0x7FF) {
     acc.merge(__uint_as_float(0x7F800000u), 0.f, 0x7FE);
   }
@@ -264,7 +270,7 @@ __device__ __forceinline__ double merge_warps(const float *h, const float *l, co
 }
 
 template <int B, bool VEC, uint32_t M>
-__global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p_in) {
+__global__ void __launch_bounds__(BuildCfg<B>::T, 1024 / BuildCfg<B>::T) k_tree_build(BuildArgs p_in) {
   const BuildArgs p = masked<M>(p_in);
   using Cfg = BuildCfg<B>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -289,8 +295,11 @@ __global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p_in) {
     if (p.fp16T) { s_fp16T = (uint16_t *)q + li * bb; q += Cfg::LPC * bb * 2; }
     if (p.loT) { s_loT = (uint16_t *)q + li * bb; q += Cfg::LPC * bb * 2; }
   }
+  // a leaf wholly inside the matrix loads without bounds checks
+  const bool full = stored && (int64_t)(r + 1) * B <= p.n && (int64_t)(c + 1) * B <= p.n;
   NormAcc acc;
   if (stored) {
+#pragma unroll 1
     for (int rd = 0; rd < Cfg::ROUNDS; rd++) {
       uint32_t hw[8], lw[8];   // high and low words of the round's 8 elements
       int rows[4], cols[4];
@@ -301,7 +310,9 @@ __global__ void __launch_bounds__(256, 4) k_tree_build(BuildArgs p_in) {
         cols[u] = 2 * (q % (B / 2));
         const int64_t gr = (int64_t)r * B + rows[u], gc = (int64_t)c * B + cols[u];
         double2 d = make_double2(0.0, 0.0);
-        if (gr < p.n) {
+        if (VEC && full) {
+          d = __ldcs(reinterpret_cast<const double2 *>(p.A + gr * p.n + gc));
+        } else if (gr < p.n) {
           const double *src = p.A + gr * p.n + gc;
           if (VEC && gc + 1 < p.n) {
             d = __ldcs(reinterpret_cast<const double2 *>(src));

@@ -38,6 +38,7 @@ MAX_LEVELS = 24
 # Every entry point declared in include/spamm.h.
 EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_error",
            "spamm_kernel_launches", "spamm_tree_build", "spamm_tree_update", "spamm_tree_free", "spamm_tree_info",
+           "spamm_tree_build_ms",
            "spamm_tree_norms", "spamm_tree_to_dense", "spamm_multiply", "spamm_stats",
            "spamm_triples", "spamm_cull_noalloc", "spamm_sp2", "spamm_multiply_batched",
            "spamm_tune_leaf", "spamm_mlp_create", "spamm_mlp_free", "spamm_mlp_num_params",
@@ -94,6 +95,7 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.spamm_tree_build.argtypes = [_P, _P, _I64, _I32, _I32, ctypes.POINTER(_P)]
     L.spamm_tree_free.argtypes = [_P]
     L.spamm_tree_update.argtypes = [_P, _P, _I32]
+    L.spamm_tree_build_ms.argtypes = [_P, ctypes.POINTER(ctypes.c_float)]
     L.spamm_tree_info.argtypes = [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32),
                                   ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
     L.spamm_tree_norms.argtypes = [_P, _I32, _P]
@@ -213,6 +215,13 @@ def spamm_tree_update(t: Tree, A) -> Tree:
     flags = SPAMM_HOST_INPUT if isinstance(A, np.ndarray) else 0
     t.ctx.check(LIB.spamm_tree_update(t.h, _ptr(A), flags), "spamm_tree_update")
     return t
+
+
+def spamm_tree_build_ms(t: Tree) -> float:
+    """Device time (ms) of the leaf-block kernel in t's last build or update (timing contexts)."""
+    ms = ctypes.c_float()
+    t.ctx.check(LIB.spamm_tree_build_ms(t.h, ctypes.byref(ms)), "spamm_tree_build_ms")
+    return ms.value
 
 
 def spamm_tree_free(t: Tree):
