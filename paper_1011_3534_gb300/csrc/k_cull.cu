@@ -403,16 +403,22 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
   }
 }
 
-// The upper tiers in one CTA. Tiers 0..T (T < k_max, at most kTopTiers of them) hold
-// at most 4^(T-1) parent groups and 8^T entries, far too little work for a launch per
-// tier: a single CTA runs the same expansion as k_cull_tier tier after tier with the
-// lists in shared memory (a warp per parent group, entries 32 at a time, the same
-// per-lane order, so the counters and the per-group culled bounds are the same values),
-// and writes only the tier-T list and the counters of tiers 0..T.
+// The upper tiers in one CTA. Tiers 0..T (T < k_max, at most kTopTiers of them) hold at
+// most 8^T triples, far too little work for a launch per tier. Tier l is evaluated for
+// all its 4^l output blocks at once, a thread per block (I, J) in Morton order (so the
+// parent block is index >> 2), each over its K < 2^l: the triple (I, J, K) is tested
+// when its parent (I/2, J/2, K/2) survived tier l-1 (and, for a symmetric product,
+// I <= J) and survives when ||A^l_IK||_F ||B^l_KJ||_F >= tau: exactly the calls of the
+// Eq. 4 recursion, as in k_cull_tier. A block's survivors form a bit mask over K, which
+// is the next tier's parent test. Only the tier-T list (groups in Morton order, K
+// ascending) and the counters of tiers 0..T are written; the culled bound of tier l
+// (summed per thread over K, per warp by a fixed tree, then over warps in order) goes
+// to the first parent-group slot of the tier and zeros to the others, so the fixed-
+// order reduction of the slots returns it unchanged.
 constexpr int kTopTiers = 5;                 // tiers 0..4
-constexpr int kTopGroups = 256;              // groups of the tier-4 list (4^4)
-constexpr int kTopEntries = 4096;            // entries of the tier-4 list (8^4)
+constexpr int kTopBlocks = 256;              // output blocks of tier 4 (4^4)
 constexpr int kTopThreads = 1024;
+constexpr int kTopWarps = kTopThreads / 32;
 constexpr int kTopNorms = ((1 << (2 * kTopTiers)) - 1) / 3;   // norms of tiers 0..4 per operand
 
 struct TopArgs {
@@ -430,15 +436,24 @@ struct TopArgs {
   uint32_t *status;
 };
 
+// (I, J) of Morton index m: bit 2b of m is bit b of J, bit 2b + 1 is bit b of I.
+__device__ __forceinline__ void morton_ij(uint32_t m, uint32_t &I, uint32_t &J) {
+  I = 0;
+  J = 0;
+#pragma unroll
+  for (int b = 0; b < kTopTiers; b++) {
+    J |= ((m >> (2 * b)) & 1u) << b;
+    I |= ((m >> (2 * b + 1)) & 1u) << b;
+  }
+}
+
 __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
-  __shared__ uint32_t s_gij[2][kTopGroups], s_gstart[2][kTopGroups], s_glen[2][kTopGroups];
-  __shared__ uint16_t s_K[2][kTopEntries];
-  __shared__ uint8_t s_bits[kTopEntries];
-  __shared__ uint32_t s_cnt[kTopGroups], s_off[kTopGroups + 1], s_gix[kTopGroups + 1];
-  __shared__ unsigned long long s_tested, s_surv;
-  __shared__ uint32_t s_ng, s_ne;
   __shared__ double s_nA[kTopNorms], s_nB[kTopNorms];   // the tier norms, read once
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kTopThreads / 32;
+  __shared__ uint16_t s_mask[2][kTopBlocks];            // survivors over K per block: tiers l-1, l
+  __shared__ double s_wb[kTopWarps];                    // per-warp culled bounds
+  __shared__ uint32_t s_wg[kTopWarps], s_we[kTopWarps];
+  __shared__ unsigned long long s_tested, s_surv;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double tau = t.tau_dev ? *t.tau_dev : t.tau;
   for (int l = 0; l <= t.T; l++) {
     const int64_t off = level_offset(l);
@@ -447,129 +462,91 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
       s_nB[off + q] = t.nB[l][q];
     }
   }
-  if (threadIdx.x == 0) {   // tier -1: one group (0, 0) holding K = 0
-    s_gij[0][0] = 0;
-    s_gstart[0][0] = 0;
-    s_glen[0][0] = 1;
-    s_K[0][0] = 0;
-    s_ng = 1;
-    s_ne = 1;
+  if (threadIdx.x == 0) {
+    s_tested = 0;
+    s_surv = 0;
   }
   __syncthreads();
-  int cur = 0;
+  const uint32_t m = threadIdx.x;
+  uint32_t I = 0, J = 0;
+  morton_ij(m, I, J);
+  int cur = 0;                 // s_mask[cur]: the tier just evaluated
+  uint32_t parent_groups = 1;  // groups of the tier l-1 list (tier -1: the root group)
   for (int l = 0; l <= t.T; l++) {
-    CullArgs a{};
-    a.nA = s_nA + level_offset(l);
-    a.nB = s_nB + level_offset(l);
-    a.D = 1 << l;
-    a.sym = t.sym;
-    const uint32_t ng = s_ng;
-    const int nx = cur ^ 1;
+    const uint32_t D = 1u << l, nblk = D * D;
+    const double *nA = s_nA + level_offset(l), *nB = s_nB + level_offset(l);
+    uint32_t mask = 0;
+    int tests = 0;
+    double bound = 0.0;
+    if (m < nblk && !(t.sym && I > J)) {   // below the diagonal: the mirror of (J, I)
+      const uint32_t pm = l ? s_mask[cur][m >> 2] : 1u;   // tier 0's parent: K = 0 of the root
+      for (uint32_t K = 0; K < D; K++) {
+        if (!((pm >> (K >> 1)) & 1u)) continue;          // parent culled: not a call
+        const double p = nA[I * D + K] * nB[K * D + J];
+        tests++;
+        if (p < tau) bound += p;
+        else mask |= 1u << K;
+      }
+    }
+    const int nx = l ? cur ^ 1 : 0;
+    if (m < nblk) s_mask[nx][m] = (uint16_t)mask;
+    tests = warp_sum(tests);
+    const unsigned int surv = warp_sum((unsigned int)__popc(mask));
+    if (__any_sync(0xffffffffu, bound != 0.0)) bound = warp_sum(bound);   // else every lane holds +0
+    if (lane == 0) {
+      s_wb[warp] = bound;
+      atomicAdd(&s_tested, (unsigned long long)tests);
+      atomicAdd(&s_surv, (unsigned long long)surv);
+    }
+    const uint32_t groups = (uint32_t)__syncthreads_count(m < nblk && mask != 0u);
     if (threadIdx.x == 0) {
+      double b = 0.0;
+      for (int w = 0; w < kTopWarps; w++) b += s_wb[w];
+      t.bound_part[t.bound_off[l]] = b;
+      t.cnt->tested[l] = s_tested;
+      t.cnt->culled[l] = s_tested - s_surv;
+      t.cnt->ngroups[l + 1] = groups;
+      t.cnt->nentries[l + 1] = s_surv;
       s_tested = 0;
       s_surv = 0;
     }
-    __syncthreads();
-    // pass 1: survival bits, per child-quadrant counts, tests and culled bounds
-    for (uint32_t g = warp; g < ng; g += nw) {
-      const uint32_t ij = s_gij[cur][g], I = ij >> 16, J = ij & 0xFFFFu;
-      const uint32_t start = s_gstart[cur][g], len = s_glen[cur][g];
-      unsigned int cq[4] = {0, 0, 0, 0};
-      int tests = 0;
-      double bound = 0.0;
-      for (uint32_t p0 = 0; p0 < len; p0 += 32) {
-        const uint32_t p = p0 + lane;
-        uint32_t bits = 0;
-        if (p < len) {
-          bits = child_bits(a, tau, I, J, s_K[cur][start + p], tests, bound);
-          s_bits[start + p] = (uint8_t)bits;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; q++) cq[q] += __popc((bits >> (2 * q)) & 3u);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; q++) cq[q] = warp_sum(cq[q]);
-      tests = warp_sum(tests);
-      bound = warp_sum(bound);
-      if (lane < 4) s_cnt[4 * g + lane] = cq[lane];
-      if (lane == 0) {
-        t.bound_part[t.bound_off[l] + g] = bound;
-        atomicAdd(&s_tested, (unsigned long long)tests);
-        atomicAdd(&s_surv, (unsigned long long)(cq[0] + cq[1] + cq[2] + cq[3]));
-      }
-    }
-    __syncthreads();
-    // child groups (parent group, quadrant) in order: entry offsets and group indices
-    if (warp == 0) {
-      uint32_t base_e = 0, base_g = 0;
-      for (uint32_t c0 = 0; c0 < 4 * ng; c0 += 32) {
-        const uint32_t c = c0 + lane;
-        const uint32_t v = c < 4 * ng ? s_cnt[c] : 0u, f = v ? 1u : 0u;
-        const uint32_t iv = warp_inclusive_scan(v), ifl = warp_inclusive_scan(f);
-        if (c < 4 * ng) {
-          s_off[c] = base_e + iv - v;
-          s_gix[c] = base_g + ifl - f;
-        }
-        base_e += __shfl_sync(0xffffffffu, iv, 31);
-        base_g += __shfl_sync(0xffffffffu, ifl, 31);
-      }
-      if (lane == 0) {
-        s_ne = base_e;
-        s_ng = base_g;
-        t.cnt->ngroups[l + 1] = base_g;
-        t.cnt->nentries[l + 1] = base_e;
-        t.cnt->tested[l] = s_tested;
-        t.cnt->culled[l] = s_tested - s_surv;
-        if (base_e > (uint32_t)kTopEntries || base_g > (uint32_t)kTopGroups) flag_error(t.status, DEV_OVERFLOW);
-      }
-    }
-    __syncthreads();
-    // pass 2: child group records and entries
-    for (uint32_t g = warp; g < ng; g += nw) {
-      const uint32_t ij = s_gij[cur][g], I = ij >> 16, J = ij & 0xFFFFu;
-      const uint32_t start = s_gstart[cur][g], len = s_glen[cur][g];
-      if (lane < 4 && s_cnt[4 * g + lane]) {
-        const uint32_t gi = s_gix[4 * g + lane];
-        if (gi < (uint32_t)kTopGroups) {
-          s_gij[nx][gi] = ((2 * I + (lane >> 1)) << 16) | (2 * J + (lane & 1));
-          s_gstart[nx][gi] = s_off[4 * g + lane];
-          s_glen[nx][gi] = s_cnt[4 * g + lane];
-        }
-      }
-      unsigned int run[4];
-#pragma unroll
-      for (int q = 0; q < 4; q++) run[q] = s_off[4 * g + q];
-      for (uint32_t p0 = 0; p0 < len; p0 += 32) {
-        const uint32_t p = p0 + lane;
-        const uint32_t bits = p < len ? s_bits[start + p] : 0u;
-        const uint32_t K = p < len ? s_K[cur][start + p] : 0u;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const uint32_t two = (bits >> (2 * q)) & 3u;
-          const unsigned int m = __popc(two);
-          const unsigned int inc = warp_inclusive_scan(m);
-          unsigned int pos = run[q] + inc - m;
-          if ((two & 1u) && pos < (unsigned)kTopEntries) s_K[nx][pos++] = (uint16_t)(2 * K);
-          if ((two & 2u) && pos < (unsigned)kTopEntries) s_K[nx][pos] = (uint16_t)(2 * K + 1);
-          run[q] += __shfl_sync(0xffffffffu, inc, 31);
-        }
-      }
-    }
-    __syncthreads();
+    for (uint32_t g = 1 + threadIdx.x; g < parent_groups; g += blockDim.x) t.bound_part[t.bound_off[l] + g] = 0.0;
+    parent_groups = groups;
     cur = nx;
+    __syncthreads();
   }
-  // the tier-T list, for the launch of tier T + 1
-  const uint32_t ng = s_ng < (uint32_t)kTopGroups ? s_ng : (uint32_t)kTopGroups;
-  const uint32_t ne = s_ne < (uint32_t)kTopEntries ? s_ne : (uint32_t)kTopEntries;
-  for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
-    if ((int64_t)g < t.cap_groups) {
-      t.gij[g] = s_gij[cur][g];
-      t.gstart[g] = s_gstart[cur][g];
-      t.glen[g] = s_glen[cur][g];
+  // the tier-T list, for the launch of tier T + 1: groups and entries placed by a
+  // block-wide exclusive scan over the blocks in Morton order
+  const uint32_t DT = 1u << t.T;
+  const uint32_t mask = m < DT * DT ? s_mask[cur][m] : 0u;
+  const uint32_t has = mask ? 1u : 0u, cntK = (uint32_t)__popc(mask);
+  const uint32_t ig = warp_inclusive_scan(has), ie = warp_inclusive_scan(cntK);
+  if (lane == 31) {
+    s_wg[warp] = ig;
+    s_we[warp] = ie;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t vg = s_wg[lane], ve = s_we[lane];
+    const uint32_t sg = warp_inclusive_scan(vg), se = warp_inclusive_scan(ve);
+    s_wg[lane] = sg - vg;
+    s_we[lane] = se - ve;
+  }
+  __syncthreads();
+  if (has) {
+    const uint32_t gi = s_wg[warp] + ig - 1u, e0 = s_we[warp] + ie - cntK;
+    if ((int64_t)gi < t.cap_groups) {
+      t.gij[gi] = (I << 16) | J;
+      t.gstart[gi] = e0;
+      t.glen[gi] = cntK;
     }
+    uint32_t r = 0;
+    for (uint32_t K = 0; K < DT; K++)
+      if ((mask >> K) & 1u) {
+        if ((int64_t)(e0 + r) < t.cap_entries) t.K[e0 + r] = (uint16_t)K;
+        r++;
+      }
   }
-  for (uint32_t e = threadIdx.x; e < ne; e += blockDim.x)
-    if ((int64_t)e < t.cap_entries) t.K[e] = s_K[cur][e];
 }
 
 // Prologue of a product: zeroes the counters, the look-back words and the product's

@@ -40,7 +40,7 @@ template <int B>
 struct BuildCfg {
   // threads per CTA: a 64 x 64 leaf gets 128 threads, so that each streams four rounds
   // and the leaf's coordinates stay CTA-uniform
-  static constexpr int T = B == 64 ? 128 : 256;
+  static constexpr int T = B == 64 ? 64 : 256;
   static constexpr int PAIRS = B * B / 2;          // element pairs per leaf
   static constexpr int TPL = PAIRS / 4 < T ? PAIRS / 4 : T;   // threads per leaf
   static constexpr int LPC = T / TPL;              // leaves per CTA
@@ -129,11 +129,11 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
       // hi: sign-free top 24 significand bits; lo: the bits below
       const float hi = __uint_as_float(((uint32_t)(es + 127) << 23) | (((hw[e] & 0xFFFFFu) << 3) | (lw[e] >> 29)));
       // (the next 23 bits, as an exact FP32 integer: their last 6 bits' share of the
-      // square is below 2^-46)
-      const float lo = u23_to_float((lw[e] >> 6) & 0x7FFFFFu) * __uint_as_float((uint32_t)(es - 46 + 127) << 23);
+      // square is below 2^-46), times two: lo2 = 2 lo for the cross term 2 hi lo
+      const float lo2 = u23_to_float((lw[e] >> 6) & 0x7FFFFFu) * __uint_as_float((uint32_t)(es - 45 + 127) << 23);
       const float pp = hi * hi;
       float cc = fmaf(hi, hi, -pp);
-      cc = fmaf(2.f * hi, lo, cc);
+      cc = fmaf(hi, lo2, cc);
       float &Sx = S[e & 1], &sx = s2[e & 1];
       const float t = Sx + pp;
       const float tb = t - Sx;
