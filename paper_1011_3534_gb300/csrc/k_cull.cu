@@ -129,6 +129,13 @@ __device__ __forceinline__ int passes64(uint32_t m, int e, uint32_t (&rm)[2], ui
   return 2;
 }
 
+// p < tau for a norm product p >= +0 and tau >= +0, on the integer ALU: nonnegative
+// doubles order as their bit patterns (a NaN product compares not below, as in FP64),
+// which keeps the test off the narrow FP64 pipe.
+__device__ __forceinline__ bool below_tau(double p, double tau) {
+  return (unsigned long long)__double_as_longlong(p) < (unsigned long long)__double_as_longlong(tau);
+}
+
 // Children of entry (I, J, K) tested at tier l: survival bits, test count, and the
 // culled norm products summed in a fixed order.
 __device__ __forceinline__ uint32_t child_bits(const CullArgs &a, double tau, uint32_t I, uint32_t J,
@@ -150,7 +157,7 @@ __device__ __forceinline__ uint32_t child_bits(const CullArgs &a, double tau, ui
         if (a.sym && i > j) continue;   // below the diagonal: the mirror of (j, i)
         const double p = na * a.nB[(int64_t)k * a.D + j];
         tests++;
-        if (p < tau) bound += p;
+        if (below_tau(p, tau)) bound += p;
         else bits |= 1u << (((ai * 2 + c) * 2) + e);
       }
     }
@@ -480,11 +487,13 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
     double bound = 0.0;
     if (m < nblk && !(t.sym && I > J)) {   // below the diagonal: the mirror of (J, I)
       const uint32_t pm = l ? s_mask[cur][m >> 2] : 1u;   // tier 0's parent: K = 0 of the root
-      for (uint32_t K = 0; K < D; K++) {
+#pragma unroll
+      for (uint32_t K = 0; K < (1u << (kTopTiers - 1)); K++) {
+        if (K >= D) break;
         if (!((pm >> (K >> 1)) & 1u)) continue;          // parent culled: not a call
         const double p = nA[I * D + K] * nB[K * D + J];
         tests++;
-        if (p < tau) bound += p;
+        if (below_tau(p, tau)) bound += p;
         else mask |= 1u << K;
       }
     }
@@ -501,7 +510,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
     const uint32_t groups = (uint32_t)__syncthreads_count(m < nblk && mask != 0u);
     if (threadIdx.x == 0) {
       double b = 0.0;
-      for (int w = 0; w < kTopWarps; w++) b += s_wb[w];
+      for (int w = 0; w < (int)((nblk + 31) / 32); w++) b += s_wb[w];   // the other warps hold +0
       t.bound_part[t.bound_off[l]] = b;
       t.cnt->tested[l] = s_tested;
       t.cnt->culled[l] = s_tested - s_surv;

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ volatile int s_abort;
   __shared__ double s_norm[4][2];
   __shared__ int4 s_desc[32];                    // producer: the chunk of passes being issued
+  __shared__ float s_epi[4][32][33];             // epilogue: one 32 x 32 chunk per warp, transposed out
   __shared__ unsigned long long s_off[kMaxProd + 1];   // first global item of each product
   constexpr int RA = LEAF == 64 ? 2 : 1;        // A leaves stacked along M
   constexpr int RC = LEAF == 64 ? 2 : 1;        // B leaves stacked along N
@@ -348,7 +349,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int q = a * 2 + c;
           const int j = (int)(2 * J) + c;
           if (!((touched >> q) & 1u) || i >= P.nb || j >= P.nb) continue;   // warp-uniform
+          // plain forms: the warp's 32 rows of block (i, j) are written through shared
+          // memory, so that each store instruction covers four whole 128-byte rows; the
+          // split forms store each thread's row directly
           float *dst = P.C + (((int64_t)i * P.nb + j) * LEAF + r) * LEAF;
+          float *blk = P.C + ((int64_t)i * P.nb + j) * LEAF * LEAF + (int64_t)(r - lane) * LEAF;
+          float(*sb)[33] = s_epi[warp - 2];
 #pragma unroll
           for (int h = 0; h < LEAF / 32; h++) {
             uint32_t v[32];
@@ -359,11 +365,24 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t col = (uint32_t)acc * 128u + (uint32_t)(cc * 64 + h * 32);
               tmem_ld32(tmem + ((uint32_t)(32 * slice) << 16) + col, v);
             }
+            if (!PERPASS) {
+#pragma unroll
+              for (int x = 0; x < 32; x++) sb[lane][x] = __uint_as_float(v[x]);
+              __syncwarp();
+#pragma unroll
+              for (int it = 0; it < 8; it++) {
+                const int rl = it * 4 + (lane >> 3), c4 = (lane & 7) * 4;
+                *reinterpret_cast<float4 *>(blk + (int64_t)rl * LEAF + h * 32 + c4) =
+                    make_float4(sb[rl][c4], sb[rl][c4 + 1], sb[rl][c4 + 2], sb[rl][c4 + 3]);
+              }
+              __syncwarp();
+            }
 #pragma unroll
             for (int x = 0; x < 32; x += 4) {
-              float4 f = make_float4(__uint_as_float(v[x]), __uint_as_float(v[x + 1]),
-                                     __uint_as_float(v[x + 2]), __uint_as_float(v[x + 3]));
-              *reinterpret_cast<float4 *>(dst + h * 32 + x) = f;
+              if (PERPASS)
+                *reinterpret_cast<float4 *>(dst + h * 32 + x) =
+                    make_float4(__uint_as_float(v[x]), __uint_as_float(v[x + 1]), __uint_as_float(v[x + 2]),
+                                __uint_as_float(v[x + 3]));
 #pragma unroll
               for (int z = 0; z < 4; z++) {
                 const float fv = __uint_as_float(v[x + z]);
