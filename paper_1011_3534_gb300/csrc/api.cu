@@ -537,7 +537,7 @@ spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau
   }
   launches++;
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[2], s), "event");
-  if (Ct->sym_product) {
+  if (Ct->sym_product && (!tc || split_prec(prec))) {   // the plain tensor-core forms mirror in their epilogue
     CK(launch_mirror(Ct, s), "multiply: mirror launch");
     launches++;
   }

@@ -50,6 +50,7 @@ struct __align__(64) ProdDesc {
   double *leaf_norm2C;
   unsigned long long *mma_stages;
   int32_t nb, NB;
+  int32_t sym;                             // symmetric product: blocks i < j also written as C_ji = C_ij^T
 };
 
 struct TcCommon {
@@ -355,6 +356,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           float *dst = P.C + (((int64_t)i * P.nb + j) * LEAF + r) * LEAF;
           float *blk = P.C + ((int64_t)i * P.nb + j) * LEAF * LEAF + (int64_t)(r - lane) * LEAF;
           float(*sb)[33] = s_epi[warp - 2];
+          // symmetric product, plain forms: block (j, i) = (i, j)^T from the same staged chunk
+          const bool mir = !PERPASS && P.sym && i < j;
+          float *blkT = P.C + ((int64_t)j * P.nb + i) * LEAF * LEAF + (r - lane);
 #pragma unroll
           for (int h = 0; h < LEAF / 32; h++) {
             uint32_t v[32];
@@ -374,6 +378,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int rl = it * 4 + (lane >> 3), c4 = (lane & 7) * 4;
                 *reinterpret_cast<float4 *>(blk + (int64_t)rl * LEAF + h * 32 + c4) =
                     make_float4(sb[rl][c4], sb[rl][c4 + 1], sb[rl][c4 + 2], sb[rl][c4 + 3]);
+              }
+              if (mir) {   // row h*32 + cl of block (j, i), its 32 columns r - lane ..
+#pragma unroll
+                for (int it = 0; it < 8; it++) {
+                  const int cl = it * 4 + (lane >> 3), r4 = (lane & 7) * 4;
+                  *reinterpret_cast<float4 *>(blkT + (int64_t)(h * 32 + cl) * LEAF + r4) =
+                      make_float4(sb[r4][cl], sb[r4 + 1][cl], sb[r4 + 2][cl], sb[r4 + 3][cl]);
+                }
               }
               __syncwarp();
             }
@@ -417,14 +429,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int aa = lane >> 1, c = lane & 1;
             const int ii = (int)(2 * I) + aa, jj = (int)(2 * J) + c;
             if (((touched >> (aa * 2 + c)) & 1u) && ii < P.nb && jj < P.nb) {
-              P.leaf_norm2C[(int64_t)ii * P.NB + jj] = s_norm[2 * aa][c] + s_norm[2 * aa + 1][c];
+              const double v2 = s_norm[2 * aa][c] + s_norm[2 * aa + 1][c];
+              P.leaf_norm2C[(int64_t)ii * P.NB + jj] = v2;
               P.nzC[(int64_t)ii * P.NB + jj] = 1;
+              if (!PERPASS && P.sym && ii < jj) {
+                P.leaf_norm2C[(int64_t)jj * P.NB + ii] = v2;
+                P.nzC[(int64_t)jj * P.NB + ii] = 1;
+              }
             }
           } else if (lane == 0) {
             const int jj = (int)(2 * J) + (qd & 1);
             if (((touched >> qd) & 1u) && i < P.nb && jj < P.nb) {
-              P.leaf_norm2C[(int64_t)i * P.NB + jj] = ((s_norm[0][0] + s_norm[1][0]) + s_norm[2][0]) + s_norm[3][0];
+              const double v2 = ((s_norm[0][0] + s_norm[1][0]) + s_norm[2][0]) + s_norm[3][0];
+              P.leaf_norm2C[(int64_t)i * P.NB + jj] = v2;
               P.nzC[(int64_t)i * P.NB + jj] = 1;
+              if (!PERPASS && P.sym && i < jj) {
+                P.leaf_norm2C[(int64_t)jj * P.NB + i] = v2;
+                P.nzC[(int64_t)jj * P.NB + i] = 1;
+              }
             }
           }
         }
@@ -518,6 +540,7 @@ bool fill_desc(ProdDesc *d, spamm_tree A, spamm_tree B, spamm_tree C, int prec) 
   d->mma_stages = &C->counts->mma_tiles;
   d->nb = C->nb;
   d->NB = C->NB;
+  d->sym = C->sym_product ? 1 : 0;
   return true;
 }
 
