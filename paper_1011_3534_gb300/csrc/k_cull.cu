@@ -441,6 +441,13 @@ struct TopArgs {
   DevCounts *cnt;
   double *bound_part;
   uint32_t *status;
+  // the product's prologue, done by the other CTAs of the launch: look-back words and
+  // the product's leaf norms and presence bytes zeroed
+  uint64_t *look;
+  int64_t nlook;
+  double *leaf_norm2C;
+  uint8_t *nzC;
+  int64_t nleaves;
 };
 
 // (I, J) of Morton index m: bit 2b of m is bit b of J, bit 2b + 1 is bit b of I.
@@ -455,7 +462,26 @@ __device__ __forceinline__ void morton_ij(uint32_t m, uint32_t &I, uint32_t &J) 
 }
 
 __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
+  if (blockIdx.x > 0) {   // the prologue's zeroing, spread over CTAs 1 ..
+    const int64_t t0 = (blockIdx.x - 1) * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t st = (int64_t)(gridDim.x - 1) * blockDim.x;
+    for (int64_t q = t0; q < t.nlook; q += st) t.look[q] = 0ull;
+    if (t.leaf_norm2C)
+      for (int64_t q = t0; q < t.nleaves; q += st) t.leaf_norm2C[q] = 0.0;
+    if (t.nzC)
+      for (int64_t q = t0; q < t.nleaves; q += st) t.nzC[q] = 0;
+    return;
+  }
   __shared__ double s_nA[kTopNorms], s_nB[kTopNorms];   // the tier norms, read once
+  {   // counters zeroed (no other CTA touches them); tier 0's parent list is the root group
+    uint32_t *cw = reinterpret_cast<uint32_t *>(t.cnt);
+    for (int q = threadIdx.x; q < (int)(sizeof(DevCounts) / 4); q += blockDim.x) cw[q] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      t.cnt->ngroups[0] = 1;
+      t.cnt->nentries[0] = 1;
+    }
+  }
   __shared__ uint16_t s_mask[2][kTopBlocks];            // survivors over K per block: tiers l-1, l
   __shared__ double s_wb[kTopWarps];                    // per-warp culled bounds
   __shared__ uint32_t s_wg[kTopWarps], s_we[kTopWarps];
@@ -617,10 +643,12 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
   const TierList &root = C->tiers[0];
   const int64_t nleaves = (int64_t)C->NB * C->NB;
   const int64_t work = std::max<int64_t>(nleaves, C->cap_look);
-  const unsigned pg = (unsigned)std::min<int64_t>((work + 255) / 256, 1024);
-  k_cull_prologue<<<pg, 256, 0, s>>>(root.gij, root.gstart, root.glen, root.K, cnt, C->look, C->cap_look,
-                                     C->norm2 ? C->norm2 + level_offset(C->kmax) : nullptr, C->nz, nleaves);
-  (*launches)++;
+  if (kmax < 2) {   // with k_cull_top, its other CTAs do this
+    const unsigned pg = (unsigned)std::min<int64_t>((work + 255) / 256, 1024);
+    k_cull_prologue<<<pg, 256, 0, s>>>(root.gij, root.gstart, root.glen, root.K, cnt, C->look, C->cap_look,
+                                       C->norm2 ? C->norm2 + level_offset(C->kmax) : nullptr, C->nz, nleaves);
+    (*launches)++;
+  }
   int64_t look_off = 0, bound_off = 0;
   int l0 = 0;   // first tier launched on its own
   if (kmax >= 2) {
@@ -646,7 +674,13 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
     ta.cnt = cnt;
     ta.bound_part = C->bound_part;
     ta.status = dev_status;
-    k_cull_top<<<1, kTopThreads, 0, s>>>(ta);
+    ta.look = C->look;
+    ta.nlook = C->cap_look;
+    ta.leaf_norm2C = C->norm2 ? C->norm2 + level_offset(C->kmax) : nullptr;
+    ta.nzC = C->nz;
+    ta.nleaves = nleaves;
+    const unsigned zc = (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + kTopThreads - 1) / kTopThreads, 4 * sm_count));
+    k_cull_top<<<1 + zc, kTopThreads, 0, s>>>(ta);
     (*launches)++;
     l0 = ta.T + 1;
   }

@@ -114,9 +114,16 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
                                          NormAcc &acc, float *s_tf32T, float *s_tloT, uint16_t *s_bf16T,
                                          uint16_t *s_fp16T, uint16_t *s_loT) {
   // squared norm of the round, scaled by its largest exponent field Er
-  int Er = 0;
+  int Er = 0, Emin = 0x7FF;
 #pragma unroll
-  for (int e = 0; e < 8; e++) Er = max(Er, (int)((hw[e] >> 20) & 0x7FFu));
+  for (int e = 0; e < 8; e++) {
+    const int E = (int)((hw[e] >> 20) & 0x7FFu);
+    Er = max(Er, E);
+    Emin = min(Emin, E);
+  }
+  // a round whose 8 elements are all FP32-normal (exponent fields 897..1150) within 60
+  // binades of each other needs no per-element range test in the norm or the copies
+  const bool fast = Emin >= 897 && Er <= 1150 && Er - Emin <= 60;
   if (Er > 0 && Er < 0x7FF) {
     // two independent double-float sums (even and odd elements) halve the dependency
     // chain; they are joined once per round
@@ -125,7 +132,7 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
     for (int e = 0; e < 8; e++) {
       const int E = (int)((hw[e] >> 20) & 0x7FFu);
       const int es = E - Er;
-      if (E == 0 || es < -60) continue;   // below 2^-120 of the round's largest square
+      if (!fast && (E == 0 || es < -60)) continue;   // below 2^-120 of the round's largest square
       // hi: sign-free top 24 significand bits; lo: the bits below
       const float hi = __uint_as_float(((uint32_t)(es + 127) << 23) | (((hw[e] & 0xFFFFFu) << 3) | (lw[e] >> 29)));
       // (the next 23 bits, as an exact FP32 integer: their last 6 bits' share of the
@@ -171,7 +178,7 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
         b0 = r0.bits >> 16;
         b1 = r1.bits >> 16;
       } else {
-        if (E0 >= 897 && E0 <= 1150 && E1 >= 897 && E1 <= 1150) {
+        if (fast || (E0 >= 897 && E0 <= 1150 && E1 >= 897 && E1 <= 1150)) {
           const uint32_t pk = bf16x2_fast(h0, l0, h1, l1);
           b0 = pk & 0xFFFFu;
           b1 = pk >> 16;
