@@ -162,9 +162,15 @@ SPAMM_API spamm_status spamm_tree_info(spamm_tree t, int64_t *n, int32_t *leaf, 
 /* Copy the squared Frobenius norms of tier `level` (0 = root .. kmax), a
    2^level x 2^level row-major FP64 grid, to the host buffer `out`. */
 SPAMM_API spamm_status spamm_tree_norms(spamm_tree t, int32_t level, double *out);
-/* Write the tree as a dense n x n FP64 row-major matrix to `out` (a host pointer if
-   out_is_host, else a device pointer). Product trees in TF32/BF16/FP16/BF16X3 hold
-   an FP32 C, widened to FP64 here. */
+/* Write the tree as a dense n x n FP64 row-major matrix to `out`. out_is_host: 0 =
+   `out` is a device pointer (queued on the context's stream); 1 = a host pointer,
+   written when the call returns; 2 = a host pointer, asynchronously: the call returns
+   once the copy is queued, the copy runs on the context's copy stream while later
+   calls proceed (the next step's input transfer, say), and `out` is complete after
+   spamm_sync or any other call that synchronizes the context. Product trees in the
+   tensor-core precisions hold an FP32 C, widened to FP64 here.
+   Errors: SPAMM_EINVAL (null out, out_is_host not 0/1/2, a tree without FP64/FP32
+   tiles), SPAMM_ENOMEM, SPAMM_ECUDA. */
 SPAMM_API spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host);
 
 /* ---- the product (Eq. 4) ----

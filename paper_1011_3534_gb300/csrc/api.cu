@@ -186,6 +186,10 @@ spamm_status alloc_product_workspace(spamm_ctx ctx, spamm_tree C) {
 }
 
 spamm_status check_device_status(spamm_ctx ctx) {
+  if (ctx->d2h_pending) {   // an asynchronous dense output is part of the context's work
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->d2h_done, 0), "output copy wait");
+    ctx->d2h_pending = false;
+  }
   uint32_t st = 0;
   CK(cudaMemcpyAsync(&st, ctx->dev_status, 4, cudaMemcpyDeviceToHost, ctx->stream), "status read");
   CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
@@ -196,6 +200,18 @@ spamm_status check_device_status(spamm_ctx ctx) {
     return fail(ctx, SPAMM_ECUDA, "device-side argument check failed (0x%x)", st);
   }
   return SPAMM_OK;
+}
+
+// Device address of a page-locked, mapped host array (cudaMallocHost, cudaHostAlloc,
+// cudaHostRegister), through which kernels read or write it directly over the host
+// link; nullptr for pageable memory, which goes through the staging buffer.
+void *mapped_view(const void *p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 spamm_status ensure_stage(spamm_ctx ctx, size_t bytes) {
@@ -264,6 +280,13 @@ spamm_status spamm_ctx_destroy(spamm_ctx ctx) {
     if (ctx->side_ev[i]) cudaEventDestroy(ctx->side_ev[i]);
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->d2h) {
+    cudaStreamSynchronize(ctx->d2h);
+    cudaStreamDestroy(ctx->d2h);
+  }
+  if (ctx->d2h_staged) cudaEventDestroy(ctx->d2h_staged);
+  if (ctx->d2h_done) cudaEventDestroy(ctx->d2h_done);
+  if (ctx->stage_out) cudaFree(ctx->stage_out);
   if (ctx->batch_copied) cudaEventDestroy(ctx->batch_copied);
   if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
   if (ctx->batch_dev) cudaFree(ctx->batch_dev);
@@ -312,7 +335,10 @@ spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t
   spamm_status st = alloc_tree(ctx, n, leaf, flags, &t);
   if (st != SPAMM_OK) return st;
   const double *src = A;
-  if (flags & SPAMM_HOST_INPUT) {
+  const double *mapped = (flags & SPAMM_HOST_INPUT) ? (const double *)mapped_view(A) : nullptr;
+  if (mapped) {
+    src = mapped;
+  } else if (flags & SPAMM_HOST_INPUT) {
     st = ensure_stage(ctx, (size_t)n * n * sizeof(double));
     if (st != SPAMM_OK) {
       free_tree_memory(t);
@@ -348,7 +374,10 @@ spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags) {
   if (t->is_product) return fail(ctx, SPAMM_EINVAL, "tree_update: product trees cannot be rebuilt");
   if (flags & ~SPAMM_HOST_INPUT) return fail(ctx, SPAMM_EINVAL, "tree_update: only SPAMM_HOST_INPUT is accepted");
   const double *src = A;
-  if (flags & SPAMM_HOST_INPUT) {
+  const double *mapped = (flags & SPAMM_HOST_INPUT) ? (const double *)mapped_view(A) : nullptr;
+  if (mapped) {
+    src = mapped;
+  } else if (flags & SPAMM_HOST_INPUT) {
     spamm_status st = ensure_stage(ctx, (size_t)t->n * t->n * sizeof(double));
     if (st != SPAMM_OK) return st;
     CK(cudaMemcpyAsync(ctx->stage, A, (size_t)t->n * t->n * sizeof(double), cudaMemcpyHostToDevice,
@@ -415,19 +444,39 @@ spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host)
   if (!out) return fail(ctx, SPAMM_EINVAL, "tree_to_dense: null output");
   if (!t->copy[CK_F64] && !t->copy[CK_F32])
     return fail(ctx, SPAMM_EINVAL, "tree_to_dense: the tree keeps no FP64/FP32 tiles (SPAMM_KEEP_FP64)");
+  if (out_is_host < 0 || out_is_host > 2) return fail(ctx, SPAMM_EINVAL, "tree_to_dense: out_is_host must be 0, 1 or 2");
   const size_t bytes = (size_t)t->n * t->n * sizeof(double);
-  double *dst = out;
-  if (out_is_host) {
-    spamm_status st = ensure_stage(ctx, bytes);
-    if (st != SPAMM_OK) return st;
-    dst = (double *)ctx->stage;
+  if (!out_is_host) {
+    CK(launch_to_dense(t, out, ctx->stream), "tree_to_dense: launch");
+    ctx->launches++;
+    return SPAMM_OK;
   }
-  CK(launch_to_dense(t, dst, ctx->stream), "tree_to_dense: launch");
+  // host output: dense image into the output staging buffer on the context's stream,
+  // then the copy on the copy stream (the staging buffer is reused only after the
+  // previous copy out of it finished)
+  if (!ctx->d2h) {
+    CK(cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking), "tree_to_dense: copy stream");
+    CK(cudaEventCreateWithFlags(&ctx->d2h_staged, cudaEventDisableTiming), "tree_to_dense: event");
+    CK(cudaEventCreateWithFlags(&ctx->d2h_done, cudaEventDisableTiming), "tree_to_dense: event");
+  }
+  if (ctx->stage_out_bytes < bytes) {
+    CK(cudaStreamSynchronize(ctx->d2h), "tree_to_dense: copy stream");
+    CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    if (ctx->stage_out) cudaFree(ctx->stage_out);
+    ctx->stage_out = nullptr;
+    ctx->stage_out_bytes = 0;
+    CK(cudaMalloc(&ctx->stage_out, bytes), "tree_to_dense: staging buffer");
+    ctx->stage_out_bytes = bytes;
+  }
+  if (ctx->d2h_pending) CK(cudaStreamWaitEvent(ctx->stream, ctx->d2h_done, 0), "tree_to_dense: wait");
+  CK(launch_to_dense(t, (double *)ctx->stage_out, ctx->stream), "tree_to_dense: launch");
   ctx->launches++;
-  if (out_is_host) {
-    CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream), "tree_to_dense: copy");
-    return check_device_status(ctx);
-  }
+  CK(cudaEventRecord(ctx->d2h_staged, ctx->stream), "tree_to_dense: event");
+  CK(cudaStreamWaitEvent(ctx->d2h, ctx->d2h_staged, 0), "tree_to_dense: wait");
+  CK(cudaMemcpyAsync(out, ctx->stage_out, bytes, cudaMemcpyDeviceToHost, ctx->d2h), "tree_to_dense: copy");
+  CK(cudaEventRecord(ctx->d2h_done, ctx->d2h), "tree_to_dense: event");
+  ctx->d2h_pending = true;
+  if (out_is_host == 1) return check_device_status(ctx);
   return SPAMM_OK;
 }
 

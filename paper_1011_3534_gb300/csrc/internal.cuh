@@ -68,6 +68,13 @@ struct spamm_ctx_s {
   cudaStream_t side[kSideStreams] = {};
   cudaEvent_t side_ev[kSideStreams] = {};
   cudaEvent_t fork_ev = nullptr;
+  // dense host output: a staging buffer and a copy stream, so that the device-to-host
+  // copy of one result overlaps the context's later work
+  void *stage_out = nullptr;
+  size_t stage_out_bytes = 0;
+  cudaStream_t d2h = nullptr;
+  cudaEvent_t d2h_staged = nullptr, d2h_done = nullptr;
+  bool d2h_pending = false;
   void *batch_host = nullptr, *batch_dev = nullptr;   // descriptor tables (pinned / device)
   cudaEvent_t batch_copied = nullptr;   // the last copy out of batch_host has run
   size_t batch_cap = 0;

@@ -450,17 +450,34 @@ __global__ void __launch_bounds__(1024) k_pyramid_top(double *norm2, double *nor
   }
 }
 
+// Dense row-major FP64 image of a tree's master tiles. A thread writes four
+// consecutive columns of one row (they lie in one leaf: b is a multiple of 4), rows
+// are spread over grid.y; 16-byte stores when the output rows are 16-byte aligned. The
+// output may be device memory or mapped page-locked host memory.
 template <typename T>
-__global__ void k_to_dense(const T *tiles, const uint8_t *nz, int64_t n, int32_t b, int32_t nb,
-                           int32_t NB, double *out) {
-  const int64_t total = n * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = e / n, col = e % n;
-    const int64_t r = row / b, c = col / b;
-    double v = 0.0;
-    if (nz[r * NB + c]) v = (double)tiles[((r * nb + c) * b + (row % b)) * b + (col % b)];
-    out[e] = v;
+__global__ void __launch_bounds__(256) k_to_dense(const T *tiles, const uint8_t *nz, int64_t n, int32_t lb,
+                                                  int32_t nb, int32_t NB, double *out, int vec) {
+  const int32_t b = 1 << lb;
+  const int64_t groups = (n + 3) / 4;   // four-column groups per row
+  for (int64_t row = blockIdx.y; row < n; row += gridDim.y) {
+    const int64_t r = row >> lb, rr = row & (b - 1);
+    double *orow = out + row * n;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t col = 4 * g, c = col >> lb, cc = col & (b - 1);
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+      if (nz[r * NB + c]) {
+        const T *src = tiles + ((r * nb + c) * b + rr) * b + cc;
+#pragma unroll
+        for (int q = 0; q < 4; q++) v[q] = (double)src[q];   // col + q < b: same leaf, stored
+      }
+      if (vec && col + 3 < n) {
+        reinterpret_cast<double2 *>(orow + col)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(orow + col)[1] = make_double2(v[2], v[3]);
+      } else {
+        for (int q = 0; q < 4 && col + q < n; q++) orow[col + q] = v[q];
+      }
+    }
   }
 }
 
@@ -658,14 +675,18 @@ cudaError_t launch_mirror(spamm_tree C, cudaStream_t s) {
 }
 
 cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s) {
-  const int64_t total = t->n * t->n;
-  const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 64);
+  int lb = 0;
+  while ((1 << lb) < t->b) lb++;
+  const int64_t groups = (t->n + 3) / 4;
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((groups + 255) / 256, 8)),
+                  (unsigned)std::min<int64_t>(t->n, 8192));
+  const int vec = (t->n % 2) == 0 && ((uintptr_t)out % 16) == 0;
   if (t->copy[CK_F64]) {
-    k_to_dense<double><<<grid, 256, 0, s>>>((const double *)t->copy[CK_F64], t->nz, t->n, t->b,
-                                            t->nb, t->NB, out);
+    k_to_dense<double><<<grid, 256, 0, s>>>((const double *)t->copy[CK_F64], t->nz, t->n, lb, t->nb, t->NB,
+                                            out, vec);
   } else if (t->copy[CK_F32]) {
-    k_to_dense<float><<<grid, 256, 0, s>>>((const float *)t->copy[CK_F32], t->nz, t->n, t->b,
-                                           t->nb, t->NB, out);
+    k_to_dense<float><<<grid, 256, 0, s>>>((const float *)t->copy[CK_F32], t->nz, t->n, lb, t->nb, t->NB,
+                                           out, vec);
   } else {
     return cudaErrorInvalidValue;
   }

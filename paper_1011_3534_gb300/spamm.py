@@ -237,12 +237,14 @@ def spamm_tree_norms(t: Tree, level: int) -> np.ndarray:
     return out
 
 
-def spamm_tree_to_dense(t: Tree, out=None):
-    """Dense n x n FP64 copy: into `out` (numpy host or torch device), or a new numpy array."""
+def spamm_tree_to_dense(t: Tree, out=None, asynchronous: bool = False):
+    """Dense n x n FP64 copy: into `out` (numpy host or torch device), or a new numpy array.
+    asynchronous (host output only): return once queued; `out` is complete after spamm_sync."""
     if out is None:
         out = np.empty((t.n, t.n), dtype=np.float64)
     host = isinstance(out, np.ndarray) or (hasattr(out, "is_cuda") and not out.is_cuda)
-    t.ctx.check(LIB.spamm_tree_to_dense(t.h, _ptr(out), 1 if host else 0), "spamm_tree_to_dense")
+    mode = (2 if asynchronous else 1) if host else 0
+    t.ctx.check(LIB.spamm_tree_to_dense(t.h, _ptr(out), mode), "spamm_tree_to_dense")
     return out
 
 

@@ -223,3 +223,36 @@ def test_fp64_symmetric_product(S, ctx, n, leaf, tau, kind):
     Cref = oracle.spamm(TA, TA, tau, threads=oracle.max_threads())["C"]
     Cref = adjust_for_band(Cref, A, A, leaf, TA.NB, only_g, only_o)
     assert rel_fro(C, Cref) <= 1e-12
+
+
+def test_page_locked_host_buffers(S, ctx):
+    """Host input in page-locked memory is read by the kernels directly over the host
+    link, pageable input goes through the staging buffer; dense output is written
+    synchronously or asynchronously (complete after spamm_sync). All give the same
+    tree, product and dense output, bit for bit, for a ragged order and both precision
+    classes."""
+    n = 1000
+    A = W.algebraic_decay(n, 2, 3)
+    A_pin = torch.from_numpy(A).pin_memory()
+    for prec, leaf, fl in ((S.SPAMM_FP64, 32, S.SPAMM_KEEP_FP64),
+                           (S.SPAMM_BF16, 64, S.COPY_FLAG[S.SPAMM_BF16] | S.SPAMM_SYMMETRIC)):
+        outs = []
+        for src in (A, A_pin.numpy()):
+            t = S.spamm_tree_build(ctx, src, n, leaf, fl)
+            S.spamm_tree_update(t, src)
+            c = S.spamm_multiply(ctx, t, t, 1e-9, prec)
+            dense_pageable = S.spamm_tree_to_dense(c)
+            C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
+            S.spamm_tree_to_dense(c, C_pin.numpy())
+            # asynchronous output, overlapped with a rebuild of the input, complete after sync
+            C_async = torch.full((n, n), np.nan, dtype=torch.float64).pin_memory()
+            S.spamm_tree_to_dense(c, C_async.numpy(), asynchronous=True)
+            S.spamm_tree_update(t, src)
+            S.spamm_sync(ctx)
+            assert np.array_equal(C_async.numpy(), C_pin.numpy())
+            outs.append((S.spamm_tree_norms(t, t.kmax), dense_pageable, C_pin.numpy().copy()))
+            S.spamm_tree_free(c)
+            S.spamm_tree_free(t)
+        (n0, d0, p0), (n1, d1, p1) = outs
+        assert np.array_equal(n0, n1)
+        assert np.array_equal(d0, d1) and np.array_equal(d0, p0) and np.array_equal(d0, p1)
