@@ -73,7 +73,9 @@ typedef enum {
 #define SPAMM_HOST_INPUT   0x0001  /* spamm_tree_build: A is a host pointer (else device) */
 #define SPAMM_SYMMETRIC    0x0002  /* caller asserts A == A^T: one low-precision copy then
                                       serves both operand roles (leaf (k,j) of A^T is
-                                      leaf (j,k) of A, transposed) */
+                                      leaf (j,k) of A, transposed), and the cull reads
+                                      the tree's norms on and above the diagonal only,
+                                      so ||A_ki|| and ||A_ik|| are the same number */
 #define SPAMM_KEEP_FP64    0x0004  /* keep FP64 leaf tiles (needed by SPAMM_FP64 products) */
 #define SPAMM_COPY_TF32    0x0010  /* write TF32 leaf copies */
 #define SPAMM_COPY_BF16    0x0020  /* write BF16 leaf copies */
@@ -87,10 +89,10 @@ typedef enum {
 #define SPAMM_SYM_PRODUCT  0x0800  /* spamm_multiply of a symmetric tree by itself (B == A,
                                       built with SPAMM_SYMMETRIC): C = A A is symmetric, so
                                       only the output blocks i <= j are culled and
-                                      multiplied, and C_ji is written as C_ij^T. The norm
-                                      trees of symmetric trees are kept transpose-consistent
-                                      (||A_ki|| = ||A_ik|| bit for bit), so the surviving
-                                      triples are the mirror images of each other */
+                                      multiplied, and C_ji is written as C_ij^T. As the
+                                      cull reads a symmetric tree's norms on and above the
+                                      diagonal, the surviving triples of (i, j) and (j, i)
+                                      are the mirror images of each other */
 
 #define SPAMM_MAX_LEVELS 24
 

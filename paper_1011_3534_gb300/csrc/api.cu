@@ -356,8 +356,7 @@ spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t
   }
   cudaError_t e = timed_tree_build(t, src, ctx->stream);
   if (e == cudaSuccess) e = launch_pyramid(t, ctx->stream);
-  if (e == cudaSuccess && (flags & SPAMM_SYMMETRIC)) e = launch_sym_norms(t, ctx->stream);
-  ctx->launches += 1 + pyramid_launches(t->kmax) + ((t->flags & SPAMM_SYMMETRIC) ? 1 : 0);
+  ctx->launches += 1 + pyramid_launches(t->kmax);
   if (e != cudaSuccess) {
     free_tree_memory(t);
     delete t;
@@ -386,8 +385,7 @@ spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags) {
   }
   CK(timed_tree_build(t, src, ctx->stream), "tree_update: launch");
   CK(launch_pyramid(t, ctx->stream), "tree_update: launch");
-  if (t->flags & SPAMM_SYMMETRIC) CK(launch_sym_norms(t, ctx->stream), "tree_update: launch");
-  ctx->launches += 1 + pyramid_launches(t->kmax) + ((t->flags & SPAMM_SYMMETRIC) ? 1 : 0);
+  ctx->launches += 1 + pyramid_launches(t->kmax);
   return SPAMM_OK;
 }
 
@@ -592,10 +590,6 @@ spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau
   }
   CK(launch_pyramid(Ct, s), "multiply: pyramid launch");
   launches += pyramid_launches(Ct->kmax);
-  if (Ct->flags & SPAMM_SYMMETRIC) {
-    CK(launch_sym_norms(Ct, s), "multiply: norm symmetrisation");
-    launches++;
-  }
   bool want[CK_COUNT];
   wanted_copies(cflags & kTreeFlags, want);
   bool any_copy = false;
@@ -821,12 +815,11 @@ extern "C" spamm_status spamm_sp2_begin(spamm_ctx ctx, int64_t n, const int64_t 
   SP2CK(sp2_x0(n, r->d_ip, r->d_ix, r->d_v, emin, emax, (double *)ctx->stage, s), "sp2: X0");
   SP2CK(launch_tree_build(r->X, (const double *)ctx->stage, s), "sp2: X0 tree");
   SP2CK(launch_pyramid(r->X, s), "sp2: X0 pyramid");
-  SP2CK(launch_sym_norms(r->X, s), "sp2: X0 norms");
   SP2CK(cudaEventCreate(&r->e0), "sp2: event");
   SP2CK(cudaEventCreate(&r->e1), "sp2: event");
   SP2CK(cudaEventRecord(r->e0, s), "sp2: event");
 #undef SP2CK
-  ctx->launches += 3 + pyramid_launches(r->X->kmax);
+  ctx->launches += 2 + pyramid_launches(r->X->kmax);
   *out = r;
   return SPAMM_OK;
 }

@@ -177,7 +177,6 @@ __host__ __device__ inline int64_t level_offset(int l) { return ((int64_t(1) << 
 // ---- launchers (each returns a cudaError_t from the launch) ----
 cudaError_t launch_tree_build(spamm_tree t, const double *A, cudaStream_t s);
 cudaError_t launch_pyramid(spamm_tree t, cudaStream_t s);
-cudaError_t launch_sym_norms(spamm_tree t, cudaStream_t s);    // lower triangles := upper, every tier
 cudaError_t launch_mirror(spamm_tree C, cudaStream_t s);       // C_ji := C_ij^T for i < j
 cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s);
 cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, const double *tau_dev,

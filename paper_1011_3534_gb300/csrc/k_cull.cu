@@ -79,8 +79,16 @@ __device__ void tile_lookback(uint64_t *look, unsigned int tile, uint64_t agg_e,
   if (lane == 0) st_release_u64(look + tile, pack(kFlagPrefix, ex_g + agg_g, ex_e + agg_e));
 }
 
+// Entry (r, c) of a 2^l x 2^l tier grid; a symmetric tree is read on and above the
+// diagonal only, so ||A_rc|| and ||A_cr|| are the same number (the entries below it sum
+// the same squares in another order and may differ in the last bit).
+__device__ __forceinline__ int64_t tier_at(uint32_t r, uint32_t c, int32_t D, int32_t sym) {
+  return sym && r > c ? (int64_t)c * D + r : (int64_t)r * D + c;
+}
+
 struct CullArgs {
   const double *nA, *nB;    // norms (not squared) of tier l, 2^l x 2^l
+  int32_t symA, symB;       // operand trees of symmetric matrices
   int32_t l, D, nb, NB, final_tier;
   int32_t sym;              // symmetric product: output blocks below the diagonal are skipped
   double tau;
@@ -149,13 +157,13 @@ __device__ __forceinline__ uint32_t child_bits(const CullArgs &a, double tau, ui
     for (int ai = 0; ai < 2; ai++) {
       const uint32_t i = 2 * I + ai;
       if (i >= (uint32_t)a.D) continue;
-      const double na = a.nA[(int64_t)i * a.D + k];
+      const double na = a.nA[tier_at(i, k, a.D, a.symA)];
 #pragma unroll
       for (int c = 0; c < 2; c++) {
         const uint32_t j = 2 * J + c;
         if (j >= (uint32_t)a.D) continue;
         if (a.sym && i > j) continue;   // below the diagonal: the mirror of (j, i)
-        const double p = na * a.nB[(int64_t)k * a.D + j];
+        const double p = na * a.nB[tier_at(k, j, a.D, a.symB)];
         tests++;
         if (below_tau(p, tau)) bound += p;
         else bits |= 1u << (((ai * 2 + c) * 2) + e);
@@ -433,6 +441,7 @@ struct TopArgs {
   int64_t bound_off[kTopTiers];                  // this tier's block of bound_part
   int32_t T;                                     // last tier run here
   int32_t sym;                                   // symmetric product
+  int32_t symA, symB;                            // operand trees of symmetric matrices
   double tau;
   const double *tau_dev;
   uint32_t *gij, *gstart, *glen;                 // the tier-T list (C->tiers[T + 1])
@@ -517,7 +526,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
       for (uint32_t K = 0; K < (1u << (kTopTiers - 1)); K++) {
         if (K >= D) break;
         if (!((pm >> (K >> 1)) & 1u)) continue;          // parent culled: not a call
-        const double p = nA[I * D + K] * nB[K * D + J];
+        const double p = nA[tier_at(I, K, D, t.symA)] * nB[tier_at(K, J, D, t.symB)];
         tests++;
         if (below_tau(p, tau)) bound += p;
         else mask |= 1u << K;
@@ -664,6 +673,8 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
     ta.tau = tau;
     ta.tau_dev = tau_dev;
     ta.sym = C->sym_product ? 1 : 0;
+    ta.symA = (A->flags & SPAMM_SYMMETRIC) ? 1 : 0;
+    ta.symB = (B->flags & SPAMM_SYMMETRIC) ? 1 : 0;
     const TierList &out = C->tiers[ta.T + 1];
     ta.gij = out.gij;
     ta.gstart = out.gstart;
@@ -694,6 +705,8 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
     a.NB = A->NB;
     a.final_tier = (l == kmax);
     a.sym = C->sym_product ? 1 : 0;
+    a.symA = (A->flags & SPAMM_SYMMETRIC) ? 1 : 0;
+    a.symB = (B->flags & SPAMM_SYMMETRIC) ? 1 : 0;
     a.tau = tau;
     a.tau_dev = tau_dev;
     const TierList &par = C->tiers[l];

@@ -570,32 +570,6 @@ cudaError_t launch_pyramid(spamm_tree t, cudaStream_t s) {
 // kernels launch_pyramid issues for a tree of this depth
 int pyramid_launches(int kmax) { return 1 + (kmax - kPyrL - 1 >= 0 ? 1 : 0); }
 
-// Transpose-consistent norm tree of a symmetric matrix: on every tier, the entries below
-// the diagonal are copies of their mirror images above it. The leaf norms of A_ik and
-// A_ki are sums of the same squares in different orders, so they may differ in the last
-// bit; copying makes every cull decision of (i, j, k) and (j, i, k) the same. A parent
-// stays at least as large as each child (it sums the upper children, whose copies the
-// lower children are), so the hierarchical cull still equals the flat leaf test.
-__global__ void __launch_bounds__(256) k_sym_norms(double *norm2, double *norm, int32_t kmax) {
-  const int64_t total = level_offset(kmax + 1);
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    int l = 0;
-    while (level_offset(l + 1) <= t) l++;
-    const int64_t D = int64_t(1) << l, loc = t - level_offset(l), i = loc / D, k = loc % D;
-    if (i > k) {
-      const int64_t src = level_offset(l) + k * D + i;
-      norm2[t] = norm2[src];
-      norm[t] = norm[src];
-    }
-  }
-}
-
-cudaError_t launch_sym_norms(spamm_tree t, cudaStream_t s) {
-  const int64_t total = level_offset(t->kmax + 1);
-  const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 1024);
-  k_sym_norms<<<grid, 256, 0, s>>>(t->norm2, t->norm, t->kmax);
-  return cudaGetLastError();
-}
 
 // C_ji := C_ij^T for every stored block i < j of a symmetric product (master tiles,
 // squared leaf norm, presence byte). Work item w is sub-tile w % S (E x E elements,

@@ -272,9 +272,7 @@ cudaError_t sp2_step_finish(spamm_tree X, spamm_tree C, double n_occ, int step, 
   else k_sp2_update<float><<<grid, 256, 0, s>>>(u);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_pyramid(C, s);
-  if (e != cudaSuccess) return e;
-  return launch_sym_norms(C, s);   // the iterate is symmetric: transpose-consistent norms
+  return launch_pyramid(C, s);   // the iterate is symmetric: the cull reads its upper triangle
 }
 
 cudaError_t sp2_trace_only(spamm_tree X, int idx, void *rec_v, cudaStream_t s) {
