@@ -85,6 +85,7 @@ void free_tree_memory(spamm_tree t) {
   dfree(t->norm2);
   dfree(t->norm);
   dfree(t->nz);
+  dfree(t->pyr_ctr);
   for (int k = 0; k < CK_COUNT; k++) dfree(t->copy[k]);
   for (int l = 0; l <= SPAMM_MAX_LEVELS; l++) {
     dfree(t->tiers[l].gij);
@@ -122,6 +123,8 @@ spamm_status alloc_tree(spamm_ctx ctx, int64_t n, int32_t b, int32_t flags, spam
   cudaError_t e = dmalloc(&t->norm2, levels * sizeof(double));
   if (e == cudaSuccess) e = dmalloc(&t->norm, levels * sizeof(double));
   if (e == cudaSuccess) e = dmalloc(&t->nz, (size_t)t->NB * t->NB);
+  if (e == cudaSuccess) e = dmalloc(&t->pyr_ctr, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->pyr_ctr, 0, sizeof(unsigned int), ctx->stream);
   bool want[CK_COUNT];
   wanted_copies(flags, want);
   const size_t elems = (size_t)t->nb * t->nb * (size_t)b * b;
@@ -356,7 +359,7 @@ spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t
   }
   cudaError_t e = timed_tree_build(t, src, ctx->stream);
   if (e == cudaSuccess) e = launch_pyramid(t, ctx->stream);
-  ctx->launches += 1 + pyramid_launches(t->kmax);
+  ctx->launches += 1 + pyramid_launches(t);
   if (e != cudaSuccess) {
     free_tree_memory(t);
     delete t;
@@ -385,7 +388,7 @@ spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags) {
   }
   CK(timed_tree_build(t, src, ctx->stream), "tree_update: launch");
   CK(launch_pyramid(t, ctx->stream), "tree_update: launch");
-  ctx->launches += 1 + pyramid_launches(t->kmax);
+  ctx->launches += 1 + pyramid_launches(t);
   return SPAMM_OK;
 }
 
@@ -589,7 +592,7 @@ spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau
     launches++;
   }
   CK(launch_pyramid(Ct, s), "multiply: pyramid launch");
-  launches += pyramid_launches(Ct->kmax);
+  launches += pyramid_launches(Ct);
   bool want[CK_COUNT];
   wanted_copies(cflags & kTreeFlags, want);
   bool any_copy = false;
@@ -819,7 +822,7 @@ extern "C" spamm_status spamm_sp2_begin(spamm_ctx ctx, int64_t n, const int64_t 
   SP2CK(cudaEventCreate(&r->e1), "sp2: event");
   SP2CK(cudaEventRecord(r->e0, s), "sp2: event");
 #undef SP2CK
-  ctx->launches += 2 + pyramid_launches(r->X->kmax);
+  ctx->launches += 2 + pyramid_launches(r->X);
   *out = r;
   return SPAMM_OK;
 }
@@ -836,7 +839,7 @@ spamm_status sp2_advance(spamm_sp2_run r, double tau, bool from_record) {
                                   &out_tree);
   if (st != SPAMM_OK) return st;
   CK(sp2_step_finish(r->X, r->C, r->n_occ, step, r->d_rec, ctx->stream), "sp2: step");
-  ctx->launches += 4 + pyramid_launches(r->C->kmax);
+  ctx->launches += 4 + pyramid_launches(r->C);
   r->tau_host[step] = tau;
   r->learned[step] = from_record;
   std::swap(r->X, r->C);

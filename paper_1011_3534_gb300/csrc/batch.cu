@@ -135,7 +135,7 @@ static spamm_status batch_sequence(spamm_ctx ctx, const spamm_tree *A, const spa
   if (st != SPAMM_OK) return st;
   for (int p = 0; p < count; p++) {
     BCK(launch_pyramid(C[p], ctx->side[p % used]), "batch: pyramid");
-    ctx->launches += pyramid_launches(C[p]->kmax);
+    ctx->launches += pyramid_launches(C[p]);
   }
   return join(ctx, used);
 }

@@ -140,6 +140,7 @@ struct spamm_tree_s {
   double *norm2 = nullptr;   // every tier: tier l at offset (4^l - 1) / 3, 2^l x 2^l
   double *norm = nullptr;    // sqrt of norm2, same layout
   uint8_t *nz = nullptr;     // NB x NB: 1 if tile storage holds leaf (i, j)
+  unsigned int *pyr_ctr = nullptr;   // arrivals of the norm pyramid's region CTAs (0 between launches)
   void *copy[CK_COUNT] = {};
   // product trees
   bool is_product = false;
@@ -189,7 +190,7 @@ cudaError_t launch_finish_stats(spamm_tree C, cudaStream_t s);
 cudaError_t launch_tile_convert(spamm_tree t, cudaStream_t s);
 int64_t cull_look_words(int kmax);
 int64_t cull_bound_words(int kmax, int64_t *offsets);
-int pyramid_launches(int kmax);
+int pyramid_launches(spamm_tree t);
 cudaError_t sp2_x0(int64_t n, const int64_t *indptr, const int64_t *indices, const double *data, double emin,
                    double emax, double *X, cudaStream_t s);
 size_t sp2_record_bytes();

@@ -393,8 +393,30 @@ __global__ void __launch_bounds__(BuildCfg<B>::T, 1024 / BuildCfg<B>::T) k_tree_
 constexpr int kPyrR = 16;   // region side (leaves)
 constexpr int kPyrL = 4;    // tiers built per region: log2(kPyrR)
 
-__global__ void __launch_bounds__(256) k_pyramid_region(double *norm2, double *norm, int32_t kmax) {
+// Tiers top .. 0 from tier top + 1 (used by the last region CTA and by k_pyramid_top).
+__device__ __forceinline__ void pyramid_top_tiers(double *norm2, double *norm, int32_t top_tier) {
+  for (int l = top_tier; l >= 0; l--) {
+    const int64_t d = int64_t(1) << l, dc = 2 * d;
+    const double *c2 = norm2 + level_offset(l + 1);
+    double *p2 = norm2 + level_offset(l);
+    double *p1 = norm + level_offset(l);
+    for (int64_t t = threadIdx.x; t < d * d; t += blockDim.x) {
+      const int64_t I = t / d, K = t % d;
+      const int64_t i11 = (2 * I) * dc + 2 * K, i21 = (2 * I + 1) * dc + 2 * K;
+      const double s = ((__ldcg(c2 + i11) + __ldcg(c2 + i11 + 1)) + __ldcg(c2 + i21)) + __ldcg(c2 + i21 + 1);
+      p2[t] = s;
+      p1[t] = sqrt(s);
+    }
+    __syncthreads();
+  }
+}
+
+// With `ctr` set, the region CTA that arrives last also builds the tiers above the
+// regions (top_tier .. 0) and resets the counter for the next launch.
+__global__ void __launch_bounds__(256) k_pyramid_region(double *norm2, double *norm, int32_t kmax,
+                                                        unsigned int *ctr, int32_t top_tier) {
   __shared__ double s0[kPyrR * kPyrR], s1[kPyrR * kPyrR / 4];
+  __shared__ bool s_last;
   const int R = min(kPyrR, 1 << kmax);          // region side for small trees
   const int levels = min(kPyrL, kmax);
   const int64_t NB = int64_t(1) << kmax;
@@ -430,24 +452,20 @@ __global__ void __launch_bounds__(256) k_pyramid_region(double *norm2, double *n
     nxt = tmp;
     d = dp;
   }
+  if (!ctr) return;
+  __threadfence();   // this CTA's tiers are visible before it is counted
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  pyramid_top_tiers(norm2, norm, top_tier);
+  if (threadIdx.x == 0) *ctr = 0u;
 }
 
-// Tiers kmax - 5 .. 0 (above the regions) in one CTA.
+// Tiers kmax - 5 .. 0 (above the regions) in one CTA, for trees without a counter.
 __global__ void __launch_bounds__(1024) k_pyramid_top(double *norm2, double *norm, int32_t top_tier) {
-  for (int l = top_tier; l >= 0; l--) {
-    const int64_t d = int64_t(1) << l, dc = 2 * d;
-    const double *c2 = norm2 + level_offset(l + 1);
-    double *p2 = norm2 + level_offset(l);
-    double *p1 = norm + level_offset(l);
-    for (int64_t t = threadIdx.x; t < d * d; t += blockDim.x) {
-      const int64_t I = t / d, K = t % d;
-      const int64_t i11 = (2 * I) * dc + 2 * K, i21 = (2 * I + 1) * dc + 2 * K;
-      const double s = ((c2[i11] + c2[i11 + 1]) + c2[i21]) + c2[i21 + 1];
-      p2[t] = s;
-      p1[t] = sqrt(s);
-    }
-    __syncthreads();
-  }
+  pyramid_top_tiers(norm2, norm, top_tier);
 }
 
 // Dense row-major FP64 image of a tree's master tiles. A thread writes four
@@ -561,14 +579,15 @@ cudaError_t launch_tree_build(spamm_tree t, const double *A, cudaStream_t s) {
 cudaError_t launch_pyramid(spamm_tree t, cudaStream_t s) {
   const int R = std::min(kPyrR, 1 << t->kmax);
   const int64_t per_side = (int64_t(1) << t->kmax) / R;
-  k_pyramid_region<<<(unsigned)(per_side * per_side), 256, 0, s>>>(t->norm2, t->norm, t->kmax);
   const int top = t->kmax - kPyrL - 1;
-  if (top >= 0) k_pyramid_top<<<1, 1024, 0, s>>>(t->norm2, t->norm, top);
+  unsigned int *ctr = top >= 0 ? t->pyr_ctr : nullptr;
+  k_pyramid_region<<<(unsigned)(per_side * per_side), 256, 0, s>>>(t->norm2, t->norm, t->kmax, ctr, top);
+  if (top >= 0 && !ctr) k_pyramid_top<<<1, 1024, 0, s>>>(t->norm2, t->norm, top);
   return cudaGetLastError();
 }
 
-// kernels launch_pyramid issues for a tree of this depth
-int pyramid_launches(int kmax) { return 1 + (kmax - kPyrL - 1 >= 0 ? 1 : 0); }
+// kernels launch_pyramid issues for this tree
+int pyramid_launches(spamm_tree t) { return 1 + (t->kmax - kPyrL - 1 >= 0 && !t->pyr_ctr ? 1 : 0); }
 
 
 // C_ji := C_ij^T for every stored block i < j of a symmetric product (master tiles,
