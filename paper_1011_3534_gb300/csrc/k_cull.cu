@@ -275,9 +275,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
   __shared__ unsigned int s_cnt[kWarps * 4];
   __shared__ unsigned int s_off[kWarps * 4];
   __shared__ unsigned int s_gix[kWarps * 4];
+  // the CTA's counter sums (tested, culled, leaf products, output blocks, mirrored
+  // products), added to the product's counters once at the end
+  __shared__ unsigned long long s_acc[5];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long ngroups = *a.p_ngroups;
   const double tau = a.tau_dev ? *a.tau_dev : a.tau;
+  if (threadIdx.x < 5) s_acc[threadIdx.x] = 0ull;
+  __syncthreads();
 
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
@@ -304,6 +309,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
     uint32_t touched = 0;
     int tests = 0;
     double bound = 0.0;
+    uint32_t keep0 = 0, keep1 = 0, keep2 = 0, keep3 = 0;   // survival bits of the first 128 entries
     for (uint32_t p0 = 0; p0 < len; p0 += 32) {
       const uint32_t p = p0 + lane;
       uint32_t bits = 0;
@@ -312,6 +318,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
         bits = child_bits(a, tau, I, J, K, tests, bound);
         if (a.final_tier) a.mask[start + p] = (uint8_t)bits;
       }
+      const uint32_t it = p0 >> 5;
+      if (it == 0) keep0 = bits;
+      else if (it == 1) keep1 = bits;
+      else if (it == 2) keep2 = bits;
+      else if (it == 3) keep3 = bits;
 #pragma unroll
       for (int q = 0; q < 4; q++) {
         cnt[q] += __popc((bits >> (2 * q)) & 3u);
@@ -331,19 +342,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
     bound = warp_sum(bound);
     if (has && lane == 0) {
       const unsigned int surv = cnt[0] + cnt[1] + cnt[2] + cnt[3];
-      atomicAdd(a.tested, (unsigned long long)tests);
-      atomicAdd(a.culled, (unsigned long long)(tests - (int)surv));
+      atomicAdd(&s_acc[0], (unsigned long long)tests);
+      atomicAdd(&s_acc[1], (unsigned long long)(tests - (int)surv));
       a.bound_part[g] = bound;
       if (a.final_tier) {
-        atomicAdd(a.leaf_products, (unsigned long long)surv);
+        atomicAdd(&s_acc[2], (unsigned long long)surv);
         unsigned int blocks = 0, mir = 0;
         for (int q = 0; q < 4; q++) {
           const uint32_t bi = 2 * I + (q >> 1), bj = 2 * J + (q & 1);
           if (cnt[q] && bi < (uint32_t)a.nb && bj < (uint32_t)a.nb) blocks += (a.sym && bi < bj) ? 2 : 1;
           if (a.sym && bi < bj) mir += cnt[q];
         }
-        if (blocks) atomicAdd(a.output_blocks, (unsigned long long)blocks);
-        if (mir) atomicAdd(a.mirror_products, (unsigned long long)mir);
+        if (blocks) atomicAdd(&s_acc[3], (unsigned long long)blocks);
+        if (mir) atomicAdd(&s_acc[4], (unsigned long long)mir);
       }
     }
     if (a.final_tier) {
@@ -393,11 +404,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
     for (uint32_t p0 = 0; p0 < len; p0 += 32) {
       const uint32_t p = p0 + lane;
       uint32_t bits = 0, K = 0;
-      int dummy_t = 0;
-      double dummy_b = 0.0;
       if (p < len) {
         K = a.pK[start + p];
-        bits = child_bits(a, tau, I, J, K, dummy_t, dummy_b);
+        const uint32_t it = p0 >> 5;
+        if (it < 4) {
+          bits = it == 0 ? keep0 : it == 1 ? keep1 : it == 2 ? keep2 : keep3;
+        } else {   // beyond the kept entries: test again (the same deterministic result)
+          int dummy_t = 0;
+          double dummy_b = 0.0;
+          bits = child_bits(a, tau, I, J, K, dummy_t, dummy_b);
+        }
       }
 #pragma unroll
       for (int q = 0; q < 4; q++) {
@@ -415,6 +431,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
         run[q] += __shfl_sync(0xffffffffu, inc, 31);
       }
     }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long *dst[5] = {a.tested, a.culled, a.leaf_products, a.output_blocks, a.mirror_products};
+    for (int q = 0; q < 5; q++)
+      if (s_acc[q]) atomicAdd(dst[q], s_acc[q]);
   }
 }
 
