@@ -574,6 +574,74 @@ def run_sp2(args):
     S.spamm_ctx_destroy(ctx)
 
 
+def run_variants(args):
+    """The threshold and dropping variants against plain SpAMM. (1) The depth-scaled
+    threshold tau^{k+1} = tau^k / 8 (Sec. II) on the n = 8192 algebraic-decay product
+    (BF16, leaf 64, symmetric product): step time, leaf products and error against the
+    exact product. (2) SP2 on a 16^3 tight-binding system (n = 4096, 30 steps, leaf 64,
+    FP64 products): SpAMM at tau against scheme (I), exact products filtered at tau
+    (Sec. III), as energy error against dense SP2 (FP64 SpAMM at tau = 0) against the
+    mean block products per step."""
+    import torch
+    from paper_1011_3534_gb300 import spamm as S
+    from paper_1011_3534_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    ctx = S.spamm_ctx_create(0, stream, timing=True)
+    N = 8192
+    A = torch.from_numpy(W.algebraic_decay(N, 2, 0)).cuda()
+    depth = []
+    with ClockSampler(0) as clk:
+        fl = S.COPY_FLAG[S.SPAMM_BF16] | S.SPAMM_SYMMETRIC | S.SPAMM_NO_RIGHT
+        t = S.spamm_tree_build(ctx, A, N, 64, fl)
+        t64 = S.spamm_tree_build(ctx, A, N, 64, S.SPAMM_KEEP_FP64 | S.SPAMM_SYMMETRIC)
+        c0 = S.spamm_multiply(ctx, t64, t64, 0.0, S.SPAMM_FP64, S.SPAMM_SYM_PRODUCT)
+        exact = torch.empty((N, N), dtype=torch.float64, device=A.device)
+        S.spamm_tree_to_dense(c0, exact)
+        S.spamm_tree_free(c0)
+        S.spamm_tree_free(t64)
+        for tau in (1e-8, 1e-6, 1e-4):
+            for flags, name in ((0, "plain"), (S.SPAMM_DEPTH_TAU, "depth-scaled")):
+                box = {}
+
+                def one():
+                    S.spamm_tree_update(t, A)
+                    box["c"] = S.spamm_multiply(ctx, t, t, tau, S.SPAMM_BF16, S.SPAMM_SYM_PRODUCT | flags, box.get("c"))
+                ms = _events_ms(stream, one, args.steps, 3)
+                st = S.spamm_stats(box["c"])
+                Cd = torch.empty_like(exact)
+                S.spamm_tree_to_dense(box["c"], Cd)
+                err = float(torch.linalg.norm(Cd - exact) / torch.linalg.norm(exact))
+                depth.append({"tau": tau, "threshold": name, "ms_per_step": ms,
+                              "dense_equiv_gflops": 2.0 * N ** 3 / (ms * 1e-3) / 1e9,
+                              "leaf_products": st["leaf_products"] + st["mirrored_products"],
+                              "rel_fro_err_vs_exact": err})
+                del Cd
+                S.spamm_tree_free(box["c"])
+        S.spamm_tree_free(t)
+        del exact
+        # SP2: SpAMM against scheme (I)
+        ip, ix, d = W.tight_binding(16, seed=2)[:3]
+        n = 16 ** 3
+        ref = S.spamm_sp2(ctx, ip, ix, d, n / 2, 30, 64, S.SPAMM_FP64, 0.0)
+        e_ref = ref["energy"]
+        sp2 = []
+        for tau in (1e-2, 3.16e-3, 1e-3, 3.16e-4, 1e-4, 3.16e-5, 1e-5, 1e-6):
+            a = S.spamm_sp2(ctx, ip, ix, d, n / 2, 30, 64, S.SPAMM_FP64, tau)
+            b = S.spamm_sp2_dropping(ctx, ip, ix, d, n / 2, 30, 64, S.SPAMM_FP64, tau)
+            for name, r in (("spamm", a), ("dropping", b)):
+                sp2.append({"tau": tau, "scheme": name, "energy_rel_err": abs(r["energy"] - e_ref) / abs(e_ref),
+                            "mean_block_products": float(np.mean(r["leaf_products"])), "ms": r["ms"],
+                            "branches_equal": r["branches"] == ref["branches"]})
+    head = max(depth, key=lambda r: r["dense_equiv_gflops"] if r["threshold"] == "depth-scaled" else 0)
+    _line({"workload": "threshold and dropping variants: algebraic-decay n=8192 leaf=64 BF16 symmetric product; "
+                       "SP2 16^3 tight-binding n=4096 leaf=64 FP64 (SpAMM vs scheme (I))",
+           "n": N, "leaf": 64, "precision": "bf16", "accumulate": "fp32", "l2": "inputs larger than L2"},
+          head["dense_equiv_gflops"], head["ms_per_step"], "bf16",
+          {"depth_scaled": depth, "sp2_schemes": sp2, "sp2_reference_energy": e_ref,
+           "sp2_reference_mean_block_products": float(np.mean(ref["leaf_products"])), "clocks": clk.summary()})
+    S.spamm_ctx_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -581,7 +649,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
-    ap.add_argument("--config", default="alg8192", choices=["alg8192", "lattice32768", "batched256", "sp2-32768"])
+    ap.add_argument("--config", default="alg8192",
+                    choices=["alg8192", "lattice32768", "batched256", "sp2-32768", "variants"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -593,6 +662,8 @@ def main():
         run_batched(args)
     elif args.config == "sp2-32768":
         run_sp2(args)
+    elif args.config == "variants":
+        run_variants(args)
     else:
         run_gpu(args)
 

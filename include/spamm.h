@@ -93,6 +93,10 @@ typedef enum {
                                       cull reads a symmetric tree's norms on and above the
                                       diagonal, the surviving triples of (i, j) and (j, i)
                                       are the mirror images of each other */
+#define SPAMM_DEPTH_TAU    0x1000  /* spamm_multiply: tier k tests against tau * 8^-k, the
+                                      depth-scaled threshold tau^{k+1} = tau^k / 8 of Sec. II
+                                      (rigorous: ||C~ - AB||_F < (k_max + 1) tau), instead of
+                                      tau at every tier */
 
 #define SPAMM_MAX_LEVELS 24
 
@@ -158,6 +162,14 @@ SPAMM_API spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t 
    Waits for those launches to finish, then starts a new count.
    Errors: SPAMM_EINVAL (null argument, or no timed build since the last call), SPAMM_ECUDA. */
 SPAMM_API spamm_status spamm_tree_build_ms(spamm_tree t, float *ms);
+/* The dropping filter of the paper's scheme (I) (Sec. III: after each multiplication,
+   blocks with ||P^k||_F < tau are dropped), at leaf resolution: every stored leaf block
+   of t whose Frobenius norm is below tau is no longer stored (its presence byte and
+   norm are cleared; no reader loads an absent block's tile), and the norm pyramid is
+   rebuilt. tau = 0 drops nothing. *kept (may be NULL; then the call is asynchronous)
+   gets the number of blocks still stored. Errors: SPAMM_EINVAL (tau negative or not
+   finite), SPAMM_ECUDA. */
+SPAMM_API spamm_status spamm_drop_blocks(spamm_tree t, double tau, int64_t *kept);
 /* Shape of a tree: order n, leaf size, padded blocks per side NB, and kmax. */
 SPAMM_API spamm_status spamm_tree_info(spamm_tree t, int64_t *n, int32_t *leaf, int32_t *nb_padded,
                              int32_t *kmax);
@@ -325,8 +337,19 @@ SPAMM_API spamm_status spamm_sp2_begin(spamm_ctx ctx, int64_t n, const int64_t *
 SPAMM_API spamm_status spamm_sp2_step(spamm_sp2_run r, double tau);
 SPAMM_API spamm_status spamm_sp2_step_learned(spamm_sp2_run r, spamm_mlp m, double err_budget,
                                               double tau_min, double tau_max);
+/* One step of the paper's scheme (I) comparator (Sec. III): the product X X at the
+   smallest positive tau (exact: only sub-products with an absent or zero block are
+   skipped), then the dropping filter at leaf resolution with tau_drop
+   (spamm_drop_blocks), then the trace-correcting step on the filtered product. The
+   step's leaf products and tau_drop are recorded as for spamm_sp2_step. */
+SPAMM_API spamm_status spamm_sp2_step_drop(spamm_sp2_run r, double tau_drop);
 SPAMM_API spamm_status spamm_sp2_iterate(spamm_sp2_run r, spamm_tree *X);
 SPAMM_API spamm_status spamm_sp2_end(spamm_sp2_run r, spamm_sp2_result *out);
+/* spamm_sp2 with every step taken by scheme (I) (spamm_sp2_step_drop, tau_drop). */
+SPAMM_API spamm_status spamm_sp2_dropping(spamm_ctx ctx, int64_t n, const int64_t *indptr,
+                                          const int64_t *indices, const double *data, double n_occ,
+                                          int32_t steps, int32_t leaf, spamm_prec prec, double tau_drop,
+                                          spamm_sp2_result *out);
 /* spamm_sp2 with every step's tolerance chosen by the controller. */
 SPAMM_API spamm_status spamm_sp2_learned(spamm_ctx ctx, int64_t n, const int64_t *indptr,
                                          const int64_t *indices, const double *data,

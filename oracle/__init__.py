@@ -74,6 +74,9 @@ def _load(path: str) -> ctypes.CDLL:
                                  ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(_Stats)]
     lib.oracle_spamm.restype = ctypes.c_int
+    lib.oracle_spamm_ex.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _D, _U32,
+                                    ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_Stats)]
+    lib.oracle_spamm_ex.restype = ctypes.c_int
     lib.oracle_spamm_values.argtypes = [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, _D]
     lib.oracle_spamm_values.restype = ctypes.c_int
     lib.oracle_spamm_block.argtypes = [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _D]
@@ -133,8 +136,9 @@ class Tree:
 
 
 def spamm(A: Tree, B: Tree, tau: float, *, product: bool = True, triples: bool = False,
-          stats: bool = False, threads: int = 1):
-    """Eq. 4 from the root. Returns dict(C, triples (recursion order), count, stats)."""
+          stats: bool = False, threads: int = 1, depth_scaled: bool = False):
+    """Eq. 4 from the root. Returns dict(C, triples (recursion order), count, stats).
+    depth_scaled: tier k tests against tau * 8^-k (the rigorous variant of Sec. II)."""
     L = A.L
     C = np.empty((A.n, A.n), dtype=np.float64) if product else None
     cnt = ctypes.c_int64(0)
@@ -142,11 +146,11 @@ def spamm(A: Tree, B: Tree, tau: float, *, product: bool = True, triples: bool =
     trip = None
     if triples:
         # size the buffer with a norm-only pass first
-        rc = L.oracle_spamm(A.h, B.h, tau, 1, None, None, 0, ctypes.byref(cnt), None)
+        rc = L.oracle_spamm_ex(A.h, B.h, tau, int(depth_scaled), 1, None, None, 0, ctypes.byref(cnt), None)
         if rc:
             raise RuntimeError(rc)
         trip = np.empty((max(cnt.value, 1), 3), dtype=np.uint32)
-    rc = L.oracle_spamm(A.h, B.h, tau, threads if not (triples or stats) else 1,
+    rc = L.oracle_spamm_ex(A.h, B.h, tau, int(depth_scaled), threads if not (triples or stats) else 1,
                         _dptr(C) if C is not None else None,
                         trip.ctypes.data_as(_U32) if trip is not None else None,
                         trip.shape[0] if trip is not None else 0, ctypes.byref(cnt),

@@ -63,3 +63,51 @@ def sp2_spectral(eigs: np.ndarray, n_occ: float, steps: int, emin: float, emax: 
         branches.append(1 if sq else 0)
         traces.append(float(lam.sum()))
     return {"energy": float(np.dot(eigs, lam)), "traces": traces, "branches": branches}
+
+
+def drop_blocks(P: np.ndarray, b: int, tau: float) -> tuple[np.ndarray, int]:
+    """The dropping filter of scheme (I) (Sec. III) at b x b resolution: every block of
+    the zero-padded P whose Frobenius norm is below tau set to zero. Returns the
+    filtered n x n matrix and the number of nonzero blocks kept."""
+    n = P.shape[0]
+    nb = -(-n // b)
+    Q = np.zeros((nb * b, nb * b))
+    Q[:n, :n] = P
+    blocks = Q.reshape(nb, b, nb, b)
+    norm = np.sqrt((blocks ** 2).sum(axis=(1, 3)))
+    drop = norm < tau
+    blocks[drop[:, None, :, None].repeat(b, 1).repeat(b, 3)] = 0.0
+    kept = int(np.count_nonzero(~drop & (norm > 0)))
+    return Q[:n, :n].copy(), kept
+
+
+def block_products(X: np.ndarray, b: int, upper: bool = True) -> int:
+    """Leaf products of an exact block-sparse X X: triples (i, j, k) whose blocks X_ik and
+    X_kj are both nonzero (only output blocks i <= j when `upper`)."""
+    n = X.shape[0]
+    nb = -(-n // b)
+    Q = np.zeros((nb * b, nb * b))
+    Q[:n, :n] = X
+    nzb = (np.abs(Q.reshape(nb, b, nb, b)).sum(axis=(1, 3)) > 0).astype(np.int64)
+    cnt = nzb @ nzb                       # cnt[i, j] = #k with X_ik, X_kj nonzero
+    return int(np.triu(cnt).sum() if upper else cnt.sum())
+
+
+def sp2_dense_dropping(H: np.ndarray, n_occ: float, steps: int, emin: float, emax: float, b: int,
+                       tau: float) -> dict:
+    """SP2 by scheme (I) of Sec. III: each step's product X X exact (dense FP64 matmul),
+    then filtered by drop_blocks at tau, and the trace-correcting step taken on the
+    filtered product. Also the block products each step's exact sparse multiply needs."""
+    n = H.shape[0]
+    X = (emax * np.eye(n) - H) / (emax - emin)
+    traces, branches, products = [float(np.trace(X))], [], []
+    for _ in range(steps):
+        products.append(block_products(X, b))
+        X2, _ = drop_blocks(X @ X, b, tau)
+        t1, t2 = float(np.trace(X)), float(np.trace(X2))
+        sq = choose_square(t1, t2, n_occ)
+        X = X2 if sq else 2.0 * X - X2
+        branches.append(1 if sq else 0)
+        traces.append(float(np.trace(X)))
+    return {"energy": float(np.sum(H * X.T)), "traces": traces, "branches": branches, "X": X,
+            "leaf_products": products}

@@ -21,7 +21,10 @@
  *   - the same surviving leaf triples by brute force over all NB^3 of them (the flat
  *     form that follows from Eq. 3 and the monotone norm tree);
  *   - the naive triple-loop product, which SpAMM at tau = 0 must reproduce
- *     (Sec. III: at tau = 0 SpAMM reverts to the ordinary O(n^3) product).
+ *     (Sec. III: at tau = 0 SpAMM reverts to the ordinary O(n^3) product);
+ *   - the depth-scaled threshold of Sec. II, tau^{k+1} = tau^k / 8 with tau^0 = tau at
+ *     the root: tier k tests against tau * 8^-k (exactly, a power of two), the rigorous
+ *     but pessimistic variant the paper mentions and does not use.
  *
  * Rounding order is fixed and documented: leaf norm^2 is a sequential row-major sum
  * of fl(a*a); the leaf product accumulates c += a*b in i-k-j order with no fused
@@ -140,6 +143,7 @@ typedef struct {
   const oracle_tree *A, *B;
   const oracle_tree *Av, *Bv;  /* operands whose values the leaf products use (A, B) */
   double tau;
+  int depth_scaled;     /* 1: tier l tests against tau * 8^-l (Sec. II) */
   double *C;            /* N x N padded accumulator, or NULL (norm tests only) */
   uint32_t *trip;       /* recorded leaf triples (i, j, k), or NULL */
   int64_t cap, ntrip;
@@ -189,7 +193,12 @@ static void rec(rec_ctx *c, int l, int32_t I, int32_t J, int32_t K) {
 #pragma omp atomic
     c->st->tested[l]++;
   }
-  if (cull(nA2, nB2, c->tau)) {                 /* ||A^k|| ||B^k|| < tau: 0 */
+#if ORACLE_MUTANT == 7
+  const double tl = c->depth_scaled ? ldexp(c->tau, -3 * (l + 1)) : c->tau;
+#else
+  const double tl = c->depth_scaled ? ldexp(c->tau, -3 * l) : c->tau;
+#endif
+  if (cull(nA2, nB2, tl)) {                     /* ||A^k|| ||B^k|| < tau: 0 */
     if (c->st) {
 #pragma omp atomic
       c->st->culled[l]++;
@@ -258,14 +267,15 @@ static int compatible(const oracle_tree *A, const oracle_tree *B) {
  *              triples and stats need threads == 1 so their order is fixed)
  * Returns 0, or 1 on bad arguments, 2 on allocation failure.
  */
-int oracle_spamm(const oracle_tree *A, const oracle_tree *B, double tau, int32_t threads,
-                 double *C, uint32_t *triples, int64_t cap, int64_t *ntriples,
-                 oracle_stats *stats) {
+int oracle_spamm_ex(const oracle_tree *A, const oracle_tree *B, double tau, int32_t depth_scaled,
+                    int32_t threads, double *C, uint32_t *triples, int64_t cap, int64_t *ntriples,
+                    oracle_stats *stats) {
   if (!compatible(A, B) || !(tau >= 0.0)) return 1;
   if (threads > 1 && (triples || stats)) return 1;
   rec_ctx c;
   memset(&c, 0, sizeof c);
   c.A = A; c.B = B; c.Av = A; c.Bv = B; c.tau = tau; c.trip = triples; c.cap = cap; c.st = stats;
+  c.depth_scaled = depth_scaled != 0;
   if (stats) memset(stats, 0, sizeof *stats);
   double *Cp = NULL;
   if (C) {
@@ -291,6 +301,13 @@ int oracle_spamm(const oracle_tree *A, const oracle_tree *B, double tau, int32_t
   }
   if (ntriples) *ntriples = c.ntrip;
   return 0;
+}
+
+/* SpAMM(A, B) with the plain threshold (every tier tests against tau). */
+int oracle_spamm(const oracle_tree *A, const oracle_tree *B, double tau, int32_t threads,
+                 double *C, uint32_t *triples, int64_t cap, int64_t *ntriples,
+                 oracle_stats *stats) {
+  return oracle_spamm_ex(A, B, tau, 0, threads, C, triples, cap, ntriples, stats);
 }
 
 /*

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <vector>
 
@@ -294,6 +295,7 @@ spamm_status spamm_ctx_destroy(spamm_ctx ctx) {
   if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
   if (ctx->batch_dev) cudaFree(ctx->batch_dev);
   if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->dev_count) cudaFree(ctx->dev_count);
   if (ctx->dev_status) cudaFree(ctx->dev_status);
   delete ctx;
   return SPAMM_OK;
@@ -418,6 +420,27 @@ spamm_status spamm_tree_build_ms(spamm_tree t, float *ms) {
   return SPAMM_OK;
 }
 
+spamm_status spamm_drop_blocks(spamm_tree t, double tau, int64_t *kept) {
+  if (!t) return SPAMM_EINVAL;
+  spamm_ctx ctx = t->ctx;
+  if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(ctx, SPAMM_EINVAL, "drop_blocks: tau must be finite and >= 0");
+  if (kept) {
+    if (!ctx->dev_count) CK(cudaMalloc(&ctx->dev_count, sizeof(unsigned long long)), "drop_blocks: counter");
+    CK(cudaMemsetAsync(ctx->dev_count, 0, sizeof(unsigned long long), ctx->stream), "drop_blocks: counter");
+  }
+  CK(launch_drop(t, tau, kept ? ctx->dev_count : nullptr, ctx->stream), "drop_blocks: launch");
+  ctx->launches += 1 + pyramid_launches(t);
+  t->stats_valid = false;
+  if (kept) {
+    unsigned long long h = 0;
+    CK(cudaMemcpyAsync(&h, ctx->dev_count, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "drop_blocks: copy");
+    spamm_status st = check_device_status(ctx);
+    if (st != SPAMM_OK) return st;
+    *kept = (int64_t)h;
+  }
+  return SPAMM_OK;
+}
+
 spamm_status spamm_tree_info(spamm_tree t, int64_t *n, int32_t *leaf, int32_t *nb_padded,
                              int32_t *kmax) {
   if (!t) return SPAMM_EINVAL;
@@ -503,7 +526,7 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
     return fail(ctx, SPAMM_EINVAL, "multiply: operands differ (n %lld/%lld, leaf %d/%d)",
                 (long long)A->n, (long long)B->n, A->b, B->b);
   if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(ctx, SPAMM_EINVAL, "multiply: tau must be finite and >= 0");
-  if (flags & ~((kTreeFlags & ~SPAMM_HOST_INPUT) | SPAMM_SYM_PRODUCT))
+  if (flags & ~((kTreeFlags & ~SPAMM_HOST_INPUT) | SPAMM_SYM_PRODUCT | SPAMM_DEPTH_TAU))
     return fail(ctx, SPAMM_EINVAL, "multiply: unknown flag bits 0x%x", flags);
   const bool symp = (flags & SPAMM_SYM_PRODUCT) != 0;
   if (symp && (A != B || !(A->flags & SPAMM_SYMMETRIC)))
@@ -560,6 +583,7 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
   *C = Ct;
   Ct->is_product = true;
   Ct->sym_product = symp;
+  Ct->depth_tau = (flags & SPAMM_DEPTH_TAU) != 0;
   if (symp) Ct->flags |= SPAMM_SYMMETRIC;
   Ct->prec = prec;
   Ct->tau = tau;
@@ -849,11 +873,56 @@ spamm_status sp2_advance(spamm_sp2_run r, double tau, bool from_record) {
 
 }  // namespace
 
+// Scheme (I) of Sec. III: the product at the smallest positive tau (exact: only products
+// with an absent or zero block are skipped), then the dropping filter on it, then the
+// trace-correcting step on the filtered product.
+static spamm_status sp2_advance_drop(spamm_sp2_run r, double tau_drop) {
+  spamm_ctx ctx = r->ctx;
+  const int step = r->steps;
+  spamm_tree out_tree = r->C;
+  spamm_status st = multiply_impl(ctx, r->X, r->X, std::numeric_limits<double>::denorm_min(), nullptr, r->prec,
+                                  SPAMM_SYM_PRODUCT, &out_tree);
+  if (st != SPAMM_OK) return st;
+  CK(launch_drop(r->C, tau_drop, nullptr, ctx->stream), "sp2: dropping filter");
+  ctx->launches += 1 + pyramid_launches(r->C);
+  CK(sp2_step_finish(r->X, r->C, r->n_occ, step, r->d_rec, ctx->stream), "sp2: step");
+  ctx->launches += 4 + pyramid_launches(r->C);
+  r->tau_host[step] = tau_drop;
+  r->learned[step] = false;
+  std::swap(r->X, r->C);
+  r->steps++;
+  return SPAMM_OK;
+}
+
 extern "C" spamm_status spamm_sp2_step(spamm_sp2_run r, double tau) {
   if (!r) return SPAMM_EINVAL;
   if (r->steps >= SPAMM_SP2_MAX_STEPS) return fail(r->ctx, SPAMM_ERANGE, "sp2: more than %d steps", SPAMM_SP2_MAX_STEPS);
   if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(r->ctx, SPAMM_EINVAL, "sp2: tau invalid");
   return sp2_advance(r, tau, false);
+}
+
+extern "C" spamm_status spamm_sp2_step_drop(spamm_sp2_run r, double tau_drop) {
+  if (!r) return SPAMM_EINVAL;
+  if (r->steps >= SPAMM_SP2_MAX_STEPS) return fail(r->ctx, SPAMM_ERANGE, "sp2: more than %d steps", SPAMM_SP2_MAX_STEPS);
+  if (!(tau_drop >= 0.0) || !std::isfinite(tau_drop)) return fail(r->ctx, SPAMM_EINVAL, "sp2: tau invalid");
+  return sp2_advance_drop(r, tau_drop);
+}
+
+extern "C" spamm_status spamm_sp2_dropping(spamm_ctx ctx, int64_t n, const int64_t *indptr, const int64_t *indices,
+                                           const double *data, double n_occ, int32_t steps, int32_t leaf,
+                                           spamm_prec prec, double tau_drop, spamm_sp2_result *out) {
+  if (!ctx) return SPAMM_EINVAL;
+  if (!out) return fail(ctx, SPAMM_EINVAL, "sp2: null pointer");
+  if (steps < 0 || steps > SPAMM_SP2_MAX_STEPS) return fail(ctx, SPAMM_EINVAL, "sp2: bad steps");
+  spamm_sp2_run r = nullptr;
+  spamm_status st = spamm_sp2_begin(ctx, n, indptr, indices, data, n_occ, leaf, prec, &r);
+  if (st != SPAMM_OK) return st;
+  for (int q = 0; q < steps && st == SPAMM_OK; q++) st = spamm_sp2_step_drop(r, tau_drop);
+  if (st != SPAMM_OK) {
+    spamm_sp2_end(r, nullptr);
+    return st;
+  }
+  return spamm_sp2_end(r, out);
 }
 
 extern "C" spamm_status spamm_sp2_step_learned(spamm_sp2_run r, spamm_mlp m, double err_budget, double tau_min,

@@ -59,6 +59,7 @@ struct spamm_ctx_s {
   bool timing = false;
   std::string err;
   uint32_t *dev_status = nullptr;   // device word of DEV_* bits
+  unsigned long long *dev_count = nullptr;   // one device counter (spamm_drop_blocks)
   int64_t launches = 0;
   // staging buffer for host input / output (device)
   void *stage = nullptr;
@@ -145,6 +146,7 @@ struct spamm_tree_s {
   // product trees
   bool is_product = false;
   bool sym_product = false;               // C = A A of a symmetric A, blocks i <= j computed
+  bool depth_tau = false;                 // tier l of the cull tests against tau * 8^-l
   int32_t prec = 0;
   double tau = 0;
   TierList tiers[SPAMM_MAX_LEVELS + 1];   // tiers[l + 1] lists tier l; tiers[0] the virtual root
@@ -179,6 +181,9 @@ __host__ __device__ inline int64_t level_offset(int l) { return ((int64_t(1) << 
 cudaError_t launch_tree_build(spamm_tree t, const double *A, cudaStream_t s);
 cudaError_t launch_pyramid(spamm_tree t, cudaStream_t s);
 cudaError_t launch_mirror(spamm_tree C, cudaStream_t s);       // C_ji := C_ij^T for i < j
+// Leaf blocks with ||T_ij||_F < tau dropped (presence and norm cleared; kept counted into
+// *kept when not null), then the norm pyramid rebuilt.
+cudaError_t launch_drop(spamm_tree t, double tau, unsigned long long *kept, cudaStream_t s);
 cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s);
 cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, const double *tau_dev,
                         uint32_t *dev_status, int sm_count, cudaStream_t s, int *launches);

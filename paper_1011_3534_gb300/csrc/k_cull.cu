@@ -21,6 +21,8 @@
 // Counters: tests, culls and the sum of culled norm products per tier. Integer
 // counters use atomics (exact); the FP64 sums are written per parent group and summed
 // in a fixed order afterwards, so they are reproducible run to run.
+#include <cmath>
+
 #include "internal.cuh"
 #include "sync.cuh"
 
@@ -92,6 +94,7 @@ struct CullArgs {
   int32_t l, D, nb, NB, final_tier;
   int32_t sym;              // symmetric product: output blocks below the diagonal are skipped
   double tau;
+  double tau_scale;         // 8^-l with the depth-scaled threshold, else 1 (exact)
   const double *tau_dev;         // when set, tau is read from device memory at launch
   const uint32_t *pgij, *pgstart, *pglen;
   const uint16_t *pK;
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
   __shared__ unsigned long long s_acc[5];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long ngroups = *a.p_ngroups;
-  const double tau = a.tau_dev ? *a.tau_dev : a.tau;
+  const double tau = (a.tau_dev ? *a.tau_dev : a.tau) * a.tau_scale;
   if (threadIdx.x < 5) s_acc[threadIdx.x] = 0ull;
   __syncthreads();
 
@@ -464,6 +467,7 @@ struct TopArgs {
   int32_t T;                                     // last tier run here
   int32_t sym;                                   // symmetric product
   int32_t symA, symB;                            // operand trees of symmetric matrices
+  int32_t depth_tau;                             // tier l tests against tau * 8^-l
   double tau;
   const double *tau_dev;
   uint32_t *gij, *gstart, *glen;                 // the tier-T list (C->tiers[T + 1])
@@ -536,7 +540,9 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
   morton_ij(m, I, J);
   int cur = 0;                 // s_mask[cur]: the tier just evaluated
   uint32_t parent_groups = 1;  // groups of the tier l-1 list (tier -1: the root group)
+  double tl = tau;             // this tier's threshold
   for (int l = 0; l <= t.T; l++) {
+    if (l && t.depth_tau) tl *= 0.125;
     const uint32_t D = 1u << l, nblk = D * D;
     const double *nA = s_nA + level_offset(l), *nB = s_nB + level_offset(l);
     uint32_t mask = 0;
@@ -550,7 +556,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
         if (!((pm >> (K >> 1)) & 1u)) continue;          // parent culled: not a call
         const double p = nA[tier_at(I, K, D, t.symA)] * nB[tier_at(K, J, D, t.symB)];
         tests++;
-        if (below_tau(p, tau)) bound += p;
+        if (below_tau(p, tl)) bound += p;
         else mask |= 1u << K;
       }
     }
@@ -696,6 +702,7 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
     ta.tau_dev = tau_dev;
     ta.sym = C->sym_product ? 1 : 0;
     ta.symA = (A->flags & SPAMM_SYMMETRIC) ? 1 : 0;
+    ta.depth_tau = C->depth_tau ? 1 : 0;
     ta.symB = (B->flags & SPAMM_SYMMETRIC) ? 1 : 0;
     const TierList &out = C->tiers[ta.T + 1];
     ta.gij = out.gij;
@@ -730,6 +737,7 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
     a.symA = (A->flags & SPAMM_SYMMETRIC) ? 1 : 0;
     a.symB = (B->flags & SPAMM_SYMMETRIC) ? 1 : 0;
     a.tau = tau;
+    a.tau_scale = C->depth_tau ? std::ldexp(1.0, -3 * l) : 1.0;
     a.tau_dev = tau_dev;
     const TierList &par = C->tiers[l];
     a.pgij = par.gij;

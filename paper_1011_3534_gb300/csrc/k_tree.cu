@@ -667,6 +667,39 @@ cudaError_t launch_mirror(spamm_tree C, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The dropping filter of the paper's scheme (I) (Sec. III, after each multiplication):
+// a stored leaf block whose Frobenius norm sqrt(norm^2) is below tau is no longer stored
+// (presence byte and squared norm cleared; readers never load the tile of an absent
+// block). Counts the blocks that stay.
+__global__ void __launch_bounds__(256) k_drop_blocks(uint8_t *nz, double *leaf_norm2, int32_t nb, int32_t NB,
+                                                     double tau, unsigned long long *kept) {
+  unsigned int mine = 0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nb * nb;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t li = (t / nb) * NB + (t % nb);
+    if (!nz[li]) continue;
+    if (sqrt(leaf_norm2[li]) < tau) {
+      nz[li] = 0;
+      leaf_norm2[li] = 0.0;
+    } else {
+      mine++;
+    }
+  }
+  if (!kept) return;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, off);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(kept, (unsigned long long)mine);
+}
+
+cudaError_t launch_drop(spamm_tree t, double tau, unsigned long long *kept, cudaStream_t s) {
+  const int64_t blocks = (int64_t)t->nb * t->nb;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((blocks + 255) / 256, 4096));
+  k_drop_blocks<<<grid, 256, 0, s>>>(t->nz, t->norm2 + level_offset(t->kmax), t->nb, t->NB, tau, kept);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_pyramid(t, s);
+}
+
 cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s) {
   int lb = 0;
   while ((1 << lb) < t->b) lb++;

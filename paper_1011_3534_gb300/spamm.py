@@ -30,6 +30,7 @@ SPAMM_NO_RIGHT = 0x0100
 SPAMM_GRAPH = 0x0200
 SPAMM_COPY_TF32X3 = 0x0400
 SPAMM_SYM_PRODUCT = 0x0800
+SPAMM_DEPTH_TAU = 0x1000
 COPY_FLAG = {SPAMM_FP64: SPAMM_KEEP_FP64, SPAMM_TF32: SPAMM_COPY_TF32, SPAMM_BF16: SPAMM_COPY_BF16,
              SPAMM_FP16: SPAMM_COPY_FP16, SPAMM_BF16X3: SPAMM_COPY_BF16X3, SPAMM_TF32X3: SPAMM_COPY_TF32X3}
 MLP_FEATURES = 69
@@ -45,7 +46,8 @@ EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_er
            "spamm_mlp_get_params", "spamm_mlp_set_params", "spamm_mlp_forward", "spamm_mlp_gradient",
            "spamm_mlp_adam_step", "spamm_mlp_adam_apply", "spamm_mlp_train", "spamm_features", "spamm_tau_select",
            "spamm_tree_distance", "spamm_sp2_begin", "spamm_sp2_step", "spamm_sp2_step_learned",
-           "spamm_sp2_iterate", "spamm_sp2_end", "spamm_sp2_learned")
+           "spamm_sp2_iterate", "spamm_sp2_end", "spamm_sp2_learned", "spamm_drop_blocks",
+           "spamm_sp2_step_drop", "spamm_sp2_dropping")
 
 
 class SpammError(RuntimeError):
@@ -111,6 +113,10 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
                                     ctypes.POINTER(Sp2ResultT)]
     L.spamm_sp2_begin.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, ctypes.c_int, ctypes.POINTER(_P)]
     L.spamm_sp2_step.argtypes = [_P, _D]
+    L.spamm_sp2_step_drop.argtypes = [_P, _D]
+    L.spamm_sp2_dropping.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, _I32, ctypes.c_int, _D,
+                                     ctypes.POINTER(Sp2ResultT)]
+    L.spamm_drop_blocks.argtypes = [_P, _D, ctypes.POINTER(_I64)]
     L.spamm_sp2_step_learned.argtypes = [_P, _P, _D, _D, _D]
     L.spamm_sp2_iterate.argtypes = [_P, ctypes.POINTER(_P)]
     L.spamm_sp2_end.argtypes = [_P, ctypes.POINTER(Sp2ResultT)]
@@ -323,6 +329,24 @@ def spamm_sp2_learned(ctx: Ctx, indptr, indices, data, n_occ: float, steps: int,
     return _sp2_dict(r)
 
 
+def spamm_sp2_dropping(ctx: Ctx, indptr, indices, data, n_occ: float, steps: int, leaf: int, prec: int,
+                       tau_drop: float) -> dict:
+    """SP2 by the paper's scheme (I): exact products, each filtered by spamm_drop_blocks."""
+    ip, ix, dv = _csr(indptr, indices, data)
+    r = Sp2ResultT()
+    ctx.check(LIB.spamm_sp2_dropping(ctx.h, ip.size - 1, ip.ctypes.data, ix.ctypes.data, dv.ctypes.data,
+                                     float(n_occ), steps, leaf, int(prec), float(tau_drop), ctypes.byref(r)),
+              "spamm_sp2_dropping")
+    return _sp2_dict(r)
+
+
+def spamm_drop_blocks(t: Tree, tau: float, count: bool = True):
+    """Drop the leaf blocks of t with Frobenius norm below tau; the number kept (or None)."""
+    kept = _I64()
+    t.ctx.check(LIB.spamm_drop_blocks(t.h, float(tau), ctypes.byref(kept) if count else None), "spamm_drop_blocks")
+    return kept.value if count else None
+
+
 class Sp2Run:
     """spamm_sp2_begin .. spamm_sp2_end: the SP2 loop one step at a time."""
 
@@ -336,6 +360,9 @@ class Sp2Run:
 
     def step(self, tau: float):
         self.ctx.check(LIB.spamm_sp2_step(self.h, float(tau)), "spamm_sp2_step")
+
+    def step_drop(self, tau_drop: float):
+        self.ctx.check(LIB.spamm_sp2_step_drop(self.h, float(tau_drop)), "spamm_sp2_step_drop")
 
     def step_learned(self, mlp: "Mlp", err_budget: float, tau_min: float, tau_max: float):
         self.ctx.check(LIB.spamm_sp2_step_learned(self.h, mlp.h, float(err_budget), float(tau_min), float(tau_max)),

@@ -257,3 +257,34 @@ def test_page_locked_host_buffers(S, ctx):
         (n0, d0, p0), (n1, d1, p1) = outs
         assert np.array_equal(n0, n1)
         assert np.array_equal(d0, d1) and np.array_equal(d0, p0) and np.array_equal(d0, p1)
+
+
+@pytest.mark.parametrize("n,leaf,tau,prec_name,sym", [(1000, 32, 1e-6, "fp64", False), (2048, 64, 1e-4, "fp64", True),
+                                                      (3000, 64, 1e-5, "bf16", True), (1536, 128, 1e-3, "bf16", False)])
+def test_depth_scaled_threshold(S, ctx, n, leaf, tau, prec_name, sym):
+    # SPAMM_DEPTH_TAU: tier k tests against tau 8^-k (Sec. II); the surviving triples,
+    # tier counts and culled bounds equal the oracle's depth-scaled recursion, C equals
+    # it within the FP64 bar (FP64) or the BF16 sanity bar, and the rigorous bound holds
+    A = W.algebraic_decay(n, 2, 4)
+    prec = S.PRECISIONS[prec_name]
+    fl = (S.SPAMM_KEEP_FP64 if prec == S.SPAMM_FP64 else S.COPY_FLAG[prec]) | (S.SPAMM_SYMMETRIC if sym else 0)
+    tA = S.spamm_tree_build(ctx, torch.from_numpy(A).cuda(), n, leaf, fl)
+    flags = S.SPAMM_DEPTH_TAU | (S.SPAMM_SYM_PRODUCT if sym else 0)
+    tC = S.spamm_multiply(ctx, tA, tA, tau, prec, flags)
+    C, trip, st = S.spamm_tree_to_dense(tC), S.spamm_triples(tC), S.spamm_stats(tC)
+    S.spamm_tree_free(tC)
+    S.spamm_tree_free(tA)
+    TA = oracle.Tree(A, leaf)
+    ref = oracle.spamm(TA, TA, tau, triples=True, stats=True, product=False, depth_scaled=True)
+    assert np.array_equal(oracle.sort_triples(trip), oracle.sort_triples(ref["triples"]))
+    if not sym:
+        assert st["tested"] == ref["stats"].tested and st["culled"] == ref["stats"].culled
+        np.testing.assert_allclose(st["culled_bound"], ref["stats"].culled_bound, rtol=1e-11, atol=1e-300)
+    C64 = oracle.spamm(TA, TA, tau, threads=oracle.max_threads(), depth_scaled=True)["C"]
+    err = rel_fro(C, C64)
+    assert err < (1e-12 if prec_name == "fp64" else 1e-2)
+    exact = A @ A
+    assert np.linalg.norm(C64 - exact) < (TA.kmax + 1) * tau
+    plain = oracle.spamm(TA, TA, tau, product=False)["count"]
+    print(f"depth-scaled tau {tau} {prec_name} leaf {leaf}: {ref['count']} triples (plain {plain}), "
+          f"error {np.linalg.norm(C64 - exact):.2e} < {(TA.kmax + 1) * tau:.2e}")

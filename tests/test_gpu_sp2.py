@@ -108,3 +108,57 @@ def test_sp2_learned_with_constant_network_equals_fixed_tau(S, ctx):
         assert g["energy"] == f["energy"] and g["branches"] == f["branches"]
         assert g["leaf_products"] == f["leaf_products"]
     m.free()
+
+
+# ---------------------------------------------------------------- scheme (I): dropping
+
+@pytest.mark.parametrize("n,leaf,prec_name", [(1000, 32, "fp64"), (2048, 64, "bf16")])
+def test_drop_blocks_matches_oracle_filter(S, ctx, n, leaf, prec_name):
+    # the filter keeps exactly the blocks whose norm reaches tau (FP64 tiles: the dense
+    # image equals the oracle's filtered matrix bit for bit; BF16 trees keep FP32 tiles
+    # of the rounded product, so their presence pattern is compared)
+    A = W.algebraic_decay(n, 2, 5)
+    prec = S.PRECISIONS[prec_name]
+    fl = (S.SPAMM_KEEP_FP64 if prec == S.SPAMM_FP64 else S.COPY_FLAG[prec]) | S.SPAMM_SYMMETRIC
+    tA = S.spamm_tree_build(ctx, torch.from_numpy(A).cuda(), n, leaf, fl)
+    tC = S.spamm_multiply(ctx, tA, tA, 0.0, prec, S.SPAMM_SYM_PRODUCT)
+    C = S.spamm_tree_to_dense(tC)
+    nb = -(-n // leaf)
+    Q = np.zeros((nb * leaf, nb * leaf))
+    Q[:n, :n] = C
+    norm = np.sqrt((Q.reshape(nb, leaf, nb, leaf) ** 2).sum(axis=(1, 3)))
+    tau = float(np.quantile(norm[norm > 0], 0.6))
+    near = np.abs(norm - tau) <= 1e-12 * tau
+    kept = S.spamm_drop_blocks(tC, tau)
+    Cd = S.spamm_tree_to_dense(tC)
+    ref, rkept = O.drop_blocks(C, leaf, tau)
+    assert abs(kept - rkept) <= int(near.sum())
+    Qd = np.zeros_like(Q)
+    Qd[:n, :n] = Cd
+    present = np.abs(Qd.reshape(nb, leaf, nb, leaf)).sum(axis=(1, 3)) > 0
+    assert np.array_equal(present[~near], (norm >= tau)[~near])
+    if prec_name == "fp64" and not near.any():
+        assert np.array_equal(Cd, ref)
+    # the norm pyramid was rebuilt: the root holds the filtered matrix's norm
+    np.testing.assert_allclose(S.spamm_tree_norms(tC, 0)[0, 0], (Cd ** 2).sum(), rtol=1e-12)
+    assert S.spamm_drop_blocks(tC, 0.0) == kept
+    S.spamm_tree_free(tC)
+    S.spamm_tree_free(tA)
+
+
+@pytest.mark.parametrize("side,leaf,tau", [(8, 32, 1e-4), (10, 64, 1e-3), (12, 64, 1e-6)])
+def test_sp2_scheme_one_matches_oracle(S, ctx, side, leaf, tau):
+    # scheme (I): exact products filtered at tau; the same branches, traces and energy as
+    # the dense oracle of the scheme, and the same block products per step
+    (ip, ix, d), H, n, lo, hi = system(side)
+    ref = O.sp2_dense_dropping(H, n / 2, 30, lo, hi, leaf, tau)
+    g = S.spamm_sp2_dropping(ctx, ip, ix, d, n / 2, 30, leaf, S.SPAMM_FP64, tau)
+    assert g["branches"] == ref["branches"]
+    np.testing.assert_allclose(g["traces"], ref["traces"], rtol=1e-10)
+    assert abs(g["energy"] - ref["energy"]) <= 1e-10 * abs(ref["energy"])
+    # block products of the exact sparse multiply (near-ties of the filter aside)
+    diff = np.abs(np.array(g["leaf_products"]) - np.array(ref["leaf_products"]))
+    assert np.all(diff <= 0.01 * np.array(ref["leaf_products"]))
+    dense = O.sp2_dense(H, n / 2, 30, lo, hi)["energy"]
+    print(f"scheme (I) {side}^3 leaf {leaf} tau {tau}: error {abs(g['energy'] - dense) / abs(dense):.2e}, "
+          f"{sum(g['leaf_products'])} block products ({sum(ref['leaf_products'])} in the oracle)")

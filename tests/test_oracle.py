@@ -32,6 +32,38 @@ def brute_triples_numpy(nA2, nB2, tau):
     return np.stack([i, j, k], axis=1).astype(np.uint32)
 
 
+DEPTH_TAU = 3e-2   # the depth-scaled pin's tau (no tier product within 1e-6 of its threshold)
+
+
+def tier_norm2_numpy(nL2, l, kmax):
+    """Squared norms of tier l from the leaf tier, by summing 2^s x 2^s groups (numpy)."""
+    s = 1 << (kmax - l)
+    d = nL2.shape[0] // s
+    return nL2.reshape(d, s, d, s).sum(axis=(1, 3))
+
+
+def brute_depth_triples_numpy(A, B, b, tau, margin=None):
+    """Leaf triples (i, j, k) of the depth-scaled recursion, lexicographic: every ancestor
+    (i, j, k) >> s at tier l = kmax - s has ||A^l|| ||B^l|| >= tau * 8^-l. With `margin`,
+    also the smallest relative distance of a tested product from its threshold."""
+    nA2, _, NB = blocks_norm2_numpy(A, b)
+    nB2, _, _ = blocks_norm2_numpy(B, b)
+    kmax = NB.bit_length() - 1
+    alive = np.ones((1, 1, 1), dtype=bool)
+    gap = np.inf
+    for l in range(kmax + 1):
+        a2, b2 = tier_norm2_numpy(nA2, l, kmax), tier_norm2_numpy(nB2, l, kmax)
+        p = np.sqrt(a2)[:, None, :] * np.sqrt(b2).T[None, :, :]     # [i, j, k] at tier l
+        tl = tau * 8.0 ** -l
+        parent = alive.repeat(2, 0).repeat(2, 1).repeat(2, 2) if l else alive
+        if parent.any():
+            gap = min(gap, float(np.min(np.abs(p[parent] - tl)) / tl))
+        alive = parent & ~(p < tl)
+    i, j, k = np.nonzero(alive)
+    out = np.stack([i, j, k], axis=1).astype(np.uint32)
+    return (out, gap) if margin else out
+
+
 def spamm_numpy_from_triples(P_A, P_B, trip, b, n):
     NB = P_A.shape[0] // b
     C = np.zeros_like(P_A)
@@ -310,6 +342,12 @@ def _pins_fail(L):
         nB2, _, _ = blocks_norm2_numpy(B, 8)
         if not np.array_equal(oracle.sort_triples(rec), brute_triples_numpy(nA2, nB2, 1e-3)):
             return True
+        # the depth-scaled threshold against numpy brute force over every tier
+        A, B = rng_matrix(128, 25), rng_matrix(128, 26, decay=0.7)
+        TA, TB = tree(A, 8), tree(B, 8)
+        rec = oracle.spamm(TA, TB, DEPTH_TAU, triples=True, product=False, depth_scaled=True)["triples"]
+        if not np.array_equal(oracle.sort_triples(rec), brute_depth_triples_numpy(A, B, 8, DEPTH_TAU)):
+            return True
     except Exception:
         return True
     return False
@@ -319,7 +357,7 @@ def test_pins_pass_on_oracle():
     assert not _pins_fail(oracle.lib())
 
 
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7])
 def test_pins_catch_planted_mistake(mutant):
     L = oracle.mutant_lib(mutant)
     assert L.oracle_mutant() == mutant
@@ -371,3 +409,31 @@ def test_values_oracle_uses_substituted_leaves():
     assert np.array_equal(twice, 2.0 * plain)
     blk = oracle.spamm_block(TA, TA, 1e-4, 3, 4, T2, TA)
     assert np.array_equal(blk, 2.0 * plain[48:64, 64:80])
+
+
+# ---------------------------------------------------------------- depth-scaled threshold
+
+def test_depth_pin_has_no_near_ties():
+    # the depth-scaled pin compares two summation orders of the norms: no tested product
+    # may lie within 1e-6 of its tier's threshold
+    _, gap = brute_depth_triples_numpy(rng_matrix(128, 25), rng_matrix(128, 26, decay=0.7), 8, DEPTH_TAU, True)
+    assert gap > 1e-6
+
+
+@pytest.mark.parametrize("seed,leaf,tau", [(41, 8, 1e-2), (42, 16, 1e-3), (43, 4, 3e-2)])
+def test_depth_scaled_error_is_rigorous(seed, leaf, tau):
+    # Sec. II: with tau^{k+1} = tau^k / 8 every dropped sub-product of tier k is below
+    # tau 8^-k and tier k holds at most 8^k of them, so ||C~ - AB||_F < (kmax + 1) tau
+    A, B = rng_matrix(160, seed, decay=0.85), rng_matrix(160, seed + 100, decay=0.85)
+    TA, TB = oracle.Tree(A, leaf), oracle.Tree(B, leaf)
+    r = oracle.spamm(TA, TB, tau, depth_scaled=True, stats=True)
+    err = np.linalg.norm(r["C"] - A @ B)
+    assert err < (TA.kmax + 1) * tau
+    # tier k's culled products each stay below its threshold: their sum bounds the error
+    assert err <= sum(r["stats"].culled_bound) * (1 + 1e-12)
+    # the depth-scaled survivors include the plain ones (every threshold is <= tau)
+    plain = oracle.sort_triples(oracle.spamm(TA, TB, tau, triples=True, product=False)["triples"])
+    deep = oracle.sort_triples(oracle.spamm(TA, TB, tau, triples=True, product=False, depth_scaled=True)["triples"])
+    assert len(deep) >= len(plain)
+    assert {tuple(t) for t in plain} <= {tuple(t) for t in deep}
+

@@ -63,3 +63,62 @@ def test_traces_stay_in_range():
     r = O.sp2_spectral(np.linalg.eigvalsh(H), n / 2, 30, lo, hi)
     assert all(0 <= t <= n for t in r["traces"])
     assert abs(r["traces"][-1] - n / 2) < abs(r["traces"][0] - n / 2) + 1e-9
+
+
+# ---------------------------------------------------------------- scheme (I): dropping
+
+def test_drop_blocks_closed_form():
+    # constant blocks c_IJ of side b have Frobenius norm |c_IJ| b: the filter keeps
+    # exactly the blocks with |c_IJ| b >= tau, on a ragged order (padding never counts)
+    b, nb = 4, 5
+    c = np.arange(1, nb * nb + 1, dtype=np.float64).reshape(nb, nb) / 10.0
+    P = np.kron(c, np.ones((b, b)))[:18, :18]       # 18 = 4 * 4 + 2: ragged last blocks
+    tau = 1.05 * b
+    Q, kept = O.drop_blocks(P, b, tau)
+    norms = np.zeros((nb, nb))
+    for I in range(nb):
+        for J in range(nb):
+            blk = P[I * b:(I + 1) * b, J * b:(J + 1) * b]
+            norms[I, J] = np.sqrt((blk ** 2).sum())
+            want = blk if norms[I, J] >= tau else 0.0 * blk
+            assert np.array_equal(Q[I * b:(I + 1) * b, J * b:(J + 1) * b], want)
+    assert kept == int((norms >= tau).sum())
+    # tau = 0 drops nothing; the filter is idempotent
+    assert np.array_equal(O.drop_blocks(P, b, 0.0)[0], P)
+    assert np.array_equal(O.drop_blocks(Q, b, tau)[0], Q)
+
+
+def test_block_products_brute_force():
+    r = np.random.default_rng(4)
+    b, nb = 3, 6
+    mask = r.random((nb, nb)) < 0.4
+    X = np.kron(mask.astype(float), np.ones((b, b))) * r.uniform(0.5, 1, (nb * b, nb * b))
+    want = sum(1 for i in range(nb) for j in range(i, nb) for k in range(nb) if mask[i, k] and mask[k, j])
+    assert O.block_products(X, b) == want
+    assert O.block_products(X, b, upper=False) == int((mask.astype(int) @ mask.astype(int)).sum())
+
+
+@pytest.mark.parametrize("side", [4, 6])
+def test_dropping_at_zero_is_dense_sp2(side):
+    # scheme (I) with tau = 0 drops nothing: the same loop as sp2_dense, bit for bit
+    H, (ip, ix, d), n = tb_dense(side)
+    lo, hi = O.gershgorin(ip, ix, d, n)
+    a = O.sp2_dense(H, n / 2, 20, lo, hi)
+    z = O.sp2_dense_dropping(H, n / 2, 20, lo, hi, 8, 0.0)
+    assert a["branches"] == z["branches"] and a["traces"] == z["traces"] and a["energy"] == z["energy"]
+    assert np.array_equal(a["X"], z["X"])
+
+
+def test_dropping_error_shrinks_with_tau():
+    # the dropped mass goes to zero with tau: the energy error of scheme (I) against
+    # dense SP2 falls, and every run keeps no more blocks than the run below it
+    H, (ip, ix, d), n = tb_dense(6)
+    lo, hi = O.gershgorin(ip, ix, d, n)
+    ref = O.sp2_dense(H, n / 2, 25, lo, hi)["energy"]
+    errs, prods = [], []
+    for tau in (1e-2, 1e-4, 1e-6):
+        r = O.sp2_dense_dropping(H, n / 2, 25, lo, hi, 8, tau)
+        errs.append(abs(r["energy"] - ref) / abs(ref))
+        prods.append(sum(r["leaf_products"]))
+    assert errs[2] < errs[0] and errs[2] < 1e-5
+    assert prods[0] <= prods[1] <= prods[2]
