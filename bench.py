@@ -632,12 +632,42 @@ def run_variants(args):
                 sp2.append({"tau": tau, "scheme": name, "energy_rel_err": abs(r["energy"] - e_ref) / abs(e_ref),
                             "mean_block_products": float(np.mean(r["leaf_products"])), "ms": r["ms"],
                             "branches_equal": r["branches"] == ref["branches"]})
+        # site orderings: Morton (the default) against the Hilbert curve, same systems
+        orders = []
+        for order in ("morton", "hilbert"):
+            ipo, ixo, do = W.tight_binding(16, seed=2, order=order)
+            for tau in (1e-3, 1e-4, 1e-5):
+                r = S.spamm_sp2(ctx, ipo, ixo, do, n / 2, 30, 64, S.SPAMM_FP64, tau)
+                orders.append({"system": "sp2 16^3 fp64", "order": order, "tau": tau,
+                               "energy_rel_err": abs(r["energy"] - e_ref) / abs(e_ref),
+                               "mean_block_products": float(np.mean(r["leaf_products"])), "ms": r["ms"]})
+        L = torch.from_numpy(W.physical_decay(16, 8, 1.2, 0.1, 3, 1)).cuda()
+        perm = torch.from_numpy(W.site_permutation(16, "hilbert")).cuda()
+        pb = (perm[:, None] * 8 + torch.arange(8, device=L.device)[None, :]).reshape(-1)
+        nl = L.shape[0]
+        for order in ("morton", "hilbert"):
+            M = L if order == "morton" else L.index_select(0, pb).index_select(1, pb)
+            t = S.spamm_tree_build(ctx, M, nl, 64, S.COPY_FLAG[S.SPAMM_BF16] | S.SPAMM_SYMMETRIC | S.SPAMM_NO_RIGHT)
+            for tau in (1e-6, 1e-4):
+                box = {}
+
+                def one():
+                    S.spamm_tree_update(t, M)
+                    box["c"] = S.spamm_multiply(ctx, t, t, tau, S.SPAMM_BF16, S.SPAMM_SYM_PRODUCT, box.get("c"))
+                ms = _events_ms(stream, one, 2, 1)
+                st = S.spamm_stats(box["c"])
+                orders.append({"system": "lattice n=32768 bf16", "order": order, "tau": tau, "ms_per_step": ms,
+                               "leaf_products": st["leaf_products"] + st["mirrored_products"]})
+                S.spamm_tree_free(box["c"])
+            S.spamm_tree_free(t)
+            del M
+        del L
     head = max(depth, key=lambda r: r["dense_equiv_gflops"] if r["threshold"] == "depth-scaled" else 0)
     _line({"workload": "threshold and dropping variants: algebraic-decay n=8192 leaf=64 BF16 symmetric product; "
                        "SP2 16^3 tight-binding n=4096 leaf=64 FP64 (SpAMM vs scheme (I))",
            "n": N, "leaf": 64, "precision": "bf16", "accumulate": "fp32", "l2": "inputs larger than L2"},
           head["dense_equiv_gflops"], head["ms_per_step"], "bf16",
-          {"depth_scaled": depth, "sp2_schemes": sp2, "sp2_reference_energy": e_ref,
+          {"depth_scaled": depth, "sp2_schemes": sp2, "orderings": orders, "sp2_reference_energy": e_ref,
            "sp2_reference_mean_block_products": float(np.mean(ref["leaf_products"])), "clocks": clk.summary()})
     S.spamm_ctx_destroy(ctx)
 

@@ -130,6 +130,73 @@ def morton3(x: np.ndarray, y: np.ndarray, z: np.ndarray, bits: int) -> np.ndarra
     return code
 
 
+def hilbert3(x: np.ndarray, y: np.ndarray, z: np.ndarray, bits: int) -> np.ndarray:
+    """Index of integer lattice coordinates along the 3-D Hilbert curve of 2^bits points
+    per side, by Skilling's transform ("Programming the Hilbert curve", AIP Conf. Proc.
+    707, 2004): the coordinates are turned into the curve's transposed form (undo the
+    excess work of each level, then Gray-code), whose bits, interleaved, are the index."""
+    X = [np.asarray(x, dtype=np.int64).copy(), np.asarray(y, dtype=np.int64).copy(),
+         np.asarray(z, dtype=np.int64).copy()]
+    X = list(np.broadcast_arrays(*X))
+    X = [a.copy() for a in X]
+    m = 1 << (bits - 1)
+    q = m
+    while q > 1:                       # inverse undo
+        p = q - 1
+        for i in range(3):
+            hit = (X[i] & q) != 0
+            X[0] = np.where(hit, X[0] ^ p, X[0])                 # invert the low bits
+            t = np.where(hit, 0, (X[0] ^ X[i]) & p)              # else exchange them
+            X[0] ^= t
+            X[i] ^= t
+        q >>= 1
+    for i in range(1, 3):              # Gray encode
+        X[i] ^= X[i - 1]
+    t = np.zeros_like(X[0])
+    q = m
+    while q > 1:
+        t = np.where((X[2] & q) != 0, t ^ (q - 1), t)
+        q >>= 1
+    for i in range(3):
+        X[i] ^= t
+    code = np.zeros_like(X[0])
+    for b in range(bits - 1, -1, -1):  # interleave: bit b of X[0], X[1], X[2]
+        for i in range(3):
+            code = (code << 1) | ((X[i] >> b) & 1)
+    return code
+
+
+def site_permutation(side: int, order: str = "morton") -> np.ndarray:
+    """perm[s] = Morton rank of the site that comes s-th in `order` ("morton": the
+    identity; "hilbert": the 3-D Hilbert curve over the smallest power-of-two cube
+    holding the lattice, restricted to its side^3 sites)."""
+    n = side ** 3
+    if order == "morton":
+        return np.arange(n, dtype=np.int64)
+    if order != "hilbert":
+        raise ValueError(order)
+    bits = max(1, int(math.ceil(math.log2(side))))
+    g = np.arange(side)
+    x, y, z = np.meshgrid(g, g, g, indexing="ij")
+    x, y, z = x.ravel(), y.ravel(), z.ravel()
+    mrank = np.argsort(np.argsort(morton3(x, y, z, bits), kind="stable"), kind="stable")
+    return mrank[np.argsort(hilbert3(x, y, z, bits), kind="stable")]
+
+
+def permute_csr(indptr, indices, data, perm):
+    """(indptr, indices, data) of P H P^T with (P H P^T)[s, t] = H[perm[s], perm[t]]."""
+    n = indptr.size - 1
+    inv = np.empty(n, dtype=np.int64)
+    inv[perm] = np.arange(n)
+    rows = np.repeat(np.arange(n), np.diff(indptr))
+    r, c = inv[rows], inv[indices]
+    o = np.lexsort((c, r))
+    r, c, v = r[o], c[o], np.asarray(data)[o]
+    ip = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(ip, r + 1, 1)
+    return np.cumsum(ip), c.astype(np.int64), v
+
+
 def lattice_sites(side: int, jitter: float, workload: int, seed: int) -> np.ndarray:
     """Site positions of a side^3 cubic lattice (spacing 1), jittered by
     U[-jitter, jitter] per coordinate, listed in Morton order: row s is the site
@@ -149,10 +216,16 @@ def lattice_sites(side: int, jitter: float, workload: int, seed: int) -> np.ndar
 
 
 def physical_decay(side: int = 16, per_site: int = 8, alpha: float = 1.2,
-                   jitter: float = 0.1, workload: int = 3, seed: int = 1) -> np.ndarray:
+                   jitter: float = 0.1, workload: int = 3, seed: int = 1, order: str = "morton") -> np.ndarray:
     """Symmetric a_ij = exp(-alpha * r_ij) * u_ij, u ~ N(0, 1) (Box-Muller on two
     uniform streams), r_ij the distance between the sites carrying basis
-    functions i and j; `per_site` consecutive basis functions share a site."""
+    functions i and j; `per_site` consecutive basis functions share a site. With
+    order="hilbert" the same matrix with its sites renumbered along the Hilbert curve."""
+    if order != "morton":
+        A = physical_decay(side, per_site, alpha, jitter, workload, seed)
+        perm = site_permutation(side, order)
+        pb = (perm[:, None] * per_site + np.arange(per_site)[None, :]).ravel()
+        return A[np.ix_(pb, pb)]
     pos = lattice_sites(side, jitter, workload, seed)
     n = pos.shape[0] * per_site
     k1 = stream_key(workload, seed, 0, 0)
@@ -193,11 +266,15 @@ def batched_matrix(m: int, n: int, lam: float, workload: int = 4, seed: int = 3)
 
 
 def tight_binding(side: int, workload: int = 5, seed: int = 2, hop: float = -1.0,
-                  onsite: float = 2.0):
+                  onsite: float = 2.0, order: str = "morton"):
     """Cubic tight-binding Hamiltonian on side^3 sites with open boundaries, sites
     in Morton order: nearest-neighbour hopping `hop`, on-site energies
     U[-onsite, onsite]. Returns (indptr, indices, data) of a CSR matrix with
-    sorted column indices."""
+    sorted column indices. With order="hilbert" the same Hamiltonian with its sites
+    renumbered along the Hilbert curve."""
+    if order != "morton":
+        ip, ix, d = tight_binding(side, workload, seed, hop, onsite)
+        return permute_csr(ip, ix, d, site_permutation(side, order))
     bits = max(1, int(math.ceil(math.log2(side))))
     g = np.arange(side)
     x, y, z = np.meshgrid(g, g, g, indexing="ij")

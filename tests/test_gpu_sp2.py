@@ -29,17 +29,18 @@ def ctx(S):
     S.spamm_ctx_destroy(c)
 
 
-def system(side):
-    ip, ix, d = W.tight_binding(side)
+def system(side, order="morton"):
+    ip, ix, d = W.tight_binding(side, order=order)
     n = side ** 3
     H = W.csr_to_dense(n, ip, ix, d)
     lo, hi = O.gershgorin(ip, ix, d, n)
     return (ip, ix, d), H, n, lo, hi
 
 
-@pytest.mark.parametrize("side,leaf", [(8, 16), (8, 32), (10, 64)])
-def test_sp2_fp64_tau0_matches_dense(S, ctx, side, leaf):
-    (ip, ix, d), H, n, lo, hi = system(side)
+@pytest.mark.parametrize("side,leaf,order", [(8, 16, "morton"), (8, 32, "morton"), (10, 64, "morton"),
+                                             (8, 32, "hilbert")])
+def test_sp2_fp64_tau0_matches_dense(S, ctx, side, leaf, order):
+    (ip, ix, d), H, n, lo, hi = system(side, order)
     ref = O.sp2_dense(H, n / 2, 30, lo, hi)
     g = S.spamm_sp2(ctx, ip, ix, d, n / 2, 30, leaf, S.SPAMM_FP64, 0.0)
     assert g["eps_min"] == pytest.approx(lo, rel=1e-15) and g["eps_max"] == pytest.approx(hi, rel=1e-15)
