@@ -270,8 +270,8 @@ def run_gpu(args):
     e0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 10))
     for _ in range(e2e_steps):
-        # the kernels read A from page-locked host memory; C goes back through the
-        # context's copy stream, overlapping the next step's input transfer
+        # A goes in on the context's input copy stream and C comes back on its output
+        # copy stream, so one step's output overlaps the next step's input
         S.spamm_tree_update(tA, A_np)
         tC = S.spamm_multiply(ctx, tA, tA, TAU, prec, SYMP, tC)
         S.spamm_tree_to_dense(tC, C_np, asynchronous=True)

@@ -207,8 +207,7 @@ spamm_status check_device_status(spamm_ctx ctx) {
 }
 
 // Device address of a page-locked, mapped host array (cudaMallocHost, cudaHostAlloc,
-// cudaHostRegister), through which kernels read or write it directly over the host
-// link; nullptr for pageable memory, which goes through the staging buffer.
+// cudaHostRegister); nullptr for pageable memory.
 void *mapped_view(const void *p) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -216,6 +215,34 @@ void *mapped_view(const void *p) {
     return nullptr;
   }
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Page-locked host input: copied on the context's input stream into the input staging
+// buffer once the kernel that read the previous input is done with it; the context
+// stream waits for the copy. The caller records stage_in_free after the reading kernel.
+spamm_status stage_pinned_input(spamm_ctx ctx, const double *A, size_t bytes, const double **src) {
+  if (!ctx->h2d) {
+    CK(cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking), "input copy stream");
+    CK(cudaEventCreateWithFlags(&ctx->h2d_done, cudaEventDisableTiming), "input copy event");
+    CK(cudaEventCreateWithFlags(&ctx->stage_in_free, cudaEventDisableTiming), "input copy event");
+  }
+  if (ctx->stage_in_bytes < bytes) {
+    CK(cudaStreamSynchronize(ctx->h2d), "input copy stream");
+    CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    if (ctx->stage_in) cudaFree(ctx->stage_in);
+    ctx->stage_in = nullptr;
+    ctx->stage_in_bytes = 0;
+    ctx->stage_in_used = false;
+    CK(cudaMalloc(&ctx->stage_in, bytes), "input staging buffer");
+    ctx->stage_in_bytes = bytes;
+  }
+  if (ctx->stage_in_used) CK(cudaStreamWaitEvent(ctx->h2d, ctx->stage_in_free, 0), "input copy wait");
+  CK(cudaMemcpyAsync(ctx->stage_in, A, bytes, cudaMemcpyHostToDevice, ctx->h2d), "host to device copy");
+  CK(cudaEventRecord(ctx->h2d_done, ctx->h2d), "input copy event");
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->h2d_done, 0), "input copy wait");
+  ctx->stage_in_used = true;
+  *src = (const double *)ctx->stage_in;
+  return SPAMM_OK;
 }
 
 spamm_status ensure_stage(spamm_ctx ctx, size_t bytes) {
@@ -289,6 +316,13 @@ spamm_status spamm_ctx_destroy(spamm_ctx ctx) {
     cudaStreamDestroy(ctx->d2h);
   }
   if (ctx->d2h_staged) cudaEventDestroy(ctx->d2h_staged);
+  if (ctx->h2d) {
+    cudaStreamSynchronize(ctx->h2d);
+    cudaStreamDestroy(ctx->h2d);
+  }
+  if (ctx->h2d_done) cudaEventDestroy(ctx->h2d_done);
+  if (ctx->stage_in_free) cudaEventDestroy(ctx->stage_in_free);
+  if (ctx->stage_in) cudaFree(ctx->stage_in);
   if (ctx->d2h_done) cudaEventDestroy(ctx->d2h_done);
   if (ctx->stage_out) cudaFree(ctx->stage_out);
   if (ctx->batch_copied) cudaEventDestroy(ctx->batch_copied);
@@ -340,9 +374,14 @@ spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t
   spamm_status st = alloc_tree(ctx, n, leaf, flags, &t);
   if (st != SPAMM_OK) return st;
   const double *src = A;
-  const double *mapped = (flags & SPAMM_HOST_INPUT) ? (const double *)mapped_view(A) : nullptr;
-  if (mapped) {
-    src = mapped;
+  const bool pinned = (flags & SPAMM_HOST_INPUT) && mapped_view(A) != nullptr;
+  if (pinned) {
+    st = stage_pinned_input(ctx, A, (size_t)n * n * sizeof(double), &src);
+    if (st != SPAMM_OK) {
+      free_tree_memory(t);
+      delete t;
+      return st;
+    }
   } else if (flags & SPAMM_HOST_INPUT) {
     st = ensure_stage(ctx, (size_t)n * n * sizeof(double));
     if (st != SPAMM_OK) {
@@ -360,6 +399,7 @@ spamm_status spamm_tree_build(spamm_ctx ctx, const double *A, int64_t n, int32_t
     src = (const double *)ctx->stage;
   }
   cudaError_t e = timed_tree_build(t, src, ctx->stream);
+  if (e == cudaSuccess && pinned) e = cudaEventRecord(ctx->stage_in_free, ctx->stream);
   if (e == cudaSuccess) e = launch_pyramid(t, ctx->stream);
   ctx->launches += 1 + pyramid_launches(t);
   if (e != cudaSuccess) {
@@ -378,9 +418,10 @@ spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags) {
   if (t->is_product) return fail(ctx, SPAMM_EINVAL, "tree_update: product trees cannot be rebuilt");
   if (flags & ~SPAMM_HOST_INPUT) return fail(ctx, SPAMM_EINVAL, "tree_update: only SPAMM_HOST_INPUT is accepted");
   const double *src = A;
-  const double *mapped = (flags & SPAMM_HOST_INPUT) ? (const double *)mapped_view(A) : nullptr;
-  if (mapped) {
-    src = mapped;
+  const bool pinned = (flags & SPAMM_HOST_INPUT) && mapped_view(A) != nullptr;
+  if (pinned) {
+    spamm_status st = stage_pinned_input(ctx, A, (size_t)t->n * t->n * sizeof(double), &src);
+    if (st != SPAMM_OK) return st;
   } else if (flags & SPAMM_HOST_INPUT) {
     spamm_status st = ensure_stage(ctx, (size_t)t->n * t->n * sizeof(double));
     if (st != SPAMM_OK) return st;
@@ -389,6 +430,7 @@ spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags) {
     src = (const double *)ctx->stage;
   }
   CK(timed_tree_build(t, src, ctx->stream), "tree_update: launch");
+  if (pinned) CK(cudaEventRecord(ctx->stage_in_free, ctx->stream), "tree_update: event");
   CK(launch_pyramid(t, ctx->stream), "tree_update: launch");
   ctx->launches += 1 + pyramid_launches(t);
   return SPAMM_OK;

@@ -76,6 +76,13 @@ struct spamm_ctx_s {
   cudaStream_t d2h = nullptr;
   cudaEvent_t d2h_staged = nullptr, d2h_done = nullptr;
   bool d2h_pending = false;
+  // page-locked host input: a staging buffer filled on a copy stream, so that the
+  // transfer of the next input overlaps the context's work on the previous one
+  void *stage_in = nullptr;
+  size_t stage_in_bytes = 0;
+  cudaStream_t h2d = nullptr;
+  cudaEvent_t h2d_done = nullptr, stage_in_free = nullptr;
+  bool stage_in_used = false;
   void *batch_host = nullptr, *batch_dev = nullptr;   // descriptor tables (pinned / device)
   cudaEvent_t batch_copied = nullptr;   // the last copy out of batch_host has run
   size_t batch_cap = 0;
