@@ -227,11 +227,10 @@ def test_fp64_symmetric_product(S, ctx, n, leaf, tau, kind):
 
 
 def test_page_locked_host_buffers(S, ctx):
-    """Host input in page-locked memory is read by the kernels directly over the host
-    link, pageable input goes through the staging buffer; dense output is written
-    synchronously or asynchronously (complete after spamm_sync). All give the same
-    tree, product and dense output, bit for bit, for a ragged order and both precision
-    classes."""
+    """Host input in page-locked memory goes in on the context's input copy stream,
+    pageable input through the staging buffer; dense output is written synchronously or
+    asynchronously (complete after spamm_sync). All give the same tree, product and
+    dense output, bit for bit, for a ragged order and both precision classes."""
     n = 1000
     A = W.algebraic_decay(n, 2, 3)
     A_pin = torch.from_numpy(A).pin_memory()
