@@ -466,8 +466,9 @@ def run_lattice(args):
 
 def run_batched(args):
     """256 symmetric exponential-decay matrices, n log-uniform in [512, 8192], tau = 1e-7,
-    BF16 leaves: one step builds the 256 trees and runs the batched product (culls on
-    side streams, one tensor-core launch per leaf size) from a CUDA graph."""
+    BF16 leaves: one step rebuilds the 256 trees (spread over the side streams) and runs
+    the batched product (culls on side streams, one tensor-core launch per leaf size)
+    from a CUDA graph."""
     import torch
     from paper_1011_3534_gb300 import spamm as S
     from paper_1011_3534_gb300 import workloads as W
@@ -489,8 +490,7 @@ def run_batched(args):
         box["C"] = S.spamm_multiply_batched(ctx, trees, trees, taus, prec, S.SPAMM_GRAPH, box.get("C"))
 
     def step():
-        for t, X in zip(trees, mats):
-            S.spamm_tree_update(t, X)
+        S.spamm_tree_update_batched(ctx, trees, mats)   # the 256 rebuilds side by side
         product_graph()
 
     def singles():

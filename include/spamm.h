@@ -225,6 +225,14 @@ SPAMM_API spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, i
 SPAMM_API spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *A, const spamm_tree *B,
                                               const double *tau, int32_t count, spamm_prec prec,
                                               int32_t flags, spamm_tree *C);
+/* spamm_tree_update of trees[p] from the device matrix A[p] (row-major FP64, the
+   tree's order) for p < count, the rebuilds spread over the context's side streams
+   (largest first, each to the least loaded stream) so that small ones run side by
+   side; the context stream waits for all of them. flags must be 0 (device inputs); the
+   builds are not timed (spamm_tree_build_ms). Errors: SPAMM_EINVAL (null or product
+   trees, trees of another context, flags), SPAMM_ECUDA. */
+SPAMM_API spamm_status spamm_tree_update_batched(spamm_ctx ctx, int32_t count, const spamm_tree *trees,
+                                                 const double *const *A, int32_t flags);
 
 /* Leaf-size autotuner: times the tree build plus the product A A at every leaf size the
    precision supports (64 and 128 for tensor-core precisions, 16..128 for SPAMM_FP64) on

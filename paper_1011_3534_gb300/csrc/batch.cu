@@ -140,6 +140,36 @@ static spamm_status batch_sequence(spamm_ctx ctx, const spamm_tree *A, const spa
   return join(ctx, used);
 }
 
+extern "C" spamm_status spamm_tree_update_batched(spamm_ctx ctx, int32_t count, const spamm_tree *trees,
+                                                  const double *const *A, int32_t flags) {
+  if (!ctx) return SPAMM_EINVAL;
+  if (count < 1 || !trees || !A) return bfail(ctx, SPAMM_EINVAL, "update_batched: bad arguments");
+  if (flags != 0) return bfail(ctx, SPAMM_EINVAL, "update_batched: flags must be 0 (device inputs)");
+  for (int p = 0; p < count; p++) {
+    if (!trees[p] || !A[p]) return bfail(ctx, SPAMM_EINVAL, "update_batched: null tree or input");
+    if (trees[p]->ctx != ctx) return bfail(ctx, SPAMM_EINVAL, "update_batched: a tree of another context");
+    if (trees[p]->is_product) return bfail(ctx, SPAMM_EINVAL, "update_batched: a product tree");
+  }
+  spamm_status st = ensure_side_streams(ctx);
+  if (st != SPAMM_OK) return st;
+  const int used = std::min(count, kSideStreams);
+  // largest first, each to the stream with the least work so far (elements)
+  std::vector<int> order(count);
+  for (int p = 0; p < count; p++) order[p] = p;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return trees[a]->n > trees[b]->n; });
+  std::vector<double> load(used, 0.0);
+  st = fork(ctx, used);
+  if (st != SPAMM_OK) return st;
+  for (int p : order) {
+    const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[q] += (double)trees[p]->n * (double)trees[p]->n;
+    BCK(launch_tree_build(trees[p], A[p], ctx->side[q]), "update_batched: launch");
+    BCK(launch_pyramid(trees[p], ctx->side[q]), "update_batched: launch");
+    ctx->launches += 1 + pyramid_launches(trees[p]);
+  }
+  return join(ctx, used);
+}
+
 extern "C" spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *A, const spamm_tree *B,
                                                const double *tau, int32_t count, spamm_prec prec, int32_t flags,
                                                spamm_tree *C) {

@@ -47,7 +47,7 @@ EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_er
            "spamm_mlp_adam_step", "spamm_mlp_adam_apply", "spamm_mlp_train", "spamm_features", "spamm_tau_select",
            "spamm_tree_distance", "spamm_sp2_begin", "spamm_sp2_step", "spamm_sp2_step_learned",
            "spamm_sp2_iterate", "spamm_sp2_end", "spamm_sp2_learned", "spamm_drop_blocks",
-           "spamm_sp2_step_drop", "spamm_sp2_dropping")
+           "spamm_sp2_step_drop", "spamm_sp2_dropping", "spamm_tree_update_batched")
 
 
 class SpammError(RuntimeError):
@@ -117,6 +117,7 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.spamm_sp2_dropping.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, _I32, ctypes.c_int, _D,
                                      ctypes.POINTER(Sp2ResultT)]
     L.spamm_drop_blocks.argtypes = [_P, _D, ctypes.POINTER(_I64)]
+    L.spamm_tree_update_batched.argtypes = [_P, _I32, _P, _P, _I32]
     L.spamm_sp2_step_learned.argtypes = [_P, _P, _D, _D, _D]
     L.spamm_sp2_iterate.argtypes = [_P, ctypes.POINTER(_P)]
     L.spamm_sp2_end.argtypes = [_P, ctypes.POINTER(Sp2ResultT)]
@@ -221,6 +222,16 @@ def spamm_tree_update(t: Tree, A) -> Tree:
     flags = SPAMM_HOST_INPUT if isinstance(A, np.ndarray) else 0
     t.ctx.check(LIB.spamm_tree_update(t.h, _ptr(A), flags), "spamm_tree_update")
     return t
+
+
+def spamm_tree_update_batched(ctx: Ctx, trees: list, inputs: list):
+    """Rebuild trees[p] from the torch CUDA tensors inputs[p], the rebuilds spread over
+    the context's side streams."""
+    count = len(trees)
+    pt = (ctypes.c_void_p * count)(*[t.h for t in trees])
+    pa = (ctypes.c_void_p * count)(*[_ptr(a) for a in inputs])
+    ctx.check(LIB.spamm_tree_update_batched(ctx.h, count, ctypes.addressof(pt), ctypes.addressof(pa), 0),
+              "spamm_tree_update_batched")
 
 
 def spamm_tree_build_ms(t: Tree) -> float:

@@ -94,3 +94,29 @@ def test_tuner_picks_a_supported_leaf(S, ctx):
         assert (leaf2, ms2) == (leaf, ms)   # cached
         leaf3, _ = S.spamm_tune_leaf(ctx, d, 2048, 1e-7, S.SPAMM_FP64, S.SPAMM_SYMMETRIC)
         assert leaf3 in (16, 32, 64, 128)
+
+
+def test_batched_update_equals_single_updates(S, ctx):
+    # the rebuilds spread over the side streams give the same trees as one by one: the
+    # same norms on every tier and the same products, bit for bit
+    mats = batch_inputs(10, seed=5)
+    prec = S.SPAMM_BF16
+    leaves = [64 if i % 2 else 128 for i in range(len(mats))]
+    a = build(S, ctx, mats, leaves, prec)
+    b = build(S, ctx, mats, leaves, prec)
+    with torch.cuda.stream(ctx.stream):
+        dev = [torch.from_numpy(2.0 * M).cuda() for M in mats]
+        for t, X in zip(a, dev):
+            S.spamm_tree_update(t, X)
+        S.spamm_tree_update_batched(ctx, b, dev)
+    for ta, tb in zip(a, b):
+        for l in range(ta.kmax + 1):
+            assert np.array_equal(S.spamm_tree_norms(ta, l), S.spamm_tree_norms(tb, l))
+        ca = S.spamm_multiply(ctx, ta, ta, 1e-6, prec)
+        cb = S.spamm_multiply(ctx, tb, tb, 1e-6, prec)
+        assert np.array_equal(S.spamm_tree_to_dense(ca), S.spamm_tree_to_dense(cb))
+        S.spamm_tree_free(ca)
+        S.spamm_tree_free(cb)
+    for t in a + b:
+        S.spamm_tree_free(t)
+
