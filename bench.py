@@ -521,7 +521,7 @@ def run_sp2(args):
     FP64 SP2; dense FP64 SP2 at this size is 2e15 flop, about half an hour on this
     GPU's FP64 pipe). The fixed conservative tau is the largest of a half-decade grid
     whose split-TF32 SP2 meets the 1e-6 target against that reference; plain FP64
-    SpAMM runs at it (the method without the controller, and its judge). The controller
+    SpAMM runs at it (the method without the controller, and its arbiter). The controller
     is trained and its budget calibrated on a 16^3 system (seed 7) and applied here
     without further calibration."""
     import torch
@@ -564,7 +564,7 @@ def run_sp2(args):
            "energy_rel_err_vs_reference": {"fp64_fixed_tau": err(fixed64), "tf32x3_fixed_tau": err(fixed_tc),
                                            "tf32x3_learned_tau": err(learned),
                                            "tf32x3_grid": {f"{t:.2e}": err(r) for t, r in grid.items()}},
-           "judge_rel_diff_learned_vs_fp64_fixed_tau": abs(learned["energy"] - fixed64["energy"]) / abs(fixed64["energy"]),
+           "arbiter_rel_diff_learned_vs_fp64_fixed_tau": abs(learned["energy"] - fixed64["energy"]) / abs(fixed64["energy"]),
            "branches_equal_to_reference": {"fp64_fixed_tau": fixed64["branches"] == ref["branches"],
                                            "tf32x3_learned_tau": learned["branches"] == ref["branches"]},
            "leaf_products": {"fp64_fixed_tau": lp(fixed64), "tf32x3_fixed_tau": lp(fixed_tc),

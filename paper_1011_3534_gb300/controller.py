@@ -9,7 +9,7 @@ Workflow, all on the GPU through the C ABI:
               library's (spamm_features).
   train()     fits the library's network (spamm_mlp_*) to (features, label) pairs.
   conservative_tau()  the largest tau of a half-decade grid whose plain FP64 SP2 energy
-              meets a relative error target: the controller's fallback and judge.
+              meets a relative error target: the controller's fallback and arbiter.
   calibrate_budget()  the largest per-product error budget of a half-decade grid whose
               learned-tau SP2 energy meets the target on a training system, divided by
               a safety margin (default one decade): near-tie branch decisions of the

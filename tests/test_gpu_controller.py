@@ -11,7 +11,7 @@ runs, without further calibration, on the test system (seed 2).
 
 The method without the network is the fixed conservative tau: the largest tau on a
 half-decade grid whose plain FP64 SP2 meets the target on the test system itself. It is
-also the judge: the learned run's energy must lie within the target of the fixed-tau
+also the arbiter: the learned run's energy must lie within the target of the fixed-tau
 FP64 energy, and of the reference energy (FP64 SpAMM at tau = 0, which equals dense SP2;
 see test_gpu_sp2.py).
 
@@ -75,14 +75,14 @@ def test_learned_tau_against_fixed_conservative_tau(S, ctx):
     fixed_tc = S.spamm_sp2(ctx, *test_csr, occ, STEPS, LEAF, S.SPAMM_TF32X3, tau_c)
     learned = S.spamm_sp2_learned(ctx, *test_csr, occ, STEPS, LEAF, S.SPAMM_TF32X3, m, budget, tau_lo, tau_hi)
     err_ref = CT.energy_error(learned, e_ref)
-    err_judge = CT.energy_error(learned, fixed64["energy"])
+    err_arb = CT.energy_error(learned, fixed64["energy"])
     lp = lambda r: sum(r["leaf_products"])
     print(f"fixed conservative tau {tau_c:.2e}: FP64 {fixed64['ms']:.1f} ms, err {CT.energy_error(fixed64, e_ref):.2e}; "
           f"TF32X3 {fixed_tc['ms']:.1f} ms, {lp(fixed_tc)} leaf products, err {CT.energy_error(fixed_tc, e_ref):.2e}")
     print(f"learned tau, budget {budget:.2e}: TF32X3 {learned['ms']:.1f} ms, {lp(learned)} leaf products, "
-          f"err {err_ref:.2e} (vs judge {err_judge:.2e}); taus {['%.0e' % t for t in learned['taus']]}")
+          f"err {err_ref:.2e} (vs arbiter {err_arb:.2e}); taus {['%.0e' % t for t in learned['taus']]}")
     print(f"gain over the fixed conservative tau at TF32X3: leaf products x{lp(fixed_tc) / lp(learned):.3f}, "
           f"time x{fixed_tc['ms'] / learned['ms']:.3f}; over FP64 at that tau: time x{fixed64['ms'] / learned['ms']:.1f}")
-    assert err_ref <= TARGET and err_judge <= TARGET
+    assert err_ref <= TARGET and err_arb <= TARGET
     assert learned["ms"] < fixed64["ms"]
     m.free()
