@@ -82,6 +82,9 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()   # the sampler is live before the timed region starts
+            while not self.lines and time.time() - t0 < 3.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -92,6 +95,10 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc:
+            k = len(self.lines)   # and takes one more sample after a timed region shorter than its period
+            t0 = time.time()
+            while len(self.lines) <= k and time.time() - t0 < 1.0:
+                time.sleep(0.01)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -437,7 +444,7 @@ def run_lattice(args):
                     def one():
                         S.spamm_tree_update(t, A)
                         box["c"] = S.spamm_multiply(ctx, t, t, tau, p, S.SPAMM_SYM_PRODUCT, box.get("c"))
-                    ms = _events_ms(stream, one, 1 if name == "fp64" else args.steps, 1 if name == "fp64" else 3)
+                    ms = _events_ms(stream, one, 1 if name == "fp64" else min(args.steps, 5), 1 if name == "fp64" else 3)
                     st = S.spamm_stats(box["c"])
                     Cd = torch.empty((n, n), dtype=torch.float64, device=A.device)
                     S.spamm_tree_to_dense(box["c"], Cd)
@@ -497,9 +504,10 @@ def run_batched(args):
         box["C1"] = [S.spamm_multiply(ctx, t, t, tau, prec, 0, c) for t, c in zip(trees, box.get("C1") or [None] * len(trees))]
 
     with ClockSampler(0) as clk:
-        ms_step = _events_ms(stream, step, args.steps, args.warmup)
-        ms_graph = _events_ms(stream, product_graph, args.steps, args.warmup)
-        ms_single = _events_ms(stream, singles, args.steps, args.warmup)
+        k = min(args.steps, 20)
+        ms_step = _events_ms(stream, step, k, args.warmup)
+        ms_graph = _events_ms(stream, product_graph, k, args.warmup)
+        ms_single = _events_ms(stream, singles, k, args.warmup)
     lp = sum(S.spamm_stats(c)["leaf_products"] for c in box["C"])
     _line({"workload": "256 exponential-decay matrices, n log-uniform [512, 8192], lambda U[0.7, 0.95], seed 3",
            "matrices": len(shapes), "sum_n2": int(sum(nm * nm for nm, _ in shapes)), "leaf": leaf, "tau": tau,
@@ -606,7 +614,7 @@ def run_variants(args):
                 def one():
                     S.spamm_tree_update(t, A)
                     box["c"] = S.spamm_multiply(ctx, t, t, tau, S.SPAMM_BF16, S.SPAMM_SYM_PRODUCT | flags, box.get("c"))
-                ms = _events_ms(stream, one, args.steps, 3)
+                ms = _events_ms(stream, one, min(args.steps, 20), 3)
                 st = S.spamm_stats(box["c"])
                 Cd = torch.empty_like(exact)
                 S.spamm_tree_to_dense(box["c"], Cd)
@@ -675,13 +683,15 @@ def run_variants(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--config", default="alg8192",
                     choices=["alg8192", "lattice32768", "batched256", "sp2-32768", "variants"])
     args = ap.parse_args()
+    if args.steps is None:   # the headline: a timed region of about 0.6 s; the oracle: 20 products
+        args.steps = 20 if (args.impl == "reference" or args.config != "alg8192") else 2000
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
