@@ -62,6 +62,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, device="cpu") -> float:
+    """The largest of every rank's value (a time: the job ends with its slowest replica);
+    the value itself outside a multi-rank process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job(per_replica_rate: float, ws: int) -> float:
+    """Weak scaling, replicas only: every rank runs the whole workload, so the job's
+    throughput is the replicas' count times the rate of the slowest one."""
+    return per_replica_rate * ws
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -209,11 +227,7 @@ def run_gpu(args):
         t1.record(stream)
         torch.cuda.synchronize()
         launches = S.spamm_kernel_launches(ctx) - l0
-        ms_total = t0.elapsed_time(t1)
-        if ws > 1:
-            tt = torch.tensor([ms_total], device=dA.device)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms_total = float(tt.item())
+        ms_total = max_over_ranks(t0.elapsed_time(t1), dA.device)
         ms_build = ms_mult = ms_k1 = None
         if phases:
             ms_k1 = S.spamm_tree_build_ms(tA)   # mean over the timed steps' K1 launches
@@ -234,7 +248,7 @@ def run_gpu(args):
     st = r["stats"]
     ms = r["ms"]
     dense_gflops = 2.0 * N ** 3 / (ms * 1e-3) / 1e9
-    value = dense_gflops * ws
+    value = whole_job(dense_gflops, ws)
     # phase times inside the timed region (events on the library's stream)
     ms_leaf = st["ms_leaf"]
     ms_cull = st["ms_cull"]
@@ -285,12 +299,9 @@ def run_gpu(args):
     S.spamm_sync(ctx)                        # every step's C is on the host
     e2e_ms = (time.perf_counter() - e0) * 1e3 / e2e_steps
     S.spamm_tree_free(tA)
-    if ws > 1:
-        tt = torch.tensor([e2e_ms], device=dA.device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, dA.device)
     S.spamm_tree_free(tC)
-    e2e = {"value": 2.0 * N ** 3 / (e2e_ms * 1e-3) / 1e9 * ws, "unit": "GFLOP/s",
+    e2e = {"value": whole_job(2.0 * N ** 3 / (e2e_ms * 1e-3) / 1e9, ws), "unit": "GFLOP/s",
            "h2d_bytes_per_step": 8 * N * N, "d2h_bytes_per_step": 8 * N * N, "ms_per_step": e2e_ms}
 
     # ---- precision and tau sweep (error vs FP64 SpAMM on the GPU)

@@ -1,0 +1,52 @@
+"""The benchmark's multi-rank path on CPU (gloo, world size 2): replicas only, no data
+collective. The job time is the slowest rank's, the job throughput the replicas' count
+times that rate, and under torchrun only rank 0 runs and prints the reference arm."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+torch = pytest.importorskip("torch")
+
+
+def _worker(rank, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE="2")
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    ms = bench.max_over_ranks(10.0 + 5.0 * rank)        # rank 1 is the slow replica
+    dist.barrier()
+    out[rank] = (ms, bench.whole_job(100.0, dist.get_world_size()))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_whole_job_gloo():
+    import torch.multiprocessing as mp
+    port = 29500 + os.getpid() % 1000
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(port, out), nprocs=2, join=True)
+        assert out[0] == out[1] == (15.0, 200.0)
+
+
+def test_single_process_reduction_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5 and bench.whole_job(7.0, 1) == 7.0
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    env = dict(os.environ, OMP_NUM_THREADS="4")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(30500 + os.getpid() % 1000),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1"]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == 0
