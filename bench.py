@@ -224,6 +224,7 @@ def run_gpu(args):
         t0.record(stream)
         for s in range(steps):
             tC = step(prec, tA, tC, tau, evs[s] if phases else None)
+        S.spamm_sync(ctx)   # the last product's norm pyramid (on its own stream) is inside the region
         t1.record(stream)
         torch.cuda.synchronize()
         launches = S.spamm_kernel_launches(ctx) - l0

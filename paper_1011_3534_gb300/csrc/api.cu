@@ -190,6 +190,8 @@ spamm_status alloc_product_workspace(spamm_ctx ctx, spamm_tree C) {
 }
 
 spamm_status check_device_status(spamm_ctx ctx) {
+  spamm_status sst = settle(ctx);
+  if (sst != SPAMM_OK) return sst;
   if (ctx->d2h_pending) {   // an asynchronous dense output is part of the context's work
     CK(cudaStreamWaitEvent(ctx->stream, ctx->d2h_done, 0), "output copy wait");
     ctx->d2h_pending = false;
@@ -260,6 +262,14 @@ spamm_status ensure_stage(spamm_ctx ctx, size_t bytes) {
 
 }  // namespace
 
+spamm_status settle(spamm_ctx ctx) {
+  if (!ctx->pyr_pending) return SPAMM_OK;
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->pyr_done, 0), "pyramid wait");
+  ctx->pyr_pending = false;
+  return SPAMM_OK;
+}
+
+
 
 static int32_t COPY_FLAG_OF(spamm_prec p) {
   switch (p) {
@@ -297,7 +307,14 @@ spamm_status spamm_ctx_create(int device, void *cuda_stream, int32_t timing, spa
 
 spamm_status spamm_ctx_destroy(spamm_ctx ctx) {
   if (!ctx) return SPAMM_EINVAL;
+  settle(ctx);
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->pyr_stream) {
+    cudaStreamSynchronize(ctx->pyr_stream);
+    cudaStreamDestroy(ctx->pyr_stream);
+  }
+  if (ctx->pyr_ready) cudaEventDestroy(ctx->pyr_ready);
+  if (ctx->pyr_done) cudaEventDestroy(ctx->pyr_done);
   for (BatchGraph &g : ctx->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.tau_host) cudaFreeHost(g.tau_host);
@@ -438,6 +455,7 @@ spamm_status spamm_tree_update(spamm_tree t, const double *A, int32_t flags) {
 
 spamm_status spamm_tree_free(spamm_tree t) {
   if (!t) return SPAMM_EINVAL;
+  settle(t->ctx);
   cudaStreamSynchronize(t->ctx->stream);
   free_tree_memory(t);
   delete t;
@@ -465,6 +483,7 @@ spamm_status spamm_tree_build_ms(spamm_tree t, float *ms) {
 spamm_status spamm_drop_blocks(spamm_tree t, double tau, int64_t *kept) {
   if (!t) return SPAMM_EINVAL;
   spamm_ctx ctx = t->ctx;
+  if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(ctx, SPAMM_EINVAL, "drop_blocks: tau must be finite and >= 0");
   if (kept) {
     if (!ctx->dev_count) CK(cudaMalloc(&ctx->dev_count, sizeof(unsigned long long)), "drop_blocks: counter");
@@ -496,6 +515,7 @@ spamm_status spamm_tree_info(spamm_tree t, int64_t *n, int32_t *leaf, int32_t *n
 spamm_status spamm_tree_norms(spamm_tree t, int32_t level, double *out) {
   if (!t) return SPAMM_EINVAL;
   spamm_ctx ctx = t->ctx;
+  if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!out || level < 0 || level > t->kmax)
     return fail(ctx, SPAMM_EINVAL, "tree_norms: level %d outside 0..%d", level, t->kmax);
   const size_t cnt = (size_t)1 << (2 * level);
@@ -507,6 +527,7 @@ spamm_status spamm_tree_norms(spamm_tree t, int32_t level, double *out) {
 spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host) {
   if (!t) return SPAMM_EINVAL;
   spamm_ctx ctx = t->ctx;
+  if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!out) return fail(ctx, SPAMM_EINVAL, "tree_to_dense: null output");
   if (!t->copy[CK_F64] && !t->copy[CK_F32])
     return fail(ctx, SPAMM_EINVAL, "tree_to_dense: the tree keeps no FP64/FP32 tiles (SPAMM_KEEP_FP64)");
@@ -547,11 +568,11 @@ spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host)
 }
 
 spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau, const double *tau_dev,
-                           spamm_prec prec, int32_t flags, spamm_tree *C);
+                           spamm_prec prec, int32_t flags, spamm_tree *C, bool async_pyramid = false);
 
 spamm_status spamm_multiply(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau,
                             spamm_prec prec, int32_t flags, spamm_tree *C) {
-  return multiply_impl(ctx, A, B, tau, nullptr, prec, flags, C);
+  return multiply_impl(ctx, A, B, tau, nullptr, prec, flags, C, true);
 }
 
 }  // extern "C"
@@ -634,9 +655,11 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
 }
 
 spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau, const double *tau_dev,
-                           spamm_prec prec, int32_t flags, spamm_tree *C) {
+                           spamm_prec prec, int32_t flags, spamm_tree *C, bool async_pyramid) {
   if (!ctx) return SPAMM_EINVAL;
-  spamm_status pst = product_prepare(ctx, A, B, tau, prec, flags, C);
+  spamm_status pst = settle(ctx);
+  if (pst != SPAMM_OK) return pst;
+  pst = product_prepare(ctx, A, B, tau, prec, flags, C);
   if (pst != SPAMM_OK) return pst;
   spamm_tree Ct = *C;
   const bool tc = prec != SPAMM_FP64;
@@ -657,7 +680,20 @@ spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau
     CK(launch_mirror(Ct, s), "multiply: mirror launch");
     launches++;
   }
-  CK(launch_pyramid(Ct, s), "multiply: pyramid launch");
+  if (async_pyramid) {
+    if (!ctx->pyr_stream) {
+      CK(cudaStreamCreateWithFlags(&ctx->pyr_stream, cudaStreamNonBlocking), "multiply: pyramid stream");
+      CK(cudaEventCreateWithFlags(&ctx->pyr_ready, cudaEventDisableTiming), "multiply: pyramid event");
+      CK(cudaEventCreateWithFlags(&ctx->pyr_done, cudaEventDisableTiming), "multiply: pyramid event");
+    }
+    CK(cudaEventRecord(ctx->pyr_ready, s), "multiply: pyramid event");
+    CK(cudaStreamWaitEvent(ctx->pyr_stream, ctx->pyr_ready, 0), "multiply: pyramid wait");
+    CK(launch_pyramid(Ct, ctx->pyr_stream), "multiply: pyramid launch");
+    CK(cudaEventRecord(ctx->pyr_done, ctx->pyr_stream), "multiply: pyramid event");
+    ctx->pyr_pending = true;
+  } else {
+    CK(launch_pyramid(Ct, s), "multiply: pyramid launch");
+  }
   launches += pyramid_launches(Ct);
   bool want[CK_COUNT];
   wanted_copies(cflags & kTreeFlags, want);
@@ -676,6 +712,7 @@ extern "C" {
 spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out) {
   if (!C) return SPAMM_EINVAL;
   spamm_ctx ctx = C->ctx;
+  if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!out) return fail(ctx, SPAMM_EINVAL, "stats: null output");
   if (!C->is_product) return fail(ctx, SPAMM_EINVAL, "stats: not a product tree");
   if (!C->stats_valid) {
@@ -721,6 +758,7 @@ spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out) {
 }
 
 spamm_status spamm_triples(spamm_tree C, uint32_t *ijk, int64_t cap, int64_t *count) {
+  if (C && settle(C->ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!C) return SPAMM_EINVAL;
   spamm_ctx ctx = C->ctx;
   if (!count) return fail(ctx, SPAMM_EINVAL, "triples: null count");

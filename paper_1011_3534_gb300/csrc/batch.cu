@@ -174,6 +174,7 @@ extern "C" spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *
                                                const double *tau, int32_t count, spamm_prec prec, int32_t flags,
                                                spamm_tree *C) {
   if (!ctx) return SPAMM_EINVAL;
+  if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!A || !B || !tau || !C || count < 1) return bfail(ctx, SPAMM_EINVAL, "batched: bad arguments");
   if (flags & ~(kLowCopyFlags | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT | SPAMM_GRAPH)) return bfail(ctx, SPAMM_EINVAL, "batched: unknown flag bits");
   if (flags & kLowCopyFlags) return bfail(ctx, SPAMM_EUNSUPPORTED, "batched: leaf copies of the products are not produced");
@@ -261,6 +262,7 @@ extern "C" spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *
 extern "C" spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t n, double tau, spamm_prec prec,
                                         int32_t flags, int32_t *leaf_out, double *ms_out) {
   if (!ctx) return SPAMM_EINVAL;
+  if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!A || !leaf_out || n < 1 || !(tau >= 0.0)) return bfail(ctx, SPAMM_EINVAL, "tune: bad arguments");
   int lg = 0;
   while ((int64_t(1) << lg) < n) lg++;

@@ -78,6 +78,12 @@ struct spamm_ctx_s {
   bool d2h_pending = false;
   // page-locked host input: a staging buffer filled on a copy stream, so that the
   // transfer of the next input overlaps the context's work on the previous one
+  // the norm pyramid of a spamm_multiply product runs on its own stream, overlapping
+  // whatever the caller queues next that does not read the product (the next operand
+  // rebuild, say); every call that may read a product waits for it first (settle)
+  cudaStream_t pyr_stream = nullptr;
+  cudaEvent_t pyr_ready = nullptr, pyr_done = nullptr;
+  bool pyr_pending = false;
   void *stage_in = nullptr;
   size_t stage_in_bytes = 0;
   cudaStream_t h2d = nullptr;
@@ -203,6 +209,8 @@ cudaError_t launch_tile_convert(spamm_tree t, cudaStream_t s);
 int64_t cull_look_words(int kmax);
 int64_t cull_bound_words(int kmax, int64_t *offsets);
 int pyramid_launches(spamm_tree t);
+// The context stream waits for a product's pyramid still running on its own stream.
+spamm_status settle(spamm_ctx ctx);
 cudaError_t sp2_x0(int64_t n, const int64_t *indptr, const int64_t *indices, const double *data, double emin,
                    double emax, double *X, cudaStream_t s);
 size_t sp2_record_bytes();

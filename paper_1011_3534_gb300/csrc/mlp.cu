@@ -587,6 +587,7 @@ int mlp_inputs(spamm_mlp mm) { return mm->net.F; }
 extern "C" {
 
 spamm_status spamm_features(spamm_tree A, spamm_tree B, double tau, float *out) {
+  if (A && settle(A->ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!A || !B || !out || !(tau > 0.0) || !std::isfinite(tau)) return SPAMM_EINVAL;
   spamm_ctx ctx = A->ctx;
   if (A->n != B->n || A->b != B->b) return mfail(ctx, SPAMM_EINVAL, "features: shapes differ");
@@ -615,6 +616,7 @@ spamm_status spamm_features(spamm_tree A, spamm_tree B, double tau, float *out) 
 
 spamm_status spamm_tau_select(spamm_mlp mm, spamm_tree A, spamm_tree B, double err_budget, double tau_min,
                               double tau_max, double *tau_out) {
+  if (A && settle(A->ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!mm || !A || !B || !tau_out || !(err_budget > 0.0) || !(tau_min > 0.0) || !(tau_max >= tau_min) ||
       !std::isfinite(tau_max))
     return SPAMM_EINVAL;
@@ -707,6 +709,7 @@ cudaError_t dist_y(const TX *X, spamm_tree x, spamm_tree y, double *part, cudaSt
 }  // namespace
 
 extern "C" spamm_status spamm_tree_distance(spamm_tree X, spamm_tree Y, double *diff_fro, double *ref_fro) {
+  if (X && settle(X->ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!X || !Y || !diff_fro || !ref_fro) return SPAMM_EINVAL;
   spamm_ctx ctx = X->ctx;
   if (X->n != Y->n || X->b != Y->b) return mfail(ctx, SPAMM_EINVAL, "tree_distance: shapes differ");
