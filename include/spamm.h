@@ -198,6 +198,9 @@ SPAMM_API spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t ou
    needs (SPAMM_KEEP_FP64 for SPAMM_FP64, SPAMM_COPY_<prec> otherwise, and for B
    either SPAMM_SYMMETRIC or no SPAMM_NO_RIGHT).
    Supported: SPAMM_FP64 for every leaf; tensor-core precisions for leaf 64 and 128.
+   The norm pyramid of C runs on an internal stream of the context, overlapping later
+   calls that do not read C (spamm_tree_update of an operand, say); every call that
+   may read a product (including spamm_sync) first makes the context stream wait for it.
    Errors: SPAMM_EINVAL, SPAMM_EUNSUPPORTED, SPAMM_ENOMEM, SPAMM_ECUDA. */
 SPAMM_API spamm_status spamm_multiply(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau,
                             spamm_prec prec, int32_t flags, spamm_tree *C);
