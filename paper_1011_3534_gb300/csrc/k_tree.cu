@@ -38,7 +38,7 @@ struct BuildArgs {
 // leaf copies are rounded in integer arithmetic on the FP64 bit pattern.
 template <int B>
 struct BuildCfg {
-  // threads per CTA: a 64 x 64 leaf gets 128 threads, so that each streams four rounds
+  // threads per CTA: a 64 x 64 leaf gets 64 threads, so that each streams eight rounds
   // and the leaf's coordinates stay CTA-uniform
   static constexpr int T = B == 64 ? 64 : 256;
   static constexpr int PAIRS = B * B / 2;          // element pairs per leaf
