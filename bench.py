@@ -355,6 +355,37 @@ def run_gpu(args):
 
 # ------------------------------------------------------------------ CPU oracle
 
+_ARM_PARTS = {0xd0c: "Neoverse-N1", 0xd40: "Neoverse-V1", 0xd49: "Neoverse-N2", 0xd4f: "Neoverse-V2",
+              0xd8e: "Neoverse-N3", 0xd84: "Neoverse-V3"}
+
+
+def host_cpu(cpuinfo_text=None):
+    """The host CPU model: the x86 'model name' line of /proc/cpuinfo, or the Arm
+    implementer and part numbers (named for the Neoverse cores), else the machine type."""
+    import platform
+    if cpuinfo_text is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                cpuinfo_text = f.read()
+        except OSError:
+            cpuinfo_text = ""
+    fields = {}
+    for line in cpuinfo_text.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip().lower(), v.strip())
+    if fields.get("model name"):
+        return fields["model name"]
+    if "cpu part" in fields:
+        try:
+            impl, part = int(fields.get("cpu implementer", "0"), 16), int(fields["cpu part"], 16)
+        except ValueError:
+            return platform.machine()
+        name = _ARM_PARTS.get(part, "") if impl == 0x41 else ""
+        return f"{platform.machine()} implementer 0x{impl:02x} part 0x{part:03x}" + (f" ({name})" if name else "")
+    return platform.machine()
+
+
 def cpu_baseline(A_host, quick=False, budget_s=20.0):
     """The CPU oracle (FP64 recursive SpAMM, OpenMP over output quadrants) on the host
     cores: quadtree build + product at tau = 1e-8 on the full n = 8192 matrix, repeated
@@ -373,7 +404,7 @@ def cpu_baseline(A_host, quick=False, budget_s=20.0):
             oracle.spamm(TB, TB, TAU, threads=cores)
             dt = min(dt, time.perf_counter() - t1)
             reps += 1
-    return {"value": 2.0 * N ** 3 / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+    return {"value": 2.0 * N ** 3 / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "cpu": host_cpu(), "kind": "oracle",
             "sample": f"full n={N} product at tau={TAU} (tree build + Eq. 4 recursion, FP64), best of {reps}",
             "seconds": dt}
 
@@ -401,7 +432,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "n": N, "leaf": LEAF, "tau": TAU, "precision": "fp64"},
-            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": cores, "cpu": host_cpu(), "kind": "oracle",
                              "sample": f"full n={N} product at tau={TAU} per step"},
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
