@@ -162,9 +162,34 @@ def _ptr(x) -> int:
     raise TypeError(type(x))
 
 
+def _matrix(x, n: int, what: str, device: int | None = None, writable: bool = False) -> tuple[int, bool]:
+    """Address of an n x n row-major FP64 matrix and whether it is in host memory: a
+    numpy array or torch CPU tensor (host, pageable or page-locked) or a torch CUDA
+    tensor on the context's device. Any other type, dtype, size or layout raises here,
+    before the library sees the pointer."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous or (n >= 1 and x.size != n * n):
+            raise ValueError(f"{what}: need a C-contiguous float64 array of {n} x {n} elements, "
+                             f"got {x.dtype} {x.shape}")
+        if writable and not x.flags.writeable:
+            raise ValueError(f"{what}: the output array is read-only")
+        return x.ctypes.data, True
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if str(x.dtype) != "torch.float64" or not x.is_contiguous() or (n >= 1 and x.numel() != n * n):
+            raise ValueError(f"{what}: need a contiguous torch.float64 tensor of {n} x {n} elements, "
+                             f"got {x.dtype} {tuple(x.shape)}")
+        if not x.is_cuda:
+            return x.data_ptr(), True
+        if device is not None and x.device.index is not None and x.device.index != device:
+            raise ValueError(f"{what}: tensor on cuda:{x.device.index}, context on cuda:{device}")
+        return x.data_ptr(), False
+    raise TypeError(f"{what}: expected a numpy array or a torch CUDA tensor, got {type(x).__name__}")
+
+
 class Ctx:
-    def __init__(self, handle: int):
+    def __init__(self, handle: int, device: int | None = None):
         self.h = handle
+        self.device = device
 
     def check(self, status: int, what: str = ""):
         if status != SPAMM_OK:
@@ -186,7 +211,7 @@ def spamm_ctx_create(device: int = 0, stream=None, timing: bool = False) -> Ctx:
     rc = LIB.spamm_ctx_create(device, s, 1 if timing else 0, ctypes.byref(h))
     if rc != SPAMM_OK:
         raise SpammError(rc, "spamm_ctx_create failed (is a CUDA device present?)")
-    return Ctx(h.value)
+    return Ctx(h.value, device)
 
 
 def spamm_ctx_destroy(ctx: Ctx):
@@ -209,18 +234,18 @@ def spamm_kernel_launches(ctx: Ctx) -> int:
 
 def spamm_tree_build(ctx: Ctx, A, n: int, leaf: int, flags: int) -> Tree:
     """A: torch CUDA tensor (device) or numpy array (host; SPAMM_HOST_INPUT is added)."""
-    if isinstance(A, np.ndarray):
-        assert A.dtype == np.float64 and A.flags.c_contiguous
+    addr, host = _matrix(A, n, "spamm_tree_build", ctx.device)
+    if host:
         flags |= SPAMM_HOST_INPUT
     h = _P()
-    ctx.check(LIB.spamm_tree_build(ctx.h, _ptr(A), n, leaf, flags, ctypes.byref(h)), "spamm_tree_build")
+    ctx.check(LIB.spamm_tree_build(ctx.h, addr, n, leaf, flags, ctypes.byref(h)), "spamm_tree_build")
     return Tree(ctx, h.value)
 
 
 def spamm_tree_update(t: Tree, A) -> Tree:
     """Rebuild t in place from A (torch CUDA tensor, or numpy host array)."""
-    flags = SPAMM_HOST_INPUT if isinstance(A, np.ndarray) else 0
-    t.ctx.check(LIB.spamm_tree_update(t.h, _ptr(A), flags), "spamm_tree_update")
+    addr, host = _matrix(A, t.n, "spamm_tree_update", t.ctx.device)
+    t.ctx.check(LIB.spamm_tree_update(t.h, addr, SPAMM_HOST_INPUT if host else 0), "spamm_tree_update")
     return t
 
 
@@ -228,8 +253,16 @@ def spamm_tree_update_batched(ctx: Ctx, trees: list, inputs: list):
     """Rebuild trees[p] from the torch CUDA tensors inputs[p], the rebuilds spread over
     the context's side streams."""
     count = len(trees)
+    if len(inputs) != count:
+        raise ValueError("spamm_tree_update_batched: one input per tree")
+    addrs = []
+    for t, a in zip(trees, inputs):
+        addr, host = _matrix(a, t.n, "spamm_tree_update_batched", ctx.device)
+        if host:
+            raise ValueError("spamm_tree_update_batched: inputs must be torch CUDA tensors")
+        addrs.append(addr)
     pt = (ctypes.c_void_p * count)(*[t.h for t in trees])
-    pa = (ctypes.c_void_p * count)(*[_ptr(a) for a in inputs])
+    pa = (ctypes.c_void_p * count)(*addrs)
     ctx.check(LIB.spamm_tree_update_batched(ctx.h, count, ctypes.addressof(pt), ctypes.addressof(pa), 0),
               "spamm_tree_update_batched")
 
@@ -259,9 +292,9 @@ def spamm_tree_to_dense(t: Tree, out=None, asynchronous: bool = False):
     asynchronous (host output only): return once queued; `out` is complete after spamm_sync."""
     if out is None:
         out = np.empty((t.n, t.n), dtype=np.float64)
-    host = isinstance(out, np.ndarray) or (hasattr(out, "is_cuda") and not out.is_cuda)
+    addr, host = _matrix(out, t.n, "spamm_tree_to_dense", t.ctx.device, writable=True)
     mode = (2 if asynchronous else 1) if host else 0
-    t.ctx.check(LIB.spamm_tree_to_dense(t.h, _ptr(out), mode), "spamm_tree_to_dense")
+    t.ctx.check(LIB.spamm_tree_to_dense(t.h, addr, mode), "spamm_tree_to_dense")
     return out
 
 
@@ -489,9 +522,10 @@ def spamm_multiply_batched(ctx: Ctx, A: list, B: list, tau, prec: int, flags: in
 
 def spamm_tune_leaf(ctx: Ctx, A, n: int, tau: float, prec: int, flags: int = 0) -> tuple[int, float]:
     """Fastest leaf size for the product A A (A: torch CUDA tensor or numpy host array)."""
-    if isinstance(A, np.ndarray):
+    addr, host = _matrix(A, n, "spamm_tune_leaf", ctx.device)
+    if host:
         flags |= SPAMM_HOST_INPUT
     leaf, ms = _I32(), _D()
-    ctx.check(LIB.spamm_tune_leaf(ctx.h, _ptr(A), n, float(tau), int(prec), flags, ctypes.byref(leaf),
+    ctx.check(LIB.spamm_tune_leaf(ctx.h, addr, n, float(tau), int(prec), flags, ctypes.byref(leaf),
                                   ctypes.byref(ms)), "spamm_tune_leaf")
     return leaf.value, ms.value

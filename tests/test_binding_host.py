@@ -1,0 +1,73 @@
+"""Operand checks of the Python binding (no GPU): every matrix handed to the library is
+an n x n row-major FP64 buffer, host (numpy or torch CPU) or CUDA; anything else is
+refused in Python before the library sees the pointer."""
+import types
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+S = pytest.importorskip("paper_1011_3534_gb300.spamm")
+
+
+def test_host_arrays():
+    A = np.zeros((5, 5))
+    addr, host = S._matrix(A, 5, "t")
+    assert host and addr == A.ctypes.data
+    T = torch.zeros((5, 5), dtype=torch.float64)
+    addr, host = S._matrix(T, 5, "t")
+    assert host and addr == T.data_ptr()
+
+
+@pytest.mark.parametrize("bad", [
+    np.zeros((5, 5), dtype=np.float32),               # another dtype
+    np.zeros((5, 6)),                                 # another size
+    np.asfortranarray(np.arange(25.0).reshape(5, 5)),  # column-major
+    np.zeros((10, 10))[::2, ::2],                     # strided view
+])
+def test_bad_numpy(bad):
+    with pytest.raises(ValueError):
+        S._matrix(bad, 5, "t")
+
+
+@pytest.mark.parametrize("bad", [
+    torch.zeros((5, 5), dtype=torch.float32),
+    torch.zeros((4, 4), dtype=torch.float64),
+    torch.arange(25.0, dtype=torch.float64).reshape(5, 5).t(),
+])
+def test_bad_tensors(bad):
+    with pytest.raises(ValueError):
+        S._matrix(bad, 5, "t")
+
+
+def test_read_only_output():
+    A = np.zeros((3, 3))
+    A.flags.writeable = False
+    S._matrix(A, 3, "t")
+    with pytest.raises(ValueError):
+        S._matrix(A, 3, "t", writable=True)
+
+
+def test_other_types():
+    with pytest.raises(TypeError):
+        S._matrix([[0.0]], 1, "t")
+
+
+def _fake_cuda(index):
+    return types.SimpleNamespace(data_ptr=lambda: 4096, is_cuda=True, dtype="torch.float64",
+                                 is_contiguous=lambda: True, numel=lambda: 4,
+                                 device=types.SimpleNamespace(index=index))
+
+
+def test_device_must_match_the_context():
+    assert S._matrix(_fake_cuda(0), 2, "t", device=0) == (4096, False)
+    with pytest.raises(ValueError):
+        S._matrix(_fake_cuda(1), 2, "t", device=0)
+
+
+def test_refused_before_the_library_call():
+    ctx = S.Ctx(0)   # a null context: any call reaching the library would fail differently
+    with pytest.raises(ValueError):
+        S.spamm_tree_build(ctx, np.zeros((3, 3), dtype=np.float32), 3, 16, 0)
+    with pytest.raises(ValueError):
+        S.spamm_tune_leaf(ctx, np.zeros((2, 3)), 3, 1e-6, S.SPAMM_FP64)
