@@ -186,6 +186,17 @@ def _matrix(x, n: int, what: str, device: int | None = None, writable: bool = Fa
     raise TypeError(f"{what}: expected a numpy array or a torch CUDA tensor, got {type(x).__name__}")
 
 
+def _device_buf(x, dtypes: tuple, min_numel: int, what: str) -> int:
+    """Address of a contiguous torch CUDA tensor of one of `dtypes` holding at least
+    `min_numel` elements; anything else raises before the library sees the pointer."""
+    if not (hasattr(x, "data_ptr") and getattr(x, "is_cuda", False)):
+        raise TypeError(f"{what}: expected a torch CUDA tensor, got {type(x).__name__}")
+    if str(x.dtype) not in dtypes or not x.is_contiguous() or x.numel() < min_numel:
+        raise ValueError(f"{what}: need a contiguous {' or '.join(dtypes)} tensor of at least {min_numel} "
+                         f"elements, got {x.dtype} {tuple(x.shape)}")
+    return x.data_ptr()
+
+
 class Ctx:
     def __init__(self, handle: int, device: int | None = None):
         self.h = handle
@@ -328,10 +339,20 @@ def spamm_triples(C: Tree) -> np.ndarray:
 
 
 def spamm_cull_noalloc(normA2, normB2, nb_padded: int, tau: float, triples, cap: int, count, stream=None):
-    """Forward to the allocation-free cull: all buffers are device tensors the caller owns."""
+    """Forward to the allocation-free cull: all buffers are device tensors the caller owns
+    (the norms FP64, NB x NB; the triples int32 or uint32, 3 per slot; the count int64).
+    A block count the library refuses (not a power of two, above 128) goes through for
+    the library to report."""
     s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-    rc = LIB.spamm_cull_noalloc(_ptr(normA2), _ptr(normB2), nb_padded, float(tau),
-                                _ptr(triples) if triples is not None else None, cap, _ptr(count), s)
+    nn = nb_padded * nb_padded if 1 <= nb_padded <= 128 and nb_padded & (nb_padded - 1) == 0 else 0
+    f64, u32 = ("torch.float64",), ("torch.int32", "torch.uint32")
+    pa = _device_buf(normA2, f64, nn, "spamm_cull_noalloc normA2")
+    pb = _device_buf(normB2, f64, nn, "spamm_cull_noalloc normB2")
+    pt = _device_buf(triples, u32, 3 * max(cap, 0), "spamm_cull_noalloc triples") if triples is not None else None
+    if triples is None and cap > 0:
+        raise ValueError("spamm_cull_noalloc: cap > 0 without a triples buffer")
+    pc = _device_buf(count, ("torch.int64",), 1, "spamm_cull_noalloc count")
+    rc = LIB.spamm_cull_noalloc(pa, pb, nb_padded, float(tau), pt, cap, pc, s)
     if rc != SPAMM_OK:
         raise SpammError(rc, "spamm_cull_noalloc failed")
 
@@ -449,15 +470,25 @@ class Mlp:
         th = np.ascontiguousarray(theta, dtype=np.float32)
         self.ctx.check(LIB.spamm_mlp_set_params(self.h, th.ctypes.data, th.size), "spamm_mlp_set_params")
 
-    def forward(self, X) -> np.ndarray:
+    def _samples(self, X, y=None):
+        """X as (samples, inputs) FP32 rows and y as one FP32 label per sample."""
         X = np.ascontiguousarray(X, dtype=np.float32)
+        if X.ndim != 2 or X.shape[1] != self.inputs:
+            raise ValueError(f"Mlp: X must be (samples, {self.inputs}), got {X.shape}")
+        if y is not None:
+            y = np.ascontiguousarray(y, dtype=np.float32)
+            if y.shape != (X.shape[0],):
+                raise ValueError(f"Mlp: y must hold one label per sample ({X.shape[0]}), got {y.shape}")
+        return X, y
+
+    def forward(self, X) -> np.ndarray:
+        X, _ = self._samples(X)
         y = np.empty(X.shape[0], dtype=np.float32)
         self.ctx.check(LIB.spamm_mlp_forward(self.h, X.ctypes.data, X.shape[0], y.ctypes.data), "spamm_mlp_forward")
         return y
 
     def gradient(self, X, y) -> tuple[float, np.ndarray]:
-        X = np.ascontiguousarray(X, dtype=np.float32)
-        y = np.ascontiguousarray(y, dtype=np.float32)
+        X, y = self._samples(X, y)
         g = np.empty(self.P, dtype=np.float32)
         L = np.zeros(1, dtype=np.float32)
         self.ctx.check(LIB.spamm_mlp_gradient(self.h, X.ctypes.data, y.ctypes.data, X.shape[0], g.ctypes.data,
@@ -465,8 +496,7 @@ class Mlp:
         return float(L[0]), g
 
     def adam_step(self, X, y, lr: float) -> float:
-        X = np.ascontiguousarray(X, dtype=np.float32)
-        y = np.ascontiguousarray(y, dtype=np.float32)
+        X, y = self._samples(X, y)
         L = np.zeros(1, dtype=np.float32)
         self.ctx.check(LIB.spamm_mlp_adam_step(self.h, X.ctypes.data, y.ctypes.data, X.shape[0], float(lr),
                                                L.ctypes.data), "spamm_mlp_adam_step")
@@ -474,12 +504,12 @@ class Mlp:
 
     def adam_apply(self, grad, lr: float):
         g = np.ascontiguousarray(grad, dtype=np.float32)
-        assert g.size == self.P
+        if g.size != self.P:
+            raise ValueError(f"Mlp: gradient of {g.size} entries, the network has {self.P} parameters")
         self.ctx.check(LIB.spamm_mlp_adam_apply(self.h, g.ctypes.data, float(lr)), "spamm_mlp_adam_apply")
 
     def train(self, X, y, epochs: int, batch: int, lr: float, seed: int = 0) -> float:
-        X = np.ascontiguousarray(X, dtype=np.float32)
-        y = np.ascontiguousarray(y, dtype=np.float32)
+        X, y = self._samples(X, y)
         L = np.zeros(1, dtype=np.float32)
         self.ctx.check(LIB.spamm_mlp_train(self.h, X.ctypes.data, y.ctypes.data, X.shape[0], epochs, batch,
                                            float(lr), seed, L.ctypes.data), "spamm_mlp_train")

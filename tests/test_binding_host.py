@@ -54,7 +54,7 @@ def test_other_types():
 
 
 def _fake_cuda(index):
-    return types.SimpleNamespace(data_ptr=lambda: 4096, is_cuda=True, dtype="torch.float64",
+    return types.SimpleNamespace(data_ptr=lambda: 4096, is_cuda=True, dtype="torch.float64", shape=(2, 2),
                                  is_contiguous=lambda: True, numel=lambda: 4,
                                  device=types.SimpleNamespace(index=index))
 
@@ -71,3 +71,48 @@ def test_refused_before_the_library_call():
         S.spamm_tree_build(ctx, np.zeros((3, 3), dtype=np.float32), 3, 16, 0)
     with pytest.raises(ValueError):
         S.spamm_tune_leaf(ctx, np.zeros((2, 3)), 3, 1e-6, S.SPAMM_FP64)
+
+
+def _fake_dev(dtype, numel, contiguous=True):
+    return types.SimpleNamespace(data_ptr=lambda: 8192, is_cuda=True, dtype=dtype, shape=(numel,),
+                                 is_contiguous=lambda: contiguous, numel=lambda: numel)
+
+
+def test_device_buffers():
+    assert S._device_buf(_fake_dev("torch.float64", 16), ("torch.float64",), 16, "t") == 8192
+    with pytest.raises(ValueError):
+        S._device_buf(_fake_dev("torch.float64", 15), ("torch.float64",), 16, "t")
+    with pytest.raises(ValueError):
+        S._device_buf(_fake_dev("torch.float32", 16), ("torch.float64",), 16, "t")
+    with pytest.raises(ValueError):
+        S._device_buf(_fake_dev("torch.float64", 16, contiguous=False), ("torch.float64",), 16, "t")
+    with pytest.raises(TypeError):
+        S._device_buf(np.zeros(16), ("torch.float64",), 16, "t")
+    with pytest.raises(TypeError):
+        S._device_buf(torch.zeros(16, dtype=torch.float64), ("torch.float64",), 16, "t")
+
+
+def test_noalloc_cull_buffers_checked_before_the_call():
+    n2 = _fake_dev("torch.float64", 64 * 64)
+    cnt = _fake_dev("torch.int64", 1)
+    with pytest.raises(ValueError):   # norms of 32 x 32 blocks for NB = 64
+        S.spamm_cull_noalloc(_fake_dev("torch.float64", 32 * 32), n2, 64, 1e-6, None, 0, cnt)
+    with pytest.raises(ValueError):   # room for 9 triples, cap 10
+        S.spamm_cull_noalloc(n2, n2, 64, 1e-6, _fake_dev("torch.int32", 27), 10, cnt)
+    with pytest.raises(ValueError):   # a 32-bit count
+        S.spamm_cull_noalloc(n2, n2, 64, 1e-6, None, 0, _fake_dev("torch.int32", 1))
+    with pytest.raises(ValueError):   # cap without a buffer
+        S.spamm_cull_noalloc(n2, n2, 64, 1e-6, None, 4, cnt)
+
+
+def test_mlp_samples_shape():
+    m = object.__new__(S.Mlp)   # the shape checks only, no network on a device
+    m.inputs = 3
+    X, y = m._samples(np.zeros((5, 3)), np.zeros(5))
+    assert X.dtype == np.float32 and X.shape == (5, 3) and y.dtype == np.float32
+    with pytest.raises(ValueError):
+        m._samples(np.zeros((5, 4)))
+    with pytest.raises(ValueError):
+        m._samples(np.zeros(3))
+    with pytest.raises(ValueError):
+        m._samples(np.zeros((5, 3)), np.zeros(4))
