@@ -359,9 +359,7 @@ def spamm_cull_noalloc(normA2, normB2, nb_padded: int, tau: float, triples, cap:
 
 def spamm_sp2(ctx: Ctx, indptr, indices, data, n_occ: float, steps: int, leaf: int, prec: int, tau) -> dict:
     """SP2 purification of the symmetric CSR matrix H (host numpy arrays)."""
-    indptr = np.ascontiguousarray(indptr, dtype=np.int64)
-    indices = np.ascontiguousarray(indices, dtype=np.int64)
-    data = np.ascontiguousarray(data, dtype=np.float64)
+    indptr, indices, data = _csr(indptr, indices, data)
     tau = np.ascontiguousarray(np.broadcast_to(np.asarray(tau, dtype=np.float64), (steps,)))
     n = indptr.size - 1
     r = Sp2ResultT()
@@ -379,8 +377,15 @@ def _sp2_dict(r: Sp2ResultT) -> dict:
 
 
 def _csr(indptr, indices, data):
-    return (np.ascontiguousarray(indptr, dtype=np.int64), np.ascontiguousarray(indices, dtype=np.int64),
-            np.ascontiguousarray(data, dtype=np.float64))
+    """Host CSR arrays as int64 / int64 / FP64, with as many column indices and values as
+    indptr[-1] says (the library reads that many; it checks the index ranges itself)."""
+    ip = np.ascontiguousarray(indptr, dtype=np.int64).reshape(-1)
+    ix = np.ascontiguousarray(indices, dtype=np.int64).reshape(-1)
+    dv = np.ascontiguousarray(data, dtype=np.float64).reshape(-1)
+    if ip.size < 1 or ip[-1] != ix.size or ix.size != dv.size:
+        raise ValueError(f"CSR: indptr[-1] must equal the number of indices and values, got "
+                         f"{ip[-1] if ip.size else None}, {ix.size}, {dv.size}")
+    return ip, ix, dv
 
 
 def spamm_sp2_learned(ctx: Ctx, indptr, indices, data, n_occ: float, steps: int, leaf: int, prec: int,

@@ -116,3 +116,14 @@ def test_mlp_samples_shape():
         m._samples(np.zeros(3))
     with pytest.raises(ValueError):
         m._samples(np.zeros((5, 3)), np.zeros(4))
+
+
+def test_csr_lengths():
+    ip, ix, d = S._csr([0, 1, 3], [0, 0, 1], [1.0, 2.0, 3.0])
+    assert ip.dtype == np.int64 and ix.dtype == np.int64 and d.dtype == np.float64
+    with pytest.raises(ValueError):   # indptr promises 3 entries, 2 given
+        S._csr([0, 1, 3], [0, 0], [1.0, 2.0])
+    with pytest.raises(ValueError):   # values and indices disagree
+        S._csr([0, 1, 2], [0, 1], [1.0])
+    with pytest.raises(ValueError):
+        S._csr([], [], [])
