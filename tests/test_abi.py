@@ -50,3 +50,27 @@ def test_errors_without_device():
     assert S.LIB.spamm_multiply(None, None, None, 0.0, 0, 0, None) == S.SPAMM_EINVAL
     assert S.LIB.spamm_tree_free(None) == S.SPAMM_EINVAL
     assert S.LIB.spamm_stats(None, None) == S.SPAMM_EINVAL
+
+
+def test_every_entry_point_refuses_null_arguments():
+    # each entry point, called with null handles and pointers and zero sizes, returns
+    # SPAMM_EINVAL (or -1 / a message for the queries) and touches no memory or device
+    from paper_1011_3534_gb300 import spamm as S
+    for name in sorted(declared()):
+        f = getattr(S.LIB, name)
+        assert f.argtypes is not None, f"{name}: the binding declares no argument types"
+        args = []
+        for t in f.argtypes:
+            if t in (ctypes.c_double, ctypes.c_float):
+                args.append(0.0)
+            elif t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64):
+                args.append(0)
+            else:
+                args.append(None)
+        r = f(*args)
+        if name == "spamm_last_error":
+            assert isinstance(r, bytes) and r
+        elif name in ("spamm_kernel_launches", "spamm_mlp_num_params"):
+            assert r == -1, name
+        else:
+            assert r == S.SPAMM_EINVAL, (name, r)
