@@ -53,7 +53,7 @@ typedef enum {
   SPAMM_ERANGE = 4,        /* a caller buffer or an internal capacity is too small;
                               the size needed is returned where the call says */
   SPAMM_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
-  SPAMM_EUNSUPPORTED = 6   /* valid request this build does not implement */
+  SPAMM_EUNSUPPORTED = 6   /* valid request the library does not implement */
 } spamm_status;
 
 /* Arithmetic of the dense leaf products. Culling always uses the FP64 norms of the
