@@ -1,4 +1,5 @@
-"""Pins of the site orderings of the lattice workloads (CPU)."""
+"""Pins of the input generators (CPU): the SplitMix64 stream against its published
+outputs, exact symmetry, and the site orderings of the lattice workloads."""
 import numpy as np
 import pytest
 
@@ -62,3 +63,18 @@ def test_physical_decay_hilbert_is_a_site_permutation():
     pb = (perm[:, None] * 2 + np.arange(2)).ravel()
     assert np.array_equal(Ah, A[np.ix_(pb, pb)])
     assert np.array_equal(Ah, Ah.T)
+
+
+def test_splitmix64_known_answers():
+    # the first outputs of SplitMix64 from state 0 (Steele, Lea and Flood 2014; the
+    # sequence Java's SplittableRandom and the authors' reference code produce)
+    ref = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    u = W.uniform(0, np.arange(4, dtype=np.uint64))
+    assert np.array_equal(u, np.array([(r >> 11) * 2.0 ** -53 for r in ref]))
+    assert [W._mix64_int(W._GAMMA * (t + 1)) for t in range(4)] == ref
+
+
+def test_symmetric_generators_are_exactly_symmetric():
+    for A in (W.exp_decay(130, 0.85, 1, 0), W.algebraic_decay(130, 2, 0)):
+        assert np.array_equal(A, A.T)
+        assert A.dtype == np.float64 and A.flags.c_contiguous
