@@ -268,8 +268,11 @@ typedef struct spamm_mlp_s *spamm_mlp;
    U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed), biases 0. */
 SPAMM_API spamm_status spamm_mlp_create(spamm_ctx ctx, int32_t inputs, int32_t hidden, uint64_t seed,
                                         spamm_mlp *out);
+/* Release the network's device memory (SPAMM_EINVAL for NULL). */
 SPAMM_API spamm_status spamm_mlp_free(spamm_mlp m);
+/* Number of parameters, hidden * (inputs + hidden + 3) + 1; -1 for NULL. */
 SPAMM_API int32_t spamm_mlp_num_params(spamm_mlp m);
+/* Copy the parameters into out[cap] (cap >= spamm_mlp_num_params, else SPAMM_EINVAL). */
 SPAMM_API spamm_status spamm_mlp_get_params(spamm_mlp m, float *out, int32_t cap);
 /* Set the parameters (count == spamm_mlp_num_params) and reset the Adam state. */
 SPAMM_API spamm_status spamm_mlp_set_params(spamm_mlp m, const float *in, int32_t count);
