@@ -544,6 +544,8 @@ def spamm_tree_distance(X: Tree, Y: Tree) -> tuple[float, float]:
 def spamm_multiply_batched(ctx: Ctx, A: list, B: list, tau, prec: int, flags: int = 0, C: list | None = None) -> list:
     """C[p] ~ A[p] B[p] with tolerance tau[p]; returns the list of product trees."""
     count = len(A)
+    if len(B) != count or (C is not None and len(C) != count):
+        raise ValueError("spamm_multiply_batched: A, B (and C) must have one entry per product")
     pa = (ctypes.c_void_p * count)(*[t.h for t in A])
     pb = (ctypes.c_void_p * count)(*[t.h for t in B])
     pc = (ctypes.c_void_p * count)(*[(c.h if c is not None else None) for c in (C or [None] * count)])

@@ -127,3 +127,11 @@ def test_csr_lengths():
         S._csr([0, 1, 2], [0, 1], [1.0])
     with pytest.raises(ValueError):
         S._csr([], [], [])
+
+
+def test_batched_lists_must_match():
+    ctx = S.Ctx(0)
+    with pytest.raises(ValueError):
+        S.spamm_multiply_batched(ctx, [None, None], [None], 1e-6, S.SPAMM_BF16)
+    with pytest.raises(ValueError):
+        S.spamm_multiply_batched(ctx, [None], [None], 1e-6, S.SPAMM_BF16, C=[None, None])
