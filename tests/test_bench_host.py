@@ -1,5 +1,6 @@
 """Host-side helpers of the benchmark that need no GPU: the CPU model recorded beside
-the oracle's timing, read from /proc/cpuinfo on x86 and Arm hosts."""
+the oracle's timing, the clock-sample summary, and the kernel-source hash that keeps a
+recorded DRAM traffic figure only while the kernel is unchanged."""
 import os
 import sys
 
@@ -29,3 +30,34 @@ def test_unknown_part_and_empty_text():
 
 def test_this_host():
     assert isinstance(bench.host_cpu(), str) and bench.host_cpu()
+
+
+def test_clock_summary_parses_samples():
+    c = bench.ClockSampler(0)
+    c.lines = ["0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "0, 1965, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 950.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "garbage", ""]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+
+
+def test_clock_summary_without_samples():
+    s = bench.ClockSampler(0).summary()
+    assert s["sm_mhz"] is None and s["samples"] == 0
+
+
+def test_kernel_hash_covers_only_the_marked_region(tmp_path):
+    f = tmp_path / "k.cu"
+    f.write_text("head\n// BEGIN\nbody\n// END\ntail\n")
+    part = [{"path": str(f), "begin": "// BEGIN", "end": "// END"}]
+    h0 = bench.kernel_source_hash(part)
+    f.write_text("other head\n// BEGIN\nbody\n// END\nother tail\n")
+    assert bench.kernel_source_hash(part) == h0
+    f.write_text("head\n// BEGIN\nchanged body\n// END\ntail\n")
+    assert bench.kernel_source_hash(part) != h0
+
+
+def test_traffic_of_unknown_kernel_is_null():
+    assert bench.kernel_traffic("no_such_kernel") is None
