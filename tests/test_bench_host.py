@@ -61,3 +61,18 @@ def test_kernel_hash_covers_only_the_marked_region(tmp_path):
 
 def test_traffic_of_unknown_kernel_is_null():
     assert bench.kernel_traffic("no_such_kernel") is None
+
+
+def test_reference_arm_samples_when_the_steps_exceed_its_budget():
+    import json
+    import subprocess
+    import time
+    env = dict(os.environ, OMP_NUM_THREADS="4", SPAMM_REF_BUDGET_S="2")
+    t0 = time.time()
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "10",
+                        "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    assert d["impl"] == "reference" and d["steps"] == 10 and d["value"] > 0
+    assert "output blocks per step" in d["cpu_baseline"]["sample"]
+    assert time.time() - t0 < 120
