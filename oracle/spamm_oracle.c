@@ -152,6 +152,8 @@ typedef struct {
   int target;           /* 1: follow only the output leaf block (ti, tj) */
   int32_t ti, tj;
   int64_t row0;         /* first padded row held by C (0 unless target mode) */
+  int64_t col0;         /* first padded column held by C (0 unless target mode) */
+  int64_t ldc;          /* row stride of C in elements; 0: N */
 } rec_ctx;
 
 static int cull(double nA2, double nB2, double tau) {
@@ -165,9 +167,9 @@ static int cull(double nA2, double nB2, double tau) {
 
 static void leaf_product(const rec_ctx *c, int32_t I, int32_t J, int32_t K) {
   const oracle_tree *A = c->Av, *B = c->Bv;
-  const int64_t N = A->N, b = A->b;
+  const int64_t N = A->N, b = A->b, ldc = c->ldc ? c->ldc : N;
   for (int64_t r = 0; r < b; r++) {
-    double *crow = c->C + (I * b + r - c->row0) * N + J * b;
+    double *crow = c->C + (I * b + r - c->row0) * ldc + (J * b - c->col0);
     for (int64_t l = 0; l < b; l++) {
       double a = A->a[(I * b + r) * N + K * b + l];
 #if ORACLE_MUTANT == 3
@@ -357,19 +359,17 @@ int oracle_spamm_block(const oracle_tree *A, const oracle_tree *B, const oracle_
   if (!compatible(A, B) || !compatible(A, Av) || !compatible(B, Bv) || !(tau >= 0.0) || I < 0 ||
       J < 0 || I >= A->NB || J >= A->NB)
     return 1;
-  const int64_t b = A->b, N = A->N;
-  /* accumulate into a strip holding the b padded rows of block row I */
-  double *strip = (double *)calloc((size_t)(b * N), sizeof(double));
-  if (!strip) return 2;
+  const int64_t b = A->b;
+  /* accumulate straight into the b x b output block (I, J) */
+  memset(out, 0, (size_t)(b * b) * sizeof(double));
   rec_ctx c;
   memset(&c, 0, sizeof c);
   c.A = A; c.B = B; c.Av = Av; c.Bv = Bv; c.tau = tau; c.task_depth = -1; c.target = 1; c.ti = I; c.tj = J;
-  c.C = strip;
-  c.row0 = (int64_t)I * b; /* strip row 0 is padded row I*b */
+  c.C = out;
+  c.row0 = (int64_t)I * b; /* out row 0 is padded row I*b */
+  c.col0 = (int64_t)J * b; /* out column 0 is padded column J*b */
+  c.ldc = b;
   rec(&c, 0, 0, 0, 0);
-  for (int64_t r = 0; r < b; r++)
-    memcpy(out + r * b, strip + r * N + (int64_t)J * b, (size_t)b * sizeof(double));
-  free(strip);
   return 0;
 }
 
