@@ -65,6 +65,15 @@ def sp2_spectral(eigs: np.ndarray, n_occ: float, steps: int, emin: float, emax: 
     return {"energy": float(np.dot(eigs, lam)), "traces": traces, "branches": branches}
 
 
+def spectrum(indptr, indices, data, n: int) -> np.ndarray:
+    """Eigenvalues of a symmetric CSR matrix, ascending: the dense FP64 matrix handed to
+    LAPACK's symmetric eigensolver (numpy.linalg.eigvalsh). The input of sp2_spectral."""
+    H = np.zeros((n, n), dtype=np.float64)
+    for i in range(n):
+        H[i, indices[indptr[i]:indptr[i + 1]]] = data[indptr[i]:indptr[i + 1]]
+    return np.linalg.eigvalsh(H)
+
+
 def drop_blocks(P: np.ndarray, b: int, tau: float) -> tuple[np.ndarray, int]:
     """The dropping filter of scheme (I) (Sec. III) at b x b resolution: every block of
     the zero-padded P whose Frobenius norm is below tau set to zero. Returns the
