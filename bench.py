@@ -7,9 +7,12 @@ tier plus the leaf copies the precision needs, from the FP64 A resident in HBM),
 the product space tier by tier, and sum the surviving leaf products of C = A A into
 C's tiles and norms. A is symmetric, so C is: the output blocks i <= j are culled and
 multiplied and the blocks i > j written as their transposes (SPAMM_SYM_PRODUCT).
-Headline: tau = 1e-8, BF16 leaves with FP32 accumulation.
+Headline: tau = 1e-8, split-TF32 leaves (hi = tf32(a), lo = tf32(a - hi); the three
+products hi hi + hi lo + lo hi on the tensor cores with FP32 accumulation), the
+single-precision class of arithmetic the paper's leaves used.
 A sweep over tau in {1e-10, 1e-8, 1e-6, 1e-4} and the leaf precisions reports each
-one's time and its relative Frobenius error against the FP64 SpAMM on the GPU.
+one's time and its relative Frobenius error against the FP64 SpAMM on the GPU, one
+compact line each, printed before the JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep]
                   [--config alg8192 | lattice32768 | batched256 | sp2-32768]
@@ -40,6 +43,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N, LEAF, TAU = 8192, 64, 1e-8
+HEADLINE = "tf32x3"
+# nominal dense tensor rates per GPU (PFLOP/s): a precision's peak is the measured BF16
+# peak times the ratio of its nominal rate to BF16's
+NOMINAL_PF = {"bf16": 2.25, "fp16": 2.25, "tf32": 1.1}
 TAUS = (1e-10, 1e-8, 1e-6, 1e-4)
 WORKLOAD = "algebraic-decay n=8192 leaf=64 (a_ij=u_ij/(|i-j|^3+1), u=U[.5,1]*sign, seed 0)"
 METRIC = "SpAMM dense-equiv GFLOP/s & leaf-GEMM % of TC peak at fixed error vs FP64 SpAMM"
@@ -240,7 +247,7 @@ def run_gpu(args):
                     launches=launches, tree=tC)
 
     # ---- headline
-    prec = S.SPAMM_BF16
+    prec = S.PRECISIONS[HEADLINE]
     for _ in range(1):
         r0 = timed(prec, TAU, 2, 1)   # allocate and warm caches
         S.spamm_tree_free(r0["tree"])
@@ -253,9 +260,14 @@ def run_gpu(args):
     # phase times inside the timed region (events on the library's stream)
     ms_leaf = st["ms_leaf"]
     ms_cull = st["ms_cull"]
-    bytes_build = 8.0 * N * N + 2.0 * N * N          # read FP64 A, write the BF16 copy
+    bytes_build = (8.0 + copy_bytes(HEADLINE)) * N * N   # read FP64 A, write the leaf copies
     build_gbs = bytes_build / (r["ms_k1"] * 1e-3) / 1e9   # K1 alone, from its own launch events
+    # tensor work: the MMAs a triple needs in this precision (3 for the split forms)
+    passes = 3 if HEADLINE.endswith("x3") else 1
+    tc_flops = passes * st["leaf_flops"]
+    tc_peak = pk["bf16_sus"] * NOMINAL_PF[HEADLINE[:4]] / NOMINAL_PF["bf16"]
     leaf_tflops = st["leaf_flops"] / (ms_leaf * 1e-3) / 1e12 if ms_leaf else None
+    tc_tflops = tc_flops / (ms_leaf * 1e-3) / 1e12 if ms_leaf else None
     mma_tflops = st["mma_flops"] / (ms_leaf * 1e-3) / 1e12 if ms_leaf else None
     phases = {"build_ms": r["ms_build"], "k1_ms": r["ms_k1"], "cull_ms": ms_cull, "leaf_ms": ms_leaf,
               "multiply_ms": r["ms_mult"]}
@@ -266,27 +278,27 @@ def run_gpu(args):
                 "algorithmic_bytes_per_launch": bytes_build,
                 "peak_source": pk["source"] + " hbm_gbs"}
     else:
-        roof = {"kernel": "k_leaf_tc", "bound": "tensor", "achieved": leaf_tflops,
-                "peak": pk["bf16_sus"], "unit": "TFLOP/s", "frac": leaf_tflops / pk["bf16_sus"],
+        roof = {"kernel": "k_leaf_tc", "bound": "tensor", "achieved": tc_tflops,
+                "peak": tc_peak, "unit": "TFLOP/s", "frac": tc_tflops / tc_peak,
                 "traffic": kernel_traffic("k_leaf_tc"),
-                "algorithmic_flops_per_launch": st["leaf_flops"],
-                "peak_source": pk["source"] + " bf16_tflops_sustained"}
-    leaf = {"leaf_tflops": leaf_tflops, "mma_tflops": mma_tflops,
-            "frac_of_bf16_peak": (leaf_tflops / pk["bf16_sus"]) if leaf_tflops else None,
-            "leaf_products": st["leaf_products"], "leaf_flops": st["leaf_flops"],
-            "mma_flops": st["mma_flops"]}
+                "algorithmic_flops_per_launch": tc_flops,
+                "peak_source": f"{pk['source']} bf16_tflops_sustained x {HEADLINE[:4]}/bf16 nominal"}
+    leaf = {"useful_tflops": leaf_tflops, "tc_tflops": tc_tflops, "mma_issued_tflops": mma_tflops,
+            "tc_peak": tc_peak, "frac_of_tc_peak": (tc_tflops / tc_peak) if tc_tflops else None,
+            "leaf_products": st["leaf_products"], "mirrored_products": st["mirrored_products"]}
+    k1 = {"gbs": build_gbs, "frac_of_hbm": build_gbs / pk["hbm"], "bytes_per_launch": bytes_build}
     S.spamm_tree_free(r["tree"])
 
-    # ---- end to end through the C ABI with host buffers (pinned)
+    # ---- end to end through the C ABI with host buffers (pinned): FP64 A in, FP32 C out
     A_pin = torch.from_numpy(A_host).pin_memory()
-    C_pin = torch.empty((N, N), dtype=torch.float64).pin_memory()
+    C_pin = torch.empty((N, N), dtype=torch.float32).pin_memory()
     A_np, C_np = A_pin.numpy(), C_pin.numpy()
     tA = S.spamm_tree_build(ctx, A_np, N, LEAF, flags_for(prec))
     tC = None
     for _ in range(max(1, args.warmup)):
         S.spamm_tree_update(tA, A_np)
         tC = S.spamm_multiply(ctx, tA, tA, TAU, prec, SYMP, tC)
-        S.spamm_tree_to_dense(tC, C_np, asynchronous=True)
+        S.spamm_tree_to_dense_f32(tC, C_np, asynchronous=True)
     S.spamm_sync(ctx)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
@@ -296,14 +308,14 @@ def run_gpu(args):
         # copy stream, so one step's output overlaps the next step's input
         S.spamm_tree_update(tA, A_np)
         tC = S.spamm_multiply(ctx, tA, tA, TAU, prec, SYMP, tC)
-        S.spamm_tree_to_dense(tC, C_np, asynchronous=True)
+        S.spamm_tree_to_dense_f32(tC, C_np, asynchronous=True)
     S.spamm_sync(ctx)                        # every step's C is on the host
     e2e_ms = (time.perf_counter() - e0) * 1e3 / e2e_steps
     S.spamm_tree_free(tA)
     e2e_ms = max_over_ranks(e2e_ms, dA.device)
     S.spamm_tree_free(tC)
     e2e = {"value": whole_job(2.0 * N ** 3 / (e2e_ms * 1e-3) / 1e9, ws), "unit": "GFLOP/s",
-           "h2d_bytes_per_step": 8 * N * N, "d2h_bytes_per_step": 8 * N * N, "ms_per_step": e2e_ms}
+           "h2d_bytes_per_step": 8 * N * N, "d2h_bytes_per_step": 4 * N * N, "ms_per_step": e2e_ms}
 
     # ---- precision and tau sweep (error vs FP64 SpAMM on the GPU)
     sweep = []
@@ -321,36 +333,52 @@ def run_gpu(args):
                 else:
                     err = float(torch.linalg.norm(Cd - ref) / torch.linalg.norm(ref))
                 s2 = rr["stats"]
-                lt = s2["leaf_flops"] / (s2["ms_leaf"] * 1e-3) / 1e12 if s2["ms_leaf"] else None
-                sweep.append({"tau": tau, "prec": name, "ms_per_step": rr["ms"],
-                              "dense_equiv_gflops": 2.0 * N ** 3 / (rr["ms"] * 1e-3) / 1e9,
+                sweep.append({"tau": tau, "prec": name, "ms": rr["ms"], "k1_ms": rr["ms_k1"],
                               "build_ms": rr["ms_build"], "cull_ms": s2["ms_cull"], "leaf_ms": s2["ms_leaf"],
-                              "leaf_tflops": lt, "leaf_products": s2["leaf_products"],
-                              "rel_fro_err_vs_fp64_spamm": err})
+                              "leaf_products": s2["leaf_products"], "err": err})
                 S.spamm_tree_free(rr["tree"])
                 del Cd
             del ref
 
-    # ---- CPU oracle on this host (rank 0 only, bounded sample)
-    cpu = cpu_baseline(A_host, quick=args.no_sweep) if rank == 0 else None
+    # ---- CPU oracle on this host (rank 0 only, bounded sample, in a process of its own)
+    cpu = cpu_baseline_subprocess(quick=args.no_sweep) if rank == 0 else None
 
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "leaf": LEAF, "tau": TAU, "precision": "bf16",
-                   "accumulate": "fp32", "product": "symmetric (blocks i <= j multiplied, i > j mirrored)",
+        "scaling": "weak", "vs_baseline": None, "dtype": HEADLINE, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "leaf": LEAF, "tau": TAU, "precision": HEADLINE,
+                   "accumulate": "fp32 per pass", "product": "symmetric (blocks i <= j multiplied, i > j mirrored)",
                    "l2": "inputs larger than L2 (A is 512 MiB FP64)",
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "e2e": e2e, "gpu_launches": r["launches"], "phases": phases, "leaf_gemm": leaf,
-        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "sweep": sweep,
+        "e2e": e2e, "gpu_launches": r["launches"], "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "phases": phases, "k1": k1, "leaf_gemm": leaf,
     }
     if rank == 0:
-        print(json.dumps(line))
+        for row in sorted(sweep, key=lambda x: (x["tau"] == TAU, x["tau"])):   # tau = 1e-8 last
+            print(sweep_line(row))
+        print(json.dumps(line, default=_compact))
     S.spamm_ctx_destroy(ctx)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def copy_bytes(prec: str) -> float:
+    """Bytes per element of the leaf copies a symmetric operand needs in `prec`."""
+    return {"fp64": 8.0, "tf32": 4.0, "bf16": 2.0, "fp16": 2.0, "bf16x3": 4.0, "tf32x3": 8.0}[prec]
+
+
+def sweep_line(row: dict) -> str:
+    """One compact line per (tau, precision) of the sweep."""
+    f = lambda v, d=4: "-" if v is None else f"{v:.{d}g}"
+    return (f"sweep tau={row['tau']:.0e} {row['prec']:<6} step={f(row['ms'])}ms k1={f(row['k1_ms'])} "
+            f"build={f(row['build_ms'])} cull={f(row['cull_ms'])} leaf={f(row['leaf_ms'])}ms "
+            f"products={row['leaf_products']} err={f(row['err'], 2)}")
+
+
+def _compact(o):
+    return str(o)
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -386,11 +414,13 @@ def host_cpu(cpuinfo_text=None):
     return platform.machine()
 
 
-def cpu_baseline(A_host, quick=False, budget_s=20.0):
+def cpu_baseline(quick=False, budget_s=20.0):
     """The CPU oracle (FP64 recursive SpAMM, OpenMP over output quadrants) on the host
     cores: quadtree build + product at tau = 1e-8 on the full n = 8192 matrix, repeated
     while inside the time budget."""
+    from paper_1011_3534_gb300 import workloads as W
     import oracle
+    A_host = W.algebraic_decay(N, 2, 0)
     cores = oracle.max_threads()
     t0 = time.perf_counter()
     TA = oracle.Tree(A_host, LEAF)
@@ -405,8 +435,20 @@ def cpu_baseline(A_host, quick=False, budget_s=20.0):
             dt = min(dt, time.perf_counter() - t1)
             reps += 1
     return {"value": 2.0 * N ** 3 / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "cpu": host_cpu(), "kind": "oracle",
-            "sample": f"full n={N} product at tau={TAU} (tree build + Eq. 4 recursion, FP64), best of {reps}",
+            "sample": f"full n={N} product at tau={TAU} (tree build + Eq. 4 recursion, FP64), best of {reps}, "
+                      f"in a process of its own (no CUDA context)",
             "seconds": dt}
+
+
+def cpu_baseline_subprocess(quick=False):
+    """cpu_baseline() in a fresh interpreter, so that the oracle's threads share the host
+    with no CUDA context or torch thread pool of the GPU process."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-child"] + (["--no-sweep"] if quick else [])
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT)
+        return json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    except Exception as e:   # the GPU numbers stand without it
+        return {"value": None, "unit": "GFLOP/s", "kind": "oracle", "error": f"{type(e).__name__}: {e}"}
 
 
 def run_reference(args):
@@ -415,7 +457,9 @@ def run_reference(args):
     budget (SPAMM_REF_BUDGET_S, default 150 s); beyond that each step is a bounded
     sample: a seeded random set of the product's output blocks, each evaluated by the
     oracle's per-block recursion on all cores, with the tree of A built once before the
-    timed steps, and the value is the dense-equivalent rate of the blocks computed."""
+    timed steps, and the value is the dense-equivalent rate of the blocks computed. The
+    line records the full product's rate from the sizing step beside it either way.
+    --ref-n shrinks the matrix (tests of the mode switch only)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
@@ -423,7 +467,8 @@ def run_reference(args):
     from paper_1011_3534_gb300 import workloads as W
     import oracle
     budget = float(os.environ.get("SPAMM_REF_BUDGET_S", "150"))
-    A = W.algebraic_decay(N, 2, 0)
+    n = args.ref_n or N
+    A = W.algebraic_decay(n, 2, 0)
     cores = oracle.max_threads()
 
     def full_step():
@@ -433,6 +478,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     full_step()                                   # the first warm-up step, timed to size the rest
     t_full = time.perf_counter() - t0
+    full_gflops = 2.0 * n ** 3 / t_full / 1e9
     per_step = budget / (args.steps + args.warmup)
     times = []
     if t_full <= per_step:
@@ -443,8 +489,9 @@ def run_reference(args):
             full_step()
             times.append(time.perf_counter() - t0)
         ms = 1e3 * float(np.mean(times))
-        v = 2.0 * N ** 3 / (ms * 1e-3) / 1e9
-        sample = f"full n={N} product at tau={TAU} per step"
+        v = 2.0 * n ** 3 / (ms * 1e-3) / 1e9
+        mode = "full"
+        sample = f"full n={n} product at tau={TAU} per step"
     else:
         TA = oracle.Tree(A, LEAF)
         nblk = TA.NB * TA.NB
@@ -462,16 +509,18 @@ def run_reference(args):
                 sample_step(args.warmup + s)
                 times.append(time.perf_counter() - t0)
         ms = 1e3 * float(np.mean(times))
-        v = 2.0 * N ** 3 * m / nblk / (ms * 1e-3) / 1e9
+        v = 2.0 * n ** 3 * m / nblk / (ms * 1e-3) / 1e9
+        mode = "sampled"
         sample = (f"{m} of {nblk} output blocks per step (seeded random order; Eq. 4 recursion per "
-                  f"block on {cores} threads; tree of A built once before the timed steps), n={N}, "
+                  f"block on {cores} threads; tree of A built once before the timed steps), n={n}, "
                   f"tau={TAU}; a full step took {t_full:.2f} s")
     line = {"metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "n": N, "leaf": LEAF, "tau": TAU, "precision": "fp64"},
+            "config": {"workload": WORKLOAD if n == N else WORKLOAD.replace(f"n={N}", f"n={n}"), "n": n,
+                       "leaf": LEAF, "tau": TAU, "precision": "fp64"},
             "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": cores, "cpu": host_cpu(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "mode": mode, "full_product_gflops": full_gflops},
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -768,6 +817,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--ref-n", type=int, default=None, help=argparse.SUPPRESS)   # tests of the reference arm
+    ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--config", default="alg8192",
                     choices=["alg8192", "lattice32768", "batched256", "sp2-32768", "variants"])
     args = ap.parse_args()
@@ -775,7 +826,9 @@ def main():
         args.steps = 20 if (args.impl == "reference" or args.config != "alg8192") else 2000
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.cpu_baseline_child:
+        print(json.dumps(cpu_baseline(quick=args.no_sweep)))
+    elif args.impl == "reference":
         run_reference(args)
     elif args.config == "lattice32768":
         run_lattice(args)

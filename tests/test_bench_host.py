@@ -63,16 +63,34 @@ def test_traffic_of_unknown_kernel_is_null():
     assert bench.kernel_traffic("no_such_kernel") is None
 
 
-def test_reference_arm_samples_when_the_steps_exceed_its_budget():
+def _reference_line(n, steps, warmup, budget):
     import json
     import subprocess
-    import time
-    env = dict(os.environ, OMP_NUM_THREADS="4", SPAMM_REF_BUDGET_S="2")
-    t0 = time.time()
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "10",
-                        "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    env = dict(os.environ, OMP_NUM_THREADS="4", SPAMM_REF_BUDGET_S=str(budget))
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", str(steps),
+                        "--warmup", str(warmup), "--ref-n", str(n)], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
-    d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    return json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+
+
+def test_reference_arm_samples_when_the_steps_exceed_its_budget():
+    # n = 2048 (NB = 32): a full product takes well under a second, a 0.05 s budget
+    # forces the sampled mode
+    d = _reference_line(2048, 10, 3, 0.05)
     assert d["impl"] == "reference" and d["steps"] == 10 and d["value"] > 0
+    assert d["cpu_baseline"]["mode"] == "sampled"
     assert "output blocks per step" in d["cpu_baseline"]["sample"]
-    assert time.time() - t0 < 120
+
+
+def test_reference_arm_modes_agree():
+    # the per-block sample and the full product measure the same dense-equivalent rate:
+    # the sampled blocks run the same recursion, followed into one output block each.
+    # A 1 s budget over 6 steps samples about a quarter of the 1024 blocks per step, so
+    # the threads stay balanced; a factor of 1.5 either way allows for the full
+    # product's tree build and a shared host (measured: within 10%)
+    full = _reference_line(2048, 3, 3, 1e6)
+    samp = _reference_line(2048, 3, 3, 1.0)
+    assert full["cpu_baseline"]["mode"] == "full" and samp["cpu_baseline"]["mode"] == "sampled"
+    ratio = samp["value"] / full["value"]
+    assert 1 / 1.5 < ratio < 1.5, ratio
