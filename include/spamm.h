@@ -186,6 +186,33 @@ SPAMM_API spamm_status spamm_tree_norms(spamm_tree t, int32_t level, double *out
    Errors: SPAMM_EINVAL (null out, out_is_host not 0/1/2, a tree without FP64/FP32
    tiles), SPAMM_ENOMEM, SPAMM_ECUDA. */
 SPAMM_API spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host);
+/* Leaf copies a tree may hold, as spamm_tree_leaf_copy names them: the FP64 tiles; the
+   FP32 tiles of a tensor-core product; the values rounded to TF32 (FP32 storage), BF16
+   and FP16; the low parts of the split forms, fmt(a - fmt(a)) (BF16 in 16 bits, TF32 in
+   FP32 storage); each also transposed (_T: every leaf stored transposed in place), the
+   orientation a non-symmetric right operand keeps. */
+typedef enum {
+  SPAMM_LEAF_F64 = 0, SPAMM_LEAF_F32 = 1, SPAMM_LEAF_TF32 = 2, SPAMM_LEAF_TF32_T = 3,
+  SPAMM_LEAF_BF16 = 4, SPAMM_LEAF_BF16_T = 5, SPAMM_LEAF_FP16 = 6, SPAMM_LEAF_FP16_T = 7,
+  SPAMM_LEAF_BF16LO = 8, SPAMM_LEAF_BF16LO_T = 9, SPAMM_LEAF_TF32LO = 10, SPAMM_LEAF_TF32LO_T = 11
+} spamm_leaf_copy;
+/* Copy one stored leaf copy (spamm_leaf_copy `which`) of a tree, in the library's tile
+   layout, to `out`: the leaves of the quadtree's finest tier (Eq. 1), leaf (r, c) with
+   r, c < ceil(n / leaf) at element (r * ceil(n / leaf) + c) * leaf^2, row-major inside
+   the leaf; nb^2 leaf^2 elements of 8, 4 or 2 bytes. Padding rows and columns of the
+   edge leaves hold zeros; leaves of a product tree that hold no block (no surviving
+   triple) hold unspecified values. out_is_host: 1 = host pointer (the call
+   synchronises), 0 = device pointer (queued on the context's stream). `bytes` is the
+   capacity of `out`. Errors: SPAMM_EINVAL (null arguments, `which` not held by the
+   tree), SPAMM_ERANGE (`bytes` too small; nothing copied), SPAMM_ECUDA. */
+SPAMM_API spamm_status spamm_tree_leaf_copy(spamm_tree t, int32_t which, void *out, int64_t bytes,
+                                            int32_t out_is_host);
+/* As spamm_tree_to_dense, into a dense n x n FP32 row-major matrix: FP32 tiles (the
+   products in the tensor-core precisions) are copied as they are, FP64 tiles rounded
+   to nearest FP32. Half the bytes of the FP64 image, for callers that read a
+   tensor-core product back to the host. The paper has no counterpart (its C stays in
+   the quadtree). Errors as spamm_tree_to_dense. */
+SPAMM_API spamm_status spamm_tree_to_dense_f32(spamm_tree t, float *out, int32_t out_is_host);
 
 /* ---- the product (Eq. 4) ----
    C ~ A B with tolerance tau: the tier-by-tier cull of Eq. 4 from the root

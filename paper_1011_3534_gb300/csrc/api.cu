@@ -117,8 +117,9 @@ spamm_status alloc_tree(spamm_ctx ctx, int64_t n, int32_t b, int32_t flags, spam
   t->flags = flags;
   shape(n, b, &t->nb, &t->NB, &t->kmax);
   if (t->kmax >= SPAMM_MAX_LEVELS - 1 || t->NB > 65536) {
+    const int32_t NB = t->NB;
     delete t;
-    return fail(ctx, SPAMM_EUNSUPPORTED, "n / leaf too large (NB = %d)", t->NB);
+    return fail(ctx, SPAMM_EUNSUPPORTED, "n / leaf too large (NB = %d)", NB);
   }
   const size_t levels = (size_t)level_offset(t->kmax + 1);
   cudaError_t e = dmalloc(&t->norm2, levels * sizeof(double));
@@ -524,23 +525,45 @@ spamm_status spamm_tree_norms(spamm_tree t, int32_t level, double *out) {
   return check_device_status(ctx);
 }
 
-spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host) {
+spamm_status spamm_tree_leaf_copy(spamm_tree t, int32_t which, void *out, int64_t bytes, int32_t out_is_host) {
   if (!t) return SPAMM_EINVAL;
   spamm_ctx ctx = t->ctx;
   if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
-  if (!out) return fail(ctx, SPAMM_EINVAL, "tree_to_dense: null output");
+  if (!out || which < 0 || which >= CK_COUNT || (out_is_host != 0 && out_is_host != 1))
+    return fail(ctx, SPAMM_EINVAL, "tree_leaf_copy: bad arguments");
+  if (!t->copy[which]) return fail(ctx, SPAMM_EINVAL, "tree_leaf_copy: the tree holds no copy %d", which);
+  const int64_t need = (int64_t)t->nb * t->nb * t->b * t->b * copy_elem_bytes(which);
+  if (bytes < need) return fail(ctx, SPAMM_ERANGE, "tree_leaf_copy: %lld bytes needed", (long long)need);
+  CK(cudaMemcpyAsync(out, t->copy[which], (size_t)need, out_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     ctx->stream), "tree_leaf_copy: copy");
+  return out_is_host ? check_device_status(ctx) : SPAMM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Dense image of a tree in FP64 (f32 = false) or FP32: on the context's stream into
+// device memory, or through the output staging buffer and the context's copy stream
+// into host memory (the staging buffer is reused only after the previous copy out of it
+// finished).
+spamm_status to_dense_impl(spamm_tree t, void *out, int32_t out_is_host, bool f32, const char *name) {
+  if (!t) return SPAMM_EINVAL;
+  spamm_ctx ctx = t->ctx;
+  if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
+  if (!out) return fail(ctx, SPAMM_EINVAL, "%s: null output", name);
   if (!t->copy[CK_F64] && !t->copy[CK_F32])
-    return fail(ctx, SPAMM_EINVAL, "tree_to_dense: the tree keeps no FP64/FP32 tiles (SPAMM_KEEP_FP64)");
-  if (out_is_host < 0 || out_is_host > 2) return fail(ctx, SPAMM_EINVAL, "tree_to_dense: out_is_host must be 0, 1 or 2");
-  const size_t bytes = (size_t)t->n * t->n * sizeof(double);
+    return fail(ctx, SPAMM_EINVAL, "%s: the tree keeps no FP64/FP32 tiles (SPAMM_KEEP_FP64)", name);
+  if (out_is_host < 0 || out_is_host > 2) return fail(ctx, SPAMM_EINVAL, "%s: out_is_host must be 0, 1 or 2", name);
+  const size_t bytes = (size_t)t->n * t->n * (f32 ? sizeof(float) : sizeof(double));
+  auto launch = [&](void *dst) {
+    return f32 ? launch_to_dense_f32(t, (float *)dst, ctx->stream) : launch_to_dense(t, (double *)dst, ctx->stream);
+  };
   if (!out_is_host) {
-    CK(launch_to_dense(t, out, ctx->stream), "tree_to_dense: launch");
+    CK(launch(out), "tree_to_dense: launch");
     ctx->launches++;
     return SPAMM_OK;
   }
-  // host output: dense image into the output staging buffer on the context's stream,
-  // then the copy on the copy stream (the staging buffer is reused only after the
-  // previous copy out of it finished)
   if (!ctx->d2h) {
     CK(cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking), "tree_to_dense: copy stream");
     CK(cudaEventCreateWithFlags(&ctx->d2h_staged, cudaEventDisableTiming), "tree_to_dense: event");
@@ -556,7 +579,7 @@ spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host)
     ctx->stage_out_bytes = bytes;
   }
   if (ctx->d2h_pending) CK(cudaStreamWaitEvent(ctx->stream, ctx->d2h_done, 0), "tree_to_dense: wait");
-  CK(launch_to_dense(t, (double *)ctx->stage_out, ctx->stream), "tree_to_dense: launch");
+  CK(launch(ctx->stage_out), "tree_to_dense: launch");
   ctx->launches++;
   CK(cudaEventRecord(ctx->d2h_staged, ctx->stream), "tree_to_dense: event");
   CK(cudaStreamWaitEvent(ctx->d2h, ctx->d2h_staged, 0), "tree_to_dense: wait");
@@ -565,6 +588,18 @@ spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host)
   ctx->d2h_pending = true;
   if (out_is_host == 1) return check_device_status(ctx);
   return SPAMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spamm_status spamm_tree_to_dense(spamm_tree t, double *out, int32_t out_is_host) {
+  return to_dense_impl(t, out, out_is_host, false, "tree_to_dense");
+}
+
+spamm_status spamm_tree_to_dense_f32(spamm_tree t, float *out, int32_t out_is_host) {
+  return to_dense_impl(t, out, out_is_host, true, "tree_to_dense_f32");
 }
 
 spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau, const double *tau_dev,

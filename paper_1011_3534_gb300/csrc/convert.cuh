@@ -198,10 +198,50 @@ __device__ __forceinline__ uint32_t f32_fast(uint32_t h, uint32_t l) {
   return (uh & 0x80000000u) | ((((uh >> 20) & 0x7FFu) - 896u) << 23) | ((uint32_t)(u >> 29) & 0x7FFFFFu);
 }
 
+// Low part of the split pair of an FP64 value, hi = fmt(x) rounded at bit K of the
+// 64-bit pattern (K = 45: BF16, K = 42: TF32): x - hi = (-1)^s M 2^(E - 1075) exactly,
+// M the integer formed by the K discarded significand bits (or 2^K minus them when hi
+// rounded up). M is normalised with a count of leading zeros and returned as an FP32
+// pattern whose last bit also holds every bit of M below the FP32 significand (sticky),
+// so that one round to nearest even at 8 or 11 significant bits gives the correctly
+// rounded fmt(x - hi). Zero when x = hi. Valid for FP64 exponent fields E in
+// [949, 1150]: a nonzero x - hi is then at least 2^-126, an FP32-normal value.
+template <int K>
+__device__ __forceinline__ uint32_t split_lo_sticky(uint32_t h, uint32_t l, int E) {
+  constexpr uint32_t mask = (1u << (K - 32)) - 1u, half = 1u << (K - 33);
+  const uint32_t rh = h & mask;
+  const bool lnz = l != 0u;
+  const bool up = rh > half || (rh == half && (lnz || ((h >> (K - 32)) & 1u)));
+  const uint32_t Mh = up ? mask + 1u - rh - (lnz ? 1u : 0u) : rh;
+  const uint32_t Ml = up ? 0u - l : l;
+  const uint32_t sign = (h ^ (up ? 0x80000000u : 0u)) & 0x80000000u;
+  const bool hz = Mh == 0u;
+  const uint32_t top = hz ? Ml : Mh, bot = hz ? 0u : Ml;
+  if (top == 0u) return 0u;
+  const int lz = __clz((int)top);                        // < 32: top != 0
+  const uint32_t T = __funnelshift_lc(bot, top, lz);    // bits p .. p - 31 of M
+  const uint32_t rest = bot << lz;
+  const int be = E - 948 + (hz ? 31 : 63) - lz;          // FP32 biased exponent of M 2^(E - 1075)
+  return sign | ((uint32_t)be << 23) | ((T >> 8) & 0x7FFFFFu) | (((T & 0xFFu) | rest) != 0u ? 1u : 0u);
+}
+
+// TF32 (as FP32 bits) of an FP32 pattern with a sticky last bit: round to nearest
+// even at bit 13.
+__device__ __forceinline__ uint32_t tf32_of_sticky(uint32_t f) {
+  return (f + 0xFFFu + ((f >> 13) & 1u)) & 0xFFFFE000u;
+}
+
 // Out-of-line rounding for the rare inputs outside a fast path's range, so the fast
 // paths stay short branches instead of predicated copies of the general code.
 static __device__ __noinline__ uint32_t slow_round_bits(uint32_t h, uint32_t l, int p, int emin) {
   return round_f64bits(((uint64_t)h << 32) | l, p, emin).bits;
+}
+
+// fmt(x - fmt(x)) (BF16: p = 8, TF32: p = 11) as FP32 bits, for inputs outside the fast
+// split's range.
+static __device__ __noinline__ uint32_t slow_split_lo(uint32_t h, uint32_t l, int p) {
+  const uint64_t bits = ((uint64_t)h << 32) | l;
+  return split_lo_bits(bits, round_f64bits(bits, p, -126), p);
 }
 
 static __device__ __noinline__ uint32_t slow_fp16_bits(uint32_t h, uint32_t l) {

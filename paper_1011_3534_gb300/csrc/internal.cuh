@@ -198,6 +198,7 @@ cudaError_t launch_mirror(spamm_tree C, cudaStream_t s);       // C_ji := C_ij^T
 // *kept when not null), then the norm pyramid rebuilt.
 cudaError_t launch_drop(spamm_tree t, double tau, unsigned long long *kept, cudaStream_t s);
 cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s);
+cudaError_t launch_to_dense_f32(spamm_tree t, float *out, cudaStream_t s);
 cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, const double *tau_dev,
                         uint32_t *dev_status, int sm_count, cudaStream_t s, int *launches);
 cudaError_t launch_leaf_f64(spamm_tree A, spamm_tree B, spamm_tree C, uint32_t *dev_status,

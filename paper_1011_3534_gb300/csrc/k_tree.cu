@@ -124,6 +124,8 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
   // a round whose 8 elements are all FP32-normal (exponent fields 897..1150) within 60
   // binades of each other needs no per-element range test in the norm or the copies
   const bool fast = Emin >= 897 && Er <= 1150 && Er - Emin <= 60;
+  // ... and a round whose elements all have exponent fields 949..1150 splits on the fast path
+  const bool fast_split = Emin >= 949 && Er <= 1150;
   if (Er > 0 && Er < 0x7FF) {
     // two independent double-float sums (even and odd elements) halve the dependency
     // chain; they are joined once per round
@@ -170,31 +172,33 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
     }
     if (p.bf16 || s_bf16T || p.lo || s_loT) {
       uint32_t b0, b1;
-      Rounded r0, r1;
-      const bool need_r = p.lo || s_loT;
-      if (need_r) {   // the split needs the rounded significands
-        r0 = round_f64bits(((uint64_t)h0 << 32) | l0, 8, -126);
-        r1 = round_f64bits(((uint64_t)h1 << 32) | l1, 8, -126);
-        b0 = r0.bits >> 16;
-        b1 = r1.bits >> 16;
-      } else {
-        if (fast || (E0 >= 897 && E0 <= 1150 && E1 >= 897 && E1 <= 1150)) {
-          const uint32_t pk = bf16x2_fast(h0, l0, h1, l1);
-          b0 = pk & 0xFFFFu;
-          b1 = pk >> 16;
-        } else {   // out of the FP32-normal range: out of line
-          b0 = (E0 >= 897 && E0 <= 1150) ? bf16_fast(h0, l0) : (slow_round_bits(h0, l0, 8, -126) >> 16);
-          b1 = (E1 >= 897 && E1 <= 1150) ? bf16_fast(h1, l1) : (slow_round_bits(h1, l1, 8, -126) >> 16);
-        }
+      if (fast || (E0 >= 897 && E0 <= 1150 && E1 >= 897 && E1 <= 1150)) {
+        const uint32_t pk = bf16x2_fast(h0, l0, h1, l1);
+        b0 = pk & 0xFFFFu;
+        b1 = pk >> 16;
+      } else {   // out of the FP32-normal range: out of line
+        b0 = (E0 >= 897 && E0 <= 1150) ? bf16_fast(h0, l0) : (slow_round_bits(h0, l0, 8, -126) >> 16);
+        b1 = (E1 >= 897 && E1 <= 1150) ? bf16_fast(h1, l1) : (slow_round_bits(h1, l1, 8, -126) >> 16);
       }
       if (p.bf16) *reinterpret_cast<uint32_t *>(p.bf16 + o) = b0 | (b1 << 16);
       if (s_bf16T) {
         s_bf16T[cols[u] * B + rows[u]] = (uint16_t)b0;
         s_bf16T[(cols[u] + 1) * B + rows[u]] = (uint16_t)b1;
       }
-      if (need_r) {
-        const uint32_t q0 = bf16_lo_bits(((uint64_t)h0 << 32) | l0, r0) >> 16;
-        const uint32_t q1 = bf16_lo_bits(((uint64_t)h1 << 32) | l1, r1) >> 16;
+      if (p.lo || s_loT) {   // low parts of the split: bf16(x - hi)
+        uint32_t q0, q1;
+        if (fast_split || (E0 >= 949 && E0 <= 1150 && E1 >= 949 && E1 <= 1150)) {
+          uint32_t pk;
+          asm("cvt.rn.bf16x2.f32 %0, %1, %2;"
+              : "=r"(pk)
+              : "f"(__uint_as_float(split_lo_sticky<45>(h1, l1, E1))),
+                "f"(__uint_as_float(split_lo_sticky<45>(h0, l0, E0))));
+          q0 = pk & 0xFFFFu;
+          q1 = pk >> 16;
+        } else {
+          q0 = slow_split_lo(h0, l0, 8) >> 16;
+          q1 = slow_split_lo(h1, l1, 8) >> 16;
+        }
         if (p.lo) *reinterpret_cast<uint32_t *>(p.lo + o) = q0 | (q1 << 16);
         if (s_loT) {
           s_loT[cols[u] * B + rows[u]] = (uint16_t)q0;
@@ -203,29 +207,27 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
       }
     }
     if (p.tf32 || s_tf32T || p.tlo || s_tloT) {
-      uint32_t t0, t1;
-      if (p.tlo || s_tloT) {
-        const Rounded r0 = round_f64bits(((uint64_t)h0 << 32) | l0, 11, -126);
-        const Rounded r1 = round_f64bits(((uint64_t)h1 << 32) | l1, 11, -126);
-        t0 = r0.bits;
-        t1 = r1.bits;
-        const uint32_t q0 = split_lo_bits(((uint64_t)h0 << 32) | l0, r0, 11);
-        const uint32_t q1 = split_lo_bits(((uint64_t)h1 << 32) | l1, r1, 11);
+      const uint32_t t0 = (E0 >= 897 && E0 <= 1150) ? tf32_fast(h0, l0) : slow_round_bits(h0, l0, 11, -126);
+      const uint32_t t1 = (E1 >= 897 && E1 <= 1150) ? tf32_fast(h1, l1) : slow_round_bits(h1, l1, 11, -126);
+      if (p.tf32) *reinterpret_cast<uint2 *>(p.tf32 + o) = make_uint2(t0, t1);
+      if (s_tf32T) {
+        s_tf32T[cols[u] * B + rows[u]] = __uint_as_float(t0);
+        s_tf32T[(cols[u] + 1) * B + rows[u]] = __uint_as_float(t1);
+      }
+      if (p.tlo || s_tloT) {   // low parts of the split: tf32(x - hi)
+        uint32_t q0, q1;
+        if (fast_split || (E0 >= 949 && E0 <= 1150 && E1 >= 949 && E1 <= 1150)) {
+          q0 = tf32_of_sticky(split_lo_sticky<42>(h0, l0, E0));
+          q1 = tf32_of_sticky(split_lo_sticky<42>(h1, l1, E1));
+        } else {
+          q0 = slow_split_lo(h0, l0, 11);
+          q1 = slow_split_lo(h1, l1, 11);
+        }
         if (p.tlo) *reinterpret_cast<uint2 *>(p.tlo + o) = make_uint2(q0, q1);
         if (s_tloT) {
           s_tloT[cols[u] * B + rows[u]] = __uint_as_float(q0);
           s_tloT[(cols[u] + 1) * B + rows[u]] = __uint_as_float(q1);
         }
-      } else {
-        t0 = (E0 >= 897 && E0 <= 1150) ? tf32_fast(h0, l0)
-                                       : slow_round_bits(h0, l0, 11, -126);
-        t1 = (E1 >= 897 && E1 <= 1150) ? tf32_fast(h1, l1)
-                                       : slow_round_bits(h1, l1, 11, -126);
-      }
-      if (p.tf32) *reinterpret_cast<uint2 *>(p.tf32 + o) = make_uint2(t0, t1);
-      if (s_tf32T) {
-        s_tf32T[cols[u] * B + rows[u]] = __uint_as_float(t0);
-        s_tf32T[(cols[u] + 1) * B + rows[u]] = __uint_as_float(t1);
       }
     }
     if (p.fp16 || s_fp16T) {
@@ -468,30 +470,34 @@ __global__ void __launch_bounds__(1024) k_pyramid_top(double *norm2, double *nor
   pyramid_top_tiers(norm2, norm, top_tier);
 }
 
-// Dense row-major FP64 image of a tree's master tiles. A thread writes four
-// consecutive columns of one row (they lie in one leaf: b is a multiple of 4), rows
-// are spread over grid.y; 16-byte stores when the output rows are 16-byte aligned. The
-// output may be device memory or mapped page-locked host memory.
-template <typename T>
+// Dense row-major image (FP64, or FP32 rounded to nearest) of a tree's master tiles. A
+// thread writes four consecutive columns of one row (they lie in one leaf: b is a
+// multiple of 4), rows are spread over grid.y; 16-byte stores when the output rows are
+// 16-byte aligned. The output may be device memory or mapped page-locked host memory.
+template <typename T, typename O>
 __global__ void __launch_bounds__(256) k_to_dense(const T *tiles, const uint8_t *nz, int64_t n, int32_t lb,
-                                                  int32_t nb, int32_t NB, double *out, int vec) {
+                                                  int32_t nb, int32_t NB, O *out, int vec) {
   const int32_t b = 1 << lb;
   const int64_t groups = (n + 3) / 4;   // four-column groups per row
   for (int64_t row = blockIdx.y; row < n; row += gridDim.y) {
     const int64_t r = row >> lb, rr = row & (b - 1);
-    double *orow = out + row * n;
+    O *orow = out + row * n;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
          g += (int64_t)gridDim.x * blockDim.x) {
       const int64_t col = 4 * g, c = col >> lb, cc = col & (b - 1);
-      double v[4] = {0.0, 0.0, 0.0, 0.0};
+      O v[4] = {O(0), O(0), O(0), O(0)};
       if (nz[r * NB + c]) {
         const T *src = tiles + ((r * nb + c) * b + rr) * b + cc;
 #pragma unroll
-        for (int q = 0; q < 4; q++) v[q] = (double)src[q];   // col + q < b: same leaf, stored
+        for (int q = 0; q < 4; q++) v[q] = (O)src[q];   // col + q < b: same leaf, stored
       }
       if (vec && col + 3 < n) {
-        reinterpret_cast<double2 *>(orow + col)[0] = make_double2(v[0], v[1]);
-        reinterpret_cast<double2 *>(orow + col)[1] = make_double2(v[2], v[3]);
+        if constexpr (sizeof(O) == 8) {
+          reinterpret_cast<double2 *>(orow + col)[0] = make_double2(v[0], v[1]);
+          reinterpret_cast<double2 *>(orow + col)[1] = make_double2(v[2], v[3]);
+        } else {
+          *reinterpret_cast<float4 *>(orow + col) = make_float4(v[0], v[1], v[2], v[3]);
+        }
       } else {
         for (int q = 0; q < 4 && col + q < n; q++) orow[col + q] = v[q];
       }
@@ -700,24 +706,30 @@ cudaError_t launch_drop(spamm_tree t, double tau, unsigned long long *kept, cuda
   return launch_pyramid(t, s);
 }
 
-cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s) {
+template <typename O>
+static cudaError_t to_dense_as(spamm_tree t, O *out, cudaStream_t s) {
   int lb = 0;
   while ((1 << lb) < t->b) lb++;
   const int64_t groups = (t->n + 3) / 4;
   const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((groups + 255) / 256, 8)),
                   (unsigned)std::min<int64_t>(t->n, 8192));
-  const int vec = (t->n % 2) == 0 && ((uintptr_t)out % 16) == 0;
+  // 16-byte stores need 16-byte aligned rows
+  const int vec = (t->n * (int64_t)sizeof(O)) % 16 == 0 && ((uintptr_t)out % 16) == 0;
   if (t->copy[CK_F64]) {
-    k_to_dense<double><<<grid, 256, 0, s>>>((const double *)t->copy[CK_F64], t->nz, t->n, lb, t->nb, t->NB,
-                                            out, vec);
+    k_to_dense<double, O><<<grid, 256, 0, s>>>((const double *)t->copy[CK_F64], t->nz, t->n, lb, t->nb, t->NB,
+                                               out, vec);
   } else if (t->copy[CK_F32]) {
-    k_to_dense<float><<<grid, 256, 0, s>>>((const float *)t->copy[CK_F32], t->nz, t->n, lb, t->nb, t->NB,
-                                           out, vec);
+    k_to_dense<float, O><<<grid, 256, 0, s>>>((const float *)t->copy[CK_F32], t->nz, t->n, lb, t->nb, t->NB,
+                                              out, vec);
   } else {
     return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
+
+cudaError_t launch_to_dense(spamm_tree t, double *out, cudaStream_t s) { return to_dense_as<double>(t, out, s); }
+
+cudaError_t launch_to_dense_f32(spamm_tree t, float *out, cudaStream_t s) { return to_dense_as<float>(t, out, s); }
 
 // ---- leaf copies of a product tree, from its master tiles (FP64 or FP32) ----
 namespace {

@@ -40,7 +40,7 @@ MAX_LEVELS = 24
 EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_error",
            "spamm_kernel_launches", "spamm_tree_build", "spamm_tree_update", "spamm_tree_free", "spamm_tree_info",
            "spamm_tree_build_ms",
-           "spamm_tree_norms", "spamm_tree_to_dense", "spamm_multiply", "spamm_stats",
+           "spamm_tree_norms", "spamm_tree_to_dense", "spamm_tree_to_dense_f32", "spamm_tree_leaf_copy", "spamm_multiply", "spamm_stats",
            "spamm_triples", "spamm_cull_noalloc", "spamm_sp2", "spamm_multiply_batched",
            "spamm_tune_leaf", "spamm_mlp_create", "spamm_mlp_free", "spamm_mlp_num_params",
            "spamm_mlp_get_params", "spamm_mlp_set_params", "spamm_mlp_forward", "spamm_mlp_gradient",
@@ -102,6 +102,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
                                   ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
     L.spamm_tree_norms.argtypes = [_P, _I32, _P]
     L.spamm_tree_to_dense.argtypes = [_P, _P, _I32]
+    L.spamm_tree_to_dense_f32.argtypes = [_P, _P, _I32]
+    L.spamm_tree_leaf_copy.argtypes = [_P, _I32, _P, _I64, _I32]
     L.spamm_multiply.argtypes = [_P, _P, _P, _D, ctypes.c_int, _I32, ctypes.POINTER(_P)]
     L.spamm_stats.argtypes = [_P, ctypes.POINTER(StatsT)]
     L.spamm_triples.argtypes = [_P, _P, _I64, ctypes.POINTER(_I64)]
@@ -162,21 +164,22 @@ def _ptr(x) -> int:
     raise TypeError(type(x))
 
 
-def _matrix(x, n: int, what: str, device: int | None = None, writable: bool = False) -> tuple[int, bool]:
-    """Address of an n x n row-major FP64 matrix and whether it is in host memory: a
-    numpy array or torch CPU tensor (host, pageable or page-locked) or a torch CUDA
-    tensor on the context's device. Any other type, dtype, size or layout raises here,
-    before the library sees the pointer."""
+def _matrix(x, n: int, what: str, device: int | None = None, writable: bool = False,
+            dtype: str = "float64") -> tuple[int, bool]:
+    """Address of an n x n row-major matrix of `dtype` (FP64 unless stated) and whether
+    it is in host memory: a numpy array or torch CPU tensor (host, pageable or
+    page-locked) or a torch CUDA tensor on the context's device. Any other type, dtype,
+    size or layout raises here, before the library sees the pointer."""
     if isinstance(x, np.ndarray):
-        if x.dtype != np.float64 or not x.flags.c_contiguous or (n >= 1 and x.size != n * n):
-            raise ValueError(f"{what}: need a C-contiguous float64 array of {n} x {n} elements, "
+        if x.dtype != np.dtype(dtype) or not x.flags.c_contiguous or (n >= 1 and x.size != n * n):
+            raise ValueError(f"{what}: need a C-contiguous {dtype} array of {n} x {n} elements, "
                              f"got {x.dtype} {x.shape}")
         if writable and not x.flags.writeable:
             raise ValueError(f"{what}: the output array is read-only")
         return x.ctypes.data, True
     if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
-        if str(x.dtype) != "torch.float64" or not x.is_contiguous() or (n >= 1 and x.numel() != n * n):
-            raise ValueError(f"{what}: need a contiguous torch.float64 tensor of {n} x {n} elements, "
+        if str(x.dtype) != f"torch.{dtype}" or not x.is_contiguous() or (n >= 1 and x.numel() != n * n):
+            raise ValueError(f"{what}: need a contiguous torch.{dtype} tensor of {n} x {n} elements, "
                              f"got {x.dtype} {tuple(x.shape)}")
         if not x.is_cuda:
             return x.data_ptr(), True
@@ -306,6 +309,34 @@ def spamm_tree_to_dense(t: Tree, out=None, asynchronous: bool = False):
     addr, host = _matrix(out, t.n, "spamm_tree_to_dense", t.ctx.device, writable=True)
     mode = (2 if asynchronous else 1) if host else 0
     t.ctx.check(LIB.spamm_tree_to_dense(t.h, addr, mode), "spamm_tree_to_dense")
+    return out
+
+
+def spamm_tree_to_dense_f32(t: Tree, out=None, asynchronous: bool = False):
+    """Dense n x n FP32 copy (FP32 tiles as they are, FP64 tiles rounded to nearest):
+    into `out` (numpy float32 host or torch float32 device), or a new numpy array.
+    asynchronous (host output only): return once queued; `out` is complete after spamm_sync."""
+    if out is None:
+        out = np.empty((t.n, t.n), dtype=np.float32)
+    addr, host = _matrix(out, t.n, "spamm_tree_to_dense_f32", t.ctx.device, writable=True, dtype="float32")
+    mode = (2 if asynchronous else 1) if host else 0
+    t.ctx.check(LIB.spamm_tree_to_dense_f32(t.h, addr, mode), "spamm_tree_to_dense_f32")
+    return out
+
+
+SPAMM_LEAF = {"f64": 0, "f32": 1, "tf32": 2, "tf32_t": 3, "bf16": 4, "bf16_t": 5, "fp16": 6, "fp16_t": 7,
+              "bf16lo": 8, "bf16lo_t": 9, "tf32lo": 10, "tf32lo_t": 11}
+_LEAF_DTYPE = {"f64": np.float64, "f32": np.float32, "tf32": np.float32, "tf32lo": np.float32,
+               "bf16": np.uint16, "fp16": np.uint16, "bf16lo": np.uint16}
+
+
+def spamm_tree_leaf_copy(t: Tree, which: str) -> np.ndarray:
+    """One stored leaf copy of a tree as a host array of shape (nb, nb, leaf, leaf) (leaf
+    (r, c) at [r, c]; BF16 and FP16 copies as their uint16 bit patterns)."""
+    nb = -(-t.n // t.leaf)
+    out = np.empty((nb, nb, t.leaf, t.leaf), dtype=_LEAF_DTYPE[which.replace("_t", "")])
+    t.ctx.check(LIB.spamm_tree_leaf_copy(t.h, SPAMM_LEAF[which], out.ctypes.data, out.nbytes, 1),
+                "spamm_tree_leaf_copy")
     return out
 
 
