@@ -635,8 +635,6 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
     if (!A->copy[CK_F64] || !B->copy[CK_F64])
       return fail(ctx, SPAMM_EINVAL, "multiply: SPAMM_FP64 needs SPAMM_KEEP_FP64 operands");
   } else {
-    if (A->b != 64 && A->b != 128)
-      return fail(ctx, SPAMM_EUNSUPPORTED, "multiply: tensor-core precisions need leaf 64 or 128");
     int row = tf32_prec(prec) ? CK_TF32 : prec == SPAMM_FP16 ? CK_FP16 : CK_BF16;
     int rowT = row + 1;
     const int lo = prec == SPAMM_TF32X3 ? CK_TF32LO : CK_BF16LO;
@@ -704,14 +702,16 @@ spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau
   int launches = 0;
   CK(launch_cull(A, B, Ct, tau, tau_dev, ctx->dev_status, ctx->sm_count, s, &launches), "multiply: cull launch");
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[1], s), "event");
-  if (tc) {
+  if (tc && Ct->b >= 64) {
     CK(launch_leaf_tc(A, B, Ct, prec, ctx->dev_status, ctx->sm_count, s), "multiply: leaf launch");
+  } else if (tc) {
+    CK(launch_leaf_mma(A, B, Ct, prec, ctx->dev_status, ctx->sm_count, s), "multiply: leaf launch");
   } else {
     CK(launch_leaf_f64(A, B, Ct, ctx->dev_status, ctx->sm_count, s), "multiply: leaf launch");
   }
   launches++;
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[2], s), "event");
-  if (Ct->sym_product && (!tc || split_prec(prec))) {   // the plain tensor-core forms mirror in their epilogue
+  if (Ct->sym_product && mirror_after_leaf(Ct)) {   // the plain tcgen05 forms mirror in their epilogue
     CK(launch_mirror(Ct, s), "multiply: mirror launch");
     launches++;
   }
@@ -774,9 +774,12 @@ spamm_status spamm_stats(spamm_tree C, spamm_stats_t *out) {
     const double b = C->b;
     S.leaf_flops = 2.0 * b * b * b * (double)h.leaf_products;
     S.dense_equiv_flops = 2.0 * (double)C->n * (double)C->n * (double)C->n;
-    // tensor-core kernel: one stage = a 128 x 128 x (128-byte K chunk) MMA chain
+    // tensor-core kernel: counted in 128 x 64 x (128-byte K chunk) MMA chains (an N = 128
+    // MMA of one operand pair is two, a split stage's three products three times that)
     const double chunk_k = tf32_prec(C->prec) ? 32.0 : 64.0;
-    S.mma_flops = C->prec == SPAMM_FP64 ? S.leaf_flops : (double)h.mma_tiles * 2.0 * 128.0 * 128.0 * chunk_k;
+    S.mma_flops = C->prec == SPAMM_FP64 ? S.leaf_flops : (double)h.mma_tiles * 2.0 * 128.0 * 64.0 * chunk_k;
+    // small leaves: warp-level m16n8k16 (BF16, FP16) or m16n8k8 (TF32) instructions
+    if (C->prec != SPAMM_FP64) S.mma_flops += (double)h.mma_small * 2.0 * 16.0 * 8.0 * (tf32_prec(C->prec) ? 8.0 : 16.0);
     S.prec = C->prec;
     S.tau = C->tau;
     if (ctx->timing && C->ev[0]) {

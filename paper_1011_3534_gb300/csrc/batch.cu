@@ -125,6 +125,11 @@ static spamm_status batch_sequence(spamm_ctx ctx, const spamm_tree *A, const spa
           "batch: leaf launch");
       ctx->launches++;
     }
+    for (int p = 0; p < count; p++)   // leaves of 16 and 32: the warp-level kernel, one launch per product
+      if (C[p]->b < 64) {
+        BCK(launch_leaf_mma(A[p], B[p], C[p], prec, ctx->dev_status, ctx->sm_count, ctx->stream), "batch: leaf launch");
+        ctx->launches++;
+      }
   } else {
     for (int p = 0; p < count; p++) {
       BCK(launch_leaf_f64(A[p], B[p], C[p], ctx->dev_status, ctx->sm_count, ctx->stream), "batch: leaf launch");
@@ -275,7 +280,7 @@ extern "C" spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t 
     return SPAMM_OK;
   }
   const bool tc = prec != SPAMM_FP64;
-  std::vector<int> cand = tc ? std::vector<int>{64, 128} : std::vector<int>{16, 32, 64, 128};
+  std::vector<int> cand = {16, 32, 64, 128};
   const int32_t copy = tc ? (prec == SPAMM_TF32 ? SPAMM_COPY_TF32 : prec == SPAMM_FP16 ? SPAMM_COPY_FP16
                              : prec == SPAMM_BF16X3 ? SPAMM_COPY_BF16X3
                              : prec == SPAMM_TF32X3 ? SPAMM_COPY_TF32X3 : SPAMM_COPY_BF16)

@@ -139,8 +139,9 @@ struct DevCounts {                     // device-resident counters of one produc
   unsigned long long leaf_products;
   unsigned long long mirror_products;  // triples of blocks i < j (mirrored to j > i)
   unsigned long long output_blocks;
-  unsigned long long mma_tiles;        // leaf-kernel MMA tile-steps issued
+  unsigned long long mma_tiles;        // leaf-kernel MMA chains issued, in 128 x 64 x chunk units
   unsigned long long npasses;          // passes of the tensor-core task plan
+  unsigned long long mma_small;        // warp-level MMA instructions of the small-leaf kernel
   unsigned int tile_ctr[SPAMM_MAX_LEVELS + 2];        // dynamic tile counters
   unsigned int work_ctr;
   double culled_bound[SPAMM_MAX_LEVELS];
@@ -188,6 +189,13 @@ struct spamm_tree_s {
   int build_pos = 0, build_count = 0;
 };
 
+// A symmetric product whose blocks j > i are written by k_mirror after the leaf kernel:
+// FP64, the split forms, and the small-leaf kernel (the plain tcgen05 forms write them in
+// their epilogue).
+inline bool mirror_after_leaf(const spamm_tree_s *C) {
+  return C->prec == SPAMM_FP64 || split_prec(C->prec) || C->b < 64;
+}
+
 __host__ __device__ inline int64_t level_offset(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
 
 // ---- launchers (each returns a cudaError_t from the launch) ----
@@ -202,6 +210,9 @@ cudaError_t launch_to_dense_f32(spamm_tree t, float *out, cudaStream_t s);
 cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, const double *tau_dev,
                         uint32_t *dev_status, int sm_count, cudaStream_t s, int *launches);
 cudaError_t launch_leaf_f64(spamm_tree A, spamm_tree B, spamm_tree C, uint32_t *dev_status,
+                            int sm_count, cudaStream_t s);
+// Tensor-core leaf products of leaf 16 and 32 (warp-level MMA), any tensor-core precision.
+cudaError_t launch_leaf_mma(spamm_tree A, spamm_tree B, spamm_tree C, int prec, uint32_t *dev_status,
                             int sm_count, cudaStream_t s);
 cudaError_t launch_leaf_tc(spamm_tree A, spamm_tree B, spamm_tree C, int prec,
                            uint32_t *dev_status, int sm_count, cudaStream_t s);

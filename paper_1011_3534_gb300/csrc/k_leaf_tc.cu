@@ -3,22 +3,35 @@
 // Work item. Leaf 64: one tier kmax-1 group (I, J), i.e. the 2 x 2 output blocks
 // (2I + a, 2J + c), a 128 x 128 FP32 accumulator in TMEM. Leaf 128: one output block
 // (2I + a, 2J + c), also 128 x 128. Items are dealt to a persistent grid of one CTA per
-// SM round-robin in Morton order of the output blocks.
+// SM in Morton order of the output blocks, serpentine: CTA b takes items b, 2G - 1 - b,
+// 2G + b, ... of a grid of G, so that the heavy and light ends of each round of G items
+// even out.
 //
 // Candidates. For each entry K of the group (ascending) and e = 0, 1, the surviving
 // children form a 2 x 2 pattern over (a, c). A pattern that is an outer product of a
 // row mask and a column mask is one pass: the A leaves (2I + a, k) of unmasked rows and
 // the B leaves (k, 2J + c) of unmasked columns are loaded, the others are zero-filled
-// by the TMA (a leaf coordinate past the end of the tensor), and one 128 x 128 x b MMA
-// chain adds exactly the surviving products. Other patterns take one pass per row.
-// Each output block therefore sums its surviving k in ascending order, in FP32.
+// by the TMA (a leaf coordinate past the end of the tensor), and one 128 x N x b MMA
+// chain adds exactly the surviving products: N = 128, or N = 64 on the one column half
+// a single-column pass touches (leaf 64). Other patterns take one pass per row. Each
+// output block therefore sums its surviving k in ascending order, in FP32.
 //
-// Pipeline (one CTA, 192 threads): warp 0 issues TMA loads into a ring of 6 stages of
-// 32 KB (A 128 x 128 B, B 128 x 128 B, 128-byte swizzle, one 128-byte K chunk per stage);
-// warp 1 issues tcgen05.mma (4 K-steps of 32 bytes per stage) into one of four TMEM
-// accumulators and commits to the stage's empty barrier; warps 2-5 drain a finished
-// accumulator with tcgen05.ld, store C (FP32 tiles) and its squared Frobenius norms
-// (double-float, fixed-order sums) while later items accumulate in the other buffers.
+// Pipeline (one CTA, 192 threads): warp 0 issues TMA loads into a ring of stages, one
+// 128-byte K chunk of every operand per stage (plain forms: 6 stages of A 128 x 128 B +
+// B 128 x 128 B; split forms: 3 stages of A hi, B hi, A lo, B lo, each hi and lo box
+// loaded once per chunk and read by the three products), 128-byte swizzle; warp 1
+// issues tcgen05.mma (4 K-steps of 32 bytes per operand pair and stage) and commits to
+// the stage's empty barrier; warps 2-5 drain finished accumulators with tcgen05.ld,
+// store C (FP32 tiles) and its squared Frobenius norms (double-float, fixed-order
+// sums) while later work accumulates in the other TMEM buffers.
+//
+// Accumulation. The tensor cores of this GPU truncate each MMA's FP32 sum (measured
+// bias about -0.5 unit in the last place per instruction), so the error of one
+// accumulator grows with the instructions it takes at its own magnitude. Plain forms:
+// one accumulator per item (four in TMEM). Split forms (hi hi + hi lo + lo hi): every
+// pass gets a fresh pair, the large hi hi products in one and the small corrections in
+// the other, and the epilogue adds the pair and the passes in FP32 registers with round
+// to nearest, in the order of the plan (two pass slots of two accumulators in TMEM).
 // Every wait is bounded; a wait that runs out sets an error bit and the CTA unwinds.
 #include <cudaTypedefs.h>
 
@@ -27,13 +40,23 @@
 
 namespace {
 
-constexpr int kStages = 6;
-constexpr int kStageA = 16384;
-constexpr int kStageBytes = 32768;
 constexpr int kThreads = 192;
 constexpr uint32_t kTmemCols = 512;   // four 128-column FP32 accumulators
-constexpr int kAcc = 4;
-constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024;
+constexpr int kBoxBytes = 16384;      // one operand of one stage: 128 rows x 128 bytes
+constexpr size_t kSmemBytes = (size_t)6 * 32768 + 1024;   // the ring (either form) + alignment
+
+// Stage ring of the plain (one operand pair) and split (hi and lo of both operands) forms.
+template <bool SPLIT>
+struct Ring {
+  static constexpr int kStages = SPLIT ? 3 : 6;
+  static constexpr int kStageBytes = SPLIT ? 4 * kBoxBytes : 2 * kBoxBytes;
+  // byte offsets inside a stage
+  static constexpr int kAhi = 0, kBhi = kBoxBytes, kAlo = 2 * kBoxBytes, kBlo = 3 * kBoxBytes;
+  static constexpr int kAcc = SPLIT ? 2 : 4;                 // accumulator slots
+  static constexpr uint32_t kAccCols = SPLIT ? 256u : 128u;  // TMEM columns per slot
+};
+static_assert((size_t)Ring<true>::kStages * Ring<true>::kStageBytes + 1024 <= kSmemBytes, "split ring");
+static_assert((size_t)Ring<false>::kStages * Ring<false>::kStageBytes + 1024 <= kSmemBytes, "plain ring");
 
 // One product of a launch. The table lives in device memory (64-byte aligned for the
 // tensor maps); a single product and a batch use the same kernel.
@@ -43,6 +66,7 @@ struct __align__(64) ProdDesc {
   const uint2 *items;                      // per item: {first pass, passes | touched << 24}
   const int4 *plan;                        // per pass: leaf coordinates of the four boxes
   int64_t cap_plan;
+  int64_t cap_items;
   const uint32_t *gij;                     // groups of the last tier list: (I << 16) | J
   const unsigned long long *ngroups;       // number of those groups (device)
   float *C;                                // FP32 tiles of the product
@@ -54,10 +78,10 @@ struct __align__(64) ProdDesc {
 };
 
 struct TcCommon {
-  uint32_t idesc;
+  uint32_t idesc;        // M = 128, N = 128
+  uint32_t idesc64;      // M = 128, N = 64
   int32_t chunks;        // 128-byte K chunks per leaf
   int32_t chunk_elems;   // elements per chunk
-  int32_t nsrc;          // 1, or 3 for the split products (hi hi, hi lo, lo hi)
   uint32_t *status;
 };
 
@@ -82,15 +106,41 @@ __device__ __forceinline__ int find_prod(const unsigned long long *s_off, int np
   return lo;
 }
 
-template <int LEAF, bool TF32, bool PERPASS>
+// Column halves a pass multiplies (leaf 64): bit c set when the B leaf of column c is
+// loaded (a coordinate below nb^2); a pass with neither (absent leaves, tau = 0) is
+// treated as a full one. Leaf 128 items have one column: always 3 (N = 128).
+template <int LEAF>
+__device__ __forceinline__ uint32_t pass_cols(const int4 &d, int oob) {
+  if (LEAF != 64) return 3u;
+  const uint32_t cm = (d.z < oob ? 1u : 0u) | (d.w < oob ? 2u : 0u);
+  return cm ? cm : 3u;
+}
+
+// Passes of an item that the kernel may read: the plan's count, cut at its capacity
+// (an overflowing plan is also flagged by the cull).
+__device__ __forceinline__ uint32_t item_passes(const ProdDesc &P, uint2 meta, uint32_t *status) {
+  const uint32_t first = meta.x;
+  uint32_t np = meta.y & 0xFFFFFFu;
+  if ((int64_t)first + np > P.cap_plan) {
+    flag_error(status, DEV_BADARG);
+    np = (int64_t)first >= P.cap_plan ? 0u : (uint32_t)(P.cap_plan - first);
+  }
+  return np;
+}
+
+template <int LEAF, bool TF32, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_leaf_tc(const ProdDesc *__restrict__ prods, int nprod, TcCommon cm) {
+  using R = Ring<SPLIT>;
+  constexpr int kStages = R::kStages;
+  constexpr int kAcc = R::kAcc;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[kAcc], acce[kAcc];
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   __shared__ double s_norm[4][2];
   __shared__ int4 s_desc[32];                    // producer: the chunk of passes being issued
+  __shared__ uint8_t s_cols[kStages];            // producer -> MMA: column halves of a stage
   __shared__ float s_epi[4][32][33];             // epilogue: one 32 x 32 chunk per warp, transposed out
   __shared__ unsigned long long s_off[kMaxProd + 1];   // first global item of each product
   constexpr int RA = LEAF == 64 ? 2 : 1;        // A leaves stacked along M
@@ -124,14 +174,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   const uint32_t tmem = s_tmem;
   const unsigned long long nitems = s_off[nprod];
-  const unsigned long long my_items =
-      nitems > blockIdx.x ? (nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0ull;
-  // item t of this CTA is global item blockIdx.x + t * gridDim.x; every role reads the
-  // metadata of 32 of its items at a time (lane l: item t0 + l)
+  const unsigned long long G = gridDim.x, b = blockIdx.x;
+  // serpentine dealing: round t of G items goes b-th from the front (t even) or back
+  const unsigned long long rounds = nitems / G, rest = nitems % G;
+  const unsigned long long my_items = rounds + (((rounds & 1ull) ? G - 1ull - b : b) < rest ? 1ull : 0ull);
+  // item t of this CTA; every role reads the metadata of 32 of its items at a time
+  // (lane l: item t0 + l)
   auto item_meta = [&](unsigned long long t, int &prod, unsigned long long &local) -> uint2 {
-    const unsigned long long g = blockIdx.x + t * gridDim.x;
+    const unsigned long long g = t * G + ((t & 1ull) ? G - 1ull - b : b);
     prod = find_prod(s_off, nprod, g);
     local = g - s_off[prod];
+    if ((int64_t)local >= prods[prod].cap_items) {   // cannot happen for a well-formed list
+      flag_error(cm.status, DEV_BADARG);
+      return make_uint2(0u, 0u);
+    }
     return prods[prod].items[local];
   };
 
@@ -142,6 +198,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0 && nprod == 1) {
       tma_prefetch_desc(&prods[0].mA);
       tma_prefetch_desc(&prods[0].mB);
+      if (SPLIT) {
+        tma_prefetch_desc(&prods[0].mAlo);
+        tma_prefetch_desc(&prods[0].mBlo);
+      }
     }
     int stage = 0;
     uint32_t phase = 0;
@@ -153,10 +213,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int ti = 0; ti < nt; ti++) {
         const int pr = __shfl_sync(0xffffffffu, prod, ti);
         const ProdDesc &P = prods[pr];
-        const uint32_t first = __shfl_sync(0xffffffffu, meta.x, ti);
-        uint32_t np = __shfl_sync(0xffffffffu, meta.y, ti) & 0xFFFFFFu;
-        const int64_t cap = P.cap_plan;
-        np = (int64_t)first >= cap ? 0u : ((int64_t)first + np > cap ? (uint32_t)(cap - first) : np);
+        const uint2 mt = make_uint2(__shfl_sync(0xffffffffu, meta.x, ti), __shfl_sync(0xffffffffu, meta.y, ti));
+        const uint32_t first = mt.x;
+        const uint32_t np = item_passes(P, mt, cm.status);
+        const int oob = P.nb * P.nb;
         const int4 *plan = P.plan;
         int4 cur = make_int4(0, 0, 0, 0);
         if ((uint32_t)lane < np) cur = plan[(int64_t)first + lane];
@@ -168,28 +228,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int nl = (int)min(32u, np - c0);
             for (int l = 0; l < nl && !s_abort; l++) {
               const int4 d = s_desc[l];
-              for (int si = 0; si < cm.nsrc && !s_abort; si++) {
-                // split forms: hi lo, lo hi, then hi hi, so the small products are summed
-                // before the accumulator holds the large one
-                const int src = cm.nsrc == 3 ? (si + 1) % 3 : 0;
-                const CUtensorMap *ma = src == 2 ? &P.mAlo : &P.mA;
-                const CUtensorMap *mb = src == 1 ? &P.mBlo : &P.mB;
-                for (int ch = 0; ch < cm.chunks; ch++) {
-                  if (!mbar_wait(&empty[stage], phase ^ 1u, &s_abort)) {
-                    s_abort = 1;
-                    flag_error(cm.status, DEV_TIMEOUT);
-                    break;
-                  }
-                  mbar_expect_tx(&full[stage], kStageBytes);
-                  const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
-                  tma_load_3d(sa, ma, &full[stage], ch * cm.chunk_elems, 0, d.x);
-                  if (RA == 2) tma_load_3d(sa + kBox, ma, &full[stage], ch * cm.chunk_elems, 0, d.y);
-                  tma_load_3d(sb, mb, &full[stage], ch * cm.chunk_elems, 0, d.z);
-                  if (RC == 2) tma_load_3d(sb + kBox, mb, &full[stage], ch * cm.chunk_elems, 0, d.w);
-                  if (++stage == kStages) {
-                    stage = 0;
-                    phase ^= 1u;
-                  }
+              // the first pass of a plain item initialises both column halves (N = 128)
+              const uint32_t cols = (!SPLIT && c0 + l == 0) ? 3u : pass_cols<LEAF>(d, oob);
+              const int boxes = (SPLIT ? 2 : 1) * (RA + (RC == 2 ? __popc(cols) : 1));
+              for (int ch = 0; ch < cm.chunks; ch++) {
+                if (!mbar_wait(&empty[stage], phase ^ 1u, &s_abort)) {
+                  s_abort = 1;
+                  flag_error(cm.status, DEV_TIMEOUT);
+                  break;
+                }
+                s_cols[stage] = (uint8_t)cols;   // read by the MMA warp after the full barrier
+                mbar_expect_tx(&full[stage], (uint32_t)boxes * kBox);
+                const uint32_t st = base + stage * R::kStageBytes;
+                const int x = ch * cm.chunk_elems;
+#pragma unroll
+                for (int h = 0; h < (SPLIT ? 2 : 1); h++) {   // hi, then (split) lo
+                  const CUtensorMap *ma = h ? &P.mAlo : &P.mA;
+                  const CUtensorMap *mb = h ? &P.mBlo : &P.mB;
+                  const uint32_t sa = st + (h ? R::kAlo : R::kAhi), sb = st + (h ? R::kBlo : R::kBhi);
+                  tma_load_3d(sa, ma, &full[stage], x, 0, d.x);
+                  if (RA == 2) tma_load_3d(sa + kBox, ma, &full[stage], x, 0, d.y);
+                  if (cols & 1u) tma_load_3d(sb, mb, &full[stage], x, 0, d.z);
+                  if (RC == 2 && (cols & 2u)) tma_load_3d(sb + kBox, mb, &full[stage], x, 0, d.w);
+                }
+                if (++stage == kStages) {
+                  stage = 0;
+                  phase ^= 1u;
                 }
               }
             }
@@ -206,6 +270,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t acc_phase = 0;
     unsigned long long nst = 0;
     int last_prod = -1;
+    // one MMA of the K-step kk of a stage: N = 128, or N = 64 on the column half c
+    auto mma = [&](uint32_t d, uint32_t sa, uint32_t sb, uint32_t cols, int kk, uint32_t accum) {
+      const uint64_t da = desc_sw128(sa + kk * 32);
+      if (cols == 3u) {
+        const uint64_t db = desc_sw128(sb + kk * 32);
+        if (TF32) mma_tf32(d, da, db, cm.idesc, accum); else mma_f16(d, da, db, cm.idesc, accum);
+      } else {
+        const uint32_t c = cols == 2u ? 1u : 0u;
+        const uint64_t db = desc_sw128(sb + c * kBox + kk * 32);
+        if (TF32) mma_tf32(d + 64u * c, da, db, cm.idesc64, accum);
+        else mma_f16(d + 64u * c, da, db, cm.idesc64, accum);
+      }
+    };
     for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
       int prod = 0;
       unsigned long long local = 0;
@@ -213,28 +290,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nt = (int)min(32ull, my_items - t0);
       for (int ti = 0; ti < nt; ti++) {
         const int pr = __shfl_sync(0xffffffffu, prod, ti);
-        const uint32_t first = __shfl_sync(0xffffffffu, meta.x, ti);
-        uint32_t np = __shfl_sync(0xffffffffu, meta.y, ti) & 0xFFFFFFu;
-        const int64_t cap = prods[pr].cap_plan;
-        np = (int64_t)first >= cap ? 0u : ((int64_t)first + np > cap ? (uint32_t)(cap - first) : np);
-        const int total = (int)np * cm.nsrc * cm.chunks;
+        const uint2 mt = make_uint2(__shfl_sync(0xffffffffu, meta.x, ti), __shfl_sync(0xffffffffu, meta.y, ti));
+        const uint32_t np = item_passes(prods[pr], mt, cm.status);
         if (lane == 0 && pr != last_prod) {
           // stage counts are kept per product: flush this CTA's count of the previous one
           if (last_prod >= 0 && nst) atomicAdd(prods[last_prod].mma_stages, nst);
           nst = 0;
           last_prod = pr;
         }
-        // one accumulator per item, or (PERPASS) a fresh one for every pass
-        const int chains = PERPASS ? (int)np : 1;
-        const int per_chain = PERPASS ? cm.nsrc * cm.chunks : total;
+        // plain: one accumulator per item; split: a fresh pair for every pass
+        const int chains = SPLIT ? (int)np : 1;
+        const int per_chain = SPLIT ? cm.chunks : (int)np * cm.chunks;
         for (int p = 0; p < chains && lane == 0 && !s_abort; p++) {
           if (!mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort)) {
             s_abort = 1;
             flag_error(cm.status, DEV_TIMEOUT);
           } else {
             tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)acc * 128u;
-            uint32_t accum = 0;
+            const uint32_t d = tmem + (uint32_t)acc * R::kAccCols;   // plain, or split hi hi
+            const uint32_t ds = d + 128u;                             // split: hi lo + lo hi
+            uint32_t acc_big = 0, acc_small = 0;
             for (int t = 0; t < per_chain; t++) {
               if (!mbar_wait(&full[stage], phase, &s_abort)) {
                 s_abort = 1;
@@ -242,16 +317,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
               }
               tc_fence_after();
-              const uint32_t sa = base + stage * kStageBytes, sb = sa + kStageA;
+              const uint32_t cols = s_cols[stage];
+              const uint32_t st = base + stage * R::kStageBytes;
 #pragma unroll
               for (int kk = 0; kk < 4; kk++) {
-                const uint64_t da = desc_sw128(sa + kk * 32), db = desc_sw128(sb + kk * 32);
-                if (TF32) mma_tf32(d, da, db, cm.idesc, accum);
-                else mma_f16(d, da, db, cm.idesc, accum);
-                accum = 1;
+                if (SPLIT) {
+                  mma(ds, st + R::kAhi, st + R::kBlo, cols, kk, acc_small);
+                  acc_small = 1;
+                  mma(ds, st + R::kAlo, st + R::kBhi, cols, kk, 1);
+                }
+                mma(d, st + R::kAhi, st + R::kBhi, cols, kk, acc_big);
+                acc_big = 1;
               }
               mma_commit(&empty[stage]);
-              nst++;
+              nst += (SPLIT ? 3u : 1u) * (cols == 3u ? 2u : 1u);   // 128 x 64 x chunk MMA chains
               if (++stage == kStages) {
                 stage = 0;
                 phase ^= 1u;
@@ -259,13 +338,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             mma_commit(&accf[acc]);
           }
-          if (PERPASS && ++acc == kAcc) {
+          if (SPLIT && ++acc == kAcc) {
             acc = 0;
             acc_phase ^= 1u;
           }
         }
         __syncwarp();
-        if (!PERPASS && ++acc == kAcc) {
+        if (!SPLIT && ++acc == kAcc) {
           acc = 0;
           acc_phase ^= 1u;
         }
@@ -276,13 +355,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue ----------------
     const int slice = warp & 3;            // TMEM lanes 32 * slice .. + 31
     const int row = 32 * slice + lane;     // accumulator row
+    const uint32_t lanes = (uint32_t)(32 * slice) << 16;
     int acc = 0;
     uint32_t acc_phase = 0;
     for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
       int prod = 0;
       unsigned long long local = 0;
       const uint2 meta = t0 + lane < my_items ? item_meta(t0 + lane, prod, local) : make_uint2(0u, 0u);
-      const uint32_t ij_l = t0 + lane < my_items ? prods[prod].gij[LEAF == 64 ? local : (local >> 2)] : 0u;
+      uint32_t ij_l = 0u;
+      if (t0 + lane < my_items) {
+        const unsigned long long gq = LEAF == 64 ? local : (local >> 2);
+        ij_l = (int64_t)gq < prods[prod].cap_items ? prods[prod].gij[gq] : 0u;
+      }
       const int nt = (int)min(32ull, my_items - t0);
       for (int ti = 0; ti < nt; ti++) {
         const int pr = __shfl_sync(0xffffffffu, prod, ti);
@@ -290,20 +374,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t ij = __shfl_sync(0xffffffffu, ij_l, ti);
         const int qd = LEAF == 64 ? 0 : (int)(__shfl_sync(0xffffffffu, (uint32_t)local, ti) & 3u);
         const uint32_t I = ij >> 16, J = ij & 0xFFFFu;
-        uint32_t touched = __shfl_sync(0xffffffffu, meta.y, ti) >> 24;   // quadrants with a product
+        const uint2 mt = make_uint2(__shfl_sync(0xffffffffu, meta.x, ti), __shfl_sync(0xffffffffu, meta.y, ti));
+        uint32_t touched = mt.y >> 24;   // quadrants with a product
         if (LEAF == 128) touched = touched ? (1u << qd) : 0u;
-        // PERPASS: the passes arrive one accumulator each and are summed here in FP32
-        // (round to nearest) in the order of the plan
+        // split: the passes arrive one accumulator pair each and are summed here in
+        // FP32 (round to nearest) in the order of the plan
         float run[128];
-        if (PERPASS) {
-          const uint32_t first = __shfl_sync(0xffffffffu, meta.x, ti);
-          uint32_t np = __shfl_sync(0xffffffffu, meta.y, ti) & 0xFFFFFFu;
-          const int64_t cap = P.cap_plan;
-          np = (int64_t)first >= cap ? 0u : ((int64_t)first + np > cap ? (uint32_t)(cap - first) : np);
+        if (SPLIT) {
+          const uint32_t first = mt.x;
+          const uint32_t np = item_passes(P, mt, cm.status);
+          const int oob = P.nb * P.nb;
 #pragma unroll
           for (int x = 0; x < 128; x++) run[x] = 0.f;
           bool all_ok = true;
+          int4 pl = make_int4(0, 0, 0, 0);
           for (uint32_t p = 0; p < np; p++) {
+            if ((p & 31u) == 0u && p + lane < np) pl = P.plan[(int64_t)first + p + lane];
+            const uint32_t cols = __shfl_sync(0xffffffffu, pass_cols<LEAF>(pl, oob), p & 31u);
             bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
             if (!ok) {
               s_abort = 1;
@@ -313,12 +400,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             all_ok = all_ok && ok;
             if (ok) {
               tc_fence_after();
+              const uint32_t d = tmem + lanes + (uint32_t)acc * R::kAccCols;
 #pragma unroll
               for (int h = 0; h < 4; h++) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * slice) << 16) + (uint32_t)acc * 128u + (uint32_t)(h * 32), v);
+                if (!((cols >> (h >> 1)) & 1u)) continue;   // a column half this pass left alone
+                uint32_t v[32], w[32];
+                tmem_ld32(d + (uint32_t)(h * 32), v);
+                tmem_ld32(d + 128u + (uint32_t)(h * 32), w);
 #pragma unroll
-                for (int x = 0; x < 32; x++) run[h * 32 + x] += __uint_as_float(v[x]);
+                for (int x = 0; x < 32; x++) run[h * 32 + x] += __uint_as_float(v[x]) + __uint_as_float(w[x]);
               }
             }
             tc_fence_before();
@@ -357,19 +447,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           float *blk = P.C + ((int64_t)i * P.nb + j) * LEAF * LEAF + (int64_t)(r - lane) * LEAF;
           float(*sb)[33] = s_epi[warp - 2];
           // symmetric product, plain forms: block (j, i) = (i, j)^T from the same staged chunk
-          const bool mir = !PERPASS && P.sym && i < j;
+          const bool mir = !SPLIT && P.sym && i < j;
           float *blkT = P.C + ((int64_t)j * P.nb + i) * LEAF * LEAF + (r - lane);
 #pragma unroll
           for (int h = 0; h < LEAF / 32; h++) {
             uint32_t v[32];
-            if (PERPASS) {
+            if (SPLIT) {
 #pragma unroll
               for (int x = 0; x < 32; x++) v[x] = __float_as_uint(run[cc * 64 + h * 32 + x]);
             } else {
               const uint32_t col = (uint32_t)acc * 128u + (uint32_t)(cc * 64 + h * 32);
-              tmem_ld32(tmem + ((uint32_t)(32 * slice) << 16) + col, v);
+              tmem_ld32(tmem + lanes + col, v);
             }
-            if (!PERPASS) {
+            if (!SPLIT) {
 #pragma unroll
               for (int x = 0; x < 32; x++) sb[lane][x] = __uint_as_float(v[x]);
               __syncwarp();
@@ -391,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
 #pragma unroll
             for (int x = 0; x < 32; x += 4) {
-              if (PERPASS)
+              if (SPLIT)
                 *reinterpret_cast<float4 *>(dst + h * 32 + x) =
                     make_float4(__uint_as_float(v[x]), __uint_as_float(v[x + 1]), __uint_as_float(v[x + 2]),
                                 __uint_as_float(v[x + 3]));
@@ -408,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-        if (!PERPASS) {
+        if (!SPLIT) {
           tc_fence_before();
           mbar_arrive(&acce[acc]);
         }
@@ -432,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const double v2 = s_norm[2 * aa][c] + s_norm[2 * aa + 1][c];
               P.leaf_norm2C[(int64_t)ii * P.NB + jj] = v2;
               P.nzC[(int64_t)ii * P.NB + jj] = 1;
-              if (!PERPASS && P.sym && ii < jj) {
+              if (!SPLIT && P.sym && ii < jj) {
                 P.leaf_norm2C[(int64_t)jj * P.NB + ii] = v2;
                 P.nzC[(int64_t)jj * P.NB + ii] = 1;
               }
@@ -443,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const double v2 = ((s_norm[0][0] + s_norm[1][0]) + s_norm[2][0]) + s_norm[3][0];
               P.leaf_norm2C[(int64_t)i * P.NB + jj] = v2;
               P.nzC[(int64_t)i * P.NB + jj] = 1;
-              if (!PERPASS && P.sym && i < jj) {
+              if (!SPLIT && P.sym && i < jj) {
                 P.leaf_norm2C[(int64_t)jj * P.NB + i] = v2;
                 P.nzC[(int64_t)jj * P.NB + i] = 1;
               }
@@ -451,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (!PERPASS && ++acc == kAcc) {
+        if (!SPLIT && ++acc == kAcc) {
           acc = 0;
           acc_phase ^= 1u;
         }
@@ -501,12 +591,12 @@ bool make_map(CUtensorMap *m, const void *data, int elem, int b, int nb) {
   return r == CUDA_SUCCESS;
 }
 
-template <int LEAF, bool TF32, bool PERPASS>
+template <int LEAF, bool TF32, bool SPLIT>
 cudaError_t run(const ProdDesc *table, int nprod, const TcCommon &cm, int sm_count, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, TF32, PERPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, TF32, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kSmemBytes);
   if (e != cudaSuccess) return e;
-  k_leaf_tc<LEAF, TF32, PERPASS><<<sm_count, kThreads, kSmemBytes, s>>>(table, nprod, cm);
+  k_leaf_tc<LEAF, TF32, SPLIT><<<sm_count, kThreads, kSmemBytes, s>>>(table, nprod, cm);
   return cudaGetLastError();
 }
 
@@ -532,6 +622,7 @@ bool fill_desc(ProdDesc *d, spamm_tree A, spamm_tree B, spamm_tree C, int prec) 
   d->items = C->items;
   d->plan = C->plan;
   d->cap_plan = C->cap_plan;
+  d->cap_items = C->cap_items;
   d->gij = C->tiers[C->kmax].gij;
   d->ngroups = &C->counts->ngroups[C->kmax];
   d->C = (float *)C->copy[CK_F32];
@@ -548,10 +639,11 @@ TcCommon common_of(int prec, int b, uint32_t *status) {
   const bool tf32 = tf32_prec(prec);
   const int elem = tf32 ? 4 : 2;
   TcCommon cm{};
-  cm.idesc = make_idesc(tf32 ? kFmtTF32 : prec == SPAMM_FP16 ? kFmtF16 : kFmtBF16, 128, 128);
+  const uint32_t fmt = tf32 ? kFmtTF32 : prec == SPAMM_FP16 ? kFmtF16 : kFmtBF16;
+  cm.idesc = make_idesc(fmt, 128, 128);
+  cm.idesc64 = make_idesc(fmt, 128, 64);
   cm.chunks = b * elem / 128;
   cm.chunk_elems = 128 / elem;
-  cm.nsrc = split_prec(prec) ? 3 : 1;
   cm.status = status;
   return cm;
 }

@@ -666,6 +666,8 @@ cudaError_t launch_mirror(spamm_tree C, cudaStream_t s) {
   } else if (C->copy[CK_F32]) {
     float *t = (float *)C->copy[CK_F32];
     if (C->b >= 64) run_mirror<float, 64, 4>(C, t, ln2, s);
+    else if (C->b == 32) run_mirror<float, 32, 4>(C, t, ln2, s);
+    else if (C->b == 16) run_mirror<float, 16, 1>(C, t, ln2, s);
     else return cudaErrorInvalidValue;
   } else {
     return cudaErrorInvalidValue;

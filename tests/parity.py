@@ -57,3 +57,28 @@ def rel_fro(X, R) -> float:
     d = np.linalg.norm(X - R)
     r = np.linalg.norm(R)
     return d / r if r > 0 else d
+
+
+# products one tcgen05 MMA instruction sums: K = 32 bytes of each operand
+MMA_K = {"bf16": 16, "fp16": 16, "bf16x3": 16, "tf32": 8, "tf32x3": 8}
+
+
+def tc_units(products, prec: str):
+    """Units of 2^-23 of the magnitude sum |A||B| that bound the FP32 accumulation
+    error of `products` exact products on the tensor cores: one per product for the
+    sequential FP32 sums, one more per MMA instruction (its Kq products are aligned to
+    the largest magnitude taking part before the truncating add), and one instruction's
+    Kq as margin for the first alignment and (split forms) the epilogue's sums of the
+    passes in FP32."""
+    kq = MMA_K[prec]
+    return products + np.ceil(products / kq) + kq
+
+
+FP32_MIN_NORMAL = 2.0 ** -126
+
+
+def tc_bound(products, prec: str, cabs):
+    """Elementwise bound of |C_gpu - C_ref| for tensor-core products: tc_units(...) units
+    of 2^-23 of the magnitude sum, plus one FP32 minimum normal per product for results
+    below FP32's normal range (subnormal sums flushed to zero by the accumulator)."""
+    return tc_units(products, prec) * 2.0 ** -23 * cabs + products * FP32_MIN_NORMAL + 1e-300

@@ -120,3 +120,47 @@ def test_batched_update_equals_single_updates(S, ctx):
     for t in a + b:
         S.spamm_tree_free(t)
 
+
+
+def test_batched_config4_against_oracle(S, ctx):
+    # config-4 shapes (256 symmetric exponential-decay matrices, n log-uniform in
+    # [512, 8192], seed 3): five products spanning n, the largest n = 8192 among them,
+    # leaf 128 BF16 (the tuner's pick for this batch), one persistent launch from a
+    # CUDA graph captured at another tau and replayed at tau = 1e-7. Every product's
+    # triple list against the oracle's, and C on sampled output blocks against the
+    # oracle with BF16-rounded leaf operands under the FP32 bound of test_gpu_tc.py
+    from oracle import formats as F
+    from parity import tc_bound
+    shapes = W.batched_shapes()
+    order = sorted(range(len(shapes)), key=lambda m: shapes[m][0])
+    pick = [order[0], order[len(order) // 4], order[len(order) // 2], order[3 * len(order) // 4], order[-1]]
+    assert shapes[pick[-1]][0] == 8192
+    mats = [W.batched_matrix(m, *shapes[m]) for m in pick]
+    leaf, tau, prec = 128, 1e-7, S.SPAMM_BF16
+    trees = build(S, ctx, mats, [leaf] * len(mats), prec)
+    C = S.spamm_multiply_batched(ctx, trees, trees, [1e-5] * len(mats), prec, S.SPAMM_GRAPH)
+    C = S.spamm_multiply_batched(ctx, trees, trees, [tau] * len(mats), prec, S.SPAMM_GRAPH, C)
+    rng = np.random.default_rng(7)
+    for p, M in enumerate(mats):
+        T = oracle.Tree(M, leaf)
+        ref = oracle.spamm(T, T, tau, triples=True, product=False)
+        only_g, only_o = compare_triples(S.spamm_triples(C[p]), oracle.sort_triples(ref["triples"]), T.NB,
+                                         T.norm2(T.kmax), T.norm2(T.kmax), tau)
+        assert not len(only_g) and not len(only_o)
+        cnt = np.zeros((T.NB, T.NB), dtype=np.int64)
+        np.add.at(cnt, (ref["triples"][:, 0], ref["triples"][:, 1]), 1)
+        Mr = F.round_to(M, "bf16")
+        tR, tAbs = oracle.Tree(Mr, leaf), oracle.Tree(np.abs(Mr), leaf)
+        nb = -(-M.shape[0] // leaf)
+        blocks = [(0, 0), (0, nb - 1), (nb - 1, nb - 1)] + [tuple(int(v) for v in x) for x in rng.integers(0, nb, (6, 2))]
+        got_all = S.spamm_tree_to_dense(C[p])
+        for i, j in blocks:
+            Cref = oracle.spamm_block(T, T, tau, i, j, tR, tR)
+            Cabs = oracle.spamm_block(T, T, tau, i, j, tAbs, tAbs)
+            got = np.zeros((leaf, leaf))
+            blk = got_all[i * leaf:(i + 1) * leaf, j * leaf:(j + 1) * leaf]
+            got[:blk.shape[0], :blk.shape[1]] = blk
+            bound = tc_bound(leaf * cnt[i, j], "bf16", Cabs)
+            assert np.all(np.abs(got - Cref) <= bound), (p, i, j)
+    for t in C + trees:
+        S.spamm_tree_free(t)

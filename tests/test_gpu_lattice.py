@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 from oracle import formats as F
-from parity import compare_triples
+from parity import compare_triples, tc_bound
 from paper_1011_3534_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -43,13 +43,17 @@ def A():
     return W.physical_decay(16, 8, 1.2, 0.1, 3, 1)
 
 
-@pytest.mark.parametrize("leaf,prec,tau", [(64, "bf16", 1e-6), (128, "fp16", 1e-4)])
-def test_lattice32768_parity(S, ctx, A, leaf, prec, tau):
+@pytest.mark.parametrize("leaf,prec,tau,sym", [(64, "bf16", 1e-6, False), (128, "fp16", 1e-4, False),
+                                              (64, "bf16", 1e-6, True), (128, "bf16", 1e-4, True)])
+def test_lattice32768_parity(S, ctx, A, leaf, prec, tau, sym):
+    # sym: the benchmark's lattice mode, a symmetric operand with the symmetric product
+    # (blocks i <= j multiplied, C_ji = C_ij^T written by the epilogue)
     n = A.shape[0]
     assert n == 32768
     p = S.PRECISIONS[prec]
-    tA = S.spamm_tree_build(ctx, torch.from_numpy(A).cuda(), n, leaf, S.COPY_FLAG[p] | S.SPAMM_SYMMETRIC)
-    tC = S.spamm_multiply(ctx, tA, tA, tau, p)
+    fl = S.COPY_FLAG[p] | S.SPAMM_SYMMETRIC | (S.SPAMM_NO_RIGHT if sym else 0)
+    tA = S.spamm_tree_build(ctx, torch.from_numpy(A).cuda(), n, leaf, fl)
+    tC = S.spamm_multiply(ctx, tA, tA, tau, p, S.SPAMM_SYM_PRODUCT if sym else 0)
     trip = S.spamm_triples(tC)
     st = S.spamm_stats(tC)
     TA = oracle.Tree(A, leaf)
@@ -57,7 +61,7 @@ def test_lattice32768_parity(S, ctx, A, leaf, prec, tau):
     NB = TA.NB
     only_g, only_o = compare_triples(trip, oracle.sort_triples(ref["triples"]), NB, TA.norm2(TA.kmax),
                                      TA.norm2(TA.kmax), tau)
-    assert st["leaf_products"] == ref["count"] + len(only_g) - len(only_o)
+    assert st["leaf_products"] + st["mirrored_products"] == ref["count"] + len(only_g) - len(only_o)
     print(f"lattice n={n} leaf {leaf} {prec} tau {tau}: {ref['count']} surviving triples of {NB ** 3}")
     # sampled output blocks against the rounded-operand oracle
     Ar = F.round_to(A, prec)
@@ -70,14 +74,15 @@ def test_lattice32768_parity(S, ctx, A, leaf, prec, tau):
     rng = np.random.default_rng(7)
     blocks = [(0, j) for j in range(0, nb, max(1, nb // 8))] + [(i, i) for i in range(0, nb, max(1, nb // 8))]
     blocks += [tuple(int(v) for v in x) for x in rng.integers(0, nb, (12, 2))]
+    blocks += [(j, i) for i, j in blocks if i != j][:8]   # mirrored blocks of a symmetric product
     C = S.spamm_tree_to_dense(tC)
     for i, j in blocks:
         Cref = oracle.spamm_block(TA, TA, tau, i, j, tAr, tAr)
         Cabs = oracle.spamm_block(TA, TA, tau, i, j, tAbs, tAbs)
         Csub = oracle.spamm_block(TA, TA, tau, i, j, sub, sub) if sub is not None else 0.0
-        K = leaf * cnt[i, j] + 16
+        K = leaf * cnt[i, j]
         got = C[i * leaf:(i + 1) * leaf, j * leaf:(j + 1) * leaf]
-        bad = np.abs(got - Cref) > K * 2.0 ** -23 * Cabs + Csub + 1e-300
+        bad = np.abs(got - Cref) > tc_bound(K, prec, Cabs) + Csub
         assert not np.any(bad), (i, j, np.argwhere(bad)[:3])
     S.spamm_tree_free(tC)
     S.spamm_tree_free(tA)

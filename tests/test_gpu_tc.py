@@ -4,8 +4,11 @@ The cull is the FP64 one, so the triple list must equal the oracle's exactly (ou
 the near-tau band). C is compared with the oracle's SpAMM whose leaf products use the
 operands rounded to the leaf format (oracle/formats.py, from the format definitions)
 and summed in FP64: the only remaining difference is FP32 accumulation, bounded
-elementwise by K * 2^-23 * (|A| |B|)_ij, K the number of products summed into entry
-(i, j) (b per surviving k, three times that for the split forms). The error
+elementwise by U * 2^-23 * (|A| |B|)_ij + K * 2^-126 with U = K + ceil(K / Kq) + Kq
+(parity.tc_bound), K the number of products summed into entry (i, j) (b per
+surviving k, three times that for the split forms) and Kq the products of one MMA
+instruction (16 for BF16 and FP16, 8 for TF32); the last term covers sums below FP32's
+normal range, which the accumulator flushes to zero. The error
 against the plain FP64 SpAMM is reported, not asserted beyond a sanity range.
 """
 import numpy as np
@@ -13,7 +16,7 @@ import pytest
 
 import oracle
 from oracle import formats as F
-from parity import compare_triples, rel_fro
+from parity import compare_triples, rel_fro, tc_bound
 from paper_1011_3534_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -69,8 +72,10 @@ FP16_MIN_NORMAL = 2.0 ** -14
 
 def reference(A, B, leaf, tau, prec_name, threads):
     """Oracle C with rounded leaf operands and |A||B| over the same triples. For FP16
-    also the total magnitude of the products whose two operands are both FP16
-    subnormals, which the tensor cores of this GPU do not sum exactly (measured)."""
+    also the total magnitude of the products with FP16-subnormal operands, which the
+    tensor cores of this GPU do not sum exactly (measured): products of two subnormals
+    on the tcgen05 path (leaf 64, 128), products with at least one subnormal operand on
+    the warp-level MMA path (leaf 16, 32)."""
     TA, TB = oracle.Tree(A, leaf), oracle.Tree(B, leaf)
     Ah, Al = rounded_operands(A, prec_name)
     Bh, Bl = rounded_operands(B, prec_name)
@@ -87,7 +92,11 @@ def reference(A, B, leaf, tau, prec_name, threads):
     Csub = 0.0
     if prec_name == "fp16":
         sub = lambda X: np.where(np.abs(X) < FP16_MIN_NORMAL, np.abs(X), 0.0)
-        Csub = oracle.spamm_values(TA, TB, T(sub(Ah)), T(sub(Bh)), tau, threads)
+        if leaf >= 64:
+            Csub = oracle.spamm_values(TA, TB, T(sub(Ah)), T(sub(Bh)), tau, threads)
+        else:
+            Csub = (oracle.spamm_values(TA, TB, T(sub(Ah)), T(np.abs(Bh)), tau, threads)
+                    + oracle.spamm_values(TA, TB, T(np.abs(Ah)), T(sub(Bh)), tau, threads))
     return TA, TB, Cref, Cabs + 0.0, Csub
 
 
@@ -103,10 +112,10 @@ def check(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product=False):
     # products summed into each output block
     cnt = np.zeros((NB, NB), dtype=np.int64)
     np.add.at(cnt, (ref["triples"][:, 0], ref["triples"][:, 1]), 1)
-    K = leaf * cnt * (3 if prec_name in SPLIT else 1) + 16
+    K = leaf * cnt * (3 if prec_name in SPLIT else 1)
     n = A.shape[0]
     Kel = np.repeat(np.repeat(K, leaf, 0), leaf, 1)[:n, :n]
-    bound = Kel * 2.0 ** -23 * Cabs + Csub + 1e-300
+    bound = tc_bound(Kel, prec_name, Cabs) + Csub
     viol = np.abs(g["C"] - Cref) > bound
     assert not np.any(viol), (np.argwhere(viol)[:5], g["C"][viol][:5], Cref[viol][:5])
     C64 = oracle.spamm(TA, TB, tau, threads=thr)["C"]
@@ -115,7 +124,8 @@ def check(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product=False):
     assert err < SANITY[prec_name]
     st = g["stats"]
     assert st["leaf_products"] + st["mirrored_products"] == ref["count"]
-    assert st["mma_flops"] >= st["leaf_flops"] * (3 if prec_name in SPLIT else 1)
+    if tau > 0:   # at tau = 0 the products of absent (padding) leaves survive; the kernel skips them
+        assert st["mma_flops"] >= st["leaf_flops"] * (3 if prec_name in SPLIT else 1)
     return g
 
 
@@ -131,8 +141,21 @@ def test_tc_parity_symmetric(S, ctx, prec, n, leaf, tau, kind):
     check(S, ctx, A, A, leaf, tau, prec, symmetric=True)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("n,leaf,tau,kind", [
+    (1024, 32, 1e-8, "exp"),      # the exp-decay parity workload: n = 1024, 0.85^|i-j|, seed 0
+    (1000, 16, 1e-6, "alg"),      # ragged: 1000 = 62 * 16 + 8
+    (700, 32, 0.0, "exp"),        # tau = 0: padding blocks survive
+    (20, 16, 1e-8, "exp"),        # two leaves, one ragged
+])
+def test_tc_small_leaves(S, ctx, prec, n, leaf, tau, kind):
+    # leaves of 16 and 32 take the warp-level MMA kernel
+    A = W.algebraic_decay(n, 2, 0) if kind == "alg" else W.exp_decay(n, 0.85, 1, 0)
+    check(S, ctx, A, A, leaf, tau, prec, symmetric=True)
+
+
 @pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3", "tf32x3"])
-@pytest.mark.parametrize("leaf", [64, 128])
+@pytest.mark.parametrize("leaf", [16, 32, 64, 128])
 def test_tc_parity_nonsymmetric(S, ctx, prec, leaf):
     n = 1500
     r = np.random.default_rng(9)
@@ -144,7 +167,7 @@ def test_tc_parity_nonsymmetric(S, ctx, prec, leaf):
 
 @pytest.mark.parametrize("prec", ["bf16", "tf32x3", "fp16"])
 @pytest.mark.parametrize("n,leaf,tau,kind", [(1000, 64, 1e-6, "alg"), (2100, 128, 1e-6, "alg"), (2048, 64, 1e-8, "exp"),
-                                             (60, 64, 0.0, "exp")])
+                                             (60, 64, 0.0, "exp"), (1024, 32, 1e-8, "exp"), (1000, 16, 1e-6, "alg")])
 def test_tc_symmetric_product(S, ctx, prec, n, leaf, tau, kind):
     # blocks i <= j multiplied, i > j mirrored: the full triple list, C against the
     # oracle, C symmetric bit for bit; the stored norm trees are symmetric up to the
@@ -211,9 +234,9 @@ def test_workload_alg8192_tc_sampled(S, ctx, prec, tau):
             Cref = (oracle.spamm_block(TA, TA, tau, i, j, tAh, tAh) + oracle.spamm_block(TA, TA, tau, i, j, tAh, tAl)
                     + oracle.spamm_block(TA, TA, tau, i, j, tAl, tAh))
         Cabs = oracle.spamm_block(TA, TA, tau, i, j, tAbs, tAbs)
-        K = leaf * cnt[i, j] * (3 if tAl is not None else 1) + 16
+        K = leaf * cnt[i, j] * (3 if tAl is not None else 1)
         got = g["C"][i * leaf:(i + 1) * leaf, j * leaf:(j + 1) * leaf]
-        assert np.all(np.abs(got - Cref) <= K * 2.0 ** -23 * Cabs + 1e-300), (i, j)
+        assert np.all(np.abs(got - Cref) <= tc_bound(K, prec, Cabs)), (i, j)
 
 
 @pytest.mark.parametrize("n", [4096, 1000, 130])
