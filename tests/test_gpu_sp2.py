@@ -163,3 +163,32 @@ def test_sp2_scheme_one_matches_oracle(S, ctx, side, leaf, tau):
     dense = O.sp2_dense(H, n / 2, 30, lo, hi)["energy"]
     print(f"scheme (I) {side}^3 leaf {leaf} tau {tau}: error {abs(g['energy'] - dense) / abs(dense):.2e}, "
           f"{sum(g['leaf_products'])} block products ({sum(ref['leaf_products'])} in the oracle)")
+
+
+def golden_spectral(side):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sp2_tb_spectral.json")
+    rec = json.load(open(path))
+    return next(s for s in rec["systems"] if s["side"] == side and s["seed"] == 2)
+
+
+@pytest.mark.parametrize("prec,tau,tol", [("tf32x3", 1e-6, 1e-6), ("bf16x3", 1e-6, 1e-5)])
+def test_sp2_32cubed_against_spectral_reference(S, ctx, prec, tau, tol):
+    # 32^3 sites (n = 32768, seed 2), 30 steps, leaf 64: split-precision SpAMM SP2
+    # against the spectral SP2 of the dense FP64 eigensolve of H (tests/golden, written
+    # by the CPU oracle): the same Gershgorin interval, the same 30 branches, the energy
+    # Tr(H X) within the stated relative error and every trace within ten times it
+    ref = golden_spectral(32)
+    ip, ix, d = W.tight_binding(32, seed=2)[:3]
+    n = 32 ** 3
+    r = S.spamm_sp2(ctx, ip, ix, d, n / 2, 30, 64, S.PRECISIONS[prec], tau)
+    assert abs(r["eps_min"] - ref["emin"]) <= 1e-13 * abs(ref["emin"])
+    assert abs(r["eps_max"] - ref["emax"]) <= 1e-13 * abs(ref["emax"])
+    assert r["branches"] == ref["branches"]
+    np.testing.assert_allclose(r["traces"], ref["traces"], rtol=10 * tol, atol=0)
+    err = abs(r["energy"] - ref["energy"]) / abs(ref["energy"])
+    print(f"sp2 32^3 {prec} tau {tau}: energy error vs spectral {err:.2e}, {sum(r['leaf_products'])} leaf products, "
+          f"{r['ms']:.0f} ms")
+    assert err <= tol
+

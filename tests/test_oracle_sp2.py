@@ -122,3 +122,42 @@ def test_dropping_error_shrinks_with_tau():
         prods.append(sum(r["leaf_products"]))
     assert errs[2] < errs[0] and errs[2] < 1e-5
     assert prods[0] <= prods[1] <= prods[2]
+
+
+def _golden_systems():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sp2_tb_spectral.json")
+    return json.load(open(path))["systems"]
+
+
+@pytest.mark.parametrize("side", [16, 32])
+def test_spectral_golden_invariants(side):
+    # the stored spectral SP2 references (tests/golden/make_sp2_reference.py) against
+    # facts that do not need the eigensolve: the Gershgorin interval of H, the sum of the
+    # eigenvalues = Tr H (the sum of the on-site energies), Tr X0 = (n emax - Tr H) /
+    # (emax - emin), traces inside [0, n], and 30 branches
+    from paper_1011_3534_gb300 import workloads as W
+    rec = next(s for s in _golden_systems() if s["side"] == side)
+    ip, ix, d = W.tight_binding(side, seed=rec["seed"])[:3]
+    n = side ** 3
+    lo, hi = O.gershgorin(ip, ix, d, n)
+    assert (lo, hi) == (rec["emin"], rec["emax"])
+    diag = np.array([d[ip[i]:ip[i + 1]][ix[ip[i]:ip[i + 1]] == i].sum() for i in range(n)])
+    trH = float(diag.sum())
+    assert abs(rec["eig_sum"] - trH) <= 1e-9 * n
+    assert abs(rec["traces"][0] - (n * hi - trH) / (hi - lo)) <= 1e-9 * n
+    assert len(rec["branches"]) == 30 and len(rec["traces"]) == 31
+    assert all(0.0 <= t <= n for t in rec["traces"])
+    assert lo <= rec["eig_min"] and rec["eig_max"] <= hi
+
+
+def test_spectral_golden_16_equals_the_dense_oracle_run_on_its_spectrum():
+    # the 16^3 record is what the spectral oracle gives on the dense eigensolve now
+    from paper_1011_3534_gb300 import workloads as W
+    rec = next(s for s in _golden_systems() if s["side"] == 16)
+    ip, ix, d = W.tight_binding(16, seed=rec["seed"])[:3]
+    n = 16 ** 3
+    r = O.sp2_spectral(O.spectrum(ip, ix, d, n), n / 2, 30, rec["emin"], rec["emax"])
+    assert r["branches"] == rec["branches"]
+    assert abs(r["energy"] - rec["energy"]) <= 1e-10 * abs(rec["energy"])
