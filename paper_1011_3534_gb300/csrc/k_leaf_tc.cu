@@ -28,10 +28,12 @@
 // Accumulation. The tensor cores of this GPU truncate each MMA's FP32 sum (measured
 // bias about -0.5 unit in the last place per instruction), so the error of one
 // accumulator grows with the instructions it takes at its own magnitude. Plain forms:
-// one accumulator per item (four in TMEM). Split forms (hi hi + hi lo + lo hi): every
-// pass gets a fresh pair, the large hi hi products in one and the small corrections in
-// the other, and the epilogue adds the pair and the passes in FP32 registers with round
-// to nearest, in the order of the plan (two pass slots of two accumulators in TMEM).
+// one accumulator per item (four in TMEM). Split forms (hi hi + hi lo + lo hi): the
+// large hi hi products of every pass go to a fresh accumulator (two in TMEM, alternating)
+// and the epilogue adds the passes in FP32 registers with round to nearest, in the order
+// of the plan; the small corrections hi lo + lo hi, 2^-11 of the products and so of the
+// truncation bias, accumulate over the whole item in one accumulator (two in TMEM, one
+// item ahead), added once at the end.
 // Every wait is bounded; a wait that runs out sets an error bit and the CTA unwinds.
 #include <cudaTypedefs.h>
 
@@ -52,8 +54,12 @@ struct Ring {
   static constexpr int kStageBytes = SPLIT ? 4 * kBoxBytes : 2 * kBoxBytes;
   // byte offsets inside a stage
   static constexpr int kAhi = 0, kBhi = kBoxBytes, kAlo = 2 * kBoxBytes, kBlo = 3 * kBoxBytes;
-  static constexpr int kAcc = SPLIT ? 2 : 4;                 // accumulator slots
-  static constexpr uint32_t kAccCols = SPLIT ? 256u : 128u;  // TMEM columns per slot
+  // accumulator slots of 128 columns: plain, one per item (four); split, one per pass
+  // for hi hi (two) and one per item for the corrections hi lo + lo hi (two, from
+  // column 256)
+  static constexpr int kAcc = SPLIT ? 2 : 4;
+  static constexpr int kSmall = SPLIT ? 2 : 1;
+  static constexpr uint32_t kSmallCol = 256u;
 };
 static_assert((size_t)Ring<true>::kStages * Ring<true>::kStageBytes + 1024 <= kSmemBytes, "split ring");
 static_assert((size_t)Ring<false>::kStages * Ring<false>::kStageBytes + 1024 <= kSmemBytes, "plain ring");
@@ -135,7 +141,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kStages = R::kStages;
   constexpr int kAcc = R::kAcc;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[kAcc], acce[kAcc];
+  constexpr int kSmall = R::kSmall;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[kAcc], acce[kAcc], smf[kSmall], sme[kSmall];
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   __shared__ double s_norm[4][2];
@@ -158,6 +165,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int a = 0; a < kAcc; a++) {
       mbar_init(&accf[a], 1);
       mbar_init(&acce[a], 128);
+    }
+    for (int a = 0; a < kSmall; a++) {
+      mbar_init(&smf[a], 1);
+      mbar_init(&sme[a], 128);
     }
     s_abort = 0;
     mbar_fence_init();
@@ -228,8 +239,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int nl = (int)min(32u, np - c0);
             for (int l = 0; l < nl && !s_abort; l++) {
               const int4 d = s_desc[l];
-              // the first pass of a plain item initialises both column halves (N = 128)
-              const uint32_t cols = (!SPLIT && c0 + l == 0) ? 3u : pass_cols<LEAF>(d, oob);
+              // the first pass of an item initialises both column halves (N = 128) of the
+              // item's accumulator (plain) or correction accumulator (split)
+              const uint32_t cols = c0 + l == 0 ? 3u : pass_cols<LEAF>(d, oob);
               const int boxes = (SPLIT ? 2 : 1) * (RA + (RC == 2 ? __popc(cols) : 1));
               for (int ch = 0; ch < cm.chunks; ch++) {
                 if (!mbar_wait(&empty[stage], phase ^ 1u, &s_abort)) {
@@ -266,8 +278,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- MMA issuer (warp 1) ----------------
     int stage = 0;
     uint32_t phase = 0;
-    int acc = 0;
-    uint32_t acc_phase = 0;
+    int acc = 0, sm_idx = 0;
+    uint32_t acc_phase = 0, sm_phase = 0;
     unsigned long long nst = 0;
     int last_prod = -1;
     // one MMA of the K-step kk of a stage: N = 128, or N = 64 on the column half c
@@ -298,18 +310,29 @@ __global__ void __launch_bounds__(kThreads, 1)
           nst = 0;
           last_prod = pr;
         }
-        // plain: one accumulator per item; split: a fresh pair for every pass
+        // plain: one accumulator per item; split: a fresh hi hi accumulator for every
+        // pass and one correction accumulator for the item
         const int chains = SPLIT ? (int)np : 1;
         const int per_chain = SPLIT ? cm.chunks : (int)np * cm.chunks;
+        bool small_ok = true;
+        if (SPLIT && lane == 0 && !s_abort) {
+          small_ok = mbar_wait(&sme[sm_idx], sm_phase ^ 1u, &s_abort);
+          if (!small_ok) {
+            s_abort = 1;
+            flag_error(cm.status, DEV_TIMEOUT);
+          }
+          tc_fence_after();
+        }
+        const uint32_t ds = tmem + R::kSmallCol + (uint32_t)sm_idx * 128u;   // split: hi lo + lo hi
+        uint32_t acc_small = 0;
         for (int p = 0; p < chains && lane == 0 && !s_abort; p++) {
           if (!mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort)) {
             s_abort = 1;
             flag_error(cm.status, DEV_TIMEOUT);
           } else {
             tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)acc * R::kAccCols;   // plain, or split hi hi
-            const uint32_t ds = d + 128u;                             // split: hi lo + lo hi
-            uint32_t acc_big = 0, acc_small = 0;
+            const uint32_t d = tmem + (uint32_t)acc * 128u;   // plain, or split hi hi
+            uint32_t acc_big = 0;
             for (int t = 0; t < per_chain; t++) {
               if (!mbar_wait(&full[stage], phase, &s_abort)) {
                 s_abort = 1;
@@ -343,6 +366,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             acc_phase ^= 1u;
           }
         }
+        if (SPLIT) {
+          if (lane == 0 && small_ok) mma_commit(&smf[sm_idx]);   // after the item's last MMA
+          if (++sm_idx == kSmall) {
+            sm_idx = 0;
+            sm_phase ^= 1u;
+          }
+        }
         __syncwarp();
         if (!SPLIT && ++acc == kAcc) {
           acc = 0;
@@ -356,8 +386,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int slice = warp & 3;            // TMEM lanes 32 * slice .. + 31
     const int row = 32 * slice + lane;     // accumulator row
     const uint32_t lanes = (uint32_t)(32 * slice) << 16;
-    int acc = 0;
-    uint32_t acc_phase = 0;
+    int acc = 0, sm_idx = 0;
+    uint32_t acc_phase = 0, sm_phase = 0;
     for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
       int prod = 0;
       unsigned long long local = 0;
@@ -377,8 +407,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint2 mt = make_uint2(__shfl_sync(0xffffffffu, meta.x, ti), __shfl_sync(0xffffffffu, meta.y, ti));
         uint32_t touched = mt.y >> 24;   // quadrants with a product
         if (LEAF == 128) touched = touched ? (1u << qd) : 0u;
-        // split: the passes arrive one accumulator pair each and are summed here in
-        // FP32 (round to nearest) in the order of the plan
+        // split: the hi hi products of each pass arrive in an accumulator of their own and
+        // are summed here in FP32 (round to nearest) in the order of the plan, then the
+        // item's corrections are added
         float run[128];
         if (SPLIT) {
           const uint32_t first = mt.x;
@@ -387,10 +418,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int x = 0; x < 128; x++) run[x] = 0.f;
           bool all_ok = true;
+          // 32 columns x 32 lanes from two TMEM column chunks, one wait for both
+          auto add2 = [&](uint32_t d, int h) {
+            uint32_t v[32], w[32];
+            tmem_ld32_nowait(d + (uint32_t)(h * 32), v);
+            tmem_ld32_nowait(d + (uint32_t)(h * 32 + 32), w);
+            tmem_wait_ld();
+#pragma unroll
+            for (int x = 0; x < 32; x++) {
+              run[h * 32 + x] += __uint_as_float(v[x]);
+              run[h * 32 + 32 + x] += __uint_as_float(w[x]);
+            }
+          };
           int4 pl = make_int4(0, 0, 0, 0);
           for (uint32_t p = 0; p < np; p++) {
             if ((p & 31u) == 0u && p + lane < np) pl = P.plan[(int64_t)first + p + lane];
-            const uint32_t cols = __shfl_sync(0xffffffffu, pass_cols<LEAF>(pl, oob), p & 31u);
+            const uint32_t cols = p == 0 ? 3u : __shfl_sync(0xffffffffu, pass_cols<LEAF>(pl, oob), p & 31u);
             bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
             if (!ok) {
               s_abort = 1;
@@ -400,16 +443,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             all_ok = all_ok && ok;
             if (ok) {
               tc_fence_after();
-              const uint32_t d = tmem + lanes + (uint32_t)acc * R::kAccCols;
-#pragma unroll
-              for (int h = 0; h < 4; h++) {
-                if (!((cols >> (h >> 1)) & 1u)) continue;   // a column half this pass left alone
-                uint32_t v[32], w[32];
-                tmem_ld32(d + (uint32_t)(h * 32), v);
-                tmem_ld32(d + 128u + (uint32_t)(h * 32), w);
-#pragma unroll
-                for (int x = 0; x < 32; x++) run[h * 32 + x] += __uint_as_float(v[x]) + __uint_as_float(w[x]);
-              }
+              const uint32_t d = tmem + lanes + (uint32_t)acc * 128u;
+              if (cols & 1u) add2(d, 0);   // column half 0 (a column half this pass left alone is skipped)
+              if (cols & 2u) add2(d, 2);
             }
             tc_fence_before();
             mbar_arrive(&acce[acc]);
@@ -417,6 +453,25 @@ __global__ void __launch_bounds__(kThreads, 1)
               acc = 0;
               acc_phase ^= 1u;
             }
+          }
+          bool ok = mbar_wait(&smf[sm_idx], sm_phase, &s_abort);
+          if (!ok) {
+            s_abort = 1;
+            flag_error(cm.status, DEV_TIMEOUT);
+          }
+          ok = __all_sync(0xffffffffu, ok);
+          all_ok = all_ok && ok;
+          if (ok && np > 0) {
+            tc_fence_after();
+            const uint32_t d = tmem + lanes + R::kSmallCol + (uint32_t)sm_idx * 128u;
+            add2(d, 0);
+            add2(d, 2);
+          }
+          tc_fence_before();
+          mbar_arrive(&sme[sm_idx]);
+          if (++sm_idx == kSmall) {
+            sm_idx = 0;
+            sm_phase ^= 1u;
           }
           if (!all_ok) touched = 0;
         } else {

@@ -34,8 +34,11 @@ struct BuildArgs {
 // is kept idle: each round's squared norm is accumulated from an exact FP32 hi/lo split
 // of its elements scaled by the round's largest exponent, with error-free (TwoSum)
 // accumulation, rounds and threads are merged in double-float after rescaling to a
-// common exponent (relative error ~2^-46, far inside the 1e-12 near-tau band), and the
-// leaf copies are rounded in integer arithmetic on the FP64 bit pattern.
+// common exponent (relative error of the squared norm about 2^-46 typically and at most
+// 4e-13: 3 2^-46 from the dropped low bits, 1.25 2^-46 from the cross-term rounding,
+// 2^-42 from the FP32 sums of a round's error terms, about 20 double-float merges of
+// 2^-47; inside the 1e-12 near-tau band), and the leaf copies are rounded to nearest
+// even from the FP64 bit pattern (integer arithmetic, or the FP32-pipe split round).
 template <int B>
 struct BuildCfg {
   // threads per CTA: a 64 x 64 leaf gets 64 threads, so that each streams eight rounds
@@ -104,11 +107,99 @@ __device__ __forceinline__ uint32_t bf16x2_fast(uint32_t h0, uint32_t l0, uint32
   return r;   // element 0 in the low half
 }
 
+// Leaf copies a kernel instance writes: one bit per output. The instance for kAllCopies
+// checks every pointer at run time; the specialised instances (the copy sets of the
+// common symmetric operands) compile only their own outputs, which keeps the kernel
+// small enough for the instruction cache.
+constexpr uint32_t kF64 = 1u << 0, kF32 = 1u << 1, kTF32 = 1u << 2, kTF32T = 1u << 3, kTLO = 1u << 4,
+                   kTLOT = 1u << 5, kBF16 = 1u << 6, kBF16T = 1u << 7, kLO = 1u << 8, kLOT = 1u << 9,
+                   kFP16 = 1u << 10, kFP16T = 1u << 11, kAllCopies = (1u << 12) - 1;
+
+// One round of a split operand (copy set TF32 hi + lo, or BF16 hi + lo, one orientation)
+// whose elements all have FP64 exponent fields 949..1149 within 60 binades of each
+// other, on the FP32 pipe. Per element x (magnitude |x| handled, sign applied last):
+//   a  = |x| truncated to 24 significant bits, m = the next 23 bits (an integer), and
+//   j = 1 if any of the last 6 bits is set, so |x| = a + m 2^(p-46) + (last bits) with
+//   p the exponent of x; all exact FP32 values.
+//   norm: a and 2 m 2^(p-46), scaled by 2^(1023 - Er) (the round's largest exponent),
+//   are the same hi and lo2 as the general path's, so the squared norm is the same bits.
+//   hi = fmt(x): a with a sticky bit for the discarded bits, rounded to nearest even.
+//   lo = fmt(x - hi): d = a - hi (exact), b = (2m + j) 2^(p-47) (the rest of |x|,
+//   truncated with a sticky last bit, exact), s = d + b rounded toward zero and its exact
+//   error e = b - (s - d); s with a sticky bit for e != 0, rounded to nearest even, is
+//   fmt(d + b), and that equals fmt(|x| - hi) whenever fmt's rounding unit at |s| is at
+//   least 2^(p-45), i.e. |s| >= 2^(p-34) (TF32) or 2^(p-37) (BF16). A remainder below
+//   that (the low bits of x nearly cancel hi's rounding), rare, takes the integer route.
+template <int B, bool TF>
+__device__ __forceinline__ void k1_round_split(const BuildArgs &p, int64_t tile, const uint32_t (&hw)[8],
+                                               const uint32_t (&lw)[8], const int (&rows)[4], const int (&cols)[4],
+                                               int Er, NormAcc &acc) {
+  const float scR = __uint_as_float((uint32_t)(1150 - Er) << 23);   // 2^(1023 - Er), Er <= 1149
+  float S[2] = {0.f, 0.f}, s2[2] = {0.f, 0.f};
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    uint32_t hb[2], lb[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const uint32_t h = hw[2 * u + k], l = lw[2 * u + k];
+      const uint32_t E = (h >> 20) & 0x7FFu;
+      const uint32_t a_bits = __funnelshift_l(l, (h & 0x7FFFFFFFu) - (896u << 20), 3);
+      const float a = __uint_as_float(a_bits);
+      const float m_f = u23_to_float((l >> 6) & 0x7FFFFFu);
+      const float jf = __saturatef(u23_to_float(l & 63u));
+      const float sc47 = __uint_as_float((E - 943u) << 23);          // 2^(p - 47)
+      // squared norm: the same terms as the general path, chain k
+      const float hi_s = a * scR;
+      const float lo2_s = m_f * (sc47 * (4.f * scR));
+      const float pp = hi_s * hi_s;
+      float cc = fmaf(hi_s, hi_s, -pp);
+      cc = fmaf(hi_s, lo2_s, cc);
+      const float t = S[k] + pp;
+      const float tb = t - S[k];
+      s2[k] += ((S[k] - (t - tb)) + (pp - tb)) + cc;
+      S[k] = t;
+      // hi = fmt(|x|) from a and a sticky bit for the bits below it
+      const uint32_t jam = a_bits | ((l & 0x1FFFFFFFu) != 0u ? 1u : 0u);
+      uint32_t himag;   // FP32 pattern of fmt(|x|)
+      if (TF) {
+        himag = tf32_of_sticky(jam);
+      } else {
+        himag = (jam + 0x7FFFu + ((jam >> 16) & 1u)) & 0xFFFF0000u;
+      }
+      const float d = a - __uint_as_float(himag);
+      const float bj = fmaf(m_f, 2.f, jf) * sc47;
+      const float sr = __fadd_rz(d, bj);
+      const float ee = bj - (sr - d);
+      const float thr = sc47 * (TF ? 8192.f : 1024.f);
+      uint32_t lo;
+      if (fabsf(sr) >= thr || (sr == 0.f && ee == 0.f)) {
+        const uint32_t sb = (__float_as_uint(sr) & 0x7FFFFFFFu) | (ee != 0.f ? 1u : 0u);
+        const uint32_t lm = TF ? tf32_of_sticky(sb) : ((sb + 0x7FFFu + ((sb >> 16) & 1u)) & 0xFFFF0000u);
+        lo = lm ? lm | ((h ^ __float_as_uint(sr)) & 0x80000000u) : 0u;
+      } else {
+        lo = slow_split_lo(h, l, TF ? 11 : 8);
+      }
+      hb[k] = himag | (h & 0x80000000u);
+      lb[k] = lo;
+    }
+    const int64_t o = tile + (int64_t)rows[u] * B + cols[u];
+    if (TF) {
+      *reinterpret_cast<uint2 *>(p.tf32 + o) = make_uint2(hb[0], hb[1]);
+      *reinterpret_cast<uint2 *>(p.tlo + o) = make_uint2(lb[0], lb[1]);
+    } else {
+      *reinterpret_cast<uint32_t *>(p.bf16 + o) = (hb[0] >> 16) | (hb[1] & 0xFFFF0000u);
+      *reinterpret_cast<uint32_t *>(p.lo + o) = (lb[0] >> 16) | (lb[1] & 0xFFFF0000u);
+    }
+  }
+  df_add(S[0], s2[0], S[1], s2[1]);
+  acc.merge(S[0], s2[0], Er);
+}
+
 // Squared norm (into acc) and leaf copies of one round: the 8 elements of 4 pairs
 // (row rows[u], columns cols[u] and cols[u] + 1 of the leaf at element offset `tile`),
 // given as the high and low words of their FP64 patterns. Transposed copies go to
 // shared-memory leaf images (nullptr: not written).
-template <int B>
+template <int B, uint32_t M>
 __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const uint32_t (&hw)[8],
                                          const uint32_t (&lw)[8], const int (&rows)[4], const int (&cols)[4],
                                          NormAcc &acc, float *s_tf32T, float *s_tloT, uint16_t *s_bf16T,
@@ -126,6 +217,12 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
   const bool fast = Emin >= 897 && Er <= 1150 && Er - Emin <= 60;
   // ... and a round whose elements all have exponent fields 949..1150 splits on the fast path
   const bool fast_split = Emin >= 949 && Er <= 1150;
+  if constexpr (M == (kTF32 | kTLO) || M == (kBF16 | kLO)) {   // split operands: norm and copies on the FP32 pipe
+    if (Emin >= 949 && Er <= 1149 && Er - Emin <= 60) {
+      k1_round_split<B, M == (kTF32 | kTLO)>(p, tile, hw, lw, rows, cols, Er, acc);
+      return;
+    }
+  }
   if (Er > 0 && Er < 0x7FF) {
     // two independent double-float sums (even and odd elements) halve the dependency
     // chain; they are joined once per round
@@ -244,14 +341,6 @@ __device__ __forceinline__ void k1_round(const BuildArgs &p, int64_t tile, const
   }
 }
 
-// Leaf copies a kernel instance writes: one bit per output. The instance for kAllCopies
-// checks every pointer at run time; the specialised instances (the copy sets of the
-// common symmetric operands) compile only their own outputs, which keeps the kernel
-// small enough for the instruction cache.
-constexpr uint32_t kF64 = 1u << 0, kF32 = 1u << 1, kTF32 = 1u << 2, kTF32T = 1u << 3, kTLO = 1u << 4,
-                   kTLOT = 1u << 5, kBF16 = 1u << 6, kBF16T = 1u << 7, kLO = 1u << 8, kLOT = 1u << 9,
-                   kFP16 = 1u << 10, kFP16T = 1u << 11, kAllCopies = (1u << 12) - 1;
-
 template <uint32_t M>
 __device__ __forceinline__ BuildArgs masked(const BuildArgs &in) {
   BuildArgs p = in;
@@ -335,7 +424,7 @@ __global__ void __launch_bounds__(BuildCfg<B>::T, 1024 / BuildCfg<B>::T) k_tree_
         hw[2 * u + 1] = (uint32_t)__double2hiint(d.y);
         lw[2 * u + 1] = (uint32_t)__double2loint(d.y);
       }
-      k1_round<B>(p, tile, hw, lw, rows, cols, acc, s_tf32T, s_tloT, s_bf16T, s_fp16T, s_loT);
+      k1_round<B, M>(p, tile, hw, lw, rows, cols, acc, s_tf32T, s_tloT, s_bf16T, s_fp16T, s_loT);
     }
   }
   // leaf norm: threads -> warp (rescale to the warp's largest exponent) -> leaf
