@@ -2,10 +2,9 @@
 //
 // Work item. Leaf 64: one tier kmax-1 group (I, J), i.e. the 2 x 2 output blocks
 // (2I + a, 2J + c), a 128 x 128 FP32 accumulator in TMEM. Leaf 128: one output block
-// (2I + a, 2J + c), also 128 x 128. Items are dealt to a persistent grid of one CTA per
-// SM in Morton order of the output blocks, serpentine: CTA b takes items b, 2G - 1 - b,
-// 2G + b, ... of a grid of G, so that the heavy and light ends of each round of G items
-// even out.
+// (2I + a, 2J + c), also 128 x 128. A persistent grid of one CTA per SM takes items in
+// Morton order of the output blocks from one counter, each CTA the next item when its
+// producer gets to it, so that the SMs finish together however uneven the items are.
 //
 // Candidates. For each entry K of the group (ascending) and e = 0, 1, the surviving
 // children form a 2 x 2 pattern over (a, c). A pattern that is an outer product of a
@@ -79,6 +78,7 @@ struct __align__(64) ProdDesc {
   uint8_t *nzC;
   double *leaf_norm2C;
   unsigned long long *mma_stages;
+  unsigned int *work_ctr;                  // item counter of a launch (the first product's, zeroed by its cull)
   int32_t nb, NB;
   int32_t sym;                             // symmetric product: blocks i < j also written as C_ji = C_ij^T
 };
@@ -150,6 +150,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint8_t s_cols[kStages];            // producer -> MMA: column halves of a stage
   __shared__ float s_epi[4][32][33];             // epilogue: one 32 x 32 chunk per warp, transposed out
   __shared__ unsigned long long s_off[kMaxProd + 1];   // first global item of each product
+  constexpr int kQ = 4;                          // item ring: producer -> MMA and epilogue warps
+  __shared__ __align__(8) uint64_t qfull[kQ], qempty[kQ];
+  __shared__ int4 s_qe[kQ];                      // {product, index in it, first pass, passes | touched << 24}
+  __shared__ uint32_t s_qij[kQ];                 // the item's group (I << 16) | J
   constexpr int RA = LEAF == 64 ? 2 : 1;        // A leaves stacked along M
   constexpr int RC = LEAF == 64 ? 2 : 1;        // B leaves stacked along N
   constexpr uint32_t kBox = LEAF * 128;         // bytes of one leaf box (LEAF rows x 128 B)
@@ -170,6 +174,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&smf[a], 1);
       mbar_init(&sme[a], 128);
     }
+    for (int q = 0; q < kQ; q++) {
+      mbar_init(&qfull[q], 1);
+      mbar_init(&qempty[q], 5);   // the MMA warp and the four epilogue warps
+    }
     s_abort = 0;
     mbar_fence_init();
   }
@@ -185,21 +193,52 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   const uint32_t tmem = s_tmem;
   const unsigned long long nitems = s_off[nprod];
-  const unsigned long long G = gridDim.x, b = blockIdx.x;
-  // serpentine dealing: round t of G items goes b-th from the front (t even) or back
-  const unsigned long long rounds = nitems / G, rest = nitems % G;
-  const unsigned long long my_items = rounds + (((rounds & 1ull) ? G - 1ull - b : b) < rest ? 1ull : 0ull);
-  // item t of this CTA; every role reads the metadata of 32 of its items at a time
-  // (lane l: item t0 + l)
-  auto item_meta = [&](unsigned long long t, int &prod, unsigned long long &local) -> uint2 {
-    const unsigned long long g = t * G + ((t & 1ull) ? G - 1ull - b : b);
-    prod = find_prod(s_off, nprod, g);
-    local = g - s_off[prod];
-    if ((int64_t)local >= prods[prod].cap_items) {   // cannot happen for a well-formed list
-      flag_error(cm.status, DEV_BADARG);
-      return make_uint2(0u, 0u);
+  // Items are taken from a counter shared by all CTAs (the product's work counter,
+  // zeroed by its cull) as the producer gets to them, so that every SM keeps working
+  // until the list is empty; the producer hands each item to the MMA warp and the
+  // epilogue warps through a ring of kQ slots in shared memory (a negative product
+  // index ends the list).
+  unsigned int *const ctr = prods[0].work_ctr;
+  // the item after this CTA's current one: its product, index in the product and
+  // metadata {first pass, passes | touched << 24}, and its group (I << 16) | J
+  auto claim = [&]() -> unsigned int { return lane == 0 ? atomicAdd(ctr, 1u) : 0u; };
+  auto describe = [&](unsigned int g, int4 &e, uint32_t &ij) {
+    g = __shfl_sync(0xffffffffu, g, 0);
+    e = make_int4(-1, 0, 0, 0);
+    ij = 0u;
+    if ((unsigned long long)g >= nitems) return;
+    const int prod = find_prod(s_off, nprod, g);
+    const unsigned long long local = g - s_off[prod];
+    const unsigned long long gq = LEAF == 64 ? local : (local >> 2);
+    if ((int64_t)local >= prods[prod].cap_items || (int64_t)gq >= prods[prod].cap_items) {
+      flag_error(cm.status, DEV_BADARG);   // cannot happen for a well-formed list
+      return;
     }
-    return prods[prod].items[local];
+    const uint2 meta = prods[prod].items[local];
+    e = make_int4(prod, (int)local, (int)meta.x, (int)meta.y);
+    ij = prods[prod].gij[gq];
+  };
+  // consumers: the next slot of the ring (lane 0 waits; every lane reads it)
+  auto take = [&](int &qs, uint32_t &qp, int4 &e, uint32_t &ij) -> bool {
+    bool ok = true;
+    if (lane == 0) ok = mbar_wait(&qfull[qs], qp, &s_abort);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (!ok) {
+      if (lane == 0) {
+        s_abort = 1;
+        flag_error(cm.status, DEV_TIMEOUT);
+      }
+      return false;
+    }
+    e = s_qe[qs];
+    ij = s_qij[qs];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&qempty[qs]);
+    if (++qs == kQ) {
+      qs = 0;
+      qp ^= 1u;
+    }
+    return e.x >= 0;
   };
 
   if (warp == 0) {
@@ -216,15 +255,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     int stage = 0;
     uint32_t phase = 0;
-    for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
-      int prod = 0;
-      unsigned long long local = 0;
-      const uint2 meta = t0 + lane < my_items ? item_meta(t0 + lane, prod, local) : make_uint2(0u, 0u);
-      const int nt = (int)min(32ull, my_items - t0);
-      for (int ti = 0; ti < nt; ti++) {
-        const int pr = __shfl_sync(0xffffffffu, prod, ti);
-        const ProdDesc &P = prods[pr];
-        const uint2 mt = make_uint2(__shfl_sync(0xffffffffu, meta.x, ti), __shfl_sync(0xffffffffu, meta.y, ti));
+    int qs = 0;
+    uint32_t qp = 0;
+    int4 cur_e;
+    uint32_t cur_ij;
+    describe(claim(), cur_e, cur_ij);
+    for (;;) {
+      // publish the item to the other roles
+      if (lane == 0) {
+        if (!mbar_wait(&qempty[qs], qp ^ 1u, &s_abort)) {
+          s_abort = 1;
+          flag_error(cm.status, DEV_TIMEOUT);
+        }
+        s_qe[qs] = s_abort ? make_int4(-1, 0, 0, 0) : cur_e;
+        s_qij[qs] = cur_ij;
+        mbar_arrive(&qfull[qs]);
+      }
+      if (++qs == kQ) {
+        qs = 0;
+        qp ^= 1u;
+      }
+      if (cur_e.x < 0 || __shfl_sync(0xffffffffu, s_abort ? 1 : 0, 0)) break;
+      const unsigned int g_next = claim();   // the claim's reply arrives while this item's loads go out
+      {
+        const ProdDesc &P = prods[cur_e.x];
+        const uint2 mt = make_uint2((uint32_t)cur_e.z, (uint32_t)cur_e.w);
         const uint32_t first = mt.x;
         const uint32_t np = item_passes(P, mt, cm.status);
         const int oob = P.nb * P.nb;
@@ -273,6 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           __syncwarp();
         }
       }
+      describe(g_next, cur_e, cur_ij);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (warp 1) ----------------
@@ -295,14 +351,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         else mma_f16(d + 64u * c, da, db, cm.idesc64, accum);
       }
     };
-    for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
-      int prod = 0;
-      unsigned long long local = 0;
-      const uint2 meta = t0 + lane < my_items ? item_meta(t0 + lane, prod, local) : make_uint2(0u, 0u);
-      const int nt = (int)min(32ull, my_items - t0);
-      for (int ti = 0; ti < nt; ti++) {
-        const int pr = __shfl_sync(0xffffffffu, prod, ti);
-        const uint2 mt = make_uint2(__shfl_sync(0xffffffffu, meta.x, ti), __shfl_sync(0xffffffffu, meta.y, ti));
+    int qs = 0;
+    uint32_t qp = 0;
+    for (;;) {
+      int4 e;
+      uint32_t ij_unused;
+      if (!take(qs, qp, e, ij_unused)) break;
+      {
+        const int pr = e.x;
+        const uint2 mt = make_uint2((uint32_t)e.z, (uint32_t)e.w);
         const uint32_t np = item_passes(prods[pr], mt, cm.status);
         if (lane == 0 && pr != last_prod) {
           // stage counts are kept per product: flush this CTA's count of the previous one
@@ -388,23 +445,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lanes = (uint32_t)(32 * slice) << 16;
     int acc = 0, sm_idx = 0;
     uint32_t acc_phase = 0, sm_phase = 0;
-    for (unsigned long long t0 = 0; t0 < my_items; t0 += 32) {
-      int prod = 0;
-      unsigned long long local = 0;
-      const uint2 meta = t0 + lane < my_items ? item_meta(t0 + lane, prod, local) : make_uint2(0u, 0u);
-      uint32_t ij_l = 0u;
-      if (t0 + lane < my_items) {
-        const unsigned long long gq = LEAF == 64 ? local : (local >> 2);
-        ij_l = (int64_t)gq < prods[prod].cap_items ? prods[prod].gij[gq] : 0u;
-      }
-      const int nt = (int)min(32ull, my_items - t0);
-      for (int ti = 0; ti < nt; ti++) {
-        const int pr = __shfl_sync(0xffffffffu, prod, ti);
+    int qs = 0;
+    uint32_t qp = 0;
+    for (;;) {
+      int4 e;
+      uint32_t ij;
+      if (!take(qs, qp, e, ij)) break;
+      {
+        const int pr = e.x;
         const ProdDesc &P = prods[pr];
-        const uint32_t ij = __shfl_sync(0xffffffffu, ij_l, ti);
-        const int qd = LEAF == 64 ? 0 : (int)(__shfl_sync(0xffffffffu, (uint32_t)local, ti) & 3u);
+        const int qd = LEAF == 64 ? 0 : (e.y & 3);
         const uint32_t I = ij >> 16, J = ij & 0xFFFFu;
-        const uint2 mt = make_uint2(__shfl_sync(0xffffffffu, meta.x, ti), __shfl_sync(0xffffffffu, meta.y, ti));
+        const uint2 mt = make_uint2((uint32_t)e.z, (uint32_t)e.w);
         uint32_t touched = mt.y >> 24;   // quadrants with a product
         if (LEAF == 128) touched = touched ? (1u << qd) : 0u;
         // split: the hi hi products of each pass arrive in an accumulator of their own and
@@ -684,6 +736,7 @@ bool fill_desc(ProdDesc *d, spamm_tree A, spamm_tree B, spamm_tree C, int prec) 
   d->nzC = C->nz;
   d->leaf_norm2C = C->norm2 + level_offset(C->kmax);
   d->mma_stages = &C->counts->mma_tiles;
+  d->work_ctr = &C->counts->work_ctr;
   d->nb = C->nb;
   d->NB = C->NB;
   d->sym = C->sym_product ? 1 : 0;
