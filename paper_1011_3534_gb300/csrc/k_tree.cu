@@ -687,10 +687,10 @@ int pyramid_launches(spamm_tree t) { return 1 + (t->kmax - kPyrL - 1 >= 0 && !t-
 
 // C_ji := C_ij^T for every stored block i < j of a symmetric product (master tiles,
 // squared leaf norm, presence byte). Work item w is sub-tile w % S (E x E elements,
-// S = (b / E)^2) of block w / S in row-major block order; a CTA of 256 threads moves one
-// sub-tile per iteration with 16-byte loads and stores (V elements each) through a
-// padded shared-memory tile. Items of blocks on or below the diagonal, or absent, are
-// skipped.
+// S = (b / E)^2) of block w / S in row-major block order; a CTA of 256 threads first
+// tests 256 of its items at once and then moves the sub-tiles of stored blocks above the
+// diagonal, one per iteration, with 16-byte loads and stores (V elements each) through a
+// padded shared-memory tile.
 template <typename T, int E, int V>
 __global__ void __launch_bounds__(256) k_mirror(T *tiles, uint8_t *nz, double *leaf_norm2, int32_t b, int32_t nb,
                                                 int32_t NB) {
@@ -701,40 +701,59 @@ __global__ void __launch_bounds__(256) k_mirror(T *tiles, uint8_t *nz, double *l
   using Vec = typename std::conditional<V * sizeof(T) == 16, uint4,
               typename std::conditional<V * sizeof(T) == 8, uint2, uint32_t>::type>::type;
   __shared__ T s[E][E + 1];
+  __shared__ int64_t s_list[256];   // this CTA's items that need moving, from one parallel scan
+  __shared__ int s_cnt;
   const int sub = b / E, S = sub * sub;
   const int vc = threadIdx.x % VR, vr = threadIdx.x / VR;
   const int64_t items = (int64_t)nb * nb * S;
-  for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
-    const int64_t t = w / S;
-    const int q = (int)(w % S);
-    const int32_t i = (int32_t)(t / nb), j = (int32_t)(t % nb);
-    const int64_t uij = (int64_t)i * NB + j, uji = (int64_t)j * NB + i;
-    if (i >= j || !nz[uij]) continue;   // block-uniform; an absent lower block stays absent
-    const int r0 = (q / sub) * E, c0 = (q % sub) * E;   // sub-tile origin in block (i, j)
-    const T *src = tiles + ((int64_t)i * nb + j) * b * b;
-    T *dst = tiles + ((int64_t)j * nb + i) * b * b;
-    __syncthreads();   // the previous item's reads of s are done
-#pragma unroll
-    for (int k = 0; k < PER; k++) {
-      const int y = vr + k * RSTEP;
-      union { Vec v; T e[V]; } u;
-      u.v = *reinterpret_cast<const Vec *>(src + (int64_t)(r0 + y) * b + c0 + vc * V);
-#pragma unroll
-      for (int e = 0; e < V; e++) s[y][vc * V + e] = u.e[e];
+  // the CTA's items are blockIdx.x + m * gridDim.x; 256 of them are tested at once (one
+  // presence byte each) and only the blocks above the diagonal that are stored are moved
+  for (int64_t m0 = 0; (int64_t)blockIdx.x + m0 * gridDim.x < items; m0 += 256) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    {
+      const int64_t w = (int64_t)blockIdx.x + (m0 + threadIdx.x) * gridDim.x;
+      if (w < items) {
+        const int64_t t = w / S;
+        const int32_t i = (int32_t)(t / nb), j = (int32_t)(t % nb);
+        if (i < j && nz[(int64_t)i * NB + j]) s_list[atomicAdd(&s_cnt, 1)] = w;
+      }
     }
     __syncthreads();
+    const int cnt = s_cnt;
+    for (int m = 0; m < cnt; m++) {
+      const int64_t w = s_list[m];
+      const int64_t t = w / S;
+      const int q = (int)(w % S);
+      const int32_t i = (int32_t)(t / nb), j = (int32_t)(t % nb);
+      const int64_t uij = (int64_t)i * NB + j, uji = (int64_t)j * NB + i;
+      const int r0 = (q / sub) * E, c0 = (q % sub) * E;   // sub-tile origin in block (i, j)
+      const T *src = tiles + ((int64_t)i * nb + j) * b * b;
+      T *dst = tiles + ((int64_t)j * nb + i) * b * b;
+      __syncthreads();   // the previous item's reads of s are done
 #pragma unroll
-    for (int k = 0; k < PER; k++) {
-      const int y = vr + k * RSTEP;   // row c0 + y of block (j, i) = column c0 + y of (i, j)
-      union { Vec v; T e[V]; } u;
+      for (int k = 0; k < PER; k++) {
+        const int y = vr + k * RSTEP;
+        union { Vec v; T e[V]; } u;
+        u.v = *reinterpret_cast<const Vec *>(src + (int64_t)(r0 + y) * b + c0 + vc * V);
 #pragma unroll
-      for (int e = 0; e < V; e++) u.e[e] = s[vc * V + e][y];
-      *reinterpret_cast<Vec *>(dst + (int64_t)(c0 + y) * b + r0 + vc * V) = u.v;
+        for (int e = 0; e < V; e++) s[y][vc * V + e] = u.e[e];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < PER; k++) {
+        const int y = vr + k * RSTEP;   // row c0 + y of block (j, i) = column c0 + y of (i, j)
+        union { Vec v; T e[V]; } u;
+#pragma unroll
+        for (int e = 0; e < V; e++) u.e[e] = s[vc * V + e][y];
+        *reinterpret_cast<Vec *>(dst + (int64_t)(c0 + y) * b + r0 + vc * V) = u.v;
+      }
+      if (q == 0 && threadIdx.x == 0) {
+        leaf_norm2[uji] = leaf_norm2[uij];
+        nz[uji] = 1;
+      }
     }
-    if (q == 0 && threadIdx.x == 0) {
-      leaf_norm2[uji] = leaf_norm2[uij];
-      nz[uji] = 1;
-    }
+    __syncthreads();   // s_list and s_cnt are reused
   }
 }
 
