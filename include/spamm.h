@@ -378,6 +378,17 @@ SPAMM_API spamm_status spamm_sp2_begin(spamm_ctx ctx, int64_t n, const int64_t *
 SPAMM_API spamm_status spamm_sp2_step(spamm_sp2_run r, double tau);
 SPAMM_API spamm_status spamm_sp2_step_learned(spamm_sp2_run r, spamm_mlp m, double err_budget,
                                               double tau_min, double tau_max);
+/* spamm_sp2_step_learned with the step's budget loosened where its branch decision is
+   far from a tie (not in the paper; the energy error of the trace-correcting loop is
+   decided at near-tie steps): budget x clamp(m / mu_ref, 1, gain_max), with m the
+   relative margin | |t2 - N| - |2 t1 - t2 - N| | / N of the step's decision, t1 = Tr X
+   (from the previous step) and t2 = Tr X^2 = ||X||_F^2 (X symmetric: the root of its
+   norm pyramid), computed on the device before the product. The first step keeps the
+   base budget. Errors: as spamm_sp2_step_learned; SPAMM_EINVAL for mu_ref <= 0 or
+   gain_max < 1 or not finite. */
+SPAMM_API spamm_status spamm_sp2_step_learned_margin(spamm_sp2_run r, spamm_mlp m, double err_budget,
+                                                     double tau_min, double tau_max, double mu_ref,
+                                                     double gain_max);
 /* One step of the paper's scheme (I) comparator (Sec. III): the product X X at the
    smallest positive tau (exact: only sub-products with an absent or zero block are
    skipped), then the dropping filter at leaf resolution with tau_drop
@@ -397,6 +408,12 @@ SPAMM_API spamm_status spamm_sp2_learned(spamm_ctx ctx, int64_t n, const int64_t
                                          double n_occ, int32_t steps, int32_t leaf,
                                          spamm_prec prec, spamm_mlp m, double err_budget,
                                          double tau_min, double tau_max, spamm_sp2_result *out);
+/* spamm_sp2 with every step taken by spamm_sp2_step_learned_margin. */
+SPAMM_API spamm_status spamm_sp2_learned_margin(spamm_ctx ctx, int64_t n, const int64_t *indptr,
+                                                const int64_t *indices, const double *data, double n_occ,
+                                                int32_t steps, int32_t leaf, spamm_prec prec, spamm_mlp m,
+                                                double err_budget, double tau_min, double tau_max,
+                                                double mu_ref, double gain_max, spamm_sp2_result *out);
 
 /* ---- cull without device allocation ----
    For callers that cannot allocate device memory: code running inside a CUDA graph

@@ -16,6 +16,10 @@ Workflow, all on the GPU through the C ABI:
               trace-correcting step make the energy error jump when a product error
               crosses a system-dependent threshold, so a budget that just passes on one
               system need not pass on another.
+  calibrate_margin()  the same for the branch-margin rule (spamm_sp2_learned_margin): the
+              per-product budget is loosened at steps whose trace-correcting decision is
+              far from a tie; the settings with the fewest leaf products that meet the
+              target with a safety factor on the training system.
 """
 from __future__ import annotations
 
@@ -89,3 +93,20 @@ def calibrate_budget(ctx, mlp, csr, n_occ, steps, leaf, prec, e_ref, target, bud
         else:
             break
     return best
+
+
+def calibrate_margin(ctx, mlp, csr, n_occ, steps, leaf, prec, e_ref, target, budgets, mu_refs, gains, tau_min,
+                     tau_max, safety: float = 2.0):
+    """The branch-margin rule's settings (budget, mu_ref, gain_max) with the fewest leaf
+    products among those whose learned-tau SP2 (spamm_sp2_learned_margin) meets
+    target / safety on a training system; (settings, run) or None."""
+    best = None
+    for b in budgets:
+        for mu in mu_refs:
+            for g in gains:
+                r = S.spamm_sp2_learned_margin(ctx, *csr, n_occ, steps, leaf, prec, mlp, b, tau_min, tau_max, mu, g)
+                if energy_error(r, e_ref) <= target / safety:
+                    lp = int(sum(r["leaf_products"]))
+                    if best is None or lp < best[2]:
+                        best = ((b, mu, g), r, lp)
+    return None if best is None else best[:2]

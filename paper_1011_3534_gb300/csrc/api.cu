@@ -1043,18 +1043,22 @@ extern "C" spamm_status spamm_sp2_dropping(spamm_ctx ctx, int64_t n, const int64
   return spamm_sp2_end(r, out);
 }
 
-extern "C" spamm_status spamm_sp2_step_learned(spamm_sp2_run r, spamm_mlp m, double err_budget, double tau_min,
-                                               double tau_max) {
+// One learned step; mu_ref > 0 loosens the step's budget by its branch margin on the device.
+static spamm_status sp2_step_learned_impl(spamm_sp2_run r, spamm_mlp m, double err_budget, double tau_min,
+                                          double tau_max, double mu_ref, double gain_max) {
   if (!r || !m) return SPAMM_EINVAL;
   spamm_ctx ctx = r->ctx;
   if (r->steps >= SPAMM_SP2_MAX_STEPS) return fail(ctx, SPAMM_ERANGE, "sp2: more than %d steps", SPAMM_SP2_MAX_STEPS);
   if (!(err_budget > 0.0) || !(tau_min > 0.0) || !(tau_max >= tau_min) || !std::isfinite(tau_max))
     return fail(ctx, SPAMM_EINVAL, "sp2: bad budget or tau range");
+  if (mu_ref < 0.0 || !std::isfinite(mu_ref) || (mu_ref > 0.0 && !(gain_max >= 1.0 && std::isfinite(gain_max))))
+    return fail(ctx, SPAMM_EINVAL, "sp2: bad margin reference or gain");
   if (mlp_inputs(m) != SPAMM_MLP_FEATURES) return fail(ctx, SPAMM_EINVAL, "sp2: network has the wrong input width");
   cudaStream_t s = ctx->stream;
   const size_t nw = bound_workspace_doubles(r->X);
-  if (!r->d_ctrl) CK(dmalloc(&r->d_ctrl, sizeof(double) * (nw + kTauGrid)), "sp2: allocation");
-  double *grid = r->d_ctrl + nw, *bound = r->d_ctrl + (nw - kTauGrid);
+  // the bound workspace, the tolerance grid, then the step's device budget
+  if (!r->d_ctrl) CK(dmalloc(&r->d_ctrl, sizeof(double) * (nw + kTauGrid + 1)), "sp2: allocation");
+  double *grid = r->d_ctrl + nw, *bound = r->d_ctrl + (nw - kTauGrid), *budget_dev = r->d_ctrl + nw + kTauGrid;
   if (r->grid_lo != tau_min || r->grid_hi != tau_max) {   // the grid, uploaded once per range
     double h[kTauGrid];
     tau_grid(tau_min, tau_max, h);
@@ -1065,10 +1069,28 @@ extern "C" spamm_status spamm_sp2_step_learned(spamm_sp2_run r, spamm_mlp m, dou
   }
   CK(launch_feat_hist(r->X, r->d_feat, s), "sp2: features");
   CK(launch_flat_bound(r->X, r->X, grid, kTauGrid, r->d_ctrl, bound, s), "sp2: flat bound");
-  CK(launch_tau_select(m, r->d_feat, r->d_feat, grid, bound, std::log10(err_budget), sp2_tau_slot(r->d_rec, r->steps), s),
+  if (mu_ref > 0.0) {
+    CK(sp2_margin_budget(r->X, r->steps, r->d_rec, r->n_occ, mu_ref, gain_max, std::log10(err_budget), budget_dev, s),
+       "sp2: margin budget");
+    ctx->launches++;
+  }
+  CK(launch_tau_select(m, r->d_feat, r->d_feat, grid, bound, std::log10(err_budget), sp2_tau_slot(r->d_rec, r->steps), s,
+                       mu_ref > 0.0 ? budget_dev : nullptr),
      "sp2: tau selection");
   ctx->launches += 4;
   return sp2_advance(r, 0.0, true);
+}
+
+extern "C" spamm_status spamm_sp2_step_learned(spamm_sp2_run r, spamm_mlp m, double err_budget, double tau_min,
+                                               double tau_max) {
+  return sp2_step_learned_impl(r, m, err_budget, tau_min, tau_max, 0.0, 1.0);
+}
+
+extern "C" spamm_status spamm_sp2_step_learned_margin(spamm_sp2_run r, spamm_mlp m, double err_budget,
+                                                      double tau_min, double tau_max, double mu_ref,
+                                                      double gain_max) {
+  if (r && !(mu_ref > 0.0)) return fail(r->ctx, SPAMM_EINVAL, "sp2: the margin reference must be positive");
+  return sp2_step_learned_impl(r, m, err_budget, tau_min, tau_max, mu_ref, gain_max);
 }
 
 extern "C" spamm_status spamm_sp2_iterate(spamm_sp2_run r, spamm_tree *X) {
@@ -1136,6 +1158,27 @@ extern "C" spamm_status spamm_sp2_learned(spamm_ctx ctx, int64_t n, const int64_
   spamm_status st = spamm_sp2_begin(ctx, n, indptr, indices, data, n_occ, leaf, prec, &r);
   if (st != SPAMM_OK) return st;
   for (int q = 0; q < steps && st == SPAMM_OK; q++) st = spamm_sp2_step_learned(r, m, err_budget, tau_min, tau_max);
+  if (st != SPAMM_OK) {
+    spamm_sp2_end(r, nullptr);
+    return st;
+  }
+  return spamm_sp2_end(r, out);
+}
+
+extern "C" spamm_status spamm_sp2_learned_margin(spamm_ctx ctx, int64_t n, const int64_t *indptr,
+                                                 const int64_t *indices, const double *data, double n_occ,
+                                                 int32_t steps, int32_t leaf, spamm_prec prec, spamm_mlp m,
+                                                 double err_budget, double tau_min, double tau_max, double mu_ref,
+                                                 double gain_max, spamm_sp2_result *out) {
+  if (!ctx) return SPAMM_EINVAL;
+  if (!m || !out) return fail(ctx, SPAMM_EINVAL, "sp2: null pointer");
+  if (steps < 0 || steps > SPAMM_SP2_MAX_STEPS) return fail(ctx, SPAMM_EINVAL, "sp2: bad steps");
+  if (!(mu_ref > 0.0)) return fail(ctx, SPAMM_EINVAL, "sp2: the margin reference must be positive");
+  spamm_sp2_run r = nullptr;
+  spamm_status st = spamm_sp2_begin(ctx, n, indptr, indices, data, n_occ, leaf, prec, &r);
+  if (st != SPAMM_OK) return st;
+  for (int q = 0; q < steps && st == SPAMM_OK; q++)
+    st = spamm_sp2_step_learned_margin(r, m, err_budget, tau_min, tau_max, mu_ref, gain_max);
   if (st != SPAMM_OK) {
     spamm_sp2_end(r, nullptr);
     return st;

@@ -232,6 +232,9 @@ cudaError_t sp2_energy(spamm_tree X, int64_t n, const int64_t *indptr, const int
                        const double *data, double *partial, void *rec, cudaStream_t s);
 void sp2_read_record(const void *host_rec, int steps, spamm_sp2_result *out);
 double *sp2_tau_slot(void *rec, int step);   // device address of the record's tau of a step
+// log10 of a step's error budget, loosened by its branch margin (into *out, device)
+cudaError_t sp2_margin_budget(spamm_tree X, int step, void *rec, double n_occ, double mu_ref, double gain_max,
+                              double log10_budget, double *out, cudaStream_t s);
 constexpr int kTreeFeatures = 34;            // per-tree part of the controller's features
 size_t tc_desc_bytes();
 // Batched tensor-core products: host descriptors of `count` products (same leaf size
@@ -244,7 +247,8 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
                              int32_t flags, spamm_tree *C);
 cudaError_t launch_feat_hist(spamm_tree t, float *out, cudaStream_t s);
 cudaError_t launch_tau_select(spamm_mlp mm, const float *fa, const float *fb, const double *grid, const double *bound,
-                              double log10_budget, double *tau_out, cudaStream_t s);
+                              double log10_budget, double *tau_out, cudaStream_t s,
+                              const double *log10_budget_dev = nullptr);
 cudaError_t launch_flat_bound(spamm_tree A, spamm_tree B, const double *grid, int G, double *work, double *bound,
                               cudaStream_t s);
 size_t bound_workspace_doubles(spamm_tree A);   // work + bound of launch_flat_bound on the 37-point grid

@@ -533,16 +533,18 @@ __device__ float net_eval(const Net &n, const float *th, const float *x) {
 // relative error is within the budget is written to *tau_out (grid[0] when none is).
 __global__ void __launch_bounds__(128) k_tau_select(Net n, const float *th, const float *fa, const float *fb,
                                                     const double *grid, const double *bound, int G,
-                                                    double log10_budget, double *tau_out) {
+                                                    double log10_budget, const double *log10_budget_dev,
+                                                    double *tau_out) {
   __shared__ int s_best;
   if (threadIdx.x == 0) s_best = -1;
   __syncthreads();
   const int g = threadIdx.x;
+  const double lb = log10_budget_dev ? *log10_budget_dev : log10_budget;   // a budget chosen on the device
   if (g < G) {
     float f[SPAMM_MLP_FEATURES];
     assemble(fa, fb, log10(grid[g]), bound[g], f);
     const float pred = net_eval(n, th, f);
-    if (pred <= (float)log10_budget) atomicMax(&s_best, g);
+    if (pred <= (float)lb) atomicMax(&s_best, g);
   }
   __syncthreads();
   if (threadIdx.x == 0) *tau_out = grid[s_best < 0 ? 0 : s_best];
@@ -572,8 +574,8 @@ cudaError_t launch_flat_bound(spamm_tree A, spamm_tree B, const double *grid, in
 }
 
 cudaError_t launch_tau_select(spamm_mlp mm, const float *fa, const float *fb, const double *grid, const double *bound,
-                              double log10_budget, double *tau_out, cudaStream_t s) {
-  k_tau_select<<<1, 128, 0, s>>>(mm->net, mm->th, fa, fb, grid, bound, kGrid, log10_budget, tau_out);
+                              double log10_budget, double *tau_out, cudaStream_t s, const double *log10_budget_dev) {
+  k_tau_select<<<1, 128, 0, s>>>(mm->net, mm->th, fa, fb, grid, bound, kGrid, log10_budget, log10_budget_dev, tau_out);
   return cudaGetLastError();
 }
 

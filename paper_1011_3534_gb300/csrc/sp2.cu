@@ -314,3 +314,33 @@ void sp2_read_record(const void *host_rec, int steps, spamm_sp2_result *out) {
 }
 
 double *sp2_tau_slot(void *rec, int step) { return &((StepRec *)rec)->tau[step]; }
+
+namespace {
+
+// log10 of the per-product error budget of step `step`: the base budget times
+// clamp(m / mu_ref, 1, gain_max), m the relative margin of the step's branch decision,
+// | |t2 - N| - |2 t1 - t2 - N| | / N, with t1 = Tr X (from the previous step's traces and
+// branch) and t2 = Tr X^2 = ||X||_F^2 (X is symmetric: the root of its norm pyramid).
+// Step 0 keeps the base budget.
+__global__ void k_sp2_margin_budget(const StepRec *rec, int step, const double *x_norm2_root, double n_occ,
+                                    double mu_ref, double gain_max, double log10_budget, double *out) {
+  if (threadIdx.x != 0) return;
+  double lb = log10_budget;
+  if (step > 0) {
+    const double tp = rec->trace[step - 1], tp2 = rec->trace2[step - 1];
+    const double t1 = rec->branch[step - 1] ? tp2 : 2.0 * tp - tp2;
+    const double t2 = *x_norm2_root;
+    const double m = fabs(fabs(t2 - n_occ) - fabs(2.0 * t1 - t2 - n_occ)) / n_occ;
+    lb += log10(fmin(gain_max, fmax(1.0, m / mu_ref)));
+  }
+  *out = lb;
+}
+
+}  // namespace
+
+cudaError_t sp2_margin_budget(spamm_tree X, int step, void *rec, double n_occ, double mu_ref, double gain_max,
+                              double log10_budget, double *out, cudaStream_t s) {
+  k_sp2_margin_budget<<<1, 32, 0, s>>>((const StepRec *)rec, step, X->norm2, n_occ, mu_ref, gain_max, log10_budget,
+                                       out);
+  return cudaGetLastError();
+}

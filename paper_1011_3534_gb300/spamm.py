@@ -46,7 +46,8 @@ EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_er
            "spamm_mlp_get_params", "spamm_mlp_set_params", "spamm_mlp_forward", "spamm_mlp_gradient",
            "spamm_mlp_adam_step", "spamm_mlp_adam_apply", "spamm_mlp_train", "spamm_features", "spamm_tau_select",
            "spamm_tree_distance", "spamm_sp2_begin", "spamm_sp2_step", "spamm_sp2_step_learned",
-           "spamm_sp2_iterate", "spamm_sp2_end", "spamm_sp2_learned", "spamm_drop_blocks",
+           "spamm_sp2_iterate", "spamm_sp2_end", "spamm_sp2_learned", "spamm_sp2_step_learned_margin",
+           "spamm_sp2_learned_margin", "spamm_drop_blocks",
            "spamm_sp2_step_drop", "spamm_sp2_dropping", "spamm_tree_update_batched")
 
 
@@ -121,6 +122,9 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.spamm_drop_blocks.argtypes = [_P, _D, ctypes.POINTER(_I64)]
     L.spamm_tree_update_batched.argtypes = [_P, _I32, _P, _P, _I32]
     L.spamm_sp2_step_learned.argtypes = [_P, _P, _D, _D, _D]
+    L.spamm_sp2_step_learned_margin.argtypes = [_P, _P, _D, _D, _D, _D, _D]
+    L.spamm_sp2_learned_margin.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, _I32, ctypes.c_int, _P, _D, _D, _D, _D,
+                                           _D, ctypes.POINTER(Sp2ResultT)]
     L.spamm_sp2_iterate.argtypes = [_P, ctypes.POINTER(_P)]
     L.spamm_sp2_end.argtypes = [_P, ctypes.POINTER(Sp2ResultT)]
     L.spamm_mlp_create.argtypes = [_P, _I32, _I32, ctypes.c_uint64, ctypes.POINTER(_P)]
@@ -417,6 +421,20 @@ def _csr(indptr, indices, data):
         raise ValueError(f"CSR: indptr[-1] must equal the number of indices and values, got "
                          f"{ip[-1] if ip.size else None}, {ix.size}, {dv.size}")
     return ip, ix, dv
+
+
+def spamm_sp2_learned_margin(ctx: Ctx, indptr, indices, data, n_occ: float, steps: int, leaf: int, prec: int,
+                             mlp: "Mlp", err_budget: float, tau_min: float, tau_max: float, mu_ref: float,
+                             gain_max: float) -> dict:
+    """SP2 with every step's tolerance chosen on the device by the controller, each step's
+    budget loosened by the margin of its branch decision (clamp(margin / mu_ref, 1, gain_max))."""
+    ip, ix, dv = _csr(indptr, indices, data)
+    r = Sp2ResultT()
+    ctx.check(LIB.spamm_sp2_learned_margin(ctx.h, ip.size - 1, ip.ctypes.data, ix.ctypes.data, dv.ctypes.data,
+                                           float(n_occ), steps, leaf, int(prec), mlp.h, float(err_budget),
+                                           float(tau_min), float(tau_max), float(mu_ref), float(gain_max),
+                                           ctypes.byref(r)), "spamm_sp2_learned_margin")
+    return _sp2_dict(r)
 
 
 def spamm_sp2_learned(ctx: Ctx, indptr, indices, data, n_occ: float, steps: int, leaf: int, prec: int,

@@ -104,7 +104,7 @@ def _worker(rank, port, out):
 def test_exchange_and_segment_products_gloo():
     import torch.multiprocessing as mp
     port = 28500 + os.getpid() % 1000
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork of this (threaded) process
         out = m.dict()
         mp.spawn(_worker, args=(port, out), nprocs=2, join=True)
         res = {r: out[r] for r in (0, 1)}
