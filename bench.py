@@ -23,7 +23,8 @@ The other --config values measure the remaining workloads once, one JSON line ea
 lattice32768 (n = 32768 physical-distance decay, FP16/BF16 leaves, leaf 64/128, three
 tau), batched256 (256 exponential-decay matrices of uneven n in one launch under a CUDA
 graph), sp2-32768 (SP2 on 32^3 tight-binding sites: fixed conservative tau in FP64
-against the learned controller with split-TF32 leaves).
+against the learned controller with split-TF32 leaves, errors against the stored
+spectral reference).
 """
 from __future__ import annotations
 
@@ -683,6 +684,8 @@ def run_sp2(args):
     cal = CT.calibrate_budget(ctx, m, small, ns / 2, steps, leaf, S.SPAMM_TF32X3, e_small, target,
                               CT.half_decades(1e-8, 1e-3), 1e-12, 1e-3)
     budget = cal[0]
+    calm = CT.calibrate_margin(ctx, m, small, ns / 2, steps, leaf, S.SPAMM_TF32X3, e_small, target,
+                               CT.half_decades(1e-8, 1e-4), (3e-3, 1e-2, 3e-2, 1e-1), (10.0, 100.0), 1e-12, 1e-3)
     big = W.tight_binding(32, seed=2)[:3]
     n = 32 ** 3
     spec = sp2_reference(32)
@@ -697,14 +700,18 @@ def run_sp2(args):
         fixed_tc = grid[tau_c]
         fixed64 = S.spamm_sp2(ctx, *big, n / 2, steps, leaf, S.SPAMM_FP64, tau_c)
         learned = S.spamm_sp2_learned(ctx, *big, n / 2, steps, leaf, S.SPAMM_TF32X3, m, budget, 1e-12, 1e-3)
+        margin = (S.spamm_sp2_learned_margin(ctx, *big, n / 2, steps, leaf, S.SPAMM_TF32X3, m, calm[0][0], 1e-12,
+                                             1e-3, calm[0][1], calm[0][2]) if calm else None)
     dense = steps * 2.0 * n ** 3
     err = lambda r: CT.energy_error(r, e_ref)
     lp = lambda r: int(sum(r["leaf_products"]))
+    head = margin if margin is not None else learned   # the learned form with the branch-margin budget
     _line({"workload": "SP2, 3-D tight binding on 32^3 sites (open boundaries, on-site U[-2,2], seed 2), "
-                       "half filling, 30 steps", "n": n, "leaf": leaf, "precision": "tf32x3 (learned tau)",
+                       "half filling, 30 steps", "n": n, "leaf": leaf,
+           "precision": "tf32x3 (learned tau, branch-margin budget)" if margin is not None else "tf32x3 (learned tau)",
            "accumulate": "fp32 per pass", "tau_fixed": tau_c, "error_budget": budget,
            "reference": "spectral SP2 of the dense FP64 eigensolve of H (CPU oracle, stored)"},
-          dense / (learned["ms"] * 1e-3) / 1e9, learned["ms"], "tf32x3",
+          dense / (head["ms"] * 1e-3) / 1e9, head["ms"], "tf32x3",
           {"time_to_solution_ms": {"fp64_fixed_tau": fixed64["ms"], "tf32x3_fixed_tau": fixed_tc["ms"],
                                    "tf32x3_learned_tau": learned["ms"], "tf32x3_tau1e-8": ref["ms"]},
            "energy_rel_err_vs_reference": {"fp64_fixed_tau": err(fixed64), "tf32x3_fixed_tau": err(fixed_tc),
@@ -717,7 +724,12 @@ def run_sp2(args):
                                            "tf32x3_learned_tau": learned["branches"] == spec["branches"]},
            "leaf_products": {"fp64_fixed_tau": lp(fixed64), "tf32x3_fixed_tau": lp(fixed_tc),
                              "tf32x3_learned_tau": lp(learned), "tf32x3_tau1e-8": lp(ref)},
-           "learned_taus": learned["taus"], "controller_train_loss": loss, "clocks": clk.summary()})
+           "learned_taus": learned["taus"], "controller_train_loss": loss, "clocks": clk.summary(),
+           "margin_rule": None if margin is None else {
+               "settings": {"budget": calm[0][0], "mu_ref": calm[0][1], "gain_max": calm[0][2]},
+               "time_to_solution_ms": margin["ms"], "energy_rel_err_vs_reference": err(margin),
+               "arbiter_rel_diff_vs_fp64_fixed_tau": abs(margin["energy"] - fixed64["energy"]) / abs(fixed64["energy"]),
+               "leaf_products": lp(margin), "branches_equal_to_reference": margin["branches"] == spec["branches"]}})
     m.free()
     S.spamm_ctx_destroy(ctx)
 

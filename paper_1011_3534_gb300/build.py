@@ -35,7 +35,13 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(verbose: bool = False, extra: list[str] | None = None, out_dir: str | None = None,
+          lib_name: str = "libspamm.so") -> str:
+    """Compile csrc/ into out_dir (default _build/) and link lib_name there; `extra`
+    nvcc flags apply to every translation unit (a separate out_dir keeps such a build
+    apart from the library's own)."""
+    BUILD = out_dir or globals()["BUILD"]
+    LIB = os.path.join(BUILD, lib_name)
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [

@@ -39,6 +39,20 @@
 #include "internal.cuh"
 #include "tc_ptx.cuh"
 
+// Optional per-role cycle counters (build with -DSPAMM_LEAF_ROLE_CYCLES; the library's
+// own build compiles none of this): per CTA, the cycles each role spends waiting and
+// working, read back by spamm_leaf_role_cycles (paper_1011_3534_gb300/leaf_role_cycles.py).
+#ifdef SPAMM_LEAF_ROLE_CYCLES
+__device__ unsigned long long g_role_cycles[1024][10];
+#define ROLE_T0(v) const long long v = clock64()
+#define ROLE_ADD(slot, v) atomicAdd(&g_role_cycles[blockIdx.x & 1023][slot], (unsigned long long)(clock64() - (v)))
+#define ROLE_COUNT(slot) atomicAdd(&g_role_cycles[blockIdx.x & 1023][slot], 1ull)
+#else
+#define ROLE_T0(v)
+#define ROLE_ADD(slot, v)
+#define ROLE_COUNT(slot)
+#endif
+
 namespace {
 
 constexpr int kThreads = 192;
@@ -161,6 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  ROLE_T0(t_kernel);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; s++) {
       mbar_init(&full[s], 1);
@@ -299,7 +314,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t cols = c0 + l == 0 ? 3u : pass_cols<LEAF>(d, oob);
               const int boxes = (SPLIT ? 2 : 1) * (RA + (RC == 2 ? __popc(cols) : 1));
               for (int ch = 0; ch < cm.chunks; ch++) {
-                if (!mbar_wait(&empty[stage], phase ^ 1u, &s_abort)) {
+                ROLE_T0(t_we);
+                const bool ok_e = mbar_wait(&empty[stage], phase ^ 1u, &s_abort);
+                ROLE_ADD(0, t_we);
+                if (!ok_e) {
                   s_abort = 1;
                   flag_error(cm.status, DEV_TIMEOUT);
                   break;
@@ -373,7 +391,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int per_chain = SPLIT ? cm.chunks : (int)np * cm.chunks;
         bool small_ok = true;
         if (SPLIT && lane == 0 && !s_abort) {
+          ROLE_T0(t_ws);
           small_ok = mbar_wait(&sme[sm_idx], sm_phase ^ 1u, &s_abort);
+          ROLE_ADD(3, t_ws);
           if (!small_ok) {
             s_abort = 1;
             flag_error(cm.status, DEV_TIMEOUT);
@@ -382,8 +402,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const uint32_t ds = tmem + R::kSmallCol + (uint32_t)sm_idx * 128u;   // split: hi lo + lo hi
         uint32_t acc_small = 0;
+        if (lane == 0) ROLE_COUNT(8);
         for (int p = 0; p < chains && lane == 0 && !s_abort; p++) {
-          if (!mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort)) {
+          ROLE_T0(t_wa);
+          const bool ok_a = mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort);
+          ROLE_ADD(3, t_wa);
+          if (!ok_a) {
             s_abort = 1;
             flag_error(cm.status, DEV_TIMEOUT);
           } else {
@@ -391,7 +415,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t d = tmem + (uint32_t)acc * 128u;   // plain, or split hi hi
             uint32_t acc_big = 0;
             for (int t = 0; t < per_chain; t++) {
-              if (!mbar_wait(&full[stage], phase, &s_abort)) {
+              ROLE_T0(t_wf);
+              const bool ok_f = mbar_wait(&full[stage], phase, &s_abort);
+              ROLE_ADD(2, t_wf);
+              if (!ok_f) {
                 s_abort = 1;
                 flag_error(cm.status, DEV_TIMEOUT);
                 break;
@@ -399,6 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               tc_fence_after();
               const uint32_t cols = s_cols[stage];
               const uint32_t st = base + stage * R::kStageBytes;
+              ROLE_T0(t_is);
 #pragma unroll
               for (int kk = 0; kk < 4; kk++) {
                 if (SPLIT) {
@@ -409,6 +437,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mma(d, st + R::kAhi, st + R::kBhi, cols, kk, acc_big);
                 acc_big = 1;
               }
+              ROLE_ADD(4, t_is);
+              ROLE_COUNT(9);
               mma_commit(&empty[stage]);
               nst += (SPLIT ? 3u : 1u) * (cols == 3u ? 2u : 1u);   // 128 x 64 x chunk MMA chains
               if (++stage == kStages) {
@@ -486,7 +516,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (uint32_t p = 0; p < np; p++) {
             if ((p & 31u) == 0u && p + lane < np) pl = P.plan[(int64_t)first + p + lane];
             const uint32_t cols = p == 0 ? 3u : __shfl_sync(0xffffffffu, pass_cols<LEAF>(pl, oob), p & 31u);
+            ROLE_T0(t_ep);
             bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
+            if (warp == 2 && lane == 0) ROLE_ADD(6, t_ep);
             if (!ok) {
               s_abort = 1;
               flag_error(cm.status, DEV_TIMEOUT);
@@ -506,7 +538,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               acc_phase ^= 1u;
             }
           }
+          ROLE_T0(t_es);
           bool ok = mbar_wait(&smf[sm_idx], sm_phase, &s_abort);
+          if (warp == 2 && lane == 0) ROLE_ADD(6, t_es);
           if (!ok) {
             s_abort = 1;
             flag_error(cm.status, DEV_TIMEOUT);
@@ -527,7 +561,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (!all_ok) touched = 0;
         } else {
+          ROLE_T0(t_ea);
           bool ok = mbar_wait(&accf[acc], acc_phase, &s_abort);
+          if (warp == 2 && lane == 0) ROLE_ADD(6, t_ea);
           if (!ok) {
             s_abort = 1;
             flag_error(cm.status, DEV_TIMEOUT);
@@ -655,6 +691,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   }
+  if (lane == 0 && warp <= 2) ROLE_ADD(warp == 0 ? 1 : warp == 1 ? 5 : 7, t_kernel);
   tc_fence_before();
   __syncthreads();
   if (s_abort) {
@@ -813,3 +850,15 @@ cudaError_t launch_leaf_tc_table(const void *dev_table, int count, int b, int pr
   if (count < 1 || count > kMaxProd) return cudaErrorInvalidValue;
   return run_table((const ProdDesc *)dev_table, count, b, prec, dev_status, sm_count, s);
 }
+
+#ifdef SPAMM_LEAF_ROLE_CYCLES
+// The per-role counters of the probe build: copy them to `host` (1024 x 10 unsigned
+// 64-bit values, row = CTA) or, with reset != 0, zero them.
+extern "C" __attribute__((visibility("default"))) int spamm_leaf_role_cycles(void *host, int reset) {
+  if (reset) {
+    static unsigned long long zero[1024][10] = {};
+    return (int)cudaMemcpyToSymbol(g_role_cycles, zero, sizeof zero);
+  }
+  return (int)cudaMemcpyFromSymbol(host, g_role_cycles, sizeof(unsigned long long) * 1024 * 10);
+}
+#endif

@@ -257,3 +257,28 @@ def test_symmetric_and_transposed_layouts_agree(S, ctx, n):
     assert np.array_equal(S.spamm_tree_to_dense(c1), S.spamm_tree_to_dense(c2))
     for t in (c1, c2, t1, t2):
         S.spamm_tree_free(t)
+
+
+@pytest.mark.parametrize("leaf", [32, 64, 128])
+def test_split_tf32_accumulation_bias(S, ctx, leaf):
+    # The tensor cores truncate each MMA's FP32 sum; on a product with positive entries a
+    # single accumulator per output block gave a mean relative error of -2.2e-5. The split
+    # forms keep each pass's hi hi products in an accumulator of their own (leaf 64, 128)
+    # or add every MMA's result in FP32 with round to nearest (leaf 32), so the bias
+    # against FP64 SpAMM on the same triples is at most that of one pass: leaf / 8 TF32
+    # MMAs (K = 8 each), at most half a unit in the last place each on average, hence
+    # |mean| <= (leaf / 8) 2^-24 and rms <= (leaf / 8) 2^-23 (the operands' split adds
+    # 2^-22 at most)
+    n = 2048
+    r = np.random.default_rng(17)
+    d = np.abs(np.arange(n)[:, None] - np.arange(n)[None, :])
+    U = r.uniform(0.5, 1.0, (n, n))
+    A = (U + U.T) / 2 * 0.97 ** d          # symmetric, positive, exponential decay
+    g = gpu_product(S, ctx, A, A, leaf, 1e-10, "tf32x3", True)
+    TA = oracle.Tree(A, leaf)
+    C64 = oracle.spamm(TA, TA, 1e-10, threads=oracle.max_threads())["C"]
+    big = C64 > 1e-3 * C64.max()
+    rel = (g["C"][big] - C64[big]) / C64[big]
+    print(f"split TF32 leaf {leaf}: mean relative error {rel.mean():.2e}, rms {np.sqrt((rel ** 2).mean()):.2e}")
+    assert abs(rel.mean()) <= (leaf / 8) * 2.0 ** -24
+    assert np.sqrt((rel ** 2).mean()) <= (leaf / 8) * 2.0 ** -23 + 2.0 ** -22
