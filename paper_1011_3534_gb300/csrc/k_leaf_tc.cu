@@ -43,10 +43,17 @@
 // own build compiles none of this): per CTA, the cycles each role spends waiting and
 // working, read back by spamm_leaf_role_cycles (paper_1011_3534_gb300/leaf_role_cycles.py).
 #ifdef SPAMM_LEAF_ROLE_CYCLES
-__device__ unsigned long long g_role_cycles[1024][10];
+__device__ unsigned long long g_role_cycles[1024][16];
 #define ROLE_T0(v) const long long v = clock64()
-#define ROLE_ADD(slot, v) atomicAdd(&g_role_cycles[blockIdx.x & 1023][slot], (unsigned long long)(clock64() - (v)))
-#define ROLE_COUNT(slot) atomicAdd(&g_role_cycles[blockIdx.x & 1023][slot], 1ull)
+#define ROLE_ADD(slot, v)                                                                               \
+  do {                                                                                                  \
+    if ((threadIdx.x & 31) == 0)                                                                        \
+      atomicAdd(&g_role_cycles[blockIdx.x & 1023][slot], (unsigned long long)(clock64() - (v)));       \
+  } while (0)
+#define ROLE_COUNT(slot)                                                                                \
+  do {                                                                                                  \
+    if ((threadIdx.x & 31) == 0) atomicAdd(&g_role_cycles[blockIdx.x & 1023][slot], 1ull);            \
+  } while (0)
 #else
 #define ROLE_T0(v)
 #define ROLE_ADD(slot, v)
@@ -256,6 +263,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     return e.x >= 0;
   };
 
+  // whole-warp bounded wait: every lane polls, the outcome is made warp-uniform, and a
+  // wait that ran out sets the abort flag and the error bit
+  auto wwait = [&](uint64_t *bar, uint32_t parity) -> bool {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, parity, &s_abort));
+    if (!ok && lane == 0) {
+      s_abort = 1;
+      flag_error(cm.status, DEV_TIMEOUT);
+    }
+    return ok;
+  };
+  auto aborted = [&]() -> bool { return __any_sync(0xffffffffu, s_abort != 0); };
+
   if (warp == 0) {
     // ---------------- TMA producer (warp 0) ----------------
     // Each item's passes are loaded 32 at a time, the next chunk while lane 0 issues
@@ -276,6 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t cur_ij;
     describe(claim(), cur_e, cur_ij);
     for (;;) {
+      ROLE_T0(t_pub);
       // publish the item to the other roles
       if (lane == 0) {
         if (!mbar_wait(&qempty[qs], qp ^ 1u, &s_abort)) {
@@ -290,6 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         qs = 0;
         qp ^= 1u;
       }
+      ROLE_ADD(11, t_pub);
       if (cur_e.x < 0 || __shfl_sync(0xffffffffu, s_abort ? 1 : 0, 0)) break;
       const unsigned int g_next = claim();   // the claim's reply arrives while this item's loads go out
       {
@@ -305,23 +326,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           s_desc[lane] = cur;
           __syncwarp();
           if (c0 + 32 < np && c0 + 32 + lane < np) cur = plan[(int64_t)first + c0 + 32 + lane];
-          if (lane == 0) {
-            const int nl = (int)min(32u, np - c0);
-            for (int l = 0; l < nl && !s_abort; l++) {
-              const int4 d = s_desc[l];
-              // the first pass of an item initialises both column halves (N = 128) of the
-              // item's accumulator (plain) or correction accumulator (split)
-              const uint32_t cols = c0 + l == 0 ? 3u : pass_cols<LEAF>(d, oob);
-              const int boxes = (SPLIT ? 2 : 1) * (RA + (RC == 2 ? __popc(cols) : 1));
-              for (int ch = 0; ch < cm.chunks; ch++) {
-                ROLE_T0(t_we);
-                const bool ok_e = mbar_wait(&empty[stage], phase ^ 1u, &s_abort);
-                ROLE_ADD(0, t_we);
-                if (!ok_e) {
-                  s_abort = 1;
-                  flag_error(cm.status, DEV_TIMEOUT);
-                  break;
-                }
+          // the whole warp walks the passes and waits; one elected lane issues each
+          // stage's copies
+          const int nl = (int)min(32u, np - c0);
+          for (int l = 0; l < nl && !aborted(); l++) {
+            const int4 d = s_desc[l];
+            // the first pass of an item initialises both column halves (N = 128) of the
+            // item's accumulator (plain) or correction accumulator (split)
+            const uint32_t cols = c0 + l == 0 ? 3u : pass_cols<LEAF>(d, oob);
+            const int boxes = (SPLIT ? 2 : 1) * (RA + (RC == 2 ? __popc(cols) : 1));
+            for (int ch = 0; ch < cm.chunks; ch++) {
+              ROLE_T0(t_we);
+              const bool ok_e = wwait(&empty[stage], phase ^ 1u);
+              ROLE_ADD(0, t_we);
+              if (!ok_e) break;
+              if (elect_one()) {
                 s_cols[stage] = (uint8_t)cols;   // read by the MMA warp after the full barrier
                 mbar_expect_tx(&full[stage], (uint32_t)boxes * kBox);
                 const uint32_t st = base + stage * R::kStageBytes;
@@ -336,17 +355,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                   if (cols & 1u) tma_load_3d(sb, mb, &full[stage], x, 0, d.z);
                   if (RC == 2 && (cols & 2u)) tma_load_3d(sb + kBox, mb, &full[stage], x, 0, d.w);
                 }
-                if (++stage == kStages) {
-                  stage = 0;
-                  phase ^= 1u;
-                }
+              }
+              __syncwarp();
+              if (++stage == kStages) {
+                stage = 0;
+                phase ^= 1u;
               }
             }
           }
           __syncwarp();
         }
       }
+      ROLE_T0(t_ds);
       describe(g_next, cur_e, cur_ij);
+      ROLE_ADD(12, t_ds);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (warp 1) ----------------
@@ -356,25 +378,54 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t acc_phase = 0, sm_phase = 0;
     unsigned long long nst = 0;
     int last_prod = -1;
-    // one MMA of the K-step kk of a stage: N = 128, or N = 64 on the column half c
-    auto mma = [&](uint32_t d, uint32_t sa, uint32_t sb, uint32_t cols, int kk, uint32_t accum) {
-      const uint64_t da = desc_sw128(sa + kk * 32);
-      if (cols == 3u) {
-        const uint64_t db = desc_sw128(sb + kk * 32);
-        if (TF32) mma_tf32(d, da, db, cm.idesc, accum); else mma_f16(d, da, db, cm.idesc, accum);
-      } else {
-        const uint32_t c = cols == 2u ? 1u : 0u;
-        const uint64_t db = desc_sw128(sb + c * kBox + kk * 32);
-        if (TF32) mma_tf32(d + 64u * c, da, db, cm.idesc64, accum);
-        else mma_f16(d + 64u * c, da, db, cm.idesc64, accum);
+    // All MMAs of a stage (4 K-steps of 32 bytes; split: hi lo and lo hi into the
+    // correction accumulator ds, then hi hi into d) and the stage's commit, issued back
+    // to back by one elected lane: N = 128, or N = 64 on the column half c. The
+    // descriptors of the stage's boxes are formed once; a K-step adds 2 (32 bytes >> 4)
+    // to the address field, which stays below 2^14 for every stage of the ring. Issuing
+    // each MMA under its own election and warp sync cost ~115 cycles per 128 x 128 MMA
+    // against 64 for this form (measured on this GPU).
+    auto stage_mmas = [&](uint32_t st, uint32_t cols, uint32_t d, uint32_t ds, uint32_t accb, uint32_t accs,
+                          uint64_t *done) {
+      const bool both = cols == 3u;
+      const uint32_t c = cols == 2u ? 1u : 0u;
+      const uint32_t boff = both ? 0u : c * kBox, doff = both ? 0u : 64u * c;
+      const uint32_t id = both ? cm.idesc : cm.idesc64;
+      const uint64_t dAhi = desc_sw128(st + R::kAhi), dBhi = desc_sw128(st + R::kBhi + boff);
+      const uint64_t dAlo = SPLIT ? desc_sw128(st + R::kAlo) : 0ull;
+      const uint64_t dBlo = SPLIT ? desc_sw128(st + R::kBlo + boff) : 0ull;
+      if (elect_one()) {
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+          if (SPLIT) {
+            if (TF32) {
+              mma_tf32(ds + doff, dAhi + 2 * kk, dBlo + 2 * kk, id, kk ? 1u : accs);
+              mma_tf32(ds + doff, dAlo + 2 * kk, dBhi + 2 * kk, id, 1u);
+            } else {
+              mma_f16(ds + doff, dAhi + 2 * kk, dBlo + 2 * kk, id, kk ? 1u : accs);
+              mma_f16(ds + doff, dAlo + 2 * kk, dBhi + 2 * kk, id, 1u);
+            }
+          }
+          if (TF32) mma_tf32(d + doff, dAhi + 2 * kk, dBhi + 2 * kk, id, kk ? 1u : accb);
+          else mma_f16(d + doff, dAhi + 2 * kk, dBhi + 2 * kk, id, kk ? 1u : accb);
+        }
+        mma_commit(done);
       }
+      __syncwarp();
+    };
+    auto commit = [&](uint64_t *bar) {
+      if (elect_one()) mma_commit(bar);
+      __syncwarp();
     };
     int qs = 0;
     uint32_t qp = 0;
     for (;;) {
       int4 e;
       uint32_t ij_unused;
-      if (!take(qs, qp, e, ij_unused)) break;
+      ROLE_T0(t_tk);
+      const bool more = take(qs, qp, e, ij_unused);
+      ROLE_ADD(10, t_tk);
+      if (!more) break;
       {
         const int pr = e.x;
         const uint2 mt = make_uint2((uint32_t)e.z, (uint32_t)e.w);
@@ -390,63 +441,44 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int chains = SPLIT ? (int)np : 1;
         const int per_chain = SPLIT ? cm.chunks : (int)np * cm.chunks;
         bool small_ok = true;
-        if (SPLIT && lane == 0 && !s_abort) {
+        if (SPLIT && !aborted()) {
           ROLE_T0(t_ws);
-          small_ok = mbar_wait(&sme[sm_idx], sm_phase ^ 1u, &s_abort);
+          small_ok = wwait(&sme[sm_idx], sm_phase ^ 1u);
           ROLE_ADD(3, t_ws);
-          if (!small_ok) {
-            s_abort = 1;
-            flag_error(cm.status, DEV_TIMEOUT);
-          }
           tc_fence_after();
         }
         const uint32_t ds = tmem + R::kSmallCol + (uint32_t)sm_idx * 128u;   // split: hi lo + lo hi
         uint32_t acc_small = 0;
-        if (lane == 0) ROLE_COUNT(8);
-        for (int p = 0; p < chains && lane == 0 && !s_abort; p++) {
+        ROLE_COUNT(8);
+        for (int p = 0; p < chains && !aborted(); p++) {
           ROLE_T0(t_wa);
-          const bool ok_a = mbar_wait(&acce[acc], acc_phase ^ 1u, &s_abort);
+          const bool ok_a = wwait(&acce[acc], acc_phase ^ 1u);
           ROLE_ADD(3, t_wa);
-          if (!ok_a) {
-            s_abort = 1;
-            flag_error(cm.status, DEV_TIMEOUT);
-          } else {
+          if (ok_a) {
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)acc * 128u;   // plain, or split hi hi
             uint32_t acc_big = 0;
             for (int t = 0; t < per_chain; t++) {
               ROLE_T0(t_wf);
-              const bool ok_f = mbar_wait(&full[stage], phase, &s_abort);
+              const bool ok_f = wwait(&full[stage], phase);
               ROLE_ADD(2, t_wf);
-              if (!ok_f) {
-                s_abort = 1;
-                flag_error(cm.status, DEV_TIMEOUT);
-                break;
-              }
+              if (!ok_f) break;
               tc_fence_after();
               const uint32_t cols = s_cols[stage];
               const uint32_t st = base + stage * R::kStageBytes;
               ROLE_T0(t_is);
-#pragma unroll
-              for (int kk = 0; kk < 4; kk++) {
-                if (SPLIT) {
-                  mma(ds, st + R::kAhi, st + R::kBlo, cols, kk, acc_small);
-                  acc_small = 1;
-                  mma(ds, st + R::kAlo, st + R::kBhi, cols, kk, 1);
-                }
-                mma(d, st + R::kAhi, st + R::kBhi, cols, kk, acc_big);
-                acc_big = 1;
-              }
+              stage_mmas(st, cols, d, ds, acc_big, acc_small, &empty[stage]);
+              acc_big = 1;
+              acc_small = 1;
               ROLE_ADD(4, t_is);
               ROLE_COUNT(9);
-              mma_commit(&empty[stage]);
               nst += (SPLIT ? 3u : 1u) * (cols == 3u ? 2u : 1u);   // 128 x 64 x chunk MMA chains
               if (++stage == kStages) {
                 stage = 0;
                 phase ^= 1u;
               }
             }
-            mma_commit(&accf[acc]);
+            commit(&accf[acc]);
           }
           if (SPLIT && ++acc == kAcc) {
             acc = 0;
@@ -454,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (SPLIT) {
-          if (lane == 0 && small_ok) mma_commit(&smf[sm_idx]);   // after the item's last MMA
+          if (small_ok) commit(&smf[sm_idx]);   // after the item's last MMA
           if (++sm_idx == kSmall) {
             sm_idx = 0;
             sm_phase ^= 1u;
@@ -480,7 +512,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (;;) {
       int4 e;
       uint32_t ij;
-      if (!take(qs, qp, e, ij)) break;
+      ROLE_T0(t_tk);
+      const bool more = take(qs, qp, e, ij);
+      if (warp == 2) ROLE_ADD(14, t_tk);
+      if (!more) break;
       {
         const int pr = e.x;
         const ProdDesc &P = prods[pr];
@@ -572,6 +607,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!ok) touched = 0;
           tc_fence_after();
         }
+        ROLE_T0(t_fin);
         const int a = LEAF == 64 ? row / 64 : (qd >> 1);
         const int r = LEAF == 64 ? row % 64 : row;
         const int i = (int)(2 * I) + a;
@@ -684,6 +720,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (warp == 2) ROLE_ADD(13, t_fin);
         if (!SPLIT && ++acc == kAcc) {
           acc = 0;
           acc_phase ^= 1u;
@@ -856,9 +893,9 @@ cudaError_t launch_leaf_tc_table(const void *dev_table, int count, int b, int pr
 // 64-bit values, row = CTA) or, with reset != 0, zero them.
 extern "C" __attribute__((visibility("default"))) int spamm_leaf_role_cycles(void *host, int reset) {
   if (reset) {
-    static unsigned long long zero[1024][10] = {};
+    static unsigned long long zero[1024][16] = {};
     return (int)cudaMemcpyToSymbol(g_role_cycles, zero, sizeof zero);
   }
-  return (int)cudaMemcpyFromSymbol(host, g_role_cycles, sizeof(unsigned long long) * 1024 * 10);
+  return (int)cudaMemcpyFromSymbol(host, g_role_cycles, sizeof(unsigned long long) * 1024 * 16);
 }
 #endif

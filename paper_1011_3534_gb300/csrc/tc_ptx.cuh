@@ -10,6 +10,22 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// One lane of a converged warp (the lowest active one) for a single-thread issue of
+// TMA and tcgen05 instructions. The issue loops run on the whole warp and elect the
+// issuing lane per instruction: the same loop run by one lane in a divergent branch
+// issued tcgen05.mma at 73-280 cycles per instruction against 48 (N = 64) and 64
+// (N = 128) cycles converged (measured on this GPU).
+__device__ __forceinline__ bool elect_one() {
+  uint32_t p = 0;
+  asm volatile(
+      "{\n\t.reg .b32 rx;\n\t.reg .pred px;\n\t"
+      "elect.sync rx|px, %1;\n\t"
+      "selp.u32 %0, 1, 0, px;\n\t}\n"
+      : "=r"(p)
+      : "r"(0xffffffffu));
+  return p != 0;
+}
+
 // ---- mbarrier ----
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

@@ -8,7 +8,10 @@ build, and prints, per CTA on average, the cycles each role of `k_leaf_tc` spend
   producer  (TMA, warp 0)     total, waiting for a free stage
   MMA       (warp 1)          total, waiting for a stage's data, waiting for a free
                               accumulator, issuing tcgen05.mma (per stage)
-  epilogue  (warps 2-5)       total, waiting for a finished accumulator
+  epilogue  (warps 2-5)       total, waiting for a finished accumulator, storing C and
+                              its norms
+  item hand-off               MMA and epilogue waiting for the next item, producer
+                              publishing it and reading the next item's description
 
 and the spread of the CTAs' totals (load balance).
 
@@ -26,6 +29,7 @@ import numpy as np
 def main(n: int = 8192):
     import torch
     from . import build as B
+    B.build()                       # the library's own build, which the binding loads on import
     from . import spamm as S
     from . import workloads as W
     so = B.build(extra=["-DSPAMM_LEAF_ROLE_CYCLES"], out_dir=os.path.join(B.HERE, "_build_roles"))
@@ -43,7 +47,7 @@ def main(n: int = 8192):
         L.spamm_leaf_role_cycles(None, 1)
         C = S.spamm_multiply(ctx, t, t, 1e-8, p, S.SPAMM_SYM_PRODUCT, C)
         st = S.spamm_stats(C)
-        buf = np.zeros((1024, 10), dtype=np.uint64)
+        buf = np.zeros((1024, 16), dtype=np.uint64)
         L.spamm_leaf_role_cycles(buf.ctypes.data, 0)
         grid = int(torch.cuda.get_device_properties(0).multi_processor_count)
         b = buf[:grid].astype(np.float64)
@@ -54,6 +58,10 @@ def main(n: int = 8192):
               f"{b[:, 3].mean():.0f}, issuing {b[:, 4].mean():.0f} = {b[:, 4].sum() / max(stages, 1):.0f} per stage); "
               f"epilogue {b[:, 7].mean():.0f} (waiting {b[:, 6].mean():.0f}); CTA totals max/mean "
               f"{b[:, 7].max() / max(b[:, 7].mean(), 1):.2f}", flush=True)
+        print(f"  item hand-off (cycles per CTA): MMA waiting for the next item {b[:, 10].mean():.0f}, "
+              f"epilogue waiting for the next item {b[:, 14].mean():.0f}; producer publishing "
+              f"{b[:, 11].mean():.0f}, describing the next item {b[:, 12].mean():.0f}; epilogue stores and "
+              f"norms {b[:, 13].mean():.0f}", flush=True)
         S.spamm_tree_free(C)
         S.spamm_tree_free(t)
     S.spamm_ctx_destroy(ctx)
