@@ -190,11 +190,8 @@ struct spamm_tree_s {
 };
 
 // A symmetric product whose blocks j > i are written by k_mirror after the leaf kernel:
-// FP64, the split forms, and the small-leaf kernel (the plain tcgen05 forms write them in
-// their epilogue).
-inline bool mirror_after_leaf(const spamm_tree_s *C) {
-  return C->prec == SPAMM_FP64 || split_prec(C->prec) || C->b < 64;
-}
+// FP64 and the small-leaf kernel (the tcgen05 forms write them in their epilogue).
+inline bool mirror_after_leaf(const spamm_tree_s *C) { return C->prec == SPAMM_FP64 || C->b < 64; }
 
 __host__ __device__ inline int64_t level_offset(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
 

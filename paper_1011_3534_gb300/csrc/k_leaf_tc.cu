@@ -619,14 +619,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int q = a * 2 + c;
           const int j = (int)(2 * J) + c;
           if (!((touched >> q) & 1u) || i >= P.nb || j >= P.nb) continue;   // warp-uniform
-          // plain forms: the warp's 32 rows of block (i, j) are written through shared
-          // memory, so that each store instruction covers four whole 128-byte rows; the
-          // split forms store each thread's row directly
-          float *dst = P.C + (((int64_t)i * P.nb + j) * LEAF + r) * LEAF;
+          // the warp's 32 rows of block (i, j) are written through shared memory, so that
+          // each store instruction covers four whole 128-byte rows
           float *blk = P.C + ((int64_t)i * P.nb + j) * LEAF * LEAF + (int64_t)(r - lane) * LEAF;
           float(*sb)[33] = s_epi[warp - 2];
-          // symmetric product, plain forms: block (j, i) = (i, j)^T from the same staged chunk
-          const bool mir = !SPLIT && P.sym && i < j;
+          // symmetric product: block (j, i) = (i, j)^T from the same staged chunk
+          const bool mir = P.sym && i < j;
           float *blkT = P.C + ((int64_t)j * P.nb + i) * LEAF * LEAF + (r - lane);
 #pragma unroll
           for (int h = 0; h < LEAF / 32; h++) {
@@ -638,32 +636,26 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t col = (uint32_t)acc * 128u + (uint32_t)(cc * 64 + h * 32);
               tmem_ld32(tmem + lanes + col, v);
             }
-            if (!SPLIT) {
 #pragma unroll
-              for (int x = 0; x < 32; x++) sb[lane][x] = __uint_as_float(v[x]);
-              __syncwarp();
+            for (int x = 0; x < 32; x++) sb[lane][x] = __uint_as_float(v[x]);
+            __syncwarp();
+#pragma unroll
+            for (int it = 0; it < 8; it++) {
+              const int rl = it * 4 + (lane >> 3), c4 = (lane & 7) * 4;
+              *reinterpret_cast<float4 *>(blk + (int64_t)rl * LEAF + h * 32 + c4) =
+                  make_float4(sb[rl][c4], sb[rl][c4 + 1], sb[rl][c4 + 2], sb[rl][c4 + 3]);
+            }
+            if (mir) {   // row h*32 + cl of block (j, i), its 32 columns r - lane ..
 #pragma unroll
               for (int it = 0; it < 8; it++) {
-                const int rl = it * 4 + (lane >> 3), c4 = (lane & 7) * 4;
-                *reinterpret_cast<float4 *>(blk + (int64_t)rl * LEAF + h * 32 + c4) =
-                    make_float4(sb[rl][c4], sb[rl][c4 + 1], sb[rl][c4 + 2], sb[rl][c4 + 3]);
+                const int cl = it * 4 + (lane >> 3), r4 = (lane & 7) * 4;
+                *reinterpret_cast<float4 *>(blkT + (int64_t)(h * 32 + cl) * LEAF + r4) =
+                    make_float4(sb[r4][cl], sb[r4 + 1][cl], sb[r4 + 2][cl], sb[r4 + 3][cl]);
               }
-              if (mir) {   // row h*32 + cl of block (j, i), its 32 columns r - lane ..
-#pragma unroll
-                for (int it = 0; it < 8; it++) {
-                  const int cl = it * 4 + (lane >> 3), r4 = (lane & 7) * 4;
-                  *reinterpret_cast<float4 *>(blkT + (int64_t)(h * 32 + cl) * LEAF + r4) =
-                      make_float4(sb[r4][cl], sb[r4 + 1][cl], sb[r4 + 2][cl], sb[r4 + 3][cl]);
-                }
-              }
-              __syncwarp();
             }
+            __syncwarp();
 #pragma unroll
             for (int x = 0; x < 32; x += 4) {
-              if (SPLIT)
-                *reinterpret_cast<float4 *>(dst + h * 32 + x) =
-                    make_float4(__uint_as_float(v[x]), __uint_as_float(v[x + 1]), __uint_as_float(v[x + 2]),
-                                __uint_as_float(v[x + 3]));
 #pragma unroll
               for (int z = 0; z < 4; z++) {
                 const float fv = __uint_as_float(v[x + z]);
@@ -701,7 +693,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const double v2 = s_norm[2 * aa][c] + s_norm[2 * aa + 1][c];
               P.leaf_norm2C[(int64_t)ii * P.NB + jj] = v2;
               P.nzC[(int64_t)ii * P.NB + jj] = 1;
-              if (!SPLIT && P.sym && ii < jj) {
+              if (P.sym && ii < jj) {
                 P.leaf_norm2C[(int64_t)jj * P.NB + ii] = v2;
                 P.nzC[(int64_t)jj * P.NB + ii] = 1;
               }
@@ -712,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const double v2 = ((s_norm[0][0] + s_norm[1][0]) + s_norm[2][0]) + s_norm[3][0];
               P.leaf_norm2C[(int64_t)i * P.NB + jj] = v2;
               P.nzC[(int64_t)i * P.NB + jj] = 1;
-              if (!SPLIT && P.sym && i < jj) {
+              if (P.sym && i < jj) {
                 P.leaf_norm2C[(int64_t)jj * P.NB + i] = v2;
                 P.nzC[(int64_t)jj * P.NB + i] = 1;
               }
