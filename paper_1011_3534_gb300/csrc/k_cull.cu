@@ -455,11 +455,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
 // (summed per thread over K, per warp by a fixed tree, then over warps in order) goes
 // to the first parent-group slot of the tier and zeros to the others, so the fixed-
 // order reduction of the slots returns it unchanged.
-constexpr int kTopTiers = 5;                 // tiers 0..4
-constexpr int kTopBlocks = 256;              // output blocks of tier 4 (4^4)
+constexpr int kTopTiers = 6;                 // tiers 0..5
+constexpr int kTopBlocks = 1024;             // output blocks of tier 5 (4^5), a thread each
 constexpr int kTopThreads = 1024;
 constexpr int kTopWarps = kTopThreads / 32;
-constexpr int kTopNorms = ((1 << (2 * kTopTiers)) - 1) / 3;   // norms of tiers 0..4 per operand
+constexpr int kTopNorms = ((1 << (2 * kTopTiers)) - 1) / 3;   // norms of tiers 0..5 per operand
+static_assert(kTopBlocks == 1 << (2 * (kTopTiers - 1)) && kTopBlocks <= kTopThreads, "a thread per tier-T block");
 
 struct TopArgs {
   const double *nA[kTopTiers], *nB[kTopTiers];   // tier norms (not squared)
@@ -517,7 +518,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
       t.cnt->nentries[0] = 1;
     }
   }
-  __shared__ uint16_t s_mask[2][kTopBlocks];            // survivors over K per block: tiers l-1, l
+  __shared__ uint32_t s_mask[2][kTopBlocks];            // survivors over K per block: tiers l-1, l
   __shared__ double s_wb[kTopWarps];                    // per-warp culled bounds
   __shared__ uint32_t s_wg[kTopWarps], s_we[kTopWarps];
   __shared__ unsigned long long s_tested, s_surv;
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
       }
     }
     const int nx = l ? cur ^ 1 : 0;
-    if (m < nblk) s_mask[nx][m] = (uint16_t)mask;
+    if (m < nblk) s_mask[nx][m] = mask;
     tests = warp_sum(tests);
     const unsigned int surv = warp_sum((unsigned int)__popc(mask));
     if (__any_sync(0xffffffffu, bound != 0.0)) bound = warp_sum(bound);   // else every lane holds +0
