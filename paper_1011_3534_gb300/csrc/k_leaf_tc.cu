@@ -15,14 +15,16 @@
 // a single-column pass touches (leaf 64). Other patterns take one pass per row. Each
 // output block therefore sums its surviving k in ascending order, in FP32.
 //
-// Pipeline (one CTA, 192 threads): warp 0 issues TMA loads into a ring of stages, one
+// Pipeline (one CTA, 320 threads): warp 0 issues TMA loads into a ring of stages, one
 // 128-byte K chunk of every operand per stage (plain forms: 6 stages of A 128 x 128 B +
 // B 128 x 128 B; split forms: 3 stages of A hi, B hi, A lo, B lo, each hi and lo box
 // loaded once per chunk and read by the three products), 128-byte swizzle; warp 1
 // issues tcgen05.mma (4 K-steps of 32 bytes per operand pair and stage) and commits to
-// the stage's empty barrier; warps 2-5 drain finished accumulators with tcgen05.ld,
-// store C (FP32 tiles) and its squared Frobenius norms (double-float, fixed-order
-// sums) while later work accumulates in the other TMEM buffers.
+// the stage's empty barrier; warps 2-9 (two per TMEM lane quarter, each on 64 of the
+// 128 accumulator columns) drain finished accumulators with tcgen05.ld, store C (FP32
+// tiles, and the transposed block of a symmetric product) and its squared Frobenius
+// norms (double-float, fixed-order sums) while later work accumulates in the other TMEM
+// buffers.
 //
 // Accumulation. The tensor cores of this GPU truncate each MMA's FP32 sum (measured
 // bias about -0.5 unit in the last place per instruction), so the error of one
@@ -62,7 +64,7 @@ __device__ unsigned long long g_role_cycles[1024][16];
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;   // producer, MMA issuer, eight epilogue warps
 constexpr uint32_t kTmemCols = 512;   // four 128-column FP32 accumulators
 constexpr int kBoxBytes = 16384;      // one operand of one stage: 128 rows x 128 bytes
 constexpr size_t kSmemBytes = (size_t)6 * 32768 + 1024;   // the ring (either form) + alignment
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ double s_norm[4][2];
   __shared__ int4 s_desc[32];                    // producer: the chunk of passes being issued
   __shared__ uint8_t s_cols[kStages];            // producer -> MMA: column halves of a stage
-  __shared__ float s_epi[4][32][33];             // epilogue: one 32 x 32 chunk per warp, transposed out
+  __shared__ float s_epi[8][32][17];             // epilogue: one 32 x 16 piece per warp, transposed out
   __shared__ unsigned long long s_off[kMaxProd + 1];   // first global item of each product
   constexpr int kQ = 4;                          // item ring: producer -> MMA and epilogue warps
   __shared__ __align__(8) uint64_t qfull[kQ], qempty[kQ];
@@ -190,15 +192,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < kAcc; a++) {
       mbar_init(&accf[a], 1);
-      mbar_init(&acce[a], 128);
+      mbar_init(&acce[a], 256);
     }
     for (int a = 0; a < kSmall; a++) {
       mbar_init(&smf[a], 1);
-      mbar_init(&sme[a], 128);
+      mbar_init(&sme[a], 256);
     }
     for (int q = 0; q < kQ; q++) {
       mbar_init(&qfull[q], 1);
-      mbar_init(&qempty[q], 5);   // the MMA warp and the four epilogue warps
+      mbar_init(&qempty[q], 9);   // the MMA warp and the eight epilogue warps
     }
     s_abort = 0;
     mbar_fence_init();
@@ -501,8 +503,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (lane == 0 && last_prod >= 0 && nst) atomicAdd(prods[last_prod].mma_stages, nst);
   } else if (warp >= 2) {
-    // ---------------- epilogue ----------------
+    // ---------------- epilogue (warps 2-9) ----------------
+    // Two warps per TMEM lane quarter: warp w reads lanes 32 (w % 4) .. + 31 (the rows
+    // it may access) and the 64 accumulator columns of its half, (w - 2) / 4: leaf 64,
+    // output block column c = half; leaf 128, columns 64 half .. + 63 of the block.
+    const int ew = warp - 2;
     const int slice = warp & 3;            // TMEM lanes 32 * slice .. + 31
+    const int half = ew >> 2;              // accumulator columns 64 * half .. + 63
     const int row = 32 * slice + lane;     // accumulator row
     const uint32_t lanes = (uint32_t)(32 * slice) << 16;
     int acc = 0, sm_idx = 0;
@@ -527,24 +534,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         // split: the hi hi products of each pass arrive in an accumulator of their own and
         // are summed here in FP32 (round to nearest) in the order of the plan, then the
         // item's corrections are added
-        float run[128];
+        float run[64];
         if (SPLIT) {
           const uint32_t first = mt.x;
           const uint32_t np = item_passes(P, mt, cm.status);
           const int oob = P.nb * P.nb;
 #pragma unroll
-          for (int x = 0; x < 128; x++) run[x] = 0.f;
+          for (int x = 0; x < 64; x++) run[x] = 0.f;
           bool all_ok = true;
-          // 32 columns x 32 lanes from two TMEM column chunks, one wait for both
-          auto add2 = [&](uint32_t d, int h) {
+          // this warp's 64 columns x 32 lanes from two TMEM column chunks, one wait for both
+          auto add2 = [&](uint32_t d) {
             uint32_t v[32], w[32];
-            tmem_ld32_nowait(d + (uint32_t)(h * 32), v);
-            tmem_ld32_nowait(d + (uint32_t)(h * 32 + 32), w);
+            tmem_ld32_nowait(d + (uint32_t)(half * 64), v);
+            tmem_ld32_nowait(d + (uint32_t)(half * 64 + 32), w);
             tmem_wait_ld();
 #pragma unroll
             for (int x = 0; x < 32; x++) {
-              run[h * 32 + x] += __uint_as_float(v[x]);
-              run[h * 32 + 32 + x] += __uint_as_float(w[x]);
+              run[x] += __uint_as_float(v[x]);
+              run[32 + x] += __uint_as_float(w[x]);
             }
           };
           int4 pl = make_int4(0, 0, 0, 0);
@@ -562,9 +569,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             all_ok = all_ok && ok;
             if (ok) {
               tc_fence_after();
-              const uint32_t d = tmem + lanes + (uint32_t)acc * 128u;
-              if (cols & 1u) add2(d, 0);   // column half 0 (a column half this pass left alone is skipped)
-              if (cols & 2u) add2(d, 2);
+              // a column half this pass left alone is skipped (leaf 128 passes cover both)
+              if ((cols >> half) & 1u) add2(tmem + lanes + (uint32_t)acc * 128u);
             }
             tc_fence_before();
             mbar_arrive(&acce[acc]);
@@ -584,9 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           all_ok = all_ok && ok;
           if (ok && np > 0) {
             tc_fence_after();
-            const uint32_t d = tmem + lanes + R::kSmallCol + (uint32_t)sm_idx * 128u;
-            add2(d, 0);
-            add2(d, 2);
+            add2(tmem + lanes + R::kSmallCol + (uint32_t)sm_idx * 128u);
           }
           tc_fence_before();
           mbar_arrive(&sme[sm_idx]);
@@ -609,63 +613,61 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ROLE_T0(t_fin);
         const int a = LEAF == 64 ? row / 64 : (qd >> 1);
+        const int c = LEAF == 64 ? half : (qd & 1);
         const int r = LEAF == 64 ? row % 64 : row;
-        const int i = (int)(2 * I) + a;
-        // squared norms in double-float: f^2 = pp + e exactly, TwoSum accumulation
-        float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
-#pragma unroll
-        for (int cc = 0; cc < RC; cc++) {
-          const int c = LEAF == 64 ? cc : (qd & 1);
-          const int q = a * 2 + c;
-          const int j = (int)(2 * J) + c;
-          if (!((touched >> q) & 1u) || i >= P.nb || j >= P.nb) continue;   // warp-uniform
-          // the warp's 32 rows of block (i, j) are written through shared memory, so that
-          // each store instruction covers four whole 128-byte rows
+        const int i = (int)(2 * I) + a, j = (int)(2 * J) + c;
+        const int col0 = LEAF == 64 ? 0 : half * 64;   // this warp's first column of block (i, j)
+        // squared norm of the warp's part in double-float: f^2 = pp + e exactly, TwoSum
+        // accumulation
+        float sh = 0.f, sl = 0.f;
+        if (((touched >> (a * 2 + c)) & 1u) && i < P.nb && j < P.nb) {   // warp-uniform
+          // the warp's 32 rows of block (i, j) go through shared memory 16 columns at a
+          // time, so that each store instruction covers whole 64-byte row pieces
           float *blk = P.C + ((int64_t)i * P.nb + j) * LEAF * LEAF + (int64_t)(r - lane) * LEAF;
-          float(*sb)[33] = s_epi[warp - 2];
-          // symmetric product: block (j, i) = (i, j)^T from the same staged chunk
+          float(*sb)[17] = s_epi[ew];
+          // symmetric product: block (j, i) = (i, j)^T from the same staged piece
           const bool mir = P.sym && i < j;
           float *blkT = P.C + ((int64_t)j * P.nb + i) * LEAF * LEAF + (r - lane);
 #pragma unroll
-          for (int h = 0; h < LEAF / 32; h++) {
+          for (int hh = 0; hh < 2; hh++) {   // 32-column units of the warp's 64 columns
             uint32_t v[32];
             if (SPLIT) {
 #pragma unroll
-              for (int x = 0; x < 32; x++) v[x] = __float_as_uint(run[cc * 64 + h * 32 + x]);
+              for (int x = 0; x < 32; x++) v[x] = __float_as_uint(run[hh * 32 + x]);
             } else {
-              const uint32_t col = (uint32_t)acc * 128u + (uint32_t)(cc * 64 + h * 32);
-              tmem_ld32(tmem + lanes + col, v);
+              tmem_ld32(tmem + lanes + (uint32_t)acc * 128u + (uint32_t)(half * 64 + hh * 32), v);
             }
 #pragma unroll
-            for (int x = 0; x < 32; x++) sb[lane][x] = __uint_as_float(v[x]);
-            __syncwarp();
+            for (int g = 0; g < 2; g++) {
+              const int cb = col0 + hh * 32 + g * 16;   // first column of the piece
 #pragma unroll
-            for (int it = 0; it < 8; it++) {
-              const int rl = it * 4 + (lane >> 3), c4 = (lane & 7) * 4;
-              *reinterpret_cast<float4 *>(blk + (int64_t)rl * LEAF + h * 32 + c4) =
-                  make_float4(sb[rl][c4], sb[rl][c4 + 1], sb[rl][c4 + 2], sb[rl][c4 + 3]);
-            }
-            if (mir) {   // row h*32 + cl of block (j, i), its 32 columns r - lane ..
+              for (int x = 0; x < 16; x++) sb[lane][x] = __uint_as_float(v[g * 16 + x]);
+              __syncwarp();
 #pragma unroll
-              for (int it = 0; it < 8; it++) {
-                const int cl = it * 4 + (lane >> 3), r4 = (lane & 7) * 4;
-                *reinterpret_cast<float4 *>(blkT + (int64_t)(h * 32 + cl) * LEAF + r4) =
-                    make_float4(sb[r4][cl], sb[r4 + 1][cl], sb[r4 + 2][cl], sb[r4 + 3][cl]);
+              for (int it = 0; it < 4; it++) {   // rows rl, columns cb + c4 .. + 3
+                const int rl = it * 8 + (lane >> 2), c4 = (lane & 3) * 4;
+                *reinterpret_cast<float4 *>(blk + (int64_t)rl * LEAF + cb + c4) =
+                    make_float4(sb[rl][c4], sb[rl][c4 + 1], sb[rl][c4 + 2], sb[rl][c4 + 3]);
               }
-            }
-            __syncwarp();
+              if (mir) {   // row cb + cl of block (j, i), its 32 columns r - lane ..
 #pragma unroll
-            for (int x = 0; x < 32; x += 4) {
-#pragma unroll
-              for (int z = 0; z < 4; z++) {
-                const float fv = __uint_as_float(v[x + z]);
-                const float pp = fv * fv;
-                const float e = fmaf(fv, fv, -pp);
-                const float t = sh[cc] + pp;
-                const float bb = t - sh[cc];
-                sl[cc] += ((sh[cc] - (t - bb)) + (pp - bb)) + e;
-                sh[cc] = t;
+                for (int it = 0; it < 4; it++) {
+                  const int cl = it * 4 + (lane >> 3), r4 = (lane & 7) * 4;
+                  *reinterpret_cast<float4 *>(blkT + (int64_t)(cb + cl) * LEAF + r4) =
+                      make_float4(sb[r4][cl], sb[r4 + 1][cl], sb[r4 + 2][cl], sb[r4 + 3][cl]);
+                }
               }
+              __syncwarp();
+            }
+#pragma unroll
+            for (int x = 0; x < 32; x++) {
+              const float fv = __uint_as_float(v[x]);
+              const float pp = fv * fv;
+              const float ee = fmaf(fv, fv, -pp);
+              const float t = sh + pp;
+              const float bb = t - sh;
+              sl += ((sh - (t - bb)) + (pp - bb)) + ee;
+              sh = t;
             }
           }
         }
@@ -673,24 +675,23 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_before();
           mbar_arrive(&acce[acc]);
         }
-        // squared Frobenius norms of the written blocks: rows -> warp -> fixed pair order
-#pragma unroll
-        for (int cc = 0; cc < RC; cc++) {
-          float H = sh[cc], L = sl[cc];
+        // squared Frobenius norms of the written blocks: rows -> warp -> fixed order
+        {
+          float H = sh, L = sl;
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) {
             const float h2 = __shfl_xor_sync(0xffffffffu, H, off), l2 = __shfl_xor_sync(0xffffffffu, L, off);
             df_add(H, L, h2, l2);
           }
-          if (lane == 0) s_norm[slice][cc] = (double)H + (double)L;
+          if (lane == 0) s_norm[slice][half] = (double)H + (double)L;
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        asm volatile("bar.sync 1, 256;" ::: "memory");
         if (warp == 2 && lane < 4) {
           if (LEAF == 64) {
-            const int aa = lane >> 1, c = lane & 1;
-            const int ii = (int)(2 * I) + aa, jj = (int)(2 * J) + c;
-            if (((touched >> (aa * 2 + c)) & 1u) && ii < P.nb && jj < P.nb) {
-              const double v2 = s_norm[2 * aa][c] + s_norm[2 * aa + 1][c];
+            const int aa = lane >> 1, cc = lane & 1;
+            const int ii = (int)(2 * I) + aa, jj = (int)(2 * J) + cc;
+            if (((touched >> (aa * 2 + cc)) & 1u) && ii < P.nb && jj < P.nb) {
+              const double v2 = s_norm[2 * aa][cc] + s_norm[2 * aa + 1][cc];
               P.leaf_norm2C[(int64_t)ii * P.NB + jj] = v2;
               P.nzC[(int64_t)ii * P.NB + jj] = 1;
               if (P.sym && ii < jj) {
@@ -699,19 +700,19 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
           } else if (lane == 0) {
-            const int jj = (int)(2 * J) + (qd & 1);
-            if (((touched >> qd) & 1u) && i < P.nb && jj < P.nb) {
-              const double v2 = ((s_norm[0][0] + s_norm[1][0]) + s_norm[2][0]) + s_norm[3][0];
-              P.leaf_norm2C[(int64_t)i * P.NB + jj] = v2;
-              P.nzC[(int64_t)i * P.NB + jj] = 1;
-              if (P.sym && i < jj) {
-                P.leaf_norm2C[(int64_t)jj * P.NB + i] = v2;
-                P.nzC[(int64_t)jj * P.NB + i] = 1;
+            if (((touched >> qd) & 1u) && i < P.nb && j < P.nb) {
+              const double v2 = ((s_norm[0][0] + s_norm[0][1]) + (s_norm[1][0] + s_norm[1][1])) +
+                                ((s_norm[2][0] + s_norm[2][1]) + (s_norm[3][0] + s_norm[3][1]));
+              P.leaf_norm2C[(int64_t)i * P.NB + j] = v2;
+              P.nzC[(int64_t)i * P.NB + j] = 1;
+              if (P.sym && i < j) {
+                P.leaf_norm2C[(int64_t)j * P.NB + i] = v2;
+                P.nzC[(int64_t)j * P.NB + i] = 1;
               }
             }
           }
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        asm volatile("bar.sync 1, 256;" ::: "memory");
         if (warp == 2) ROLE_ADD(13, t_fin);
         if (!SPLIT && ++acc == kAcc) {
           acc = 0;
