@@ -284,9 +284,15 @@ def run_gpu(args):
                 "traffic": kernel_traffic("k_leaf_tc"),
                 "algorithmic_flops_per_launch": tc_flops,
                 "peak_source": f"{pk['source']} bf16_tflops_sustained x {HEADLINE[:4]}/bf16 nominal"}
+    # the leaf kernel's HBM floor: every leaf copy a computed triple reads, once, and
+    # every block of C written (the mirrored ones included)
+    lb = leaf_kernel_bytes(S.spamm_triples(r["tree"]), LEAF, copy_bytes(HEADLINE))
+    leaf_gbs = lb["bytes"] / (ms_leaf * 1e-3) / 1e9 if ms_leaf else None
     leaf = {"useful_tflops": leaf_tflops, "tc_tflops": tc_tflops, "mma_issued_tflops": mma_tflops,
             "tc_peak": tc_peak, "frac_of_tc_peak": (tc_tflops / tc_peak) if tc_tflops else None,
-            "leaf_products": st["leaf_products"], "mirrored_products": st["mirrored_products"]}
+            "leaf_products": st["leaf_products"], "mirrored_products": st["mirrored_products"],
+            "hbm": {"algorithmic_bytes": lb["bytes"], "operand_leaves": lb["leaves"], "c_blocks": lb["blocks"],
+                    "gbs": leaf_gbs, "frac": leaf_gbs / pk["hbm"] if leaf_gbs else None}}
     k1 = {"gbs": build_gbs, "frac_of_hbm": build_gbs / pk["hbm"], "bytes_per_launch": bytes_build}
     S.spamm_tree_free(r["tree"])
 
@@ -363,6 +369,19 @@ def run_gpu(args):
     S.spamm_ctx_destroy(ctx)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def leaf_kernel_bytes(trip, leaf: int, elem_bytes: float) -> dict:
+    """Algorithmic HBM bytes of one leaf-kernel launch of a symmetric product from its
+    triple list (both halves listed): the leaf copies the computed triples (i <= j) read,
+    A_ik at (i, k) and B_kj at (j, k) (rows of the symmetric operand), each once, and
+    the FP32 blocks of C written, (i, j) and its mirror."""
+    t = np.asarray(trip, dtype=np.int64)
+    up = t[t[:, 0] <= t[:, 1]]
+    leaves = np.unique(np.concatenate([up[:, 0] * 65536 + up[:, 2], up[:, 1] * 65536 + up[:, 2]])).size
+    blocks = np.unique(t[:, 0] * 65536 + t[:, 1]).size
+    return {"leaves": int(leaves), "blocks": int(blocks),
+            "bytes": float(leaves * leaf * leaf * elem_bytes + blocks * leaf * leaf * 4)}
 
 
 def copy_bytes(prec: str) -> float:

@@ -550,15 +550,20 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
     int tests = 0;
     double bound = 0.0;
     if (m < nblk && !(t.sym && I > J)) {   // below the diagonal: the mirror of (J, I)
-      const uint32_t pm = l ? s_mask[cur][m >> 2] : 1u;   // tier 0's parent: K = 0 of the root
+      // the parent's surviving K' (tier 0's parent: K' = 0 of the root); only their
+      // children 2K' + e are calls, visited in ascending K, so that the FP64 products
+      // (a narrow pipe on this GPU) are issued for the warp's calls only
+      for (uint32_t pend = l ? s_mask[cur][m >> 2] : 1u; pend; pend &= pend - 1u) {
+        const uint32_t Kp = (uint32_t)(__ffs(pend) - 1);
 #pragma unroll
-      for (uint32_t K = 0; K < (1u << (kTopTiers - 1)); K++) {
-        if (K >= D) break;
-        if (!((pm >> (K >> 1)) & 1u)) continue;          // parent culled: not a call
-        const double p = nA[tier_at(I, K, D, t.symA)] * nB[tier_at(K, J, D, t.symB)];
-        tests++;
-        if (below_tau(p, tl)) bound += p;
-        else mask |= 1u << K;
+        for (uint32_t e = 0; e < 2; e++) {
+          const uint32_t K = 2 * Kp + e;
+          if (K >= D) continue;
+          const double p = nA[tier_at(I, K, D, t.symA)] * nB[tier_at(K, J, D, t.symB)];
+          tests++;
+          if (below_tau(p, tl)) bound += p;
+          else mask |= 1u << K;
+        }
       }
     }
     const int nx = l ? cur ^ 1 : 0;

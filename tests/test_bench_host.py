@@ -94,3 +94,14 @@ def test_reference_arm_modes_agree():
     assert full["cpu_baseline"]["mode"] == "full" and samp["cpu_baseline"]["mode"] == "sampled"
     ratio = samp["value"] / full["value"]
     assert 1 / 1.5 < ratio < 1.5, ratio
+
+
+def test_leaf_kernel_bytes_counts_each_leaf_and_block_once():
+    # triples of a symmetric product, both halves listed: (0,1,0) and its mirror (1,0,0),
+    # the diagonal (1,1,0) and (1,1,1). Computed (i <= j): reads A_00, B at (1,0); A_10,
+    # B at (1,0); A_11, B at (1,1) -> copies (0,0), (1,0), (1,1); blocks (0,1), (1,0), (1,1)
+    import bench
+    trip = [(0, 1, 0), (1, 0, 0), (1, 1, 0), (1, 1, 1)]
+    r = bench.leaf_kernel_bytes(trip, 64, 8.0)
+    assert r["leaves"] == 3 and r["blocks"] == 3
+    assert r["bytes"] == 3 * 64 * 64 * 8 + 3 * 64 * 64 * 4
