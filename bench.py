@@ -203,22 +203,22 @@ def run_gpu(args):
     def flags_for(prec):
         return S.COPY_FLAG[prec] | S.SPAMM_SYMMETRIC | S.SPAMM_NO_RIGHT
 
-    def step(prec, tA, tC, tau, ev=None):
+    def step(prec, tA, tC, tau, ev=None, mflags=0):
         if ev is not None:
             ev[0].record(stream)
         S.spamm_tree_update(tA, dA)                  # quadtree build (K1 + norm pyramid)
         if ev is not None:
             ev[1].record(stream)
-        tC = S.spamm_multiply(ctx, tA, tA, tau, prec, SYMP, tC)   # cull + leaf products (+ mirror)
+        tC = S.spamm_multiply(ctx, tA, tA, tau, prec, SYMP | mflags, tC)   # cull + leaf products (+ mirror)
         if ev is not None:
             ev[2].record(stream)
         return tC
 
-    def timed(prec, tau, steps, warmup, phases=True):
+    def timed(prec, tau, steps, warmup, phases=True, mflags=0):
         tA = S.spamm_tree_build(ctx, dA, N, LEAF, flags_for(prec))
         tC = None
         for _ in range(warmup):
-            tC = step(prec, tA, tC, tau)
+            tC = step(prec, tA, tC, tau, mflags=mflags)
         torch.cuda.synchronize()
         if phases:
             S.spamm_tree_build_ms(tA)   # start the leaf-block kernel's event count here
@@ -231,7 +231,7 @@ def run_gpu(args):
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for s in range(steps):
-            tC = step(prec, tA, tC, tau, evs[s] if phases else None)
+            tC = step(prec, tA, tC, tau, evs[s] if phases else None, mflags)
         S.spamm_sync(ctx)   # the last product's norm pyramid (on its own stream) is inside the region
         t1.record(stream)
         torch.cuda.synchronize()
@@ -329,9 +329,10 @@ def run_gpu(args):
     if not args.no_sweep:
         for tau in TAUS:
             ref = None
-            for name in ("fp64", "tf32", "bf16", "bf16x3", "tf32x3", "fp16"):
-                p = S.PRECISIONS[name]
-                rr = timed(p, tau, 3, 1)
+            # "w": leaf 64 in warp tiles (SPAMM_WARP_TILES) instead of the tcgen05 items
+            for name in ("fp64", "tf32", "bf16", "bf16x3", "tf32x3", "fp16", "bf16w", "tf32x3w"):
+                p = S.PRECISIONS[name.rstrip("w")]
+                rr = timed(p, tau, 3, 1, mflags=S.SPAMM_WARP_TILES if name.endswith("w") else 0)
                 Cd = torch.empty((N, N), dtype=torch.float64, device=dA.device)
                 S.spamm_tree_to_dense(rr["tree"], Cd)
                 if name == "fp64":
@@ -347,6 +348,13 @@ def run_gpu(args):
                 del Cd
             del ref
 
+    # ---- the shape autotuner's choice for the headline product (not timed)
+    tuned = None
+    if not args.no_sweep:
+        tl, tf, tms = S.spamm_tune_shape(ctx, dA, N, TAU, prec, S.SPAMM_SYMMETRIC)
+        tuned = {"leaf": tl, "tile": "warp 64x64" if tf else "tcgen05 items", "ms": tms,
+                 "note": "build + product A A (full, not symmetric) per candidate"}
+
     # ---- CPU oracle on this host (rank 0 only, bounded sample, in a process of its own)
     cpu = cpu_baseline_subprocess(quick=args.no_sweep) if rank == 0 else None
 
@@ -360,7 +368,7 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (A is 512 MiB FP64)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": e2e, "gpu_launches": r["launches"], "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-        "phases": phases, "k1": k1, "leaf_gemm": leaf,
+        "phases": phases, "k1": k1, "leaf_gemm": leaf, "tuned_shape": tuned,
     }
     if rank == 0:
         for row in sorted(sweep, key=lambda x: (x["tau"] == TAU, x["tau"])):   # tau = 1e-8 last

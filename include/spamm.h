@@ -97,6 +97,17 @@ typedef enum {
                                       depth-scaled threshold tau^{k+1} = tau^k / 8 of Sec. II
                                       (rigorous: ||C~ - AB||_F < (k_max + 1) tau), instead of
                                       tau at every tier */
+#define SPAMM_WARP_TILES   0x2000  /* spamm_multiply, spamm_multiply_batched: the tile shape
+                                      of tensor-core products at leaf 64. Set: one warp per
+                                      64 x 64 output block (warp-level mma.sync, the block's
+                                      surviving k only). Clear (default): tcgen05 items of
+                                      2 x 2 output blocks, 128 x 128 tiles, whose passes
+                                      zero-fill the halves a k does not reach. Leaves 16 and
+                                      32 always run the warp shape (the flag is accepted);
+                                      leaf 128 has only the tcgen05 shape
+                                      (SPAMM_EUNSUPPORTED); SPAMM_FP64: SPAMM_EINVAL. The
+                                      results agree within the tensor-core bar; the sum
+                                      order inside a block differs. */
 
 #define SPAMM_MAX_LEVELS 24
 
@@ -264,14 +275,25 @@ SPAMM_API spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *A
 SPAMM_API spamm_status spamm_tree_update_batched(spamm_ctx ctx, int32_t count, const spamm_tree *trees,
                                                  const double *const *A, int32_t flags);
 
-/* Leaf-size autotuner: times the tree build plus the product A A at every leaf size the
-   precision supports (64 and 128 for tensor-core precisions, 16..128 for SPAMM_FP64) on
-   the n x n matrix A (device, or host with SPAMM_HOST_INPUT; SPAMM_SYMMETRIC honoured)
-   and returns the fastest in *leaf_out (and its time in *ms_out if not NULL). Results are
-   cached in the context per (ceil(log2 n), precision, decade of tau). */
+/* Leaf-size autotuner: times the tree build plus the product A A at every leaf size
+   (16, 32, 64, 128; each in its default tile shape) on the n x n matrix A (device, or
+   host with SPAMM_HOST_INPUT; SPAMM_SYMMETRIC honoured) and returns the fastest in
+   *leaf_out (and its time in *ms_out if not NULL). Results are cached in the context per
+   (ceil(log2 n), precision, decade of tau). */
 SPAMM_API spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t n, double tau,
                                        spamm_prec prec, int32_t flags, int32_t *leaf_out,
                                        double *ms_out);
+
+/* Leaf-size and tile-shape autotuner: as spamm_tune_leaf, over (leaf, tile shape)
+   candidates: for tensor-core precisions leaf 16 and 32 (warp tiles), leaf 64 with the
+   tcgen05 items of 2 x 2 blocks and with warp tiles (SPAMM_WARP_TILES), leaf 128
+   (tcgen05); for SPAMM_FP64 the leaf sizes alone. Returns the fastest leaf in *leaf_out,
+   the spamm_multiply flags that select its tile shape (0 or SPAMM_WARP_TILES) in
+   *tile_flags_out, and its time in *ms_out if not NULL. Cached per (ceil(log2 n),
+   precision, decade of tau), apart from spamm_tune_leaf's results. */
+SPAMM_API spamm_status spamm_tune_shape(spamm_ctx ctx, const double *A, int64_t n, double tau,
+                                        spamm_prec prec, int32_t flags, int32_t *leaf_out,
+                                        int32_t *tile_flags_out, double *ms_out);
 
 /* ---- learned tolerance controller ----
    (The paper has no counterpart: it fixes tau by hand, Sec. III.) A small network

@@ -624,8 +624,12 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
     return fail(ctx, SPAMM_EINVAL, "multiply: operands differ (n %lld/%lld, leaf %d/%d)",
                 (long long)A->n, (long long)B->n, A->b, B->b);
   if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(ctx, SPAMM_EINVAL, "multiply: tau must be finite and >= 0");
-  if (flags & ~((kTreeFlags & ~SPAMM_HOST_INPUT) | SPAMM_SYM_PRODUCT | SPAMM_DEPTH_TAU))
+  if (flags & ~((kTreeFlags & ~SPAMM_HOST_INPUT) | SPAMM_SYM_PRODUCT | SPAMM_DEPTH_TAU | SPAMM_WARP_TILES))
     return fail(ctx, SPAMM_EINVAL, "multiply: unknown flag bits 0x%x", flags);
+  if ((flags & SPAMM_WARP_TILES) && prec == SPAMM_FP64)
+    return fail(ctx, SPAMM_EINVAL, "multiply: SPAMM_WARP_TILES is a tile shape of the tensor-core precisions");
+  if ((flags & SPAMM_WARP_TILES) && A->b > 64)
+    return fail(ctx, SPAMM_EUNSUPPORTED, "multiply: leaf %d has no warp-tile shape", A->b);
   const bool symp = (flags & SPAMM_SYM_PRODUCT) != 0;
   if (symp && (A != B || !(A->flags & SPAMM_SYMMETRIC)))
     return fail(ctx, SPAMM_EINVAL, "multiply: SPAMM_SYM_PRODUCT needs B == A built with SPAMM_SYMMETRIC");
@@ -680,6 +684,7 @@ spamm_status product_prepare(spamm_ctx ctx, spamm_tree A, spamm_tree B, double t
   Ct->is_product = true;
   Ct->sym_product = symp;
   Ct->depth_tau = (flags & SPAMM_DEPTH_TAU) != 0;
+  Ct->warp_tiles = (flags & SPAMM_WARP_TILES) != 0 && Ct->b == 64;
   if (symp) Ct->flags |= SPAMM_SYMMETRIC;
   Ct->prec = prec;
   Ct->tau = tau;
@@ -702,7 +707,7 @@ spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau
   int launches = 0;
   CK(launch_cull(A, B, Ct, tau, tau_dev, ctx->dev_status, ctx->sm_count, s, &launches), "multiply: cull launch");
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[1], s), "event");
-  if (tc && Ct->b >= 64) {
+  if (tc && Ct->b >= 64 && !Ct->warp_tiles) {
     CK(launch_leaf_tc(A, B, Ct, prec, ctx->dev_status, ctx->sm_count, s), "multiply: leaf launch");
   } else if (tc) {
     CK(launch_leaf_mma(A, B, Ct, prec, ctx->dev_status, ctx->sm_count, s), "multiply: leaf launch");
@@ -711,7 +716,7 @@ spamm_status multiply_impl(spamm_ctx ctx, spamm_tree A, spamm_tree B, double tau
   }
   launches++;
   if (ctx->timing) CK(cudaEventRecord(Ct->ev[2], s), "event");
-  if (Ct->sym_product && mirror_after_leaf(Ct)) {   // the plain tcgen05 forms mirror in their epilogue
+  if (Ct->sym_product && mirror_after_leaf(Ct)) {   // the tcgen05 forms mirror in their epilogue
     CK(launch_mirror(Ct, s), "multiply: mirror launch");
     launches++;
   }

@@ -103,7 +103,7 @@ static spamm_status batch_sequence(spamm_ctx ctx, const spamm_tree *A, const spa
     for (int leaf : {64, 128}) {
       std::vector<spamm_tree> a, b, c;
       for (int p = 0; p < count; p++)
-        if (C[p]->b == leaf) {
+        if (C[p]->b == leaf && !C[p]->warp_tiles) {
           a.push_back(A[p]);
           b.push_back(B[p]);
           c.push_back(C[p]);
@@ -125,8 +125,8 @@ static spamm_status batch_sequence(spamm_ctx ctx, const spamm_tree *A, const spa
           "batch: leaf launch");
       ctx->launches++;
     }
-    for (int p = 0; p < count; p++)   // leaves of 16 and 32: the warp-level kernel, one launch per product
-      if (C[p]->b < 64) {
+    for (int p = 0; p < count; p++)   // warp tiles (leaves 16, 32, and 64 on request): one launch per product
+      if (C[p]->b < 64 || C[p]->warp_tiles) {
         BCK(launch_leaf_mma(A[p], B[p], C[p], prec, ctx->dev_status, ctx->sm_count, ctx->stream), "batch: leaf launch");
         ctx->launches++;
       }
@@ -181,13 +181,15 @@ extern "C" spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *
   if (!ctx) return SPAMM_EINVAL;
   if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
   if (!A || !B || !tau || !C || count < 1) return bfail(ctx, SPAMM_EINVAL, "batched: bad arguments");
-  if (flags & ~(kLowCopyFlags | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT | SPAMM_GRAPH)) return bfail(ctx, SPAMM_EINVAL, "batched: unknown flag bits");
+  if (flags & ~(kLowCopyFlags | SPAMM_SYMMETRIC | SPAMM_NO_RIGHT | SPAMM_GRAPH | SPAMM_WARP_TILES))
+    return bfail(ctx, SPAMM_EINVAL, "batched: unknown flag bits");
   if (flags & kLowCopyFlags) return bfail(ctx, SPAMM_EUNSUPPORTED, "batched: leaf copies of the products are not produced");
   spamm_status st = ensure_side_streams(ctx);
   if (st != SPAMM_OK) return st;
   // every product validated, created or checked, workspace allocated (before any capture)
   for (int p = 0; p < count; p++) {
-    st = product_prepare(ctx, A[p], B[p], tau[p], prec, flags & (SPAMM_SYMMETRIC | SPAMM_NO_RIGHT), &C[p]);
+    st = product_prepare(ctx, A[p], B[p], tau[p], prec, flags & (SPAMM_SYMMETRIC | SPAMM_NO_RIGHT | SPAMM_WARP_TILES),
+                         &C[p]);
     if (st != SPAMM_OK) return st;
   }
   st = ensure_batch_tables(ctx, count);
@@ -264,23 +266,14 @@ extern "C" spamm_status spamm_multiply_batched(spamm_ctx ctx, const spamm_tree *
 // Leaf-size autotuner: builds the tree of A at every candidate leaf size, times the
 // product A A (tree build included) with CUDA events, and keeps the fastest; results are
 // cached per (log2 n, precision, decade of tau).
-extern "C" spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t n, double tau, spamm_prec prec,
-                                        int32_t flags, int32_t *leaf_out, double *ms_out) {
-  if (!ctx) return SPAMM_EINVAL;
-  if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
-  if (!A || !leaf_out || n < 1 || !(tau >= 0.0)) return bfail(ctx, SPAMM_EINVAL, "tune: bad arguments");
-  int lg = 0;
-  while ((int64_t(1) << lg) < n) lg++;
-  const int tdec = tau > 0 ? (int)std::floor(std::log10(tau)) : -400;
-  const int64_t key = ((int64_t)lg * 16 + (int)prec) * 1000 + (tdec + 500);
-  auto it = ctx->tuned.find(key);
-  if (it != ctx->tuned.end()) {
-    *leaf_out = it->second.first;
-    if (ms_out) *ms_out = it->second.second;
-    return SPAMM_OK;
-  }
+namespace {
+
+// Times spamm_tree_update + spamm_multiply of A A for each (leaf, multiply flags)
+// candidate (the best of three repetitions after a first one) and returns the fastest.
+spamm_status tune_candidates(spamm_ctx ctx, const double *A, int64_t n, double tau, spamm_prec prec, int32_t flags,
+                             const std::vector<std::pair<int, int32_t>> &cand, int *best_leaf, int32_t *best_flags,
+                             double *best_ms) {
   const bool tc = prec != SPAMM_FP64;
-  std::vector<int> cand = {16, 32, 64, 128};
   const int32_t copy = tc ? (prec == SPAMM_TF32 ? SPAMM_COPY_TF32 : prec == SPAMM_FP16 ? SPAMM_COPY_FP16
                              : prec == SPAMM_BF16X3 ? SPAMM_COPY_BF16X3
                              : prec == SPAMM_TF32X3 ? SPAMM_COPY_TF32X3 : SPAMM_COPY_BF16)
@@ -289,8 +282,10 @@ extern "C" spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t 
   BCK(cudaEventCreate(&e0), "tune: event");
   BCK(cudaEventCreate(&e1), "tune: event");
   int best = -1;
-  double best_ms = 0;
-  for (int leaf : cand) {
+  int32_t bflags = 0;
+  double bms = 0;
+  for (const auto &cf : cand) {
+    const int leaf = cf.first;
     spamm_tree t = nullptr, c = nullptr;
     spamm_status st = spamm_tree_build(ctx, A, n, leaf, copy | (flags & (SPAMM_SYMMETRIC | SPAMM_HOST_INPUT)), &t);
     if (st != SPAMM_OK) continue;
@@ -298,7 +293,7 @@ extern "C" spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t 
     for (int rep = 0; rep < 4 && st == SPAMM_OK; rep++) {
       cudaEventRecord(e0, ctx->stream);
       st = spamm_tree_update(t, A, flags & SPAMM_HOST_INPUT);
-      if (st == SPAMM_OK) st = spamm_multiply(ctx, t, t, tau, prec, 0, &c);
+      if (st == SPAMM_OK) st = spamm_multiply(ctx, t, t, tau, prec, cf.second, &c);
       cudaEventRecord(e1, ctx->stream);
       if (st == SPAMM_OK && cudaEventSynchronize(e1) == cudaSuccess && rep > 0) {
         float v = 0;
@@ -308,16 +303,71 @@ extern "C" spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t 
     }
     if (c) spamm_tree_free(c);
     spamm_tree_free(t);
-    if (st == SPAMM_OK && (best < 0 || ms < best_ms)) {
+    if (st == SPAMM_OK && (best < 0 || ms < bms)) {
       best = leaf;
-      best_ms = ms;
+      bflags = cf.second;
+      bms = ms;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (best < 0) return bfail(ctx, SPAMM_EUNSUPPORTED, "tune: no candidate leaf size ran");
-  ctx->tuned[key] = {best, best_ms};
-  *leaf_out = best;
-  if (ms_out) *ms_out = best_ms;
+  if (best < 0) return bfail(ctx, SPAMM_EUNSUPPORTED, "tune: no candidate ran");
+  *best_leaf = best;
+  *best_flags = bflags;
+  *best_ms = bms;
+  return SPAMM_OK;
+}
+
+int64_t tune_key(int64_t n, double tau, spamm_prec prec, int shape) {
+  int lg = 0;
+  while ((int64_t(1) << lg) < n) lg++;
+  const int tdec = tau > 0 ? (int)std::floor(std::log10(tau)) : -400;
+  return (((int64_t)lg * 16 + (int)prec) * 1000 + (tdec + 500)) * 2 + shape;
+}
+
+}  // namespace
+
+extern "C" spamm_status spamm_tune_leaf(spamm_ctx ctx, const double *A, int64_t n, double tau, spamm_prec prec,
+                                        int32_t flags, int32_t *leaf_out, double *ms_out) {
+  if (!ctx) return SPAMM_EINVAL;
+  if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
+  if (!A || !leaf_out || n < 1 || !(tau >= 0.0)) return bfail(ctx, SPAMM_EINVAL, "tune: bad arguments");
+  const int64_t key = tune_key(n, tau, prec, 0);
+  auto it = ctx->tuned.find(key);
+  if (it == ctx->tuned.end()) {
+    int leaf = 0;
+    int32_t f = 0;
+    double ms = 0;
+    spamm_status st = tune_candidates(ctx, A, n, tau, prec, flags, {{16, 0}, {32, 0}, {64, 0}, {128, 0}}, &leaf, &f, &ms);
+    if (st != SPAMM_OK) return st;
+    it = ctx->tuned.emplace(key, std::make_pair(leaf, ms)).first;
+  }
+  *leaf_out = it->second.first;
+  if (ms_out) *ms_out = it->second.second;
+  return SPAMM_OK;
+}
+
+extern "C" spamm_status spamm_tune_shape(spamm_ctx ctx, const double *A, int64_t n, double tau, spamm_prec prec,
+                                         int32_t flags, int32_t *leaf_out, int32_t *tile_flags_out, double *ms_out) {
+  if (!ctx) return SPAMM_EINVAL;
+  if (settle(ctx) != SPAMM_OK) return SPAMM_ECUDA;
+  if (!A || !leaf_out || !tile_flags_out || n < 1 || !(tau >= 0.0)) return bfail(ctx, SPAMM_EINVAL, "tune: bad arguments");
+  const int64_t key = tune_key(n, tau, prec, 1);
+  auto it = ctx->tuned.find(key);
+  if (it == ctx->tuned.end()) {
+    std::vector<std::pair<int, int32_t>> cand = {{16, 0}, {32, 0}, {64, 0}, {128, 0}};
+    if (prec != SPAMM_FP64) cand.insert(cand.begin() + 3, {64, SPAMM_WARP_TILES});
+    int leaf = 0;
+    int32_t f = 0;
+    double ms = 0;
+    spamm_status st = tune_candidates(ctx, A, n, tau, prec, flags, cand, &leaf, &f, &ms);
+    if (st != SPAMM_OK) return st;
+    // the shape is kept in the leaf slot's sign: negative = warp tiles
+    it = ctx->tuned.emplace(key, std::make_pair(f ? -leaf : leaf, ms)).first;
+  }
+  const int v = it->second.first;
+  *leaf_out = v < 0 ? -v : v;
+  *tile_flags_out = v < 0 ? SPAMM_WARP_TILES : 0;
+  if (ms_out) *ms_out = it->second.second;
   return SPAMM_OK;
 }

@@ -161,6 +161,7 @@ struct spamm_tree_s {
   bool is_product = false;
   bool sym_product = false;               // C = A A of a symmetric A, blocks i <= j computed
   bool depth_tau = false;                 // tier l of the cull tests against tau * 8^-l
+  bool warp_tiles = false;                // leaf 64 tensor-core product in warp tiles (k_leaf_mma)
   int32_t prec = 0;
   double tau = 0;
   TierList tiers[SPAMM_MAX_LEVELS + 1];   // tiers[l + 1] lists tier l; tiers[0] the virtual root
@@ -190,8 +191,10 @@ struct spamm_tree_s {
 };
 
 // A symmetric product whose blocks j > i are written by k_mirror after the leaf kernel:
-// FP64 and the small-leaf kernel (the tcgen05 forms write them in their epilogue).
-inline bool mirror_after_leaf(const spamm_tree_s *C) { return C->prec == SPAMM_FP64 || C->b < 64; }
+// FP64 and the warp-tile kernel (the tcgen05 forms write them in their epilogue).
+inline bool mirror_after_leaf(const spamm_tree_s *C) {
+  return C->prec == SPAMM_FP64 || C->b < 64 || C->warp_tiles;
+}
 
 __host__ __device__ inline int64_t level_offset(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
 

@@ -764,7 +764,7 @@ cudaError_t launch_cull(spamm_tree A, spamm_tree B, spamm_tree C, double tau, co
       a.c_nentries = &cnt->nentries[l + 1];
     } else {
       a.mask = C->mask;
-      a.plan_mode = C->plan_mode;
+      a.plan_mode = C->warp_tiles ? 0 : C->plan_mode;   // the warp-tile kernel reads the tier lists
       a.nzA = A->nz;
       a.nzB = B->nz;
       a.bsym = (B->flags & SPAMM_SYMMETRIC) != 0;

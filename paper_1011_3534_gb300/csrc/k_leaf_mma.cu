@@ -17,7 +17,6 @@
 
 namespace {
 
-constexpr int kWarpsPerCta = 4;
 
 struct MmaArgs {
   const void *A, *Alo;          // left operand rows (hi, lo of a split)
@@ -98,8 +97,17 @@ __device__ __forceinline__ void stage(uint32_t *dst, const void *src, int lane) 
   }
 }
 
+// Warps of a CTA: four, or three where four warps' tiles would not fit in shared memory
+// (leaf 64 split TF32: 4 tiles of 17 KB per warp).
 template <int B, int FMT, bool SPLIT>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_leaf_mma(MmaArgs p) {
+struct Cta {
+  static constexpr size_t warp_bytes = (size_t)(SPLIT ? 4 : 2) * Tile<B, FMT>::words * 4;
+  static constexpr int warps = 4 * warp_bytes <= 200 * 1024 ? 4 : 3;
+  static_assert(warps * warp_bytes <= 227 * 1024, "leaf tiles exceed shared memory");
+};
+
+template <int B, int FMT, bool SPLIT>
+__global__ void __launch_bounds__(Cta<B, FMT, SPLIT>::warps * 32) k_leaf_mma(MmaArgs p) {
   using F = Fmt<FMT>;
   using TL = Tile<B, FMT>;
   constexpr int RW = TL::row_words;
@@ -162,7 +170,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_leaf_mma(MmaArgs p) {
           stage<B, FMT>(tBl, leaf(p.Blo, ib), lane);
         }
         __syncwarp();
-#pragma unroll
+        // (leaf 64: one K-step at a time keeps its 128 sums and one step's fragments in
+        // registers)
+#pragma unroll(B <= 32 ? KS : 1)
         for (int ks = 0; ks < KS; ks++) {
           // word offset of the K-step inside a row
           constexpr int kw = F::kstep * F::bytes / 4;
@@ -241,15 +251,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_leaf_mma(MmaArgs p) {
 
 template <int B, int FMT, bool SPLIT>
 cudaError_t run_mma(const MmaArgs &a, int sm_count, cudaStream_t s) {
-  const size_t sm = (size_t)kWarpsPerCta * (SPLIT ? 4 : 2) * Tile<B, FMT>::words * 4;
+  constexpr int warps = Cta<B, FMT, SPLIT>::warps;
+  const size_t sm = (size_t)warps * Cta<B, FMT, SPLIT>::warp_bytes;
   auto k = k_leaf_mma<B, FMT, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kWarpsPerCta * 32, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, warps * 32, sm);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
-  k<<<(unsigned)(sm_count * occ), kWarpsPerCta * 32, sm, s>>>(a);
+  k<<<(unsigned)(sm_count * occ), warps * 32, sm, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -302,6 +313,7 @@ cudaError_t launch_leaf_mma(spamm_tree A, spamm_tree B, spamm_tree C, int prec, 
   switch (C->b) {
     case 16: return run_leaf<16>(a, prec, sm_count, s);
     case 32: return run_leaf<32>(a, prec, sm_count, s);
+    case 64: return run_leaf<64>(a, prec, sm_count, s);   // the warp-tile shape of leaf 64
     default: return cudaErrorInvalidValue;
   }
 }

@@ -31,6 +31,7 @@ SPAMM_GRAPH = 0x0200
 SPAMM_COPY_TF32X3 = 0x0400
 SPAMM_SYM_PRODUCT = 0x0800
 SPAMM_DEPTH_TAU = 0x1000
+SPAMM_WARP_TILES = 0x2000
 COPY_FLAG = {SPAMM_FP64: SPAMM_KEEP_FP64, SPAMM_TF32: SPAMM_COPY_TF32, SPAMM_BF16: SPAMM_COPY_BF16,
              SPAMM_FP16: SPAMM_COPY_FP16, SPAMM_BF16X3: SPAMM_COPY_BF16X3, SPAMM_TF32X3: SPAMM_COPY_TF32X3}
 MLP_FEATURES = 69
@@ -42,7 +43,7 @@ EXPORTS = ("spamm_ctx_create", "spamm_ctx_destroy", "spamm_sync", "spamm_last_er
            "spamm_tree_build_ms",
            "spamm_tree_norms", "spamm_tree_to_dense", "spamm_tree_to_dense_f32", "spamm_tree_leaf_copy", "spamm_multiply", "spamm_stats",
            "spamm_triples", "spamm_cull_noalloc", "spamm_sp2", "spamm_multiply_batched",
-           "spamm_tune_leaf", "spamm_mlp_create", "spamm_mlp_free", "spamm_mlp_num_params",
+           "spamm_tune_leaf", "spamm_tune_shape", "spamm_mlp_create", "spamm_mlp_free", "spamm_mlp_num_params",
            "spamm_mlp_get_params", "spamm_mlp_set_params", "spamm_mlp_forward", "spamm_mlp_gradient",
            "spamm_mlp_adam_step", "spamm_mlp_adam_apply", "spamm_mlp_train", "spamm_features", "spamm_tau_select",
            "spamm_tree_distance", "spamm_sp2_begin", "spamm_sp2_step", "spamm_sp2_step_learned",
@@ -111,6 +112,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.spamm_cull_noalloc.argtypes = [_P, _P, _I32, _D, _P, _I64, _P, _P]
     L.spamm_multiply_batched.argtypes = [_P, _P, _P, _P, _I32, ctypes.c_int, _I32, _P]
     L.spamm_tune_leaf.argtypes = [_P, _P, _I64, _D, ctypes.c_int, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_D)]
+    L.spamm_tune_shape.argtypes = [_P, _P, _I64, _D, ctypes.c_int, _I32, ctypes.POINTER(_I32),
+                                   ctypes.POINTER(_I32), ctypes.POINTER(_D)]
     L.spamm_sp2.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, _I32, ctypes.c_int, _P, ctypes.POINTER(Sp2ResultT)]
     L.spamm_sp2_learned.argtypes = [_P, _I64, _P, _P, _P, _D, _I32, _I32, ctypes.c_int, _P, _D, _D, _D,
                                     ctypes.POINTER(Sp2ResultT)]
@@ -615,3 +618,14 @@ def spamm_tune_leaf(ctx: Ctx, A, n: int, tau: float, prec: int, flags: int = 0) 
     ctx.check(LIB.spamm_tune_leaf(ctx.h, addr, n, float(tau), int(prec), flags, ctypes.byref(leaf),
                                   ctypes.byref(ms)), "spamm_tune_leaf")
     return leaf.value, ms.value
+
+
+def spamm_tune_shape(ctx: Ctx, A, n: int, tau: float, prec: int, flags: int = 0) -> tuple[int, int, float]:
+    """Fastest (leaf size, tile-shape multiply flags, ms) for the product A A."""
+    addr, host = _matrix(A, n, "spamm_tune_shape", ctx.device)
+    if host:
+        flags |= SPAMM_HOST_INPUT
+    leaf, tf, ms = _I32(), _I32(), _D()
+    ctx.check(LIB.spamm_tune_shape(ctx.h, addr, n, float(tau), int(prec), flags, ctypes.byref(leaf), ctypes.byref(tf),
+                                   ctypes.byref(ms)), "spamm_tune_shape")
+    return leaf.value, tf.value, ms.value

@@ -89,7 +89,7 @@ def test_tuner_picks_a_supported_leaf(S, ctx):
     with torch.cuda.stream(ctx.stream):
         d = torch.from_numpy(M).cuda()
         leaf, ms = S.spamm_tune_leaf(ctx, d, 2048, 1e-7, S.SPAMM_BF16, S.SPAMM_SYMMETRIC)
-        assert leaf in (64, 128) and ms > 0
+        assert leaf in (16, 32, 64, 128) and ms > 0
         leaf2, ms2 = S.spamm_tune_leaf(ctx, d, 2048, 1e-7, S.SPAMM_BF16, S.SPAMM_SYMMETRIC)
         assert (leaf2, ms2) == (leaf, ms)   # cached
         leaf3, _ = S.spamm_tune_leaf(ctx, d, 2048, 1e-7, S.SPAMM_FP64, S.SPAMM_SYMMETRIC)
@@ -163,4 +163,47 @@ def test_batched_config4_against_oracle(S, ctx):
             bound = tc_bound(leaf * cnt[i, j], "bf16", Cabs)
             assert np.all(np.abs(got - Cref) <= bound), (p, i, j)
     for t in C + trees:
+        S.spamm_tree_free(t)
+
+
+def test_shape_tuner_returns_a_runnable_shape(S, ctx):
+    # (leaf, tile-shape flags) over leaf 16/32 warp tiles, leaf 64 tcgen05 items and warp
+    # tiles, leaf 128 items; the chosen pair runs, and a second call is served from the cache
+    M = W.batched_matrix(0, 2048, 0.85)
+    with torch.cuda.stream(ctx.stream):
+        d = torch.from_numpy(M).cuda()
+        leaf, tf, ms = S.spamm_tune_shape(ctx, d, 2048, 1e-7, S.SPAMM_TF32X3, S.SPAMM_SYMMETRIC)
+        assert leaf in (16, 32, 64, 128) and tf in (0, S.SPAMM_WARP_TILES) and ms > 0
+        assert tf == 0 or leaf == 64
+        assert S.spamm_tune_shape(ctx, d, 2048, 1e-7, S.SPAMM_TF32X3, S.SPAMM_SYMMETRIC) == (leaf, tf, ms)
+        t = S.spamm_tree_build(ctx, d, 2048, leaf, S.COPY_FLAG[S.SPAMM_TF32X3] | S.SPAMM_SYMMETRIC)
+        C = S.spamm_multiply(ctx, t, t, 1e-7, S.SPAMM_TF32X3, tf)
+        assert S.spamm_stats(C)["leaf_products"] > 0
+        leaf64, tf64, _ = S.spamm_tune_shape(ctx, d, 2048, 1e-7, S.SPAMM_FP64, S.SPAMM_SYMMETRIC)
+        assert tf64 == 0 and leaf64 in (16, 32, 64, 128)
+        for x in (C, t):
+            S.spamm_tree_free(x)
+
+
+@pytest.mark.parametrize("prec_name", ["bf16", "tf32x3"])
+def test_batched_warp_tiles(S, ctx, prec_name):
+    # leaf 64 in warp tiles inside a batch equals the single products in the same shape
+    # bit for bit; against the tcgen05 items the triples are the same and C agrees to
+    # the FP32 accumulation order
+    prec = S.PRECISIONS[prec_name]
+    mats = batch_inputs(6, seed=9)
+    trees = build(S, ctx, mats, [64] * len(mats), prec)
+    taus = [1e-7] * len(mats)
+    Cb = S.spamm_multiply_batched(ctx, trees, trees, taus, prec, S.SPAMM_WARP_TILES)
+    for p, t in enumerate(trees):
+        Cs = S.spamm_multiply(ctx, t, t, taus[p], prec, S.SPAMM_WARP_TILES)
+        assert np.array_equal(S.spamm_triples(Cb[p]), S.spamm_triples(Cs)), p
+        assert np.array_equal(S.spamm_tree_to_dense(Cb[p]), S.spamm_tree_to_dense(Cs)), p
+        Ci = S.spamm_multiply(ctx, t, t, taus[p], prec)
+        assert np.array_equal(S.spamm_triples(Ci), S.spamm_triples(Cs)), p
+        a, b = S.spamm_tree_to_dense(Cs), S.spamm_tree_to_dense(Ci)
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b), p
+        for x in (Cs, Ci):
+            S.spamm_tree_free(x)
+    for t in Cb + trees:
         S.spamm_tree_free(t)

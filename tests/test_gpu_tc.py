@@ -45,13 +45,13 @@ def prec_of(S, name):
     return S.PRECISIONS[name]
 
 
-def gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product=False):
+def gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product=False, mflags=0):
     n = A.shape[0]
     prec = prec_of(S, prec_name)
     fl = S.COPY_FLAG[prec] | (S.SPAMM_SYMMETRIC if symmetric else 0)
     tA = S.spamm_tree_build(ctx, torch.from_numpy(A).cuda(), n, leaf, fl)
     tB = tA if B is A else S.spamm_tree_build(ctx, torch.from_numpy(B).cuda(), n, leaf, fl)
-    tC = S.spamm_multiply(ctx, tA, tB, tau, prec, S.SPAMM_SYM_PRODUCT if sym_product else 0)
+    tC = S.spamm_multiply(ctx, tA, tB, tau, prec, (S.SPAMM_SYM_PRODUCT if sym_product else 0) | mflags)
     out = dict(C=S.spamm_tree_to_dense(tC), trip=S.spamm_triples(tC), stats=S.spamm_stats(tC),
                norms=[S.spamm_tree_norms(tA, l) for l in range(tA.kmax + 1)])
     S.spamm_tree_free(tC)
@@ -100,8 +100,8 @@ def reference(A, B, leaf, tau, prec_name, threads):
     return TA, TB, Cref, Cabs + 0.0, Csub
 
 
-def check(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product=False):
-    g = gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product)
+def check(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product=False, mflags=0):
+    g = gpu_product(S, ctx, A, B, leaf, tau, prec_name, symmetric, sym_product, mflags)
     thr = oracle.max_threads()
     TA, TB, Cref, Cabs, Csub = reference(A, B, leaf, tau, prec_name, thr)
     ref = oracle.spamm(TA, TB, tau, triples=True, product=False)
@@ -282,3 +282,35 @@ def test_split_tf32_accumulation_bias(S, ctx, leaf):
     print(f"split TF32 leaf {leaf}: mean relative error {rel.mean():.2e}, rms {np.sqrt((rel ** 2).mean()):.2e}")
     assert abs(rel.mean()) <= (leaf / 8) * 2.0 ** -24
     assert np.sqrt((rel ** 2).mean()) <= (leaf / 8) * 2.0 ** -23 + 2.0 ** -22
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("n,tau,kind,symp", [(1000, 1e-6, "alg", False), (2048, 1e-8, "exp", True)])
+def test_warp_tiles_leaf64(S, ctx, prec, n, tau, kind, symp):
+    # leaf 64 in the warp-tile shape (SPAMM_WARP_TILES: one warp per 64 x 64 output
+    # block, the block's surviving k only): the oracle's triples and C within the
+    # tensor-core bar; with the symmetric product the blocks i > j are exact transposes
+    A = W.algebraic_decay(n, 2, 0) if kind == "alg" else W.exp_decay(n, 0.85, 1, 0)
+    g = check(S, ctx, A, A, 64, tau, prec, symmetric=True, sym_product=symp, mflags=S.SPAMM_WARP_TILES)
+    # the warp shape issues MMAs for surviving products only: no zero-filled halves
+    st = g["stats"]
+    assert st["mma_flops"] == st["leaf_flops"] * (3 if prec in SPLIT else 1)
+    if symp:
+        C = g["C"]
+        blk = np.arange(n) // 64
+        off = blk[:, None] != blk[None, :]
+        assert np.array_equal(C[off], C.T[off])
+
+
+def test_warp_tiles_flag_checks(S, ctx):
+    A = W.exp_decay(512, 0.85, 1, 0)
+    t128 = S.spamm_tree_build(ctx, torch.from_numpy(A).cuda(), 512, 128, S.COPY_FLAG[S.SPAMM_BF16] | S.SPAMM_SYMMETRIC)
+    with pytest.raises(S.SpammError) as e:
+        S.spamm_multiply(ctx, t128, t128, 1e-6, S.SPAMM_BF16, S.SPAMM_WARP_TILES)
+    assert e.value.status == S.SPAMM_EUNSUPPORTED
+    t64 = S.spamm_tree_build(ctx, torch.from_numpy(A).cuda(), 512, 64, S.SPAMM_KEEP_FP64 | S.SPAMM_SYMMETRIC)
+    with pytest.raises(S.SpammError) as e:
+        S.spamm_multiply(ctx, t64, t64, 1e-6, S.SPAMM_FP64, S.SPAMM_WARP_TILES)
+    assert e.value.status == S.SPAMM_EINVAL
+    S.spamm_tree_free(t128)
+    S.spamm_tree_free(t64)
