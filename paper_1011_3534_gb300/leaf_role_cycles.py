@@ -15,7 +15,10 @@ build, and prints, per CTA on average, the cycles each role of `k_leaf_tc` spend
 
 and the spread of the CTAs' totals (load balance).
 
-  python -m paper_1011_3534_gb300.leaf_role_cycles [n]
+  python -m paper_1011_3534_gb300.leaf_role_cycles [n] [alg|lattice]
+
+(lattice: the n = 32768 physical-distance-decay matrix at tau = 1e-6, whose near-dense
+products give items of up to hundreds of passes.)
 """
 from __future__ import annotations
 
@@ -26,7 +29,7 @@ import sys
 import numpy as np
 
 
-def main(n: int = 8192):
+def main(n: int = 8192, workload: str = "alg"):
     import torch
     from . import build as B
     B.build()                       # the library's own build, which the binding loads on import
@@ -38,14 +41,19 @@ def main(n: int = 8192):
     S.LIB = L                       # the probe build in place of the library's own
     L.spamm_leaf_role_cycles.argtypes = [ctypes.c_void_p, ctypes.c_int]
     ctx = S.spamm_ctx_create(0, torch.cuda.current_stream(), timing=True)
-    A = torch.from_numpy(W.algebraic_decay(n, 2, 0)).cuda()
+    if workload == "lattice":   # n = 32768 physical-distance decay, near-dense products
+        A = torch.from_numpy(W.physical_decay(16, 8, 1.2, 0.1, 3, 1)).cuda()
+        n = A.shape[0]
+    else:
+        A = torch.from_numpy(W.algebraic_decay(n, 2, 0)).cuda()
+    tau = 1e-6 if workload == "lattice" else 1e-8
     for name in ("tf32x3", "bf16", "bf16x3"):
         p = S.PRECISIONS[name]
         t = S.spamm_tree_build(ctx, A, n, 64, S.COPY_FLAG[p] | S.SPAMM_SYMMETRIC | S.SPAMM_NO_RIGHT)
-        C = S.spamm_multiply(ctx, t, t, 1e-8, p, S.SPAMM_SYM_PRODUCT)   # warm-up
+        C = S.spamm_multiply(ctx, t, t, tau, p, S.SPAMM_SYM_PRODUCT)   # warm-up
         S.spamm_sync(ctx)
         L.spamm_leaf_role_cycles(None, 1)
-        C = S.spamm_multiply(ctx, t, t, 1e-8, p, S.SPAMM_SYM_PRODUCT, C)
+        C = S.spamm_multiply(ctx, t, t, tau, p, S.SPAMM_SYM_PRODUCT, C)
         st = S.spamm_stats(C)
         buf = np.zeros((1024, 16), dtype=np.uint64)
         L.spamm_leaf_role_cycles(buf.ctypes.data, 0)
@@ -68,4 +76,4 @@ def main(n: int = 8192):
 
 
 if __name__ == "__main__":
-    main(int(sys.argv[1]) if len(sys.argv) > 1 else 8192)
+    main(int(sys.argv[1]) if len(sys.argv) > 1 else 8192, sys.argv[2] if len(sys.argv) > 2 else "alg")
