@@ -619,7 +619,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int col0 = LEAF == 64 ? 0 : half * 64;   // this warp's first column of block (i, j)
         // squared norm of the warp's part in double-float: f^2 = pp + e exactly, TwoSum
         // accumulation
-        float sh = 0.f, sl = 0.f;
+        // the warp's 64 columns in registers; plain forms: both TMEM chunks behind one
+        // wait, and the accumulator handed back to the MMA warp before the stores
+        uint32_t v[2][32];
+        if (SPLIT) {
+#pragma unroll
+          for (int x = 0; x < 32; x++) {
+            v[0][x] = __float_as_uint(run[x]);
+            v[1][x] = __float_as_uint(run[32 + x]);
+          }
+        } else {
+          const uint32_t d = tmem + lanes + (uint32_t)acc * 128u + (uint32_t)(half * 64);
+          tmem_ld32_nowait(d, v[0]);
+          tmem_ld32_nowait(d + 32u, v[1]);
+          tmem_wait_ld();
+          tc_fence_before();
+          mbar_arrive(&acce[acc]);
+        }
+        // two TwoSum chains (even and odd columns) shorten the dependency chain
+        float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
         if (((touched >> (a * 2 + c)) & 1u) && i < P.nb && j < P.nb) {   // warp-uniform
           // the warp's 32 rows of block (i, j) go through shared memory 16 columns at a
           // time, so that each store instruction covers whole 64-byte row pieces
@@ -630,18 +648,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           float *blkT = P.C + ((int64_t)j * P.nb + i) * LEAF * LEAF + (r - lane);
 #pragma unroll
           for (int hh = 0; hh < 2; hh++) {   // 32-column units of the warp's 64 columns
-            uint32_t v[32];
-            if (SPLIT) {
-#pragma unroll
-              for (int x = 0; x < 32; x++) v[x] = __float_as_uint(run[hh * 32 + x]);
-            } else {
-              tmem_ld32(tmem + lanes + (uint32_t)acc * 128u + (uint32_t)(half * 64 + hh * 32), v);
-            }
 #pragma unroll
             for (int g = 0; g < 2; g++) {
               const int cb = col0 + hh * 32 + g * 16;   // first column of the piece
 #pragma unroll
-              for (int x = 0; x < 16; x++) sb[lane][x] = __uint_as_float(v[g * 16 + x]);
+              for (int x = 0; x < 16; x++) sb[lane][x] = __uint_as_float(v[hh][g * 16 + x]);
               __syncwarp();
 #pragma unroll
               for (int it = 0; it < 4; it++) {   // rows rl, columns cb + c4 .. + 3
@@ -661,23 +672,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
 #pragma unroll
             for (int x = 0; x < 32; x++) {
-              const float fv = __uint_as_float(v[x]);
+              const float fv = __uint_as_float(v[hh][x]);
               const float pp = fv * fv;
               const float ee = fmaf(fv, fv, -pp);
-              const float t = sh + pp;
-              const float bb = t - sh;
-              sl += ((sh - (t - bb)) + (pp - bb)) + ee;
-              sh = t;
+              float &S = sh[x & 1], &Sl = sl[x & 1];
+              const float t = S + pp;
+              const float bb = t - S;
+              Sl += ((S - (t - bb)) + (pp - bb)) + ee;
+              S = t;
             }
           }
         }
-        if (!SPLIT) {
-          tc_fence_before();
-          mbar_arrive(&acce[acc]);
-        }
+        df_add(sh[0], sl[0], sh[1], sl[1]);
         // squared Frobenius norms of the written blocks: rows -> warp -> fixed order
         {
-          float H = sh, L = sl;
+          float H = sh[0], L = sl[0];
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) {
             const float h2 = __shfl_xor_sync(0xffffffffu, H, off), l2 = __shfl_xor_sync(0xffffffffu, L, off);
