@@ -130,56 +130,105 @@ constexpr uint32_t kF64 = 1u << 0, kF32 = 1u << 1, kTF32 = 1u << 2, kTF32T = 1u 
 //   fmt(d + b), and that equals fmt(|x| - hi) whenever fmt's rounding unit at |s| is at
 //   least 2^(p-45), i.e. |s| >= 2^(p-34) (TF32) or 2^(p-37) (BF16). A remainder below
 //   that (the low bits of x nearly cancel hi's rounding), rare, takes the integer route.
+// Two FP32 lanes in one 64-bit register pair, for the f32x2 arithmetic of this GPU
+// family: one instruction does the same IEEE operation on both lanes. The split round
+// below runs its two chains (even and odd elements of a pair) as the two lanes.
+__device__ __forceinline__ uint64_t f2(float x, float y) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ void f2_get(uint64_t r, float &x, float &y) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t add2_rz(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 template <int B, bool TF>
 __device__ __forceinline__ void k1_round_split(const BuildArgs &p, int64_t tile, const uint32_t (&hw)[8],
                                                const uint32_t (&lw)[8], const int (&rows)[4], const int (&cols)[4],
                                                int Er, NormAcc &acc) {
   const float scR = __uint_as_float((uint32_t)(1150 - Er) << 23);   // 2^(1023 - Er), Er <= 1149
-  float S[2] = {0.f, 0.f}, s2[2] = {0.f, 0.f};
+  const uint64_t SCR = f2(scR, scR), NSCR = f2(-scR, -scR), SCR4 = f2(4.f * scR, 4.f * scR);
+  const uint64_t TWO = f2(2.f, 2.f), THR = f2(TF ? 8192.f : 1024.f, TF ? 8192.f : 1024.f);
+  uint64_t S = f2(0.f, 0.f), s2 = f2(0.f, 0.f);   // chains: even, odd elements
 #pragma unroll
   for (int u = 0; u < 4; u++) {
-    uint32_t hb[2], lb[2];
+    float a[2], m_f[2], jf[2], sc47[2], hif[2];
+    uint32_t a_bits[2], himag[2];
 #pragma unroll
     for (int k = 0; k < 2; k++) {
       const uint32_t h = hw[2 * u + k], l = lw[2 * u + k];
       const uint32_t E = (h >> 20) & 0x7FFu;
-      const uint32_t a_bits = __funnelshift_l(l, (h & 0x7FFFFFFFu) - (896u << 20), 3);
-      const float a = __uint_as_float(a_bits);
-      const float m_f = u23_to_float((l >> 6) & 0x7FFFFFu);
-      const float jf = __saturatef(u23_to_float(l & 63u));
-      const float sc47 = __uint_as_float((E - 943u) << 23);          // 2^(p - 47)
-      // squared norm: the same terms as the general path, chain k
-      const float hi_s = a * scR;
-      const float lo2_s = m_f * (sc47 * (4.f * scR));
-      const float pp = hi_s * hi_s;
-      float cc = fmaf(hi_s, hi_s, -pp);
-      cc = fmaf(hi_s, lo2_s, cc);
-      const float t = S[k] + pp;
-      const float tb = t - S[k];
-      s2[k] += ((S[k] - (t - tb)) + (pp - tb)) + cc;
-      S[k] = t;
+      a_bits[k] = __funnelshift_l(l, (h & 0x7FFFFFFFu) - (896u << 20), 3);
+      a[k] = __uint_as_float(a_bits[k]);
+      m_f[k] = u23_to_float((l >> 6) & 0x7FFFFFu);
+      jf[k] = (l & 63u) ? 1.f : 0.f;
+      sc47[k] = __uint_as_float((E - 943u) << 23);          // 2^(p - 47)
       // hi = fmt(|x|) from a and a sticky bit for the bits below it
-      const uint32_t jam = a_bits | ((l & 0x1FFFFFFFu) != 0u ? 1u : 0u);
-      uint32_t himag;   // FP32 pattern of fmt(|x|)
-      if (TF) {
-        himag = tf32_of_sticky(jam);
-      } else {
-        himag = (jam + 0x7FFFu + ((jam >> 16) & 1u)) & 0xFFFF0000u;
-      }
-      const float d = a - __uint_as_float(himag);
-      const float bj = fmaf(m_f, 2.f, jf) * sc47;
-      const float sr = __fadd_rz(d, bj);
-      const float ee = bj - (sr - d);
-      const float thr = sc47 * (TF ? 8192.f : 1024.f);
+      const uint32_t jam = a_bits[k] | ((l & 0x1FFFFFFFu) != 0u ? 1u : 0u);
+      himag[k] = TF ? tf32_of_sticky(jam) : (jam + 0x7FFFu + ((jam >> 16) & 1u)) & 0xFFFF0000u;
+      hif[k] = __uint_as_float(himag[k]);
+    }
+    const uint64_t A = f2(a[0], a[1]), M = f2(m_f[0], m_f[1]), SC = f2(sc47[0], sc47[1]);
+    // squared norm, both chains: hi_s = a 2^(1023-Er), lo2_s = 2 m 2^(p-46) 2^(1023-Er);
+    // npp = -hi_s^2 rounded, cc = (hi_s^2 - pp) + hi_s lo2_s; TwoSum of S + pp
+    const uint64_t hs = mul2(A, SCR), nhs = mul2(A, NSCR);
+    const uint64_t l2s = mul2(M, mul2(SC, SCR4));
+    const uint64_t npp = mul2(hs, nhs);
+    const uint64_t cc = fma2(hs, l2s, fma2(hs, hs, npp));
+    const uint64_t t = sub2(S, npp);
+    const uint64_t tb = sub2(t, S);
+    // (S - (t - tb)) + (pp - tb), with pp - tb = -(npp + tb)
+    s2 = add2(s2, add2(sub2(sub2(S, sub2(t, tb)), add2(npp, tb)), cc));
+    S = t;
+    // lo: d = a - hi (exact), b = (2m + j) 2^(p-47), s = d + b toward zero, e = b - (s - d)
+    const uint64_t d = sub2(A, f2(hif[0], hif[1]));
+    const uint64_t bj = mul2(fma2(M, TWO, f2(jf[0], jf[1])), SC);
+    const uint64_t sr2 = add2_rz(d, bj);
+    const uint64_t ee2 = sub2(bj, sub2(sr2, d));
+    const uint64_t thr2 = mul2(SC, THR);
+    float srk[2], eek[2], thrk[2];
+    f2_get(sr2, srk[0], srk[1]);
+    f2_get(ee2, eek[0], eek[1]);
+    f2_get(thr2, thrk[0], thrk[1]);
+    uint32_t hb[2], lb[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const uint32_t h = hw[2 * u + k], l = lw[2 * u + k];
+      const float sr = srk[k], ee = eek[k];
       uint32_t lo;
-      if (fabsf(sr) >= thr || (sr == 0.f && ee == 0.f)) {
+      if (fabsf(sr) >= thrk[k] || (sr == 0.f && ee == 0.f)) {
         const uint32_t sb = (__float_as_uint(sr) & 0x7FFFFFFFu) | (ee != 0.f ? 1u : 0u);
         const uint32_t lm = TF ? tf32_of_sticky(sb) : ((sb + 0x7FFFu + ((sb >> 16) & 1u)) & 0xFFFF0000u);
         lo = lm ? lm | ((h ^ __float_as_uint(sr)) & 0x80000000u) : 0u;
       } else {
         lo = slow_split_lo(h, l, TF ? 11 : 8);
       }
-      hb[k] = himag | (h & 0x80000000u);
+      hb[k] = himag[k] | (h & 0x80000000u);
       lb[k] = lo;
     }
     const int64_t o = tile + (int64_t)rows[u] * B + cols[u];
@@ -191,8 +240,11 @@ __device__ __forceinline__ void k1_round_split(const BuildArgs &p, int64_t tile,
       *reinterpret_cast<uint32_t *>(p.lo + o) = (lb[0] >> 16) | (lb[1] & 0xFFFF0000u);
     }
   }
-  df_add(S[0], s2[0], S[1], s2[1]);
-  acc.merge(S[0], s2[0], Er);
+  float S0, S1, e0, e1;
+  f2_get(S, S0, S1);
+  f2_get(s2, e0, e1);
+  df_add(S0, e0, S1, e1);
+  acc.merge(S0, e0, Er);
 }
 
 // Squared norm (into acc) and leaf copies of one round: the 8 elements of 4 pairs
