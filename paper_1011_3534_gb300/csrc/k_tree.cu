@@ -167,6 +167,14 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
   return r;
 }
 
+// TF32 round to nearest even of a positive FP32 pattern (the sticky-bit forms below), by
+// the hardware conversion: the same bits as tf32_of_sticky for finite normal inputs.
+__device__ __forceinline__ uint32_t tf32_rn(uint32_t f) {
+  uint32_t r;
+  asm("cvt.rn.tf32.f32 %0, %1;" : "=r"(r) : "f"(__uint_as_float(f)));
+  return r;
+}
+
 template <int B, bool TF>
 __device__ __forceinline__ void k1_round_split(const BuildArgs &p, int64_t tile, const uint32_t (&hw)[8],
                                                const uint32_t (&lw)[8], const int (&rows)[4], const int (&cols)[4],
@@ -190,7 +198,7 @@ __device__ __forceinline__ void k1_round_split(const BuildArgs &p, int64_t tile,
       sc47[k] = __uint_as_float((E - 943u) << 23);          // 2^(p - 47)
       // hi = fmt(|x|) from a and a sticky bit for the bits below it
       const uint32_t jam = a_bits[k] | ((l & 0x1FFFFFFFu) != 0u ? 1u : 0u);
-      himag[k] = TF ? tf32_of_sticky(jam) : (jam + 0x7FFFu + ((jam >> 16) & 1u)) & 0xFFFF0000u;
+      himag[k] = TF ? tf32_rn(jam) : (jam + 0x7FFFu + ((jam >> 16) & 1u)) & 0xFFFF0000u;
       hif[k] = __uint_as_float(himag[k]);
     }
     const uint64_t A = f2(a[0], a[1]), M = f2(m_f[0], m_f[1]), SC = f2(sc47[0], sc47[1]);
@@ -223,7 +231,7 @@ __device__ __forceinline__ void k1_round_split(const BuildArgs &p, int64_t tile,
       uint32_t lo;
       if (fabsf(sr) >= thrk[k] || (sr == 0.f && ee == 0.f)) {
         const uint32_t sb = (__float_as_uint(sr) & 0x7FFFFFFFu) | (ee != 0.f ? 1u : 0u);
-        const uint32_t lm = TF ? tf32_of_sticky(sb) : ((sb + 0x7FFFu + ((sb >> 16) & 1u)) & 0xFFFF0000u);
+        const uint32_t lm = TF ? tf32_rn(sb) : ((sb + 0x7FFFu + ((sb >> 16) & 1u)) & 0xFFFF0000u);
         lo = lm ? lm | ((h ^ __float_as_uint(sr)) & 0x80000000u) : 0u;
       } else {
         lo = slow_split_lo(h, l, TF ? 11 : 8);
