@@ -39,6 +39,7 @@
 #include <cudaTypedefs.h>
 
 #include "internal.cuh"
+#include "f32x2.cuh"
 #include "tc_ptx.cuh"
 
 // Optional per-role cycle counters (build with -DSPAMM_LEAF_ROLE_CYCLES; the library's
@@ -636,8 +637,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_before();
           mbar_arrive(&acce[acc]);
         }
-        // two TwoSum chains (even and odd columns) shorten the dependency chain
-        float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
+        // squared norm: two TwoSum chains (even and odd columns) as the lanes of f32x2
+        uint64_t Sh = f2(0.f, 0.f), Sl = f2(0.f, 0.f);
+        const uint64_t kNeg1 = f2(-1.f, -1.f);
         if (((touched >> (a * 2 + c)) & 1u) && i < P.nb && j < P.nb) {   // warp-uniform
           // the warp's 32 rows of block (i, j) go through shared memory 16 columns at a
           // time, so that each store instruction covers whole 64-byte row pieces
@@ -671,18 +673,22 @@ __global__ void __launch_bounds__(kThreads, 1)
               __syncwarp();
             }
 #pragma unroll
-            for (int x = 0; x < 32; x++) {
-              const float fv = __uint_as_float(v[hh][x]);
-              const float pp = fv * fv;
-              const float ee = fmaf(fv, fv, -pp);
-              float &S = sh[x & 1], &Sl = sl[x & 1];
-              const float t = S + pp;
-              const float bb = t - S;
-              Sl += ((S - (t - bb)) + (pp - bb)) + ee;
-              S = t;
+            for (int x = 0; x < 32; x += 2) {
+              // f^2 = pp + e exactly (npp = -pp); TwoSum of Sh + pp, (Sh - (t - bb)) + (pp - bb)
+              // with pp - bb = -(npp + bb)
+              const uint64_t fv = f2(__uint_as_float(v[hh][x]), __uint_as_float(v[hh][x + 1]));
+              const uint64_t npp = mul2(fv, mul2(fv, kNeg1));
+              const uint64_t ee = fma2(fv, fv, npp);
+              const uint64_t t = sub2(Sh, npp);
+              const uint64_t bb = sub2(t, Sh);
+              Sl = add2(Sl, add2(sub2(sub2(Sh, sub2(t, bb)), add2(npp, bb)), ee));
+              Sh = t;
             }
           }
         }
+        float sh[2], sl[2];
+        f2_get(Sh, sh[0], sh[1]);
+        f2_get(Sl, sl[0], sl[1]);
         df_add(sh[0], sl[0], sh[1], sl[1]);
         // squared Frobenius norms of the written blocks: rows -> warp -> fixed order
         {

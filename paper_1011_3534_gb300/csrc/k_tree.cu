@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "convert.cuh"
+#include "f32x2.cuh"
 #include "internal.cuh"
 
 namespace {
@@ -130,43 +131,6 @@ constexpr uint32_t kF64 = 1u << 0, kF32 = 1u << 1, kTF32 = 1u << 2, kTF32T = 1u 
 //   fmt(d + b), and that equals fmt(|x| - hi) whenever fmt's rounding unit at |s| is at
 //   least 2^(p-45), i.e. |s| >= 2^(p-34) (TF32) or 2^(p-37) (BF16). A remainder below
 //   that (the low bits of x nearly cancel hi's rounding), rare, takes the integer route.
-// Two FP32 lanes in one 64-bit register pair, for the f32x2 arithmetic of this GPU
-// family: one instruction does the same IEEE operation on both lanes. The split round
-// below runs its two chains (even and odd elements of a pair) as the two lanes.
-__device__ __forceinline__ uint64_t f2(float x, float y) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
-  return r;
-}
-__device__ __forceinline__ void f2_get(uint64_t r, float &x, float &y) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t add2_rz(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("add.rz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-
 // TF32 round to nearest even of a positive FP32 pattern (the sticky-bit forms below), by
 // the hardware conversion: the same bits as tf32_of_sticky for finite normal inputs.
 __device__ __forceinline__ uint32_t tf32_rn(uint32_t f) {
@@ -175,6 +139,8 @@ __device__ __forceinline__ uint32_t tf32_rn(uint32_t f) {
   return r;
 }
 
+// The two norm chains of the round (even and odd elements of each pair) and the
+// remainder arithmetic run as the two lanes of f32x2 instructions.
 template <int B, bool TF>
 __device__ __forceinline__ void k1_round_split(const BuildArgs &p, int64_t tile, const uint32_t (&hw)[8],
                                                const uint32_t (&lw)[8], const int (&rows)[4], const int (&cols)[4],
