@@ -315,7 +315,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       ROLE_ADD(11, t_pub);
       if (cur_e.x < 0 || __shfl_sync(0xffffffffu, s_abort ? 1 : 0, 0)) break;
-      const unsigned int g_next = claim();   // the claim's reply arrives while this item's loads go out
+      // the next item is claimed and its description read two passes before this one's
+      // loads end (the replies arrive while they go out): late enough that a CTA does not
+      // hold an unstarted item while others run dry at the end of the list
+      int4 nxt_e;
+      uint32_t nxt_ij;
+      bool claimed = false;
       {
         const ProdDesc &P = prods[cur_e.x];
         const uint2 mt = make_uint2((uint32_t)cur_e.z, (uint32_t)cur_e.w);
@@ -333,6 +338,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           // stage's copies
           const int nl = (int)min(32u, np - c0);
           for (int l = 0; l < nl && !aborted(); l++) {
+            if (!claimed && c0 + (uint32_t)l + 2u >= np) {
+              describe(claim(), nxt_e, nxt_ij);
+              claimed = true;
+            }
             const int4 d = s_desc[l];
             // the first pass of an item initialises both column halves (N = 128) of the
             // item's accumulator (plain) or correction accumulator (split)
@@ -370,7 +379,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       ROLE_T0(t_ds);
-      describe(g_next, cur_e, cur_ij);
+      if (!claimed) describe(claim(), nxt_e, nxt_ij);   // no passes, or an abort before the claim point
+      cur_e = nxt_e;
+      cur_ij = nxt_ij;
       ROLE_ADD(12, t_ds);
     }
   } else if (warp == 1) {
