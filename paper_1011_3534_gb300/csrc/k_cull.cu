@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_tier(CullArgs a) {
 // Eq. 4 recursion, as in k_cull_tier. A block's survivors form a bit mask over K, which
 // is the next tier's parent test. Only the tier-T list (groups in Morton order, K
 // ascending) and the counters of tiers 0..T are written; the culled bound of tier l
-// (summed per thread over K, per warp by a fixed tree, then over warps in order) goes
+// (summed per thread over K, per warp and then over warps by fixed trees) goes
 // to the first parent-group slot of the tier and zeros to the others, so the fixed-
 // order reduction of the slots returns it unchanged.
 constexpr int kTopTiers = 6;                 // tiers 0..5
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
   __shared__ uint32_t s_mask[2][kTopBlocks];            // survivors over K per block: tiers l-1, l
   __shared__ double s_wb[kTopWarps];                    // per-warp culled bounds
   __shared__ uint32_t s_wg[kTopWarps], s_we[kTopWarps];
-  __shared__ unsigned long long s_tested, s_surv;
+  __shared__ uint32_t s_wt[kTopWarps], s_ws[kTopWarps];   // per-warp tests and survivors
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double tau = t.tau_dev ? *t.tau_dev : t.tau;
   for (int l = 0; l <= t.T; l++) {
@@ -530,10 +530,6 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
       s_nA[off + q] = t.nA[l][q];
       s_nB[off + q] = t.nB[l][q];
     }
-  }
-  if (threadIdx.x == 0) {
-    s_tested = 0;
-    s_surv = 0;
   }
   __syncthreads();
   const uint32_t m = threadIdx.x;
@@ -573,20 +569,23 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_cull_top(TopArgs t) {
     if (__any_sync(0xffffffffu, bound != 0.0)) bound = warp_sum(bound);   // else every lane holds +0
     if (lane == 0) {
       s_wb[warp] = bound;
-      atomicAdd(&s_tested, (unsigned long long)tests);
-      atomicAdd(&s_surv, (unsigned long long)surv);
+      s_wt[warp] = (uint32_t)tests;
+      s_ws[warp] = surv;
     }
     const uint32_t groups = (uint32_t)__syncthreads_count(m < nblk && mask != 0u);
-    if (threadIdx.x == 0) {
-      double b = 0.0;
-      for (int w = 0; w < (int)((nblk + 31) / 32); w++) b += s_wb[w];   // the other warps hold +0
-      t.bound_part[t.bound_off[l]] = b;
-      t.cnt->tested[l] = s_tested;
-      t.cnt->culled[l] = s_tested - s_surv;
-      t.cnt->ngroups[l + 1] = groups;
-      t.cnt->nentries[l + 1] = s_surv;
-      s_tested = 0;
-      s_surv = 0;
+    if (warp == 0) {   // the warps' bounds by a fixed shuffle tree (warps without blocks hold +0)
+      double b = s_wb[lane];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);
+      const unsigned long long tested = warp_sum((unsigned long long)s_wt[lane]);
+      const unsigned long long survived = warp_sum((unsigned long long)s_ws[lane]);
+      if (lane == 0) {
+        t.bound_part[t.bound_off[l]] = b;
+        t.cnt->tested[l] = tested;
+        t.cnt->culled[l] = tested - survived;
+        t.cnt->ngroups[l + 1] = groups;
+        t.cnt->nentries[l + 1] = survived;
+      }
     }
     for (uint32_t g = 1 + threadIdx.x; g < parent_groups; g += blockDim.x) t.bound_part[t.bound_off[l] + g] = 0.0;
     parent_groups = groups;
