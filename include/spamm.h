@@ -235,7 +235,10 @@ SPAMM_API spamm_status spamm_tree_to_dense_f32(spamm_tree t, float *out, int32_t
    same n and leaf. A and B must have equal n and leaf and hold the copies `prec`
    needs (SPAMM_KEEP_FP64 for SPAMM_FP64, SPAMM_COPY_<prec> otherwise, and for B
    either SPAMM_SYMMETRIC or no SPAMM_NO_RIGHT).
-   Supported: SPAMM_FP64 for every leaf; tensor-core precisions for leaf 64 and 128.
+   Supported: every precision at every leaf (16, 32, 64, 128): tensor-core products
+   run as warp tiles at leaf 16 and 32 (and at 64 with SPAMM_WARP_TILES), as tcgen05
+   items of 2 x 2 blocks at leaf 64 and of one block at 128. Other flags:
+   SPAMM_SYM_PRODUCT, SPAMM_DEPTH_TAU, SPAMM_WARP_TILES.
    The norm pyramid of C runs on an internal stream of the context, overlapping later
    calls that do not read C (spamm_tree_update of an operand, say); every call that
    may read a product (including spamm_sync) first makes the context stream wait for it.
