@@ -427,6 +427,15 @@ __global__ void __launch_bounds__(BuildCfg<B>::T, 1024 / BuildCfg<B>::T) k_tree_
     for (int rd = 0; rd < Cfg::ROUNDS; rd++) {
       uint32_t hw[8], lw[8];   // high and low words of the round's 8 elements
       int rows[4], cols[4];
+      if (VEC && full && rd + 1 < Cfg::ROUNDS) {
+        // the next round's lines into L2 while this round's arithmetic runs
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int q = tl + Cfg::TPL * (4 * (rd + 1) + u);
+          const int64_t gr = (int64_t)r * B + q / (B / 2), gc = (int64_t)c * B + 2 * (q % (B / 2));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A + gr * p.n + gc));
+        }
+      }
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const int q = tl + Cfg::TPL * (4 * rd + u);
